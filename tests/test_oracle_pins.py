@@ -1,0 +1,341 @@
+"""Pins of the FP64 oracle against things other than itself.
+
+Closed forms (image method, Keller diffraction point, LOS length), a library
+distance transform, brute force on tiny scenes, Monte-Carlo geometry and the
+paper's Table 1.  CPU only.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2402_13747_b300 import config, scenes
+from tests.imagemethod import box_room_planes, image_paths
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _exact_by_labels(P):
+    out = {}
+    for i in range(len(P["n"])):
+        n = int(P["n"][i])
+        key = (int(P["tx"][i]), int(P["rx"][i]), tuple(int(l) for l in P["label"][i][:n]))
+        assert key not in out
+        out[key] = (P["pts"][i][:n].copy(), float(P["length"][i]), tuple(int(t) for t in P["type"][i][:n]))
+    return out
+
+
+def test_config_defaults_match_table1():
+    g = json.load(open(os.path.join(GOLDEN, "table1_params.json")))
+    p = config.Params()
+    assert p.voxel_size == g["voxel_size_m"]
+    assert p.dv == g["voxel_division_factor"]
+    assert p.kappa == g["coarse_path_duplicate_limit"]
+    assert p.delta == g["convergence_threshold"]
+    assert p.rho == g["refinement_iterations"]
+    assert p.freq_hz == g["carrier_frequency_hz"]
+
+
+@pytest.fixture(scope="module")
+def tiny_run(room_tiny):
+    p = config.params_for(room_tiny, grad_stop=1e-9)
+    s, c, e = oracle.run(room_tiny, p)
+    return room_tiny, p, s, c, e
+
+
+def test_image_method_room_tiny(tiny_run):
+    """Refined reflection paths equal the image method on the sampled box room (Section 2.3)."""
+    sc, p, s, c, e = tiny_run
+    ref = image_paths(box_room_planes(10.0, 10.0, 3.0), sc.tx[0], sc.rx[0], max_order=2)
+    assert len(ref) == 25  # 1 LOS + 6 single + 18 double on the bounded faces
+    got = _exact_by_labels(e.paths())
+    assert set(k[2] for k in got) == set(ref)
+    for (t, r, lab), (pts, length, types) in got.items():
+        assert types == (0,) * len(lab)
+        rp, rl = ref[lab]
+        np.testing.assert_allclose(pts, rp, atol=1e-6)
+        assert abs(length - rl) <= 1e-9 * rl
+
+
+def test_los_length(tiny_run):
+    sc, p, s, c, e = tiny_run
+    got = _exact_by_labels(e.paths())
+    assert got[(0, 0, ())][1] == pytest.approx(math.sqrt(25 + 9), rel=1e-15)
+
+
+@pytest.mark.parametrize("z_tx,z_rx", [(0.5, 2.5), (0.5, 2.0), (2.2, 0.7)])
+def test_keller_point_on_sampled_wedge(z_tx, z_rx):
+    """Diffraction at an exterior edge: the refined point is the closed-form Keller point.
+
+    TX and RX are both sqrt(10) m from the edge line, so the point divides the
+    height difference in the ratio r1/(r1+r2) = 1/2; the path obeys the equal-angle law.
+    """
+    sc = scenes.wedge(z_tx=z_tx, z_rx=z_rx)
+    p = config.params_for(sc, grad_stop=1e-10)
+    s, c, e = oracle.run(sc, p)
+    P = e.paths()
+    assert len(P["n"]) == 1
+    assert P["n"][0] == 1 and P["type"][0][0] == 1 and P["label"][0][0] == 2
+    r1 = r2 = math.sqrt(10.0)
+    z = z_tx + (z_rx - z_tx) * r1 / (r1 + r2)
+    np.testing.assert_allclose(P["pts"][0][0], [0.0, 0.0, z], atol=1e-6)
+    L = math.sqrt(r1 ** 2 + (z - z_tx) ** 2) + math.sqrt(r2 ** 2 + (z_rx - z) ** 2)
+    assert P["length"][0] == pytest.approx(L, rel=1e-9)
+    ein = P["pts"][0][0] - sc.tx[0]
+    eout = sc.rx[0] - P["pts"][0][0]
+    w = np.array([0, 0, 1.0])
+    assert abs(ein @ w / np.linalg.norm(ein) - eout @ w / np.linalg.norm(eout)) < 1e-6
+
+
+def _tiny_occluder_scene():
+    X, Y, Z = np.eye(3)
+    parts = [scenes.plane_patch([0.5, 0.5, 1.0], X, Y, 2.0, 2.0, 0.1, [0, 0, 1], 0),
+             scenes.plane_patch([1.5, 0.0, 0.0], Y, Z, 3.0, 2.0, 0.1, [1, 0, 0], 1),
+             scenes.plane_patch([0.0, 2.2, 0.5], X, Z, 1.2, 1.5, 0.1, [0, -1, 0], 2)]
+    xyz, nrm, lab, mat = scenes.merge_clouds(parts)
+    assert xyz.shape[0] < 2000
+    return scenes.Scene("tiny", xyz, nrm, lab, mat)
+
+
+def test_visibility_traversal_matches_brute_force():
+    """The voxel traversal visits exactly the voxels a brute-force slab test finds."""
+    sc = _tiny_occluder_scene()
+    s = oracle.Scene.from_scene(sc, config.Params())
+    rng = np.random.default_rng(7)
+    lo = s.origin + 0.3
+    hi = s.origin + s.dims * 0.5 - 0.3
+    n_block = 0
+    for _ in range(400):
+        a = lo + (hi - lo) * rng.random(3)
+        b = lo + (hi - lo) * rng.random(3)
+        v1 = s.visible(a, b)
+        v2 = s.visible(a, b, brute=True)
+        assert v1 == v2
+        n_block += not v1
+    assert 40 < n_block < 360
+
+
+def test_visibility_closed_form_plane_patch():
+    """Segments crossing the interior of a sampled plane patch are occluded; others are not."""
+    sc = _tiny_occluder_scene()
+    s = oracle.Scene.from_scene(sc, config.Params())
+    rng = np.random.default_rng(3)
+    for _ in range(100):
+        x, y = 0.8 + 1.4 * rng.random(2)   # well inside the z=1 patch [0.5,2.5]^2, left of x=1.5 wall
+        x = min(x, 1.3)
+        a = np.array([x, y, 0.4])
+        b = np.array([x + 0.05, y - 0.05, 1.6])
+        if 2.0 < y < 2.4:
+            continue
+        assert not s.visible(a, b)
+        c = np.array([x, y, 1.3])
+        d = np.array([x - 0.2, y + 0.1, 1.8])
+        if y + 0.1 < 2.3:
+            assert s.visible(c, d)
+
+
+def test_march_field_is_chessboard_distance(room_tiny):
+    """March distance (Section 2.2.4) equals scipy's chessboard distance transform."""
+    from scipy import ndimage
+    s = oracle.Scene.from_scene(room_tiny, config.Params())
+    cells = s.cells()
+    nx, ny, nz = (int(d) for d in s.dims)
+    occ = (cells["count"] > 0).reshape(nz, ny, nx)
+    ref = ndimage.distance_transform_cdt(~occ, metric="chessboard")
+    np.testing.assert_array_equal(cells["march"].reshape(nz, ny, nx), np.minimum(ref, 255))
+
+
+def test_voxel_membership_by_integer_arithmetic():
+    """Each point lands in the IE of its (subvoxel, label); IEs ordered by voxel, subvoxel, label."""
+    rng = np.random.default_rng(11)
+    p = config.Params()
+    hs = p.h_s
+    # cloud whose bounds fix the origin at -0.5: points strictly inside subvoxels
+    g = rng.integers(2, 14, size=(600, 3))
+    off = rng.uniform(0.2, 0.8, size=(600, 3)) * hs
+    org = -0.5
+    xyz = org + g * hs + off
+    xyz = np.vstack([xyz, [[0.0, 0.0, 0.0], [3.0, 3.0, 3.0]]])
+    g = np.vstack([g, [[2, 2, 2], [14, 14, 14]]])
+    lab = rng.integers(0, 3, size=xyz.shape[0]).astype(np.uint32)
+    nrm = np.tile([0, 0, 1.0], (xyz.shape[0], 1))
+    s = oracle.Scene(xyz, nrm, lab, np.zeros(xyz.shape[0], np.uint8), np.zeros((0, 12)),
+                     np.zeros(0, np.uint32), p)
+    np.testing.assert_allclose(s.origin, [org] * 3)
+    I = s.ies()
+    groups = {}
+    for i in range(xyz.shape[0]):
+        groups.setdefault((tuple(g[i]), int(lab[i])), []).append(i)
+    assert s.n_ie == len(groups)
+    dims = s.dims
+    for k in range(s.n_ie):
+        key = (tuple(int(v) for v in I["gs"][k]), int(I["label"][k]))
+        members = groups[key]
+        assert I["prange"][k][1] == len(members)
+        np.testing.assert_allclose(I["rp"][k], xyz[members].astype(np.float32).astype(np.float64).mean(0),
+                                   atol=1e-12)
+        vx, vy, vz = (int(v) // 2 for v in I["gs"][k])
+        assert I["cell"][k] == (vz * dims[1] + vy) * dims[0] + vx
+    order = [(int(I["cell"][k]), tuple(int(v) % 2 for v in I["gs"][k][::-1]), int(I["label"][k]))
+             for k in range(s.n_ie)]
+    assert order == sorted(order)
+
+
+def test_sdf_on_exact_plane(room_tiny):
+    """Eq. 1 on coplanar points with exact normals is the plane distance."""
+    s = oracle.Scene.from_scene(room_tiny, config.Params())
+    I = s.ies()
+    floor = np.where((I["label"] == 4) & (I["prange"][:, 1] >= 9))[0][:20]
+    rng = np.random.default_rng(0)
+    for k in floor:
+        for _ in range(5):
+            x = I["bbc"][k] + rng.uniform(-0.15, 0.15, 3)
+            f, n = s.sdf(k, x)
+            assert f == pytest.approx(x[2], abs=1e-12)
+            np.testing.assert_allclose(n, [0, 0, 1], atol=1e-12)
+        du = np.array([0.3, -0.2, -1.0])
+        du /= np.linalg.norm(du)
+        target = I["bbc"][k] + np.array([0.05, 0.02, 0.0])   # on the patch
+        P = target - 2.0 * du                                 # 2 m back along the ray
+        t = s.sdf_hit(k, P, du)
+        t_ref = -P[2] / du[2]
+        assert t is not None and t == pytest.approx(t_ref, abs=1e-9)
+
+
+def test_cone_sphere_against_sampling():
+    rng = np.random.default_rng(5)
+    checked = 0
+    for _ in range(300):
+        apex = rng.normal(size=3)
+        axis = rng.normal(size=3)
+        axis /= np.linalg.norm(axis)
+        alpha = rng.uniform(0.01, 0.3)
+        c = apex + rng.normal(size=3) * 2.0
+        r = rng.uniform(0.05, 0.6)
+        u = rng.normal(size=(20000, 3))
+        u /= np.linalg.norm(u, axis=1, keepdims=True)
+        pts = c + r * u * rng.random((20000, 1)) ** (1 / 3)
+        pts = np.vstack([pts, c + r * u])
+        v = pts - apex
+        ang = np.arccos(np.clip(v @ axis / np.linalg.norm(v, axis=1), -1, 1))
+        amin = ang.min()
+        got = oracle.cone_sphere(apex, axis, alpha, c, r)
+        if amin < alpha - 2e-3:
+            assert got
+            checked += 1
+        elif amin > alpha + 2e-2:
+            assert not got
+            checked += 1
+    assert checked > 250
+
+
+def test_fibonacci_lattice():
+    n = config.Params().launch_count
+    assert n == 165012  # round(4 pi / (0.5 deg)^2)
+    d = oracle.fibonacci(n)
+    np.testing.assert_allclose(np.linalg.norm(d, axis=1), 1.0, atol=1e-12)
+    # equal area: z is uniform on [-1, 1]
+    hist, _ = np.histogram(d[:, 2], bins=20, range=(-1, 1))
+    assert hist.min() >= n / 20 - 2 and hist.max() <= n / 20 + 2
+    rng = np.random.default_rng(1)
+    sample = rng.integers(0, n, 100)
+    delta = math.radians(0.5)
+    for i in sample:
+        cosang = d @ d[i]
+        cosang[i] = -2
+        nn = math.acos(min(1.0, cosang.max()))
+        assert 0.5 * delta < nn < 1.2 * delta
+
+
+def test_orthonormal_basis():
+    rng = np.random.default_rng(2)
+    ns = [np.array([0, 0, -1.0]), np.array([0, 0, 1.0]), np.array([1.0, 0, 0])]
+    ns += [v / np.linalg.norm(v) for v in rng.normal(size=(50, 3))]
+    for n in ns:
+        u, v = oracle.onb(n)
+        M = np.stack([u, v, n])
+        np.testing.assert_allclose(M @ M.T, np.eye(3), atol=1e-12)
+        np.testing.assert_allclose(np.cross(u, v), n, atol=1e-12)
+
+
+def test_fresnel_removes_label_split_duplicates():
+    """Section 2.3: a reflection near a label boundary is found under two labels and the
+    first-Fresnel-zone step keeps one.  Floor split at x = 4.5, through three specular points."""
+    sc = scenes.room_tiny()
+    lab = sc.label.copy()
+    lab[(lab == 4) & (sc.xyz[:, 0] >= 4.5)] = 6
+    sc2 = scenes.Scene("split", sc.xyz, sc.nrm, lab, sc.material, tx=sc.tx, rx=sc.rx, max_refl=2)
+    p = config.params_for(sc2, grad_stop=1e-9)
+    s, c, e = oracle.run(sc2, p)
+    A = e.paths(True)
+    valid_single = {int(A["label"][i][0]) for i in range(len(A["n"])) if A["status"][i] == 0 and A["n"][i] == 1}
+    assert {4, 6} <= valid_single                # the floor reflection under both labels
+    P = e.paths()
+    got = _exact_by_labels(P)
+    assert len(got) == 25                        # ... but only once after Fresnel removal
+    ref = image_paths(box_room_planes(10.0, 10.0, 3.0), sc.tx[0], sc.rx[0], max_order=2)
+    pts_sorted = sorted(round(v[1], 6) for v in got.values())
+    assert pts_sorted == sorted(round(v[1], 6) for v in ref.values())
+
+
+def test_kappa_keeps_nearest_axis(tiny_run):
+    """kappa = 1 keeps, per (TX, RX, label sequence), the coarse path with the smallest miss."""
+    sc, p, s, c, e = tiny_run
+    full = c.paths()
+    c1 = oracle.Scene.from_scene(sc, p.replace(kappa=1)).trace(sc.tx, sc.rx).paths()
+    best = {}
+    for i in range(len(full["n"])):
+        k = oracle.path_key(full["type"][i], full["label"][i], full["n"][i])
+        if k not in best or full["miss"][i] < best[k]:
+            best[k] = full["miss"][i]
+    got = {oracle.path_key(c1["type"][i], c1["label"][i], c1["n"][i]): c1["miss"][i]
+           for i in range(len(c1["n"]))}
+    assert len(got) == len(c1["n"])
+    assert got.keys() == best.keys()
+    for k in got:
+        assert got[k] == pytest.approx(best[k], abs=1e-12)
+
+
+def test_stationarity_on_noisy_room():
+    """Every refined path is stationary: at a reflection e_in + e_out is parallel to the
+    surface normal of Eq. 1 there; at a diffraction the equal-angle law holds and the
+    point lies on its edge."""
+    full = scenes.room_noisy(n_tx=1, n_rx=2)
+    sc = full.with_pairs(full.tx[:1], full.rx[:2])
+    p = config.params_for(sc, max_refl=1, max_diff=1, n_launch=20000)
+    s, c, e = oracle.run(sc, p)
+    P = e.paths()
+    assert len(P["n"]) >= 3
+    I = s.ies()
+    n_checked = 0
+    for i in range(len(P["n"])):
+        n = int(P["n"][i])
+        nodes = [sc.tx[P["tx"][i]]] + list(P["pts"][i][:n]) + [sc.rx[P["rx"][i]]]
+        for k in range(n):
+            x = nodes[k + 1]
+            ein = (x - nodes[k]) / np.linalg.norm(x - nodes[k])
+            eout = (x - nodes[k + 2]) / np.linalg.norm(x - nodes[k + 2])
+            ie = int(P["ie"][i][k])
+            if P["type"][i][k] == 0:
+                # the point lies on the Eq. 1 surface of one IE of its label, and e_in + e_out
+                # is parallel to that surface's normal there (the reflection law)
+                same = np.where((I["label"] == P["label"][i][k]) & (I["kind"] == 0) &
+                                (np.linalg.norm(I["bbc"] - x, axis=1) < 0.4))[0]
+                ok = False
+                for j in same:
+                    f, nn = s.sdf(j, x)
+                    if f is not None and abs(f) < 1e-4:
+                        ok = ok or np.linalg.norm(np.cross(ein + eout, nn)) < 1e-3
+                assert ok
+            else:
+                e_ = sc.edges[I["edge"][ie]]
+                p0, p1 = e_[:3], e_[3:6]
+                w = (p1 - p0) / np.linalg.norm(p1 - p0)
+                assert abs((ein + eout) @ w) < 2e-4
+                off = (x - p0) - ((x - p0) @ w) * w
+                assert np.linalg.norm(off) < 1e-9
+            n_checked += 1
+    assert n_checked >= 2

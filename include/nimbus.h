@@ -1,0 +1,245 @@
+/*
+ * nimbus.h -- C ABI of the B300 (sm_103a) point-cloud ray launcher.
+ *
+ * Implements the three GPU components of "A Ray Launching Approach for Computing
+ * Exact Paths with Point Clouds" (arXiv 2402.13747, Section 2): voxelisation of a
+ * labelled point cloud (Section 2.1), coarse path tracing by voxel cone tracing
+ * (Section 2.2) and refinement of coarse paths into exact paths (Section 2.3).
+ *
+ * Conventions for every entry point:
+ *   - Return value: NIMBUS_OK (0) or one of the NIMBUS_ERR_* codes below; a text
+ *     for the last error of a context is returned by nimbus_last_error().  No
+ *     C++ exception crosses this boundary and no kernel traps.
+ *   - Pointers to inputs may be host or device memory (detected per pointer);
+ *     inputs are copied, the caller keeps ownership.
+ *   - Scenes, coarse path sets and exact path sets are owned by the library and
+ *     named by opaque handles until nimbus_release().
+ *   - Work is enqueued on the caller's CUDA stream (cudaStream_t passed as void*;
+ *     NULL = the legacy default stream).  voxelize, trace_coarse and refine read
+ *     a few counters back to size their buffers and so return after the GPU
+ *     work they enqueued has finished; nimbus_query copies results to
+ *     caller-owned host memory and synchronises.
+ *   - Lengths in metres, angles in radians, all coordinates in one world frame.
+ *   - A context is not thread-safe: serialise calls on one context.
+ */
+#ifndef NIMBUS_H_
+#define NIMBUS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NIMBUS_OK 0
+#define NIMBUS_ERR_ARG 1      /* invalid argument (null pointer, size, TX/RX outside the grid) */
+#define NIMBUS_ERR_OOM 2      /* the context's device-memory budget or the device is exhausted */
+#define NIMBUS_ERR_CUDA 3     /* a CUDA runtime error; see nimbus_last_error() */
+#define NIMBUS_ERR_OVERFLOW 4 /* a bounded device buffer overflowed; sizes in nimbus_path_counts */
+#define NIMBUS_ERR_TIMEOUT 5  /* a bounded device wait gave up */
+#define NIMBUS_ERR_STATE 6    /* unknown handle or a handle of the wrong kind */
+
+#define NIMBUS_MAX_INTERACTIONS 8 /* interactions per path, upper bound of max_int */
+
+#if defined(__GNUC__)
+#define NIMBUS_API __attribute__((visibility("default")))
+#else
+#define NIMBUS_API
+#endif
+
+typedef struct nimbus_ctx nimbus_ctx;
+typedef uint64_t nimbus_handle;
+
+/* Labelled point cloud (Section 2): position, normal and label per point; the
+ * label is the segmentation cluster (a distinct surface).  material is carried
+ * to the output (may be NULL). */
+typedef struct {
+  const float* xyz;         /* [n*3] positions */
+  const float* nrm;         /* [n*3] unit normals */
+  const uint32_t* label;    /* [n] surface labels, < 2^24 */
+  const uint8_t* material;  /* [n] or NULL */
+  int64_t n;
+} nimbus_cloud;
+
+/* Manually inserted diffraction edges (Section 2), exterior edges only
+ * (Section 3.2): p0, p1 and the outward normals of the two faces meeting there. */
+typedef struct {
+  const double* edges;      /* [n*12]: p0[3] p1[3] n_face0[3] n_face1[3] */
+  const uint32_t* label;    /* [n] edge labels, < 2^24 */
+  int64_t n;
+} nimbus_edges;
+
+/* Voxelisation (Section 2.1) and point-set intersection (Section 2.2.1). */
+typedef struct {
+  double voxel_size;        /* low-resolution voxel edge h (Table 1: 0.5) */
+  double sdf_sigma;         /* Gaussian width of the Eq. 1 weights */
+  double sdf_eps;           /* |f| "near zero" threshold */
+  double vis_ignore;        /* hits this close to a path node on its own surface are not occlusions */
+  double region_min[3];     /* optional box the grid must also cover (TX/RX live inside the grid) */
+  double region_max[3];
+  int32_t has_region;
+  int32_t dv;               /* voxel division factor D_v (Table 1: 2), 1..4 */
+  int32_t sdf_max_steps;    /* steps of the |f| march */
+  int32_t pad_;
+} nimbus_vox_params;
+
+/* Coarse path tracing (Section 2.2). */
+typedef struct {
+  double cone_half_angle;   /* constant apex half-angle alpha of every cone */
+  double launch_spacing;    /* Delta of the uniform TX launch; primary half-angle max(alpha, Delta/sqrt2) */
+  double sep_eps;           /* reflection separation plane offset */
+  int32_t n_launch;         /* Fibonacci directions per TX (0: round(4 pi / Delta^2)) */
+  int32_t max_refl;
+  int32_t max_diff;
+  int32_t max_int;          /* maximum interactions (Table 1: 5), <= NIMBUS_MAX_INTERACTIONS */
+  int32_t kappa;            /* duplicate limit per (TX, RX, label sequence) (Table 1: 100) */
+  int32_t pad_;
+  int64_t max_nodes;        /* bound on interaction nodes per level (0: from the memory budget) */
+  int64_t max_coarse;       /* bound on coarse paths before kappa (0: from the memory budget) */
+} nimbus_trace_params;
+
+/* Path refinement (Section 2.3). */
+typedef struct {
+  double delta;             /* convergence threshold on ||grad f|| (Table 1: 1e-4) */
+  double gamma;             /* gradient-descent step scale: step = gamma / (1/a + 1/b) */
+  double grad_stop;         /* iteration stops early once ||grad f|| < grad_stop */
+  double freq_hz;           /* carrier frequency for the first Fresnel zone (Table 1: 60 GHz) */
+  int32_t rho;              /* refinement iterations (Table 1: 2000) */
+  int32_t pad_;
+} nimbus_refine_params;
+
+/* Sizes and counters of a handle (filled by nimbus_query / nimbus_query_coarse). */
+typedef struct {
+  int64_t n_paths;          /* exact paths after duplicate removal */
+  int64_t n_refined;        /* coarse paths refined (after kappa) */
+  int64_t n_refined_valid;  /* refined paths that converged and passed visibility */
+  int64_t n_coarse;         /* coarse paths after the kappa limit */
+  int64_t n_coarse_raw;     /* coarse paths before the kappa limit */
+  int64_t n_cones;          /* cones traced (primary + every level + diffraction fans) */
+  int64_t n_vis;            /* visibility rays traced during coarse tracing */
+  int64_t n_nodes;          /* interaction nodes over all levels */
+  int64_t needed_nodes;     /* on NIMBUS_ERR_OVERFLOW: largest level size requested */
+  int64_t needed_coarse;    /* on NIMBUS_ERR_OVERFLOW: coarse paths requested */
+  int64_t bytes_read;       /* algorithmic bytes of scene records read by the trace kernels */
+  int32_t overflow;         /* nonzero when a bounded buffer dropped work */
+  int32_t pad_;
+} nimbus_path_counts;
+
+/* Caller-owned host arrays for nimbus_query, each sized for n_paths entries
+ * (NIMBUS_MAX_INTERACTIONS slots per path where marked [8]).  Any may be NULL. */
+typedef struct {
+  int32_t* tx;              /* TX index */
+  int32_t* rx;              /* RX index */
+  int32_t* n_int;           /* number of interactions */
+  int32_t* types;           /* [8] 0 = reflection, 1 = diffraction, -1 unused */
+  uint32_t* labels;         /* [8] surface / edge label per interaction */
+  uint8_t* materials;       /* [8] material per interaction (255 for edges) */
+  int64_t* ies;             /* [8] intersectable entity of the coarse path it came from */
+  double* points;           /* [8*3] interaction points */
+  double* length;           /* path length (Eq. 2) */
+  double* delay;            /* length / c */
+  double* grad;             /* final ||grad f|| */
+  int32_t* iters;           /* refinement iterations used */
+  int32_t* status;          /* 0 valid, 1 re-projection miss, 2 not converged, 3 occluded, 4 left edge */
+} nimbus_path_view;
+
+/* Caller-owned host arrays for nimbus_query_coarse, sized for n_coarse entries. */
+typedef struct {
+  int32_t* tx;
+  int32_t* rx;
+  int32_t* n_int;
+  int64_t* ies;             /* [8] intersectable entities along the path */
+  int32_t* types;           /* [8] */
+  uint32_t* labels;         /* [8] */
+  float* miss;              /* distance of the RX from the last cone's axis */
+} nimbus_coarse_view;
+
+/* Scene tables for inspection (nimbus_scene_tables), caller-owned host arrays
+ * sized by nimbus_scene_info. Any may be NULL. */
+typedef struct {
+  int32_t* kind;            /* [n_ie] 0 point set, 1 edge segment */
+  uint32_t* label;          /* [n_ie] */
+  int64_t* cell;            /* [n_ie] low-resolution voxel (linear: (z*ny + y)*nx + x) */
+  int32_t* gs;              /* [n_ie*3] global subvoxel coordinates */
+  int64_t* prange;          /* [n_ie*2] first point (grouped order) and count */
+  float* rp;                /* [n_ie*3] ray reception point */
+  float* normal;            /* [n_ie*3] normalised mean normal (point IEs) */
+  float* bbc;               /* [n_ie*3] bounding-box centre of the points */
+  uint8_t* material;        /* [n_ie] */
+  int64_t* cell_begin;      /* [n_cells] first IE of each voxel */
+  int32_t* cell_count;      /* [n_cells] IEs in each voxel */
+  int32_t* march;           /* [n_cells] capped L-infinity distance to the nearest voxel with IEs */
+} nimbus_scene_view;
+
+/* Context on CUDA device `device` with a device-memory budget in bytes
+ * (0 = 90% of the free memory).  out receives the context. */
+NIMBUS_API int nimbus_create(nimbus_ctx** out, int device, size_t mem_budget_bytes);
+NIMBUS_API int nimbus_destroy(nimbus_ctx* ctx);
+NIMBUS_API const char* nimbus_last_error(nimbus_ctx* ctx);
+
+/* Section 2.1: bin the cloud into subvoxels (h / D_v) by a sort on the
+ * (voxel, subvoxel, kind, label) key, build one intersectable entity per
+ * (subvoxel, label) point group (reception point = centroid, normal =
+ * normalised mean normal) and per edge segment inside a subvoxel, give each
+ * voxel its entity range and compute the march distance field of
+ * Section 2.2.4.  edges may be NULL.  scene_out receives the scene handle. */
+NIMBUS_API int nimbus_voxelize(nimbus_ctx* ctx, const nimbus_cloud* cloud, const nimbus_edges* edges,
+                    const nimbus_vox_params* params, nimbus_handle* scene_out, void* stream);
+
+/* Dynamic scenes: drop the points of the scene whose position lies inside the
+ * box [aabb_min, aabb_max] and add `replacement` (may be NULL or empty), then
+ * rebuild the scene's tables in place on the same grid.  The result equals a
+ * full nimbus_voxelize of the updated cloud on that grid. */
+NIMBUS_API int nimbus_update_region(nimbus_ctx* ctx, nimbus_handle scene, const double aabb_min[3],
+                         const double aabb_max[3], const nimbus_cloud* replacement, void* stream);
+
+/* Section 2.2: for every TX, a uniform launch of cones on a Fibonacci lattice
+ * (transmission phase), then level by level reflected cones and Keller-cone
+ * diffraction fans (propagation phase) traversed by voxel cone tracing;
+ * cone-sphere tests, separation planes and visibility rays decide which
+ * entities a cone reaches, RXs reached give coarse paths, and at most kappa
+ * coarse paths are kept per (TX, RX, label sequence).  tx [n_tx*3], rx [n_rx*3]
+ * (host or device).  coarse_out receives the coarse set handle. */
+NIMBUS_API int nimbus_trace_coarse(nimbus_ctx* ctx, nimbus_handle scene, const double* tx, int32_t n_tx,
+                        const double* rx, int32_t n_rx, const nimbus_trace_params* params,
+                        nimbus_handle* coarse_out, void* stream);
+
+/* Section 2.3: refine every coarse path by gradient descent on the path length
+ * (Eq. 2) over the local variables (r, s) of reflections and t of
+ * diffractions, re-projecting reflection points onto the point cloud by a ray,
+ * for rho iterations or until ||grad f|| < grad_stop; keep paths with
+ * ||grad f|| < delta whose segments are all visible; remove duplicates by label
+ * sequence (shortest kept) and by first Fresnel zone (delay order).
+ * paths_out receives the exact path set handle. */
+NIMBUS_API int nimbus_refine(nimbus_ctx* ctx, nimbus_handle scene, nimbus_handle coarse,
+                  const nimbus_refine_params* params, nimbus_handle* paths_out, void* stream);
+
+/* Exact paths: counts (required) and, when view != NULL, the paths.  which = 0:
+ * paths after duplicate removal; 1: every refined coarse path with its status.
+ * Synchronises the stream. */
+NIMBUS_API int nimbus_query(nimbus_ctx* ctx, nimbus_handle paths, int32_t which, nimbus_path_counts* counts,
+                 const nimbus_path_view* view, void* stream);
+
+/* Coarse paths after the kappa limit: counts and, when view != NULL, the paths. */
+NIMBUS_API int nimbus_query_coarse(nimbus_ctx* ctx, nimbus_handle coarse, nimbus_path_counts* counts,
+                        const nimbus_coarse_view* view, void* stream);
+
+/* Grid and table sizes of a scene: origin[3], dims[3], number of entities. */
+NIMBUS_API int nimbus_scene_info(nimbus_ctx* ctx, nimbus_handle scene, double origin[3], int32_t dims[3],
+                      int64_t* n_ie, int64_t* n_points);
+
+/* Copy a scene's entity and voxel tables into caller-owned host arrays. */
+NIMBUS_API int nimbus_scene_tables(nimbus_ctx* ctx, nimbus_handle scene, const nimbus_scene_view* view,
+                        void* stream);
+
+/* Free a scene, coarse set or path set. */
+NIMBUS_API int nimbus_release(nimbus_ctx* ctx, nimbus_handle h);
+
+/* Bytes of device memory the context currently holds. */
+NIMBUS_API int nimbus_memory_used(nimbus_ctx* ctx, size_t* bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NIMBUS_H_ */

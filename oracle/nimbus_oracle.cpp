@@ -1149,11 +1149,14 @@ ExactSet* refine(const Scene& s, const CoarseSet& cs) {
   // First-Fresnel-zone duplicate removal: sort by delay; a path is dropped if an
   // earlier kept path has the same chain of interaction types and each of its
   // interaction points lies within that path's first Fresnel zone radius
-  // r_k = sqrt(lambda a_k b_k / (a_k + b_k)).
+  // r_k = sqrt(lambda a_k b_k / (a_k + b_k)).  Reading for ties: delays are
+  // compared in bins of 1 um of length, so paths of equal length up to rounding
+  // are ordered by their interaction types and labels.
   std::sort(best.begin(), best.end(), [](const Exact& a, const Exact& b) {
     if (a.tx != b.tx) return a.tx < b.tx;
     if (a.rx != b.rx) return a.rx < b.rx;
-    if (a.delay != b.delay) return a.delay < b.delay;
+    long long qa = (long long)std::floor(a.length * 1e6), qb = (long long)std::floor(b.length * 1e6);
+    if (qa != qb) return qa < qb;
     if (seq_less(a, b)) return true;
     if (seq_less(b, a)) return false;
     return ie_less(a, b);

@@ -1,0 +1,437 @@
+// C ABI of the library (include/nimbus.h): contexts, handles, the device-memory
+// budget, argument checks and the copy-out of results.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "nimbus_host.hpp"
+
+struct nimbus_ctx {
+  int device = 0;
+  nb::Mem mem;
+  std::string err;
+  std::unordered_map<uint64_t, nb::Obj*> objs;
+  std::unordered_map<uint64_t, cudaStream_t> obj_stream;
+  uint64_t next = 1;
+};
+
+namespace nb {
+
+int cuda_fail(std::string* err, cudaError_t e, const char* what) {
+  char buf[512];
+  std::snprintf(buf, sizeof buf, "CUDA error %d (%s) in %s", (int)e, cudaGetErrorString(e), what);
+  if (err) *err = buf;
+  cudaGetLastError();
+  return e == cudaErrorMemoryAllocation ? NIMBUS_ERR_OOM : NIMBUS_ERR_CUDA;
+}
+
+int num_sms() {
+  int d = 0, n = 148;
+  cudaGetDevice(&d);
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, d);
+  return n;
+}
+
+int Mem::alloc(void** p, size_t bytes, cudaStream_t st) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  if (used + bytes > budget) {
+    if (err) *err = "device memory budget exhausted";
+    return NIMBUS_ERR_OOM;
+  }
+  cudaError_t e = cudaMallocAsync(p, bytes, st);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return cuda_fail(err, e, "cudaMallocAsync");
+  }
+  sizes[*p] = bytes;
+  used += bytes;
+  peak = std::max(peak, used);
+  return NIMBUS_OK;
+}
+
+void Mem::release(void* p, cudaStream_t st) {
+  if (!p) return;
+  auto it = sizes.find(p);
+  if (it == sizes.end()) return;
+  used -= it->second;
+  sizes.erase(it);
+  cudaFreeAsync(p, st);
+}
+
+namespace {
+
+__global__ void k_gather_exact(const ExactRec* all, const uint32_t* idx, int64_t n, ExactRec* out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = all[idx[i]];
+}
+
+}  // namespace
+}  // namespace nb
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int d) {
+    cudaGetDevice(&prev);
+    if (prev != d) cudaSetDevice(d);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+template <class T>
+T* get_obj(nimbus_ctx* ctx, nimbus_handle h, int kind) {
+  auto it = ctx->objs.find(h);
+  if (it == ctx->objs.end() || it->second->kind != kind) {
+    ctx->err = "unknown handle or handle of the wrong kind";
+    return nullptr;
+  }
+  return static_cast<T*>(it->second);
+}
+
+nimbus_handle put_obj(nimbus_ctx* ctx, nb::Obj* o, cudaStream_t st) {
+  nimbus_handle h = ctx->next++;
+  ctx->objs[h] = o;
+  ctx->obj_stream[h] = st;
+  return h;
+}
+
+void drop_obj(nimbus_ctx* ctx, nb::Obj* o, cudaStream_t st) {
+  o->free_all(st);
+  if (o->kind == nb::OBJ_SCENE) {
+    auto* s = static_cast<nb::SceneObj*>(o);
+    for (void* p : s->table_bufs) ctx->mem.release(p, st);
+    s->table_bufs.clear();
+  }
+  delete o;
+}
+
+}  // namespace
+
+extern "C" {
+
+int nimbus_create(nimbus_ctx** out, int device, size_t mem_budget_bytes) {
+  if (!out) return NIMBUS_ERR_ARG;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+    cudaGetLastError();
+    return NIMBUS_ERR_ARG;
+  }
+  nimbus_ctx* ctx = new nimbus_ctx();
+  ctx->device = device;
+  ctx->mem.err = &ctx->err;
+  DeviceGuard g(device);
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+    cudaGetLastError();
+    delete ctx;
+    return NIMBUS_ERR_CUDA;
+  }
+  ctx->mem.budget = mem_budget_bytes ? mem_budget_bytes : (size_t)(0.9 * (double)free_b);
+  *out = ctx;
+  return NIMBUS_OK;
+}
+
+int nimbus_destroy(nimbus_ctx* ctx) {
+  if (!ctx) return NIMBUS_ERR_ARG;
+  {
+    DeviceGuard g(ctx->device);
+    for (auto& kv : ctx->objs) drop_obj(ctx, kv.second, ctx->obj_stream[kv.first]);
+    ctx->objs.clear();
+    cudaDeviceSynchronize();
+    cudaGetLastError();
+  }
+  delete ctx;
+  return NIMBUS_OK;
+}
+
+const char* nimbus_last_error(nimbus_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int nimbus_voxelize(nimbus_ctx* ctx, const nimbus_cloud* cloud, const nimbus_edges* edges,
+                    const nimbus_vox_params* params, nimbus_handle* scene_out, void* stream) {
+  if (!ctx) return NIMBUS_ERR_ARG;
+  if (!scene_out || !params) {
+    ctx->err = "voxelize: null argument";
+    return NIMBUS_ERR_ARG;
+  }
+  DeviceGuard g(ctx->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  auto* S = new nb::SceneObj();
+  S->mem = &ctx->mem;
+  int rc = nb::voxelize_scene(ctx->mem, cloud, edges, params, S, st);
+  if (rc != NIMBUS_OK) {
+    drop_obj(ctx, S, st);
+    return rc;
+  }
+  *scene_out = put_obj(ctx, S, st);
+  return NIMBUS_OK;
+}
+
+int nimbus_update_region(nimbus_ctx* ctx, nimbus_handle scene, const double aabb_min[3], const double aabb_max[3],
+                         const nimbus_cloud* replacement, void* stream) {
+  if (!ctx) return NIMBUS_ERR_ARG;
+  if (!aabb_min || !aabb_max) {
+    ctx->err = "update_region: null box";
+    return NIMBUS_ERR_ARG;
+  }
+  DeviceGuard g(ctx->device);
+  auto* S = get_obj<nb::SceneObj>(ctx, scene, nb::OBJ_SCENE);
+  if (!S) return NIMBUS_ERR_STATE;
+  cudaStream_t st = (cudaStream_t)stream;
+  ctx->obj_stream[scene] = st;
+  return nb::update_scene_region(ctx->mem, S, aabb_min, aabb_max, replacement, st);
+}
+
+int nimbus_trace_coarse(nimbus_ctx* ctx, nimbus_handle scene, const double* tx, int32_t n_tx, const double* rx,
+                        int32_t n_rx, const nimbus_trace_params* params, nimbus_handle* coarse_out, void* stream) {
+  if (!ctx) return NIMBUS_ERR_ARG;
+  if (!coarse_out || !params) {
+    ctx->err = "trace: null argument";
+    return NIMBUS_ERR_ARG;
+  }
+  DeviceGuard g(ctx->device);
+  auto* S = get_obj<nb::SceneObj>(ctx, scene, nb::OBJ_SCENE);
+  if (!S) return NIMBUS_ERR_STATE;
+  cudaStream_t st = (cudaStream_t)stream;
+  auto* C = new nb::CoarseObj();
+  C->mem = &ctx->mem;
+  C->scene = scene;
+  int rc = nb::trace_coarse(ctx->mem, S, tx, n_tx, rx, n_rx, params, C, st);
+  if (rc != NIMBUS_OK && rc != NIMBUS_ERR_OVERFLOW) {
+    drop_obj(ctx, C, st);
+    return rc;
+  }
+  *coarse_out = put_obj(ctx, C, st);
+  return rc;
+}
+
+int nimbus_refine(nimbus_ctx* ctx, nimbus_handle scene, nimbus_handle coarse, const nimbus_refine_params* params,
+                  nimbus_handle* paths_out, void* stream) {
+  if (!ctx) return NIMBUS_ERR_ARG;
+  if (!paths_out || !params) {
+    ctx->err = "refine: null argument";
+    return NIMBUS_ERR_ARG;
+  }
+  DeviceGuard g(ctx->device);
+  auto* S = get_obj<nb::SceneObj>(ctx, scene, nb::OBJ_SCENE);
+  if (!S) return NIMBUS_ERR_STATE;
+  auto* C = get_obj<nb::CoarseObj>(ctx, coarse, nb::OBJ_COARSE);
+  if (!C) return NIMBUS_ERR_STATE;
+  if (C->scene != scene) {
+    ctx->err = "refine: coarse set was traced on another scene";
+    return NIMBUS_ERR_STATE;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  auto* P = new nb::PathsObj();
+  P->mem = &ctx->mem;
+  int rc = nb::refine_paths(ctx->mem, S, C, params, P, st);
+  if (rc != NIMBUS_OK) {
+    drop_obj(ctx, P, st);
+    return rc;
+  }
+  *paths_out = put_obj(ctx, P, st);
+  return NIMBUS_OK;
+}
+
+int nimbus_query(nimbus_ctx* ctx, nimbus_handle paths, int32_t which, nimbus_path_counts* counts,
+                 const nimbus_path_view* view, void* stream) {
+  if (!ctx) return NIMBUS_ERR_ARG;
+  if (!counts) {
+    ctx->err = "query: null counts";
+    return NIMBUS_ERR_ARG;
+  }
+  DeviceGuard g(ctx->device);
+  auto* P = get_obj<nb::PathsObj>(ctx, paths, nb::OBJ_PATHS);
+  if (!P) return NIMBUS_ERR_STATE;
+  cudaStream_t st = (cudaStream_t)stream;
+  *counts = P->counts;
+  counts->n_paths = P->n_final;
+  const int64_t n = which ? P->n_all : P->n_final;
+  std::vector<nb::ExactRec> h;
+  if (n > 0 && (view || which)) {
+    h.resize(n);
+    if (which) {
+      NB_CUDA(&ctx->err, cudaMemcpyAsync(h.data(), P->all, n * sizeof(nb::ExactRec), cudaMemcpyDeviceToHost, st));
+    } else {
+      nb::ExactRec* tmp = nullptr;
+      int rc = ctx->mem.alloc_n(&tmp, n, st);
+      if (rc != NIMBUS_OK) return rc;
+      nb::k_gather_exact<<<nb::grid_for(n, 128), 128, 0, st>>>(P->all, P->final_idx, n, tmp);
+      cudaError_t e = cudaGetLastError();
+      if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), tmp, n * sizeof(nb::ExactRec), cudaMemcpyDeviceToHost, st);
+      ctx->mem.release(tmp, st);
+      if (e != cudaSuccess) return nb::cuda_fail(&ctx->err, e, "query copy");
+    }
+  }
+  NB_CUDA(&ctx->err, cudaStreamSynchronize(st));
+  if (which) {
+    int64_t nv = 0;
+    for (const auto& r : h) nv += r.status == nb::ST_VALID;
+    counts->n_refined_valid = nv;
+  }
+  if (!view) return NIMBUS_OK;
+  for (int64_t i = 0; i < n; ++i) {
+    const nb::ExactRec& r = h[i];
+    if (view->tx) view->tx[i] = (int32_t)r.tx;
+    if (view->rx) view->rx[i] = (int32_t)r.rx;
+    if (view->n_int) view->n_int[i] = (int32_t)r.n;
+    if (view->length) view->length[i] = r.length;
+    if (view->delay) view->delay[i] = r.delay;
+    if (view->grad) view->grad[i] = r.grad;
+    if (view->iters) view->iters[i] = (int32_t)r.iters;
+    if (view->status) view->status[i] = (int32_t)r.status;
+    for (int q = 0; q < NB_MAXI; ++q) {
+      bool in = q < (int)r.n;
+      if (view->types) view->types[i * NB_MAXI + q] = in ? (int32_t)((r.types >> q) & 1u) : -1;
+      if (view->labels) view->labels[i * NB_MAXI + q] = in ? r.lab[q] : NB_NONE_LABEL;
+      if (view->materials) view->materials[i * NB_MAXI + q] = in ? r.mat[q] : 255;
+      if (view->ies) view->ies[i * NB_MAXI + q] = in ? (int64_t)r.ie[q] : -1;
+      if (view->points)
+        for (int a = 0; a < 3; ++a) view->points[(i * NB_MAXI + q) * 3 + a] = in ? r.pts[q][a] : 0.0;
+    }
+  }
+  return NIMBUS_OK;
+}
+
+int nimbus_query_coarse(nimbus_ctx* ctx, nimbus_handle coarse, nimbus_path_counts* counts,
+                        const nimbus_coarse_view* view, void* stream) {
+  if (!ctx) return NIMBUS_ERR_ARG;
+  if (!counts) {
+    ctx->err = "query_coarse: null counts";
+    return NIMBUS_ERR_ARG;
+  }
+  DeviceGuard g(ctx->device);
+  auto* C = get_obj<nb::CoarseObj>(ctx, coarse, nb::OBJ_COARSE);
+  if (!C) return NIMBUS_ERR_STATE;
+  *counts = C->counts;
+  if (!view || C->n == 0) return NIMBUS_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t n = C->n;
+  std::vector<uint32_t> tx(n), rx(n), ni(n), ty(n), ie(n * NB_MAXI), lab(n * NB_MAXI);
+  std::vector<float> miss(n);
+  NB_CUDA(&ctx->err, cudaMemcpyAsync(tx.data(), C->tx, n * 4, cudaMemcpyDeviceToHost, st));
+  NB_CUDA(&ctx->err, cudaMemcpyAsync(rx.data(), C->rx, n * 4, cudaMemcpyDeviceToHost, st));
+  NB_CUDA(&ctx->err, cudaMemcpyAsync(ni.data(), C->nint, n * 4, cudaMemcpyDeviceToHost, st));
+  NB_CUDA(&ctx->err, cudaMemcpyAsync(ty.data(), C->types, n * 4, cudaMemcpyDeviceToHost, st));
+  NB_CUDA(&ctx->err, cudaMemcpyAsync(ie.data(), C->ie, n * NB_MAXI * 4, cudaMemcpyDeviceToHost, st));
+  NB_CUDA(&ctx->err, cudaMemcpyAsync(lab.data(), C->lab, n * NB_MAXI * 4, cudaMemcpyDeviceToHost, st));
+  NB_CUDA(&ctx->err, cudaMemcpyAsync(miss.data(), C->miss, n * 4, cudaMemcpyDeviceToHost, st));
+  NB_CUDA(&ctx->err, cudaStreamSynchronize(st));
+  for (int64_t i = 0; i < n; ++i) {
+    if (view->tx) view->tx[i] = (int32_t)tx[i];
+    if (view->rx) view->rx[i] = (int32_t)rx[i];
+    if (view->n_int) view->n_int[i] = (int32_t)ni[i];
+    if (view->miss) view->miss[i] = miss[i];
+    for (int q = 0; q < NB_MAXI; ++q) {
+      bool in = q < (int)ni[i];
+      if (view->ies) view->ies[i * NB_MAXI + q] = in ? (int64_t)ie[i * NB_MAXI + q] : -1;
+      if (view->types) view->types[i * NB_MAXI + q] = in ? (int32_t)((ty[i] >> q) & 1u) : -1;
+      if (view->labels) view->labels[i * NB_MAXI + q] = in ? lab[i * NB_MAXI + q] : NB_NONE_LABEL;
+    }
+  }
+  return NIMBUS_OK;
+}
+
+int nimbus_scene_info(nimbus_ctx* ctx, nimbus_handle scene, double origin[3], int32_t dims[3], int64_t* n_ie,
+                      int64_t* n_points) {
+  if (!ctx) return NIMBUS_ERR_ARG;
+  auto* S = get_obj<nb::SceneObj>(ctx, scene, nb::OBJ_SCENE);
+  if (!S) return NIMBUS_ERR_STATE;
+  for (int a = 0; a < 3; ++a) {
+    if (origin) origin[a] = S->origin[a];
+    if (dims) dims[a] = S->dims[a];
+  }
+  if (n_ie) *n_ie = S->n_ie;
+  if (n_points) *n_points = S->n_points;
+  return NIMBUS_OK;
+}
+
+int nimbus_scene_tables(nimbus_ctx* ctx, nimbus_handle scene, const nimbus_scene_view* view, void* stream) {
+  if (!ctx) return NIMBUS_ERR_ARG;
+  if (!view) {
+    ctx->err = "scene_tables: null view";
+    return NIMBUS_ERR_ARG;
+  }
+  DeviceGuard g(ctx->device);
+  auto* S = get_obj<nb::SceneObj>(ctx, scene, nb::OBJ_SCENE);
+  if (!S) return NIMBUS_ERR_STATE;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t n = S->n_ie;
+  const int64_t nc = (int64_t)S->dims[0] * S->dims[1] * S->dims[2];
+  std::vector<nb::IERec> ies(n);
+  std::vector<uint2> cells(nc);
+  std::vector<uint8_t> march(nc);
+  if (n) NB_CUDA(&ctx->err, cudaMemcpyAsync(ies.data(), S->d.ies, n * sizeof(nb::IERec), cudaMemcpyDeviceToHost, st));
+  NB_CUDA(&ctx->err, cudaMemcpyAsync(cells.data(), S->d.cells, nc * sizeof(uint2), cudaMemcpyDeviceToHost, st));
+  NB_CUDA(&ctx->err, cudaMemcpyAsync(march.data(), S->d.march, nc, cudaMemcpyDeviceToHost, st));
+  NB_CUDA(&ctx->err, cudaStreamSynchronize(st));
+  const int dv = S->params.dv;
+  const double hs = S->params.voxel_size / dv;
+  for (int64_t i = 0; i < n; ++i) {
+    const nb::IERec& r = ies[i];
+    uint32_t meta, lab, pb, pc;
+    std::memcpy(&meta, &r.nrm_meta.w, 4);
+    std::memcpy(&lab, &r.rp_lab.w, 4);
+    std::memcpy(&pb, &r.bbc_pb.w, 4);
+    std::memcpy(&pc, &r.sc_pc.w, 4);
+    int kind = (int)(meta & 1u);
+    if (view->kind) view->kind[i] = kind;
+    if (view->label) view->label[i] = lab;
+    if (view->material) view->material[i] = (uint8_t)((meta >> 8) & 0xffu);
+    const float sc[3] = {r.sc_pc.x, r.sc_pc.y, r.sc_pc.z};
+    int gs[3];
+    for (int a = 0; a < 3; ++a) gs[a] = (int)std::floor((sc[a] - S->origin[a]) / hs);
+    if (view->gs)
+      for (int a = 0; a < 3; ++a) view->gs[3 * i + a] = gs[a];
+    if (view->cell)
+      view->cell[i] = ((int64_t)(gs[2] / dv) * S->dims[1] + gs[1] / dv) * S->dims[0] + gs[0] / dv;
+    if (view->prange) {
+      view->prange[2 * i] = kind == 0 ? (int64_t)pb : 0;
+      view->prange[2 * i + 1] = kind == 0 ? (int64_t)pc : 0;
+    }
+    const float rp[3] = {r.rp_lab.x, r.rp_lab.y, r.rp_lab.z}, nn[3] = {r.nrm_meta.x, r.nrm_meta.y, r.nrm_meta.z},
+                bb[3] = {r.bbc_pb.x, r.bbc_pb.y, r.bbc_pb.z};
+    for (int a = 0; a < 3; ++a) {
+      if (view->rp) view->rp[3 * i + a] = rp[a];
+      if (view->normal) view->normal[3 * i + a] = nn[a];
+      if (view->bbc) view->bbc[3 * i + a] = bb[a];
+    }
+  }
+  for (int64_t c = 0; c < nc; ++c) {
+    if (view->cell_begin) view->cell_begin[c] = cells[c].x;
+    if (view->cell_count) view->cell_count[c] = (int32_t)cells[c].y;
+    if (view->march) view->march[c] = march[c];
+  }
+  return NIMBUS_OK;
+}
+
+int nimbus_release(nimbus_ctx* ctx, nimbus_handle h) {
+  if (!ctx) return NIMBUS_ERR_ARG;
+  auto it = ctx->objs.find(h);
+  if (it == ctx->objs.end()) {
+    ctx->err = "release: unknown handle";
+    return NIMBUS_ERR_STATE;
+  }
+  DeviceGuard g(ctx->device);
+  drop_obj(ctx, it->second, ctx->obj_stream[h]);
+  ctx->objs.erase(it);
+  ctx->obj_stream.erase(h);
+  return NIMBUS_OK;
+}
+
+int nimbus_memory_used(nimbus_ctx* ctx, size_t* bytes) {
+  if (!ctx || !bytes) return NIMBUS_ERR_ARG;
+  *bytes = ctx->mem.used;
+  return NIMBUS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,174 @@
+// Host-side internals of the CUDA library: device-memory accounting, the sort and
+// scan primitives and the launch wrappers of each stage.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "nimbus_internal.cuh"
+
+namespace nb {
+
+// Device memory of one context, stream-ordered (cudaMallocAsync), bounded by a budget.
+struct Mem {
+  size_t budget = 0, used = 0, peak = 0;
+  std::unordered_map<void*, size_t> sizes;
+  std::string* err = nullptr;
+  int alloc(void** p, size_t bytes, cudaStream_t st);
+  void release(void* p, cudaStream_t st);
+  template <class T>
+  int alloc_n(T** p, size_t n, cudaStream_t st) {
+    return alloc(reinterpret_cast<void**>(p), n * sizeof(T) + 16, st);
+  }
+};
+
+// A list of device allocations released together.
+struct Scratch {
+  Mem* mem;
+  cudaStream_t st;
+  std::vector<void*> ptrs;
+  Scratch(Mem* m, cudaStream_t s) : mem(m), st(s) {}
+  ~Scratch() {
+    for (void* p : ptrs) mem->release(p, st);
+  }
+  template <class T>
+  int get(T** p, size_t n) {
+    int rc = mem->alloc_n(p, n, st);
+    if (rc == NIMBUS_OK) ptrs.push_back(*p);
+    return rc;
+  }
+};
+
+int cuda_fail(std::string* err, cudaError_t e, const char* what);
+#define NB_CUDA(err, call)                                   \
+  do {                                                       \
+    cudaError_t e_ = (call);                                 \
+    if (e_ != cudaSuccess) return ::nb::cuda_fail(err, e_, #call); \
+  } while (0)
+#define NB_TRY(call)               \
+  do {                             \
+    int rc_ = (call);              \
+    if (rc_ != NIMBUS_OK) return rc_; \
+  } while (0)
+
+int num_sms();
+
+// Exclusive prefix sum of n 32-bit counts; total (device, may be null) receives the sum.
+int exclusive_scan(Scratch& sc, const uint32_t* in, uint32_t* out, int64_t n, uint32_t* total);
+
+// Stable LSD radix sort of (key, value) pairs on the low `bits` key bits.  The
+// sorted pairs end in (keys, vals); keys_alt / vals_alt are work buffers of n.
+int radix_sort(Scratch& sc, uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt,
+               int64_t n, int bits);
+
+// ----------------------------------------------------------------------------- objects
+enum { OBJ_SCENE = 1, OBJ_COARSE = 2, OBJ_PATHS = 3 };
+
+struct Obj {
+  int kind;
+  Mem* mem = nullptr;
+  std::vector<void*> bufs;   // device buffers owned by the object
+  explicit Obj(int k) : kind(k) {}
+  virtual ~Obj() {}
+  template <class T>
+  int own(T** p, size_t n, cudaStream_t st) {
+    int rc = mem->alloc_n(p, n, st);
+    if (rc == NIMBUS_OK) bufs.push_back(*p);
+    return rc;
+  }
+  void free_all(cudaStream_t st) {
+    for (void* p : bufs) mem->release(p, st);
+    bufs.clear();
+  }
+};
+
+// A voxelised scene (Section 2.1): grid, entity table, grouped points, voxel ranges,
+// march field, plus the input cloud kept on the device for region updates.
+struct SceneObj : Obj {
+  SceneObj() : Obj(OBJ_SCENE) {}
+  DScene d{};
+  nimbus_vox_params params{};
+  double origin[3] = {0, 0, 0};
+  int dims[3] = {0, 0, 0};
+  int64_t n_ie = 0, n_slots = 0, n_points = 0;
+  // device copies of the input
+  float* xyz = nullptr;
+  float* nrm = nullptr;
+  uint32_t* label = nullptr;
+  uint8_t* material = nullptr;
+  std::vector<double> edges_h;
+  std::vector<uint32_t> edge_label_h;
+  uint32_t max_label = 0;
+  // derived tables (owned; freed and rebuilt by region updates)
+  std::vector<void*> table_bufs;
+};
+
+// Coarse paths after the kappa limit (Section 2.2.3), structure of arrays.
+struct CoarseObj : Obj {
+  CoarseObj() : Obj(OBJ_COARSE) {}
+  nimbus_handle scene = 0;
+  int n_tx = 0, n_rx = 0;
+  double* txd = nullptr;     // [n_tx*3] device
+  double* rxd = nullptr;     // [n_rx*3] device
+  int64_t n = 0;
+  uint32_t* tx = nullptr;
+  uint32_t* rx = nullptr;
+  uint32_t* nint = nullptr;
+  uint32_t* types = nullptr; // bit k set: interaction k is a diffraction
+  uint32_t* ie = nullptr;    // [n*NB_MAXI]
+  uint32_t* lab = nullptr;   // [n*NB_MAXI]
+  float* miss = nullptr;
+  uint32_t* gid = nullptr;   // group of (tx, rx, types, labels)
+  uint32_t n_groups_cap = 0;
+  nimbus_path_counts counts{};
+};
+
+// One refined path (Section 2.3).
+struct ExactRec {
+  double pts[NB_MAXI][3];
+  double length, delay, grad;
+  uint32_t tx, rx, n, types, status, iters, gid, pad;
+  uint32_t lab[NB_MAXI];
+  uint32_t ie[NB_MAXI];
+  uint8_t mat[NB_MAXI];
+};
+
+struct PathsObj : Obj {
+  PathsObj() : Obj(OBJ_PATHS) {}
+  int64_t n_all = 0, n_final = 0;
+  ExactRec* all = nullptr;       // one per refined coarse path
+  uint32_t* final_idx = nullptr; // indices into all, final order
+  nimbus_path_counts counts{};
+};
+
+int trace_coarse(Mem& mem, SceneObj* S, const double* tx, int n_tx, const double* rx, int n_rx,
+                 const nimbus_trace_params* p, CoarseObj* out, cudaStream_t st);
+int refine_paths(Mem& mem, SceneObj* S, CoarseObj* C, const nimbus_refine_params* p, PathsObj* out,
+                 cudaStream_t st);
+
+int voxelize_scene(Mem& mem, const nimbus_cloud* cloud, const nimbus_edges* edges, const nimbus_vox_params* p,
+                   SceneObj* out, cudaStream_t st);
+int update_scene_region(Mem& mem, SceneObj* s, const double lo[3], const double hi[3],
+                        const nimbus_cloud* repl, cudaStream_t st);
+
+bool is_device_ptr(const void* p);
+// Copy n bytes of a host or device input into a device buffer.
+int copy_in(std::string* err, void* dst, const void* src, size_t n, cudaStream_t st);
+
+inline int bits_for(uint64_t max_value) {
+  int b = 0;
+  while (b < 64 && (max_value >> b) != 0) ++b;
+  return b;
+}
+
+inline unsigned grid_for(int64_t n, int block) {
+  int64_t g = (n + block - 1) / block;
+  if (g < 1) g = 1;
+  return (unsigned)g;
+}
+
+}  // namespace nb

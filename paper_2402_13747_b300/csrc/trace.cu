@@ -1,0 +1,939 @@
+// Coarse path tracing (Section 2.2): transmission phase, propagation phase and
+// voxel cone tracing, followed by the kappa duplicate limit.
+//
+// B300 design.  Level-synchronous: one launch per interaction depth, each a
+// grid-stride loop over cone tasks (a reflection node is one task, a diffraction
+// node one task per Keller-fan ray), sized to the SM count and reading its task
+// count from device memory, so the whole level sequence runs without host round
+// trips.  Traversal and hit tests are FP32.  Children are appended to
+// structure-of-arrays node buffers of the next level with one atomic per child.
+// TX visibility of every IE is computed once per TX (the paper's transmission
+// phase casts a ray toward each IE) and reused by the uniform launch's cones.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "nimbus_host.hpp"
+
+namespace nb {
+
+namespace {
+
+constexpr double PI_D = 3.14159265358979323846;
+constexpr int MAX_LEVELS = NB_MAXI + 1;
+constexpr uint32_t NO_NODE = 0xFFFFFFFFu;
+
+enum { CONE_PRIMARY = 0, CONE_REFLECT = 1, CONE_DIFFRACT = 2 };
+enum { ST_CONES = 0, ST_VIS = 1, ST_BYTES = 2, ST_EVALS = 3, N_STATS = 4 };
+
+struct DTrace {
+  float sin_a, cos_a, sin_a0, cos_a0;
+  int M;
+  float dphi, sep_eps;
+  int max_refl, max_diff, max_int;
+  int n_launch, n_tx, n_rx;
+  double golden;
+  const float4* tx;          // xyz
+  const float4* rx;          // xyz
+  const uint8_t* march;      // scene march field with the RX voxels folded in
+  const uint32_t* rx_bits;   // one bit per voxel: it holds an RX
+  const uint64_t* rx_sorted; // (voxel << 32) | rx, ascending
+  int n_rx_sorted;
+  const uint32_t* vis_ie;    // [n_tx * ie_words] TX -> IE visibility bits
+  int ie_words;
+  const uint32_t* vis_rx;    // [n_tx * n_rx]
+  unsigned long long* stats;
+  uint32_t* overflow;        // [0] largest node slot requested, [1] coarse slot requested
+};
+
+// Nodes of one level, structure of arrays (reflection and diffraction apart).
+//   a: apex (reception point) xyz, IE index bits
+//   b: incoming direction xyz, parent index bits
+//   m: tx | nr << 16 | nd << 20 | depth << 24 | parent_is_diffraction << 28
+struct NodeLevel {
+  float4* ra;
+  float4* rb;
+  uint32_t* rm;
+  float4* da;
+  float4* db;
+  uint32_t* dm;
+  uint32_t* cnt;   // [0] reflection nodes, [1] diffraction nodes
+  uint32_t cap_r, cap_d;
+};
+
+struct CoarseBuf {
+  uint4* rec;      // tx, rx, node ref (index | diffraction << 31), depth
+  float* miss;
+  uint32_t* cnt;
+  uint32_t cap;
+};
+
+struct ConeD {
+  float3 apex, axis;
+  float sin_a, cos_a;
+  int kind;
+  float3 pn;               // reflection: oriented surface normal
+  float3 tlo, thi, rmid;   // diffraction: separation planes and mid direction
+  Endpoint origin;
+};
+
+// Separation planes (Section 2.2.4): reflections keep what lies more than sep_eps
+// in front of the tangent plane at the apex; a diffracted ray keeps what lies
+// between the planes half-way to its fan neighbours, on its own side of the edge.
+__device__ __forceinline__ bool planes_ok(const ConeD& c, float3 q, float sep_eps) {
+  float3 r = q - c.apex;
+  if (c.kind == CONE_REFLECT) return dot(r, c.pn) > sep_eps;
+  if (c.kind == CONE_DIFFRACT) return dot(r, c.tlo) >= 0.f && dot(r, c.thi) < 0.f && dot(r, c.rmid) > 0.f;
+  return true;
+}
+
+__device__ __forceinline__ int rx_lower_bound(const DTrace& tr, uint64_t key) {
+  int lo = 0, hi = tr.n_rx_sorted;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (tr.rx_sorted[mid] < key) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Voxel cone tracing of one cone (Section 2.2.4).  The axis is walked voxel by
+// voxel; where the march distance is at most 1 the neighbouring voxels not yet
+// evaluated for this cone are tested (voxel sphere, then each IE's subvoxel
+// sphere, the separation planes, then acc's acceptance test).  A voxel whose march
+// distance m >= 2 vouches for the (2(m-2)+1)^3 box around it, which the walk
+// crosses without reading the field.  The cone stops after the first evaluation
+// that accepted a point IE.
+template <class Acc>
+__device__ void march_cone(const DScene& s, const DTrace& tr, const ConeD& c, bool test_edges, bool want_all,
+                           Acc& acc, unsigned long long& bytes, uint32_t& evals) {
+  Walk w;
+  walk_init(s, c.apex, c.axis, w);
+  int last[3] = {0, 0, 0}, anchor[3] = {0, 0, 0};
+  bool have_last = false;
+  int rad = -1;
+  const int max_steps = s.nx + s.ny + s.nz + 3;
+  const float inf = __int_as_float(0x7f800000);
+  for (int step = 0; step < max_steps; ++step) {
+    bool in_box = rad >= 0 && abs(w.v[0] - anchor[0]) <= rad && abs(w.v[1] - anchor[1]) <= rad &&
+                  abs(w.v[2] - anchor[2]) <= rad;
+    if (!in_box) {
+      long long ci = cell_index(s, w.v[0], w.v[1], w.v[2]);
+      int m = tr.march[ci];
+      bytes += 1;
+      if (m > 1) {
+        anchor[0] = w.v[0]; anchor[1] = w.v[1]; anchor[2] = w.v[2];
+        rad = m - 2;
+      } else {
+        ++evals;
+        bool stop = false;
+        for (int dz = -1; dz <= 1; ++dz)
+          for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+              int u0 = w.v[0] + dx, u1 = w.v[1] + dy, u2 = w.v[2] + dz;
+              if (!in_grid(s, u0, u1, u2)) continue;
+              if (have_last && abs(u0 - last[0]) <= 1 && abs(u1 - last[1]) <= 1 && abs(u2 - last[2]) <= 1) continue;
+              long long cu = cell_index(s, u0, u1, u2);
+              uint2 cell = __ldg(&s.cells[cu]);
+              bool has_rx = (__ldg(&tr.rx_bits[cu >> 5]) >> (cu & 31)) & 1u;
+              bytes += 12;
+              if (cell.y == 0 && !has_rx) continue;
+              if (!cone_sphere(c.apex, c.axis, c.sin_a, c.cos_a, voxel_center(s, u0, u1, u2), s.r_vox)) continue;
+              for (uint32_t k = 0; k < cell.y; ++k) {
+                uint32_t id = cell.x + k;
+                const IERec* r = &s.ies[id];
+                float4 nm = __ldg(&r->nrm_meta);
+                float4 sc = __ldg(&r->sc_pc);
+                bytes += 32;
+                uint32_t kind = __float_as_uint(nm.w) & 1u;
+                if (kind == IE_EDGE && !test_edges) continue;
+                if (kind == IE_POINT && stop && !want_all) continue;
+                if (!cone_sphere(c.apex, c.axis, c.sin_a, c.cos_a, xyz(sc), s.r_sub)) continue;
+                float4 rp = __ldg(&r->rp_lab);
+                bytes += 16;
+                if (!planes_ok(c, xyz(rp), tr.sep_eps)) continue;
+                if (acc.ie(id, xyz(rp), kind, __float_as_uint(rp.w), bytes) && kind == IE_POINT) stop = true;
+              }
+              if (has_rx) {
+                for (int q = rx_lower_bound(tr, (uint64_t)cu << 32); q < tr.n_rx_sorted; ++q) {
+                  uint64_t e = tr.rx_sorted[q];
+                  bytes += 8;
+                  if ((long long)(e >> 32) != cu) break;
+                  int j = (int)(e & 0xffffffffu);
+                  float3 pos = xyz(__ldg(&tr.rx[j]));
+                  bytes += 16;
+                  if (!cone_sphere(c.apex, c.axis, c.sin_a, c.cos_a, pos, s.r_sub)) continue;
+                  if (!planes_ok(c, pos, tr.sep_eps)) continue;
+                  float3 v = pos - c.apex;
+                  float3 perp = v - dot(v, c.axis) * c.axis;
+                  acc.rx(j, pos, len(perp), bytes);
+                }
+              }
+            }
+        have_last = true;
+        last[0] = w.v[0]; last[1] = w.v[1]; last[2] = w.v[2];
+        if (stop) break;
+      }
+    }
+    if (!walk_next(s, w, inf)) break;
+  }
+}
+
+// Transmission-phase acceptance: TX -> IE and TX -> RX visibility from the tables.
+struct PrimaryAcc {
+  const DTrace* tr;
+  int t;
+  uint32_t* first_bits;
+  uint32_t* los;
+  __device__ bool ie(uint32_t id, float3, uint32_t, uint32_t, unsigned long long& bytes) {
+    size_t wi = (size_t)t * tr->ie_words + (id >> 5);
+    uint32_t bit = 1u << (id & 31);
+    bytes += 4;
+    if (!(__ldg(&tr->vis_ie[wi]) & bit)) return false;
+    if (!(first_bits[wi] & bit)) atomicOr(&first_bits[wi], bit);
+    return true;
+  }
+  __device__ void rx(int j, float3, float miss, unsigned long long& bytes) {
+    bytes += 4;
+    if (__ldg(&tr->vis_rx[(size_t)t * tr->n_rx + j])) atomicMin(&los[(size_t)t * tr->n_rx + j], __float_as_uint(miss));
+  }
+};
+
+__device__ __forceinline__ void add_stats(const DTrace& tr, uint32_t cones, uint32_t vis, unsigned long long bytes,
+                                          uint32_t evals) {
+  // warp-aggregated counters
+  unsigned long long c = cones, v = vis, b = bytes, e = evals;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    c += __shfl_xor_sync(0xffffffffu, c, o);
+    v += __shfl_xor_sync(0xffffffffu, v, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+    e += __shfl_xor_sync(0xffffffffu, e, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&tr.stats[ST_CONES], c);
+    atomicAdd(&tr.stats[ST_VIS], v);
+    atomicAdd(&tr.stats[ST_BYTES], b);
+    atomicAdd(&tr.stats[ST_EVALS], e);
+  }
+}
+
+// TX -> IE and TX -> RX visibility (the transmission phase's ray toward each IE).
+__global__ void k_vis_tables(DScene s, DTrace tr) {
+  const int64_t n_ie = s.n_ie;
+  const int64_t per_tx = n_ie + tr.n_rx;
+  const int64_t total = per_tx * tr.n_tx;
+  unsigned long long bytes = 0;
+  uint32_t vis = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    int t = (int)(i / per_tx);
+    int64_t k = i % per_tx;
+    float3 T = xyz(tr.tx[t]);
+    Endpoint none{IGN_NONE, NB_NONE_LABEL};
+    ++vis;
+    if (k < n_ie) {
+      float4 rp = __ldg(&s.ies[k].rp_lab);
+      uint32_t kind = __float_as_uint(__ldg(&s.ies[k].nrm_meta).w) & 1u;
+      Endpoint eb{kind == IE_EDGE ? IGN_ANY : IGN_LABEL, __float_as_uint(rp.w)};
+      if (visible(s, T, xyz(rp), none, eb, bytes))
+        atomicOr(const_cast<uint32_t*>(&tr.vis_ie[(size_t)t * tr.ie_words + (k >> 5)]), 1u << (k & 31));
+    } else {
+      int j = (int)(k - n_ie);
+      const_cast<uint32_t*>(tr.vis_rx)[(size_t)t * tr.n_rx + j] =
+          visible(s, T, xyz(tr.rx[j]), none, none, bytes) ? 1u : 0u;
+    }
+  }
+  add_stats(tr, 0, vis, bytes, 0);
+}
+
+// Uniform launch (transmission phase): Fibonacci-lattice cones from every TX.
+__global__ void k_primary(DScene s, DTrace tr, uint32_t* first_bits, uint32_t* los) {
+  const int64_t total = (int64_t)tr.n_tx * tr.n_launch;
+  unsigned long long bytes = 0;
+  uint32_t cones = 0, evals = 0;
+  const bool test_edges = tr.max_int >= 1 && tr.max_diff >= 1;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    int t = (int)(i / tr.n_launch);
+    int64_t q = i % tr.n_launch;
+    double z = 1.0 - (2.0 * (double)q + 1.0) / (double)tr.n_launch;
+    double r = sqrt(fmax(0.0, 1.0 - z * z));
+    double phi = fmod((double)q * tr.golden, 2.0 * PI_D);
+    double sp, cp;
+    sincos(phi, &sp, &cp);
+    ConeD c;
+    c.apex = xyz(tr.tx[t]);
+    c.axis = f3((float)(r * cp), (float)(r * sp), (float)z);
+    c.sin_a = tr.sin_a0;
+    c.cos_a = tr.cos_a0;
+    c.kind = CONE_PRIMARY;
+    c.origin = Endpoint{IGN_NONE, NB_NONE_LABEL};
+    PrimaryAcc acc{&tr, t, first_bits, los};
+    ++cones;
+    march_cone(s, tr, c, test_edges, true, acc, bytes, evals);
+  }
+  add_stats(tr, cones, 0, bytes, evals);
+}
+
+// Depth-1 nodes: one per (TX, IE) accepted by any primary cone (a set), in IE order.
+__global__ void k_first_flags(DScene s, DTrace tr, const uint32_t* first_bits, uint32_t* fr, uint32_t* fd) {
+  const int64_t total = (int64_t)tr.n_tx * s.n_ie;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    int t = (int)(i / s.n_ie);
+    int64_t k = i % s.n_ie;
+    bool hit = (first_bits[(size_t)t * tr.ie_words + (k >> 5)] >> (k & 31)) & 1u;
+    uint32_t kind = __float_as_uint(s.ies[k].nrm_meta.w) & 1u;
+    bool ok = hit && tr.max_int >= 1 && (kind == IE_POINT ? tr.max_refl >= 1 : tr.max_diff >= 1);
+    fr[i] = ok && kind == IE_POINT;
+    fd[i] = ok && kind == IE_EDGE;
+  }
+}
+
+__global__ void k_first_nodes(DScene s, DTrace tr, const uint32_t* fr, const uint32_t* pr, const uint32_t* fd,
+                              const uint32_t* pd, NodeLevel L) {
+  const int64_t total = (int64_t)tr.n_tx * s.n_ie;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    if (!fr[i] && !fd[i]) continue;
+    int t = (int)(i / s.n_ie);
+    uint32_t k = (uint32_t)(i % s.n_ie);
+    float3 T = xyz(tr.tx[t]);
+    float3 rp = xyz(s.ies[k].rp_lab);
+    float3 e = normalize(rp - T);
+    bool refl = fr[i] != 0;
+    uint32_t slot = refl ? pr[i] : pd[i];
+    uint32_t cap = refl ? L.cap_r : L.cap_d;
+    if (slot >= cap) {
+      atomicMax(&tr.overflow[0], slot + 1);
+      continue;
+    }
+    uint32_t meta = (uint32_t)t | ((refl ? 1u : 0u) << 16) | ((refl ? 0u : 1u) << 20) | (1u << 24);
+    float4 a = make_float4(rp.x, rp.y, rp.z, __uint_as_float(k));
+    float4 b = make_float4(e.x, e.y, e.z, __uint_as_float(NO_NODE));
+    if (refl) {
+      L.ra[slot] = a; L.rb[slot] = b; L.rm[slot] = meta;
+    } else {
+      L.da[slot] = a; L.db[slot] = b; L.dm[slot] = meta;
+    }
+  }
+}
+
+__global__ void k_first_counts(const uint32_t* tot_r, const uint32_t* tot_d, NodeLevel L) {
+  L.cnt[0] = min(*tot_r, L.cap_r);
+  L.cnt[1] = min(*tot_d, L.cap_d);
+}
+
+__device__ __forceinline__ void emit_coarse(const DTrace& tr, CoarseBuf& cb, uint32_t t, uint32_t j, uint32_t node,
+                                            uint32_t depth, float miss) {
+  uint32_t slot = atomicAdd(cb.cnt, 1u);
+  if (slot >= cb.cap) {
+    atomicMax(&tr.overflow[1], slot + 1);
+    return;
+  }
+  cb.rec[slot] = make_uint4(t, j, node, depth);
+  cb.miss[slot] = miss;
+}
+
+// LOS coarse paths: RXs reached by a primary cone.
+__global__ void k_los(DTrace tr, const uint32_t* los, CoarseBuf cb) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= tr.n_tx * tr.n_rx) return;
+  uint32_t m = los[i];
+  if (m != 0xFFFFFFFFu) emit_coarse(tr, cb, i / tr.n_rx, i % tr.n_rx, NO_NODE, 0, __uint_as_float(m));
+}
+
+// Propagation acceptance: visibility ray from the apex; children and RX hits.
+struct LevelAcc {
+  const DScene* s;
+  const DTrace* tr;
+  const ConeD* c;
+  NodeLevel next;
+  CoarseBuf cb;
+  uint32_t tx, nr, nd, depth, self_ref;
+  bool can_child;
+  uint32_t vis;
+  __device__ bool ie(uint32_t id, float3 rp, uint32_t kind, uint32_t label, unsigned long long& bytes) {
+    Endpoint eb{kind == IE_EDGE ? IGN_ANY : IGN_LABEL, label};
+    ++vis;
+    if (!visible(*s, c->apex, rp, c->origin, eb, bytes)) return false;
+    if (can_child) {
+      uint32_t cnr = nr + (kind == IE_POINT), cnd = nd + (kind == IE_EDGE);
+      if ((int)cnr <= tr->max_refl && (int)cnd <= tr->max_diff) {
+        bool refl = kind == IE_POINT;
+        uint32_t slot = atomicAdd(&next.cnt[refl ? 0 : 1], 1u);
+        uint32_t cap = refl ? next.cap_r : next.cap_d;
+        if (slot >= cap) {
+          atomicMax(&tr->overflow[0], slot + 1);
+        } else {
+          float3 e = normalize(rp - c->apex);
+          uint32_t meta = tx | (cnr << 16) | (cnd << 20) | ((depth + 1) << 24) | ((self_ref >> 31) << 28);
+          float4 a = make_float4(rp.x, rp.y, rp.z, __uint_as_float(id));
+          float4 b = make_float4(e.x, e.y, e.z, __uint_as_float(self_ref & 0x7fffffffu));
+          if (refl) {
+            next.ra[slot] = a; next.rb[slot] = b; next.rm[slot] = meta;
+          } else {
+            next.da[slot] = a; next.db[slot] = b; next.dm[slot] = meta;
+          }
+        }
+      }
+    }
+    return true;
+  }
+  __device__ void rx(int j, float3 pos, float miss, unsigned long long& bytes) {
+    ++vis;
+    if (visible(*s, c->apex, pos, c->origin, Endpoint{IGN_NONE, NB_NONE_LABEL}, bytes))
+      emit_coarse(*tr, cb, tx, (uint32_t)j, self_ref, depth, miss);
+  }
+};
+
+// One propagation level: reflected cones and Keller-fan cones of every node.
+__global__ void k_level(DScene s, DTrace tr, NodeLevel cur, NodeLevel next, CoarseBuf cb) {
+  const uint32_t n_r = min(cur.cnt[0], cur.cap_r), n_d = min(cur.cnt[1], cur.cap_d);
+  const int64_t total = (int64_t)n_r + (int64_t)n_d * tr.M;
+  unsigned long long bytes = 0;
+  uint32_t cones = 0, vis = 0, evals = 0;
+  for (int64_t task = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; task < total;
+       task += (int64_t)gridDim.x * blockDim.x) {
+    bool refl = task < n_r;
+    uint32_t idx = refl ? (uint32_t)task : (uint32_t)((task - n_r) / tr.M);
+    int j = refl ? 0 : (int)((task - n_r) % tr.M);
+    float4 a = refl ? cur.ra[idx] : cur.da[idx];
+    float4 b = refl ? cur.rb[idx] : cur.db[idx];
+    uint32_t meta = refl ? cur.rm[idx] : cur.dm[idx];
+    uint32_t ie = __float_as_uint(a.w);
+    const IERec* r = &s.ies[ie];
+    float4 nm = __ldg(&r->nrm_meta);
+    uint32_t label = __float_as_uint(__ldg(&r->rp_lab).w);
+    bytes += 32 + 36;
+    float3 e = xyz(b);
+    ConeD c;
+    c.apex = xyz(a);
+    c.sin_a = tr.sin_a;
+    c.cos_a = tr.cos_a;
+    if (refl) {
+      float3 n = xyz(nm);
+      if (dot(n, e) > 0.f) n = -1.f * n;
+      c.kind = CONE_REFLECT;
+      c.axis = normalize(e - (2.f * dot(e, n)) * n);
+      c.pn = n;
+      c.origin = Endpoint{IGN_LABEL, label};
+    } else {
+      const double* E = s.edges + 12 * __float_as_uint(__ldg(&r->bbc_pb).w);
+      bytes += 96;
+      float3 w = normalize(f3((float)(E[3] - E[0]), (float)(E[4] - E[1]), (float)(E[5] - E[2])));
+      float cb_ = dot(e, w);
+      float sb2 = 1.f - cb_ * cb_;
+      if (sb2 < 1e-12f) continue;
+      float sb = sqrtf(sb2);
+      float3 ua, va;
+      onb(w, &ua, &va);
+      float phi = (float)j * tr.dphi;
+      float sp, cp;
+      sincosf(phi, &sp, &cp);
+      float3 rr = cp * ua + sp * va;
+      float3 d = cb_ * w + sb * rr;
+      float3 n0 = f3((float)E[6], (float)E[7], (float)E[8]), n1 = f3((float)E[9], (float)E[10], (float)E[11]);
+      if (!(dot(d, n0) > 0.f || dot(d, n1) > 0.f)) continue;
+      float slo, clo, shi, chi;
+      sincosf(phi - 0.5f * tr.dphi, &slo, &clo);
+      sincosf(phi + 0.5f * tr.dphi, &shi, &chi);
+      c.kind = CONE_DIFFRACT;
+      c.axis = normalize(d);
+      c.tlo = (-slo) * ua + clo * va;
+      c.thi = (-shi) * ua + chi * va;
+      c.rmid = rr;
+      c.origin = Endpoint{IGN_ANY, label};
+    }
+    uint32_t depth = (meta >> 24) & 0xfu, nr = (meta >> 16) & 0xfu, nd = (meta >> 20) & 0xfu;
+    LevelAcc acc;
+    acc.s = &s;
+    acc.tr = &tr;
+    acc.c = &c;
+    acc.next = next;
+    acc.cb = cb;
+    acc.tx = meta & 0xffffu;
+    acc.nr = nr;
+    acc.nd = nd;
+    acc.depth = depth;
+    acc.self_ref = idx | (refl ? 0u : 0x80000000u);
+    acc.can_child = (int)depth < tr.max_int;
+    acc.vis = 0;
+    bool test_edges = acc.can_child && (int)nd < tr.max_diff;
+    ++cones;
+    march_cone(s, tr, c, test_edges, acc.can_child, acc, bytes, evals);
+    vis += acc.vis;
+  }
+  add_stats(tr, cones, vis, bytes, evals);
+}
+
+// March field of one trace call: the scene's field capped at R+1, lowered to the
+// exact L-inf distance around each RX voxel out to radius R.  Exact wherever the
+// true distance is <= 1 (so the voxels evaluated are unchanged), a lower bound
+// elsewhere (so skipping stays safe).
+__global__ void k_march_cap(const uint8_t* in, uint32_t* out, int64_t n, uint32_t cap) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = min((uint32_t)in[i], cap);
+}
+
+__global__ void k_march_rx(DScene s, const int4* rx_vox, int n_rx, uint32_t* m, int R) {
+  int side = 2 * R + 1;
+  int64_t per = (int64_t)side * side * side;
+  int64_t total = per * n_rx;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    int j = (int)(i / per);
+    int64_t q = i % per;
+    int dx = (int)(q % side) - R, dy = (int)((q / side) % side) - R, dz = (int)(q / ((int64_t)side * side)) - R;
+    int4 v = rx_vox[j];
+    int x = v.x + dx, y = v.y + dy, z = v.z + dz;
+    if (!in_grid(s, x, y, z)) continue;
+    uint32_t d = (uint32_t)max(abs(dx), max(abs(dy), abs(dz)));
+    atomicMin(&m[cell_index(s, x, y, z)], d);
+  }
+}
+
+__global__ void k_march_pack(const uint32_t* in, uint8_t* out, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (uint8_t)min(in[i], 255u);
+}
+
+__global__ void k_rx_setup(DScene s, const double* rxd, int n_rx, float4* rx, int4* rx_vox, uint64_t* rx_keys,
+                           uint32_t* rx_bits) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n_rx) return;
+  float p[3] = {(float)rxd[3 * j], (float)rxd[3 * j + 1], (float)rxd[3 * j + 2]};
+  const float o[3] = {s.ox, s.oy, s.oz};
+  const int dims[3] = {s.nx, s.ny, s.nz};
+  int gs[3];
+  for (int a = 0; a < 3; ++a) gs[a] = subvoxel_axis(p[a], o[a], s.hs, dims[a] * s.dv - 1);
+  int vx = gs[0] / s.dv, vy = gs[1] / s.dv, vz = gs[2] / s.dv;
+  long long c = cell_index(s, vx, vy, vz);
+  rx[j] = make_float4(p[0], p[1], p[2], 0.f);
+  rx_vox[j] = make_int4(vx, vy, vz, 0);
+  rx_keys[j] = ((uint64_t)c << 32) | (uint64_t)j;
+  atomicOr(&rx_bits[c >> 5], 1u << (c & 31));
+}
+
+__global__ void k_tx_setup(const double* txd, int n_tx, float4* tx) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n_tx) return;
+  tx[j] = make_float4((float)txd[3 * j], (float)txd[3 * j + 1], (float)txd[3 * j + 2], 0.f);
+}
+
+// ------------------------------------------------------------------ kappa duplicate limit
+struct LevelsView {
+  const float4* ra[MAX_LEVELS];
+  const float4* rb[MAX_LEVELS];
+  const uint32_t* rm[MAX_LEVELS];
+  const float4* da[MAX_LEVELS];
+  const float4* db[MAX_LEVELS];
+  const uint32_t* dm[MAX_LEVELS];
+};
+
+// Walk a coarse path's parents: IE, type and label per interaction.
+__global__ void k_expand(DScene s, LevelsView L, const uint4* rec, const float* miss, int64_t n, uint32_t* o_tx,
+                         uint32_t* o_rx, uint32_t* o_n, uint32_t* o_types, uint32_t* o_ie, uint32_t* o_lab,
+                         float* o_miss, uint32_t* o_hash) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    uint4 r = rec[i];
+    uint32_t depth = r.w, ref = r.z, types = 0;
+    uint32_t h = 2166136261u;
+    for (int q = NB_MAXI - 1; q >= 0; --q) {
+      o_ie[i * NB_MAXI + q] = NO_NODE;
+      o_lab[i * NB_MAXI + q] = NB_NONE_LABEL;
+    }
+    for (int q = (int)depth; q >= 1; --q) {
+      bool diff = (ref >> 31) != 0;
+      uint32_t idx = ref & 0x7fffffffu;
+      float4 a = diff ? L.da[q][idx] : L.ra[q][idx];
+      float4 b = diff ? L.db[q][idx] : L.rb[q][idx];
+      uint32_t m = diff ? L.dm[q][idx] : L.rm[q][idx];
+      uint32_t ie = __float_as_uint(a.w);
+      o_ie[i * NB_MAXI + q - 1] = ie;
+      o_lab[i * NB_MAXI + q - 1] = __float_as_uint(s.ies[ie].rp_lab.w);
+      if (diff) types |= 1u << (q - 1);
+      ref = __float_as_uint(b.w) | (((m >> 28) & 1u) << 31);
+    }
+    for (int q = 0; q < (int)depth; ++q) {
+      h ^= o_ie[i * NB_MAXI + q];
+      h *= 16777619u;
+    }
+    o_tx[i] = r.x;
+    o_rx[i] = r.y;
+    o_n[i] = depth;
+    o_types[i] = types;
+    o_miss[i] = miss[i];
+    o_hash[i] = h;
+  }
+}
+
+__device__ __forceinline__ uint32_t mix32(uint32_t h, uint32_t v) {
+  h ^= v + 0x9e3779b9u + (h << 6) + (h >> 2);
+  return h;
+}
+
+// Group id of (tx, rx, interaction types, labels): open addressing with exact key
+// comparison, so distinct label sequences never share a group.
+__global__ void k_group(const uint32_t* tx, const uint32_t* rx, const uint32_t* nint, const uint32_t* types,
+                        const uint32_t* lab, int64_t n, uint32_t* owner, uint32_t cap_mask, uint32_t* gid) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t h = mix32(mix32(mix32(mix32(0x1234567u, tx[i]), rx[i]), nint[i]), types[i]);
+    for (uint32_t q = 0; q < nint[i]; ++q) h = mix32(h, lab[i * NB_MAXI + q]);
+    h ^= h >> 16;
+    h *= 0x85ebca6bu;
+    h ^= h >> 13;
+    uint32_t slot = h & cap_mask;
+    for (uint32_t probe = 0; probe <= cap_mask; ++probe) {
+      uint32_t prev = atomicCAS(&owner[slot], NO_NODE, (uint32_t)i);
+      if (prev == NO_NODE) {
+        gid[i] = slot;
+        break;
+      }
+      bool same = tx[prev] == tx[i] && rx[prev] == rx[i] && nint[prev] == nint[i] && types[prev] == types[i];
+      for (uint32_t q = 0; same && q < nint[i]; ++q) same = lab[prev * NB_MAXI + q] == lab[i * NB_MAXI + q];
+      if (same) {
+        gid[i] = slot;
+        break;
+      }
+      slot = (slot + 1) & cap_mask;
+    }
+  }
+}
+
+// Sort key: group, then distance of the RX from the cone axis (kappa selection
+// reading), then a hash of the IE sequence for ties.
+__global__ void k_kappa_keys(const uint32_t* gid, const float* miss, const uint32_t* hash, int64_t n, uint64_t* keys,
+                             uint32_t* vals) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t mb = __float_as_uint(fmaxf(miss[i], 0.f)) & 0x7fffffffu;
+    keys[i] = ((uint64_t)gid[i] << 39) | ((uint64_t)mb << 8) | (uint64_t)(hash[i] & 0xffu);
+    vals[i] = (uint32_t)i;
+  }
+}
+
+__global__ void k_kappa_keep(const uint64_t* keys, int64_t n, int kappa, uint32_t* keep) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t g = keys[i] >> 39;
+    int64_t lo = 0, hi = i;
+    while (lo < hi) {  // first position of this group
+      int64_t mid = (lo + hi) >> 1;
+      if ((keys[mid] >> 39) < g) lo = mid + 1;
+      else hi = mid;
+    }
+    keep[i] = (i - lo) < kappa ? 1u : 0u;
+  }
+}
+
+__global__ void k_kappa_compact(const uint32_t* keep, const uint32_t* pos, const uint32_t* order, int64_t n,
+                                const uint32_t* tx, const uint32_t* rx, const uint32_t* nint, const uint32_t* types,
+                                const uint32_t* ie, const uint32_t* lab, const float* miss, const uint32_t* gid,
+                                CoarseObj out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    if (!keep[i]) continue;
+    uint32_t src = order[i];
+    uint32_t d = pos[i];
+    out.tx[d] = tx[src];
+    out.rx[d] = rx[src];
+    out.nint[d] = nint[src];
+    out.types[d] = types[src];
+    out.miss[d] = miss[src];
+    out.gid[d] = gid[src];
+    for (int q = 0; q < NB_MAXI; ++q) {
+      out.ie[(size_t)d * NB_MAXI + q] = ie[(size_t)src * NB_MAXI + q];
+      out.lab[(size_t)d * NB_MAXI + q] = lab[(size_t)src * NB_MAXI + q];
+    }
+  }
+}
+
+unsigned persistent_grid(int block) {
+  static int sms = 0;
+  if (!sms) sms = num_sms();
+  return (unsigned)(sms * (2048 / block));
+}
+
+}  // namespace
+
+int trace_coarse(Mem& mem, SceneObj* S, const double* txh, int n_tx, const double* rxh, int n_rx,
+                 const nimbus_trace_params* p, CoarseObj* C, cudaStream_t st) {
+  std::string* err = mem.err;
+  if (n_tx < 1 || n_rx < 0 || !txh || (n_rx > 0 && !rxh) || n_tx > 65535) {
+    *err = "trace: invalid TX/RX arrays";
+    return NIMBUS_ERR_ARG;
+  }
+  if (p->max_refl < 0 || p->max_diff < 0 || p->kappa < 1 || !(p->cone_half_angle > 0) ||
+      !(p->cone_half_angle < 1.5) || !(p->launch_spacing > 0)) {
+    *err = "trace: invalid parameters";
+    return NIMBUS_ERR_ARG;
+  }
+  const int max_int = p->max_int >= 0 ? p->max_int : p->max_refl + p->max_diff;
+  if (max_int > NB_MAXI || p->max_refl > 15 || p->max_diff > 15) {
+    *err = "trace: too many interactions";
+    return NIMBUS_ERR_ARG;
+  }
+  const DScene& s = S->d;
+  C->mem = &mem;
+  C->n_tx = n_tx;
+  C->n_rx = n_rx;
+  // TX/RX on the host for the grid check, on the device for the kernels
+  std::vector<double> th(3 * n_tx), rh(3 * (size_t)n_rx);
+  NB_CUDA(err, cudaMemcpy(th.data(), txh, th.size() * sizeof(double), cudaMemcpyDefault));
+  if (n_rx) NB_CUDA(err, cudaMemcpy(rh.data(), rxh, rh.size() * sizeof(double), cudaMemcpyDefault));
+  for (int i = 0; i < n_tx + n_rx; ++i) {
+    const double* q = i < n_tx ? &th[3 * i] : &rh[3 * (i - n_tx)];
+    for (int a = 0; a < 3; ++a) {
+      double rel = (q[a] - S->origin[a]) / S->params.voxel_size;
+      if (!(rel >= 0.0 && rel < (double)S->dims[a])) {
+        *err = "trace: a TX or RX lies outside the voxel grid";
+        return NIMBUS_ERR_ARG;
+      }
+    }
+  }
+  NB_TRY(C->own(&C->txd, 3 * n_tx, st));
+  NB_TRY(C->own(&C->rxd, std::max(1, 3 * n_rx), st));
+  NB_CUDA(err, cudaMemcpyAsync(C->txd, th.data(), th.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+  if (n_rx) NB_CUDA(err, cudaMemcpyAsync(C->rxd, rh.data(), rh.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+
+  Scratch sc(&mem, st);
+  const int64_t n_cells = s.n_cells;
+  const int64_t n_ie = s.n_ie;
+  DTrace tr;
+  std::memset(&tr, 0, sizeof tr);
+  const double alpha = p->cone_half_angle;
+  const double alpha0 = std::max(alpha, p->launch_spacing / std::sqrt(2.0));
+  tr.sin_a = (float)std::sin(alpha);
+  tr.cos_a = (float)std::cos(alpha);
+  tr.sin_a0 = (float)std::sin(alpha0);
+  tr.cos_a0 = (float)std::cos(alpha0);
+  tr.M = (int)std::ceil(PI_D / alpha);
+  tr.dphi = (float)(2.0 * PI_D / tr.M);
+  tr.sep_eps = (float)p->sep_eps;
+  tr.max_refl = p->max_refl;
+  tr.max_diff = p->max_diff;
+  tr.max_int = max_int;
+  tr.n_launch = p->n_launch > 0 ? p->n_launch
+                                : (int)std::llround(4.0 * PI_D / (p->launch_spacing * p->launch_spacing));
+  tr.n_tx = n_tx;
+  tr.n_rx = n_rx;
+  tr.golden = PI_D * (3.0 - std::sqrt(5.0));
+  tr.ie_words = (int)((n_ie + 31) / 32);
+  float4 *tx4, *rx4;
+  int4* rx_vox;
+  uint64_t *rx_keys, *rx_keys_alt;
+  uint32_t *rx_vals, *rx_vals_alt, *rx_bits, *mtmp, *vis_ie, *vis_rx, *first_bits, *los, *overflow;
+  uint8_t* march;
+  unsigned long long* stats;
+  NB_TRY(sc.get(&tx4, n_tx));
+  NB_TRY(sc.get(&rx4, std::max(1, n_rx)));
+  NB_TRY(sc.get(&rx_vox, std::max(1, n_rx)));
+  NB_TRY(sc.get(&rx_keys, std::max(1, n_rx)));
+  NB_TRY(sc.get(&rx_keys_alt, std::max(1, n_rx)));
+  NB_TRY(sc.get(&rx_vals, std::max(1, n_rx)));
+  NB_TRY(sc.get(&rx_vals_alt, std::max(1, n_rx)));
+  NB_TRY(sc.get(&rx_bits, (n_cells + 31) / 32));
+  NB_TRY(sc.get(&mtmp, n_cells));
+  NB_TRY(sc.get(&march, n_cells));
+  NB_TRY(sc.get(&vis_ie, std::max<int64_t>(1, (int64_t)n_tx * tr.ie_words)));
+  NB_TRY(sc.get(&vis_rx, std::max<int64_t>(1, (int64_t)n_tx * n_rx)));
+  NB_TRY(sc.get(&first_bits, std::max<int64_t>(1, (int64_t)n_tx * tr.ie_words)));
+  NB_TRY(sc.get(&los, std::max<int64_t>(1, (int64_t)n_tx * n_rx)));
+  NB_TRY(sc.get(&overflow, 2));
+  NB_TRY(sc.get(&stats, N_STATS));
+  NB_CUDA(err, cudaMemsetAsync(rx_bits, 0, ((n_cells + 31) / 32) * sizeof(uint32_t), st));
+  NB_CUDA(err, cudaMemsetAsync(vis_ie, 0, std::max<int64_t>(1, (int64_t)n_tx * tr.ie_words) * 4, st));
+  NB_CUDA(err, cudaMemsetAsync(first_bits, 0, std::max<int64_t>(1, (int64_t)n_tx * tr.ie_words) * 4, st));
+  NB_CUDA(err, cudaMemsetAsync(los, 0xff, std::max<int64_t>(1, (int64_t)n_tx * n_rx) * 4, st));
+  NB_CUDA(err, cudaMemsetAsync(overflow, 0, 2 * sizeof(uint32_t), st));
+  NB_CUDA(err, cudaMemsetAsync(stats, 0, N_STATS * sizeof(unsigned long long), st));
+  k_tx_setup<<<grid_for(n_tx, 64), 64, 0, st>>>(C->txd, n_tx, tx4);
+  NB_CUDA(err, cudaGetLastError());
+  if (n_rx > 0) {
+    k_rx_setup<<<grid_for(n_rx, 64), 64, 0, st>>>(s, C->rxd, n_rx, rx4, rx_vox, rx_keys, rx_bits);
+    NB_CUDA(err, cudaGetLastError());
+    NB_CUDA(err, cudaMemsetAsync(rx_vals, 0, n_rx * sizeof(uint32_t), st));
+    NB_TRY(radix_sort(sc, rx_keys, rx_vals, rx_keys_alt, rx_vals_alt, n_rx, 64));
+  }
+  const int R = 8;
+  k_march_cap<<<std::min<unsigned>(grid_for(n_cells, 256), 2048u), 256, 0, st>>>(s.march, mtmp, n_cells, R + 1);
+  NB_CUDA(err, cudaGetLastError());
+  if (n_rx > 0) {
+    int64_t work = (int64_t)(2 * R + 1) * (2 * R + 1) * (2 * R + 1) * n_rx;
+    k_march_rx<<<std::min<unsigned>(grid_for(work, 256), 4096u), 256, 0, st>>>(s, rx_vox, n_rx, mtmp, R);
+    NB_CUDA(err, cudaGetLastError());
+  }
+  k_march_pack<<<std::min<unsigned>(grid_for(n_cells, 256), 2048u), 256, 0, st>>>(mtmp, march, n_cells);
+  NB_CUDA(err, cudaGetLastError());
+  tr.tx = tx4;
+  tr.rx = rx4;
+  tr.march = march;
+  tr.rx_bits = rx_bits;
+  tr.rx_sorted = rx_keys;
+  tr.n_rx_sorted = n_rx;
+  tr.vis_ie = vis_ie;
+  tr.vis_rx = vis_rx;
+  tr.stats = stats;
+  tr.overflow = overflow;
+
+  // bounded buffers: nodes per level and coarse paths
+  const int64_t cap_nodes = p->max_nodes > 0 ? p->max_nodes : (int64_t)8 << 20;
+  const int64_t cap_coarse = p->max_coarse > 0 ? p->max_coarse : (int64_t)8 << 20;
+  if (cap_nodes >= (1ll << 31) || cap_coarse >= (1ll << 31)) {
+    *err = "trace: buffer bounds too large";
+    return NIMBUS_ERR_ARG;
+  }
+  NodeLevel lv[MAX_LEVELS];
+  std::memset(lv, 0, sizeof lv);
+  uint32_t* cnts;
+  NB_TRY(sc.get(&cnts, 2 * MAX_LEVELS));
+  NB_CUDA(err, cudaMemsetAsync(cnts, 0, 2 * MAX_LEVELS * sizeof(uint32_t), st));
+  for (int d = 1; d <= max_int; ++d) {
+    NodeLevel& L = lv[d];
+    L.cap_r = (uint32_t)cap_nodes;
+    L.cap_d = (uint32_t)std::max<int64_t>(1024, cap_nodes / 8);
+    if (p->max_diff == 0) L.cap_d = 1;
+    if (p->max_refl == 0) L.cap_r = 1;
+    NB_TRY(sc.get(&L.ra, L.cap_r));
+    NB_TRY(sc.get(&L.rb, L.cap_r));
+    NB_TRY(sc.get(&L.rm, L.cap_r));
+    NB_TRY(sc.get(&L.da, L.cap_d));
+    NB_TRY(sc.get(&L.db, L.cap_d));
+    NB_TRY(sc.get(&L.dm, L.cap_d));
+    L.cnt = cnts + 2 * d;
+  }
+  CoarseBuf cb;
+  cb.cap = (uint32_t)cap_coarse;
+  NB_TRY(sc.get(&cb.rec, cb.cap));
+  NB_TRY(sc.get(&cb.miss, cb.cap));
+  cb.cnt = cnts;  // slot 0 of level 0 counts the coarse paths
+  // transmission phase
+  const unsigned PG = persistent_grid(256);
+  k_vis_tables<<<PG, 256, 0, st>>>(s, tr);
+  NB_CUDA(err, cudaGetLastError());
+  k_primary<<<PG, 256, 0, st>>>(s, tr, first_bits, los);
+  NB_CUDA(err, cudaGetLastError());
+  k_los<<<grid_for((int64_t)n_tx * n_rx, 128), 128, 0, st>>>(tr, los, cb);
+  NB_CUDA(err, cudaGetLastError());
+  if (max_int >= 1) {
+    int64_t nflag = (int64_t)n_tx * n_ie;
+    uint32_t *fr, *fd, *pr, *pd, *tot;
+    NB_TRY(sc.get(&fr, std::max<int64_t>(1, nflag)));
+    NB_TRY(sc.get(&fd, std::max<int64_t>(1, nflag)));
+    NB_TRY(sc.get(&pr, std::max<int64_t>(1, nflag)));
+    NB_TRY(sc.get(&pd, std::max<int64_t>(1, nflag)));
+    NB_TRY(sc.get(&tot, 2));
+    if (nflag > 0) {
+      k_first_flags<<<PG, 256, 0, st>>>(s, tr, first_bits, fr, fd);
+      NB_CUDA(err, cudaGetLastError());
+    }
+    NB_TRY(exclusive_scan(sc, fr, pr, nflag, tot));
+    NB_TRY(exclusive_scan(sc, fd, pd, nflag, tot + 1));
+    if (nflag > 0) {
+      k_first_nodes<<<PG, 256, 0, st>>>(s, tr, fr, pr, fd, pd, lv[1]);
+      NB_CUDA(err, cudaGetLastError());
+    }
+    k_first_counts<<<1, 1, 0, st>>>(tot, tot + 1, lv[1]);
+    NB_CUDA(err, cudaGetLastError());
+  }
+  // propagation phase, one launch per depth
+  for (int d = 1; d <= max_int; ++d) {
+    NodeLevel next = d < max_int ? lv[d + 1] : lv[0];
+    if (d == max_int) {
+      next.cap_r = 0;
+      next.cap_d = 0;
+      next.cnt = cnts + 2 * MAX_LEVELS - 2;  // unused sink
+    }
+    k_level<<<PG, 256, 0, st>>>(s, tr, lv[d], next, cb);
+    NB_CUDA(err, cudaGetLastError());
+  }
+  // read the sizes back
+  uint32_t hc[2 * MAX_LEVELS], hov[2];
+  unsigned long long hs[N_STATS];
+  NB_CUDA(err, cudaMemcpyAsync(hc, cnts, sizeof hc, cudaMemcpyDeviceToHost, st));
+  NB_CUDA(err, cudaMemcpyAsync(hov, overflow, sizeof hov, cudaMemcpyDeviceToHost, st));
+  NB_CUDA(err, cudaMemcpyAsync(hs, stats, sizeof hs, cudaMemcpyDeviceToHost, st));
+  NB_CUDA(err, cudaStreamSynchronize(st));
+  nimbus_path_counts& cnt = C->counts;
+  std::memset(&cnt, 0, sizeof cnt);
+  const int64_t n_raw = std::min<int64_t>(hc[0], cb.cap);
+  cnt.n_coarse_raw = hc[0];
+  cnt.n_cones = (int64_t)hs[ST_CONES];
+  cnt.n_vis = (int64_t)hs[ST_VIS];
+  cnt.bytes_read = (int64_t)hs[ST_BYTES];
+  for (int d = 1; d <= max_int; ++d) cnt.n_nodes += (int64_t)hc[2 * d] + hc[2 * d + 1];
+  cnt.needed_nodes = hov[0];
+  cnt.needed_coarse = hov[1];
+  cnt.overflow = (hov[0] != 0 || hov[1] != 0) ? 1 : 0;
+
+  // kappa: group, rank by miss, keep at most kappa per group
+  C->n = 0;
+  if (n_raw > 0) {
+    uint32_t *e_tx, *e_rx, *e_n, *e_types, *e_ie, *e_lab, *e_hash, *gid, *owner, *keep, *pos, *vals, *vals_alt,
+        *n_keep;
+    float* e_miss;
+    uint64_t *keys, *keys_alt;
+    NB_TRY(sc.get(&e_tx, n_raw));
+    NB_TRY(sc.get(&e_rx, n_raw));
+    NB_TRY(sc.get(&e_n, n_raw));
+    NB_TRY(sc.get(&e_types, n_raw));
+    NB_TRY(sc.get(&e_ie, n_raw * NB_MAXI));
+    NB_TRY(sc.get(&e_lab, n_raw * NB_MAXI));
+    NB_TRY(sc.get(&e_hash, n_raw));
+    NB_TRY(sc.get(&e_miss, n_raw));
+    NB_TRY(sc.get(&gid, n_raw));
+    uint32_t cap_h = 1024;
+    while ((int64_t)cap_h < 2 * n_raw) cap_h <<= 1;
+    if (cap_h > (1u << 25)) {
+      *err = "trace: too many coarse paths for the kappa step";
+      return NIMBUS_ERR_OVERFLOW;
+    }
+    NB_TRY(sc.get(&owner, cap_h));
+    NB_CUDA(err, cudaMemsetAsync(owner, 0xff, cap_h * sizeof(uint32_t), st));
+    LevelsView LV;
+    std::memset(&LV, 0, sizeof LV);
+    for (int d = 1; d <= max_int; ++d) {
+      LV.ra[d] = lv[d].ra; LV.rb[d] = lv[d].rb; LV.rm[d] = lv[d].rm;
+      LV.da[d] = lv[d].da; LV.db[d] = lv[d].db; LV.dm[d] = lv[d].dm;
+    }
+    const unsigned G = std::min<unsigned>(grid_for(n_raw, 256), PG);
+    k_expand<<<G, 256, 0, st>>>(s, LV, cb.rec, cb.miss, n_raw, e_tx, e_rx, e_n, e_types, e_ie, e_lab, e_miss, e_hash);
+    NB_CUDA(err, cudaGetLastError());
+    k_group<<<G, 256, 0, st>>>(e_tx, e_rx, e_n, e_types, e_lab, n_raw, owner, cap_h - 1, gid);
+    NB_CUDA(err, cudaGetLastError());
+    NB_TRY(sc.get(&keys, n_raw));
+    NB_TRY(sc.get(&keys_alt, n_raw));
+    NB_TRY(sc.get(&vals, n_raw));
+    NB_TRY(sc.get(&vals_alt, n_raw));
+    NB_TRY(sc.get(&keep, n_raw));
+    NB_TRY(sc.get(&pos, n_raw));
+    NB_TRY(sc.get(&n_keep, 1));
+    k_kappa_keys<<<G, 256, 0, st>>>(gid, e_miss, e_hash, n_raw, keys, vals);
+    NB_CUDA(err, cudaGetLastError());
+    int gbits = bits_for(cap_h - 1);
+    NB_TRY(radix_sort(sc, keys, vals, keys_alt, vals_alt, n_raw, 39 + gbits));
+    k_kappa_keep<<<G, 256, 0, st>>>(keys, n_raw, p->kappa, keep);
+    NB_CUDA(err, cudaGetLastError());
+    NB_TRY(exclusive_scan(sc, keep, pos, n_raw, n_keep));
+    uint32_t hk = 0;
+    NB_CUDA(err, cudaMemcpyAsync(&hk, n_keep, sizeof hk, cudaMemcpyDeviceToHost, st));
+    NB_CUDA(err, cudaStreamSynchronize(st));
+    C->n = hk;
+    C->n_groups_cap = cap_h;
+    NB_TRY(C->own(&C->tx, std::max<int64_t>(1, hk), st));
+    NB_TRY(C->own(&C->rx, std::max<int64_t>(1, hk), st));
+    NB_TRY(C->own(&C->nint, std::max<int64_t>(1, hk), st));
+    NB_TRY(C->own(&C->types, std::max<int64_t>(1, hk), st));
+    NB_TRY(C->own(&C->ie, std::max<int64_t>(1, hk) * NB_MAXI, st));
+    NB_TRY(C->own(&C->lab, std::max<int64_t>(1, hk) * NB_MAXI, st));
+    NB_TRY(C->own(&C->miss, std::max<int64_t>(1, hk), st));
+    NB_TRY(C->own(&C->gid, std::max<int64_t>(1, hk), st));
+    k_kappa_compact<<<G, 256, 0, st>>>(keep, pos, vals, n_raw, e_tx, e_rx, e_n, e_types, e_ie, e_lab, e_miss, gid,
+                                       *C);
+    NB_CUDA(err, cudaGetLastError());
+  }
+  cnt.n_coarse = C->n;
+  NB_CUDA(err, cudaStreamSynchronize(st));
+  if (cnt.overflow) {
+    *err = "trace: a bounded buffer overflowed (see needed_nodes / needed_coarse)";
+    return NIMBUS_ERR_OVERFLOW;
+  }
+  return NIMBUS_OK;
+}
+
+}  // namespace nb

@@ -1,0 +1,712 @@
+// Voxelisation (Section 2.1): labelled point cloud + edges -> intersectable
+// entities (IEs) per subvoxel, per-voxel IE ranges and the march distance field
+// of voxel cone tracing (Section 2.2.4).
+//
+// B300 design: a 64-bit sort key per point, (voxel, subvoxel, kind, label), packed
+// so that one stable radix sort groups every subvoxel's points by label and orders
+// the groups by voxel; then one thread per IE reduces its contiguous run, and two
+// passes over the IE table give each voxel its IE range.  Edge segments join the
+// same sort with the kind bit set, so edge IEs sit in their voxel's range.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "nimbus_host.hpp"
+
+namespace nb {
+
+namespace {
+
+constexpr uint64_t INVALID_KEY = ~0ull;
+
+struct GridK {
+  float o[3];
+  float hs;
+  int gmax[3];        // largest global subvoxel index per axis
+  int dv, nx, ny;
+  int sub_bits, id_bits;
+};
+
+__device__ __forceinline__ uint32_t f2o(float f) {  // order-preserving float -> uint
+  uint32_t u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+__global__ void k_bounds(const float* __restrict__ xyz, const uint32_t* __restrict__ label, int64_t n,
+                         uint32_t* __restrict__ out /* lo[3] hi[3] maxlabel */) {
+  float lo[3] = {3.4e38f, 3.4e38f, 3.4e38f}, hi[3] = {-3.4e38f, -3.4e38f, -3.4e38f};
+  uint32_t ml = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      float v = xyz[3 * i + a];
+      lo[a] = fminf(lo[a], v);
+      hi[a] = fmaxf(hi[a], v);
+    }
+    ml = max(ml, label[i]);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = fminf(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], o));
+      hi[a] = fmaxf(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], o));
+    }
+    ml = max(ml, __shfl_xor_sync(0xffffffffu, ml, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    for (int a = 0; a < 3; ++a) {
+      atomicMin(&out[a], f2o(lo[a]));
+      atomicMax(&out[3 + a], f2o(hi[a]));
+    }
+    atomicMax(&out[6], ml);
+  }
+}
+
+__device__ __forceinline__ uint64_t pack_key(const GridK& g, const int gs[3], uint32_t kind, uint32_t id) {
+  const int dv = g.dv;
+  uint64_t cell = ((uint64_t)(gs[2] / dv) * g.ny + (gs[1] / dv)) * g.nx + (gs[0] / dv);
+  uint64_t sub = (uint64_t)(((gs[2] % dv) * dv + (gs[1] % dv)) * dv + (gs[0] % dv));
+  return (cell << (g.sub_bits + 1 + g.id_bits)) | (sub << (1 + g.id_bits)) | ((uint64_t)kind << g.id_bits) |
+         (uint64_t)id;
+}
+
+__global__ void k_point_keys(GridK g, const float* __restrict__ xyz, const uint32_t* __restrict__ label, int64_t n,
+                             uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    int gs[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) gs[a] = subvoxel_axis(xyz[3 * i + a], g.o[a], g.hs, g.gmax[a]);
+    keys[i] = pack_key(g, gs, IE_POINT, label[i]);
+    vals[i] = (uint32_t)i;
+  }
+}
+
+// One thread per edge: the edge is cut into nf fine pieces; a piece belongs to the
+// subvoxel of its midpoint (FP64 midpoint, rounded to FP32, binned like a point),
+// and runs of pieces in one subvoxel form one edge IE.  Slots of the edge's range
+// left over get the invalid key.  FP64 operations are explicitly rounded so the
+// pieces match any IEEE implementation that performs the same steps.
+__global__ void k_edge_pieces(GridK g, const double* __restrict__ edges, int n_edges,
+                              const int64_t* __restrict__ off, const int32_t* __restrict__ nf_arr, int64_t n_points,
+                              uint64_t* __restrict__ keys, uint32_t* __restrict__ vals, int4* __restrict__ pieces,
+                              uint32_t* __restrict__ n_valid) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n_edges) return;
+  const double* E = edges + 12 * e;
+  const double d[3] = {__dsub_rn(E[3], E[0]), __dsub_rn(E[4], E[1]), __dsub_rn(E[5], E[2])};
+  const int nf = nf_arr[e];
+  const int64_t base = off[e];
+  int64_t slot = base;
+  int prev[3] = {-1, -1, -1};
+  int i0 = 0;
+  for (int i = 0; i <= nf; ++i) {
+    int gs[3] = {-2, -2, -2};
+    if (i < nf) {
+      double f = __ddiv_rn((double)i + 0.5, (double)nf);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        double m = __dadd_rn(E[a], __dmul_rn(f, d[a]));
+        gs[a] = subvoxel_axis(__double2float_rn(m), g.o[a], g.hs, g.gmax[a]);
+      }
+    }
+    bool change = (i == nf) || gs[0] != prev[0] || gs[1] != prev[1] || gs[2] != prev[2];
+    if (change && i > 0) {  // close the run [i0, i-1] held in prev
+      keys[n_points + slot] = pack_key(g, prev, IE_EDGE, (uint32_t)e);
+      vals[n_points + slot] = (uint32_t)(n_points + slot);
+      pieces[slot - 0] = make_int4(e, i0, i - 1, nf);
+      ++slot;
+    }
+    if (change) {
+      i0 = i;
+      prev[0] = gs[0]; prev[1] = gs[1]; prev[2] = gs[2];
+    }
+  }
+  atomicAdd(n_valid, (uint32_t)(slot - base));
+  for (int64_t s2 = slot; s2 < base + nf; ++s2) {
+    keys[n_points + s2] = INVALID_KEY;
+    vals[n_points + s2] = (uint32_t)(n_points + s2);
+  }
+}
+
+__global__ void k_run_flags(const uint64_t* __restrict__ keys, int64_t n, uint32_t* __restrict__ flags) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t k = keys[i];
+    flags[i] = (k != INVALID_KEY && (i == 0 || k != keys[i - 1])) ? 1u : 0u;
+  }
+}
+
+__global__ void k_run_starts(const uint32_t* __restrict__ flags, const uint32_t* __restrict__ ids, int64_t n,
+                             uint32_t* __restrict__ starts, uint32_t n_ie, uint32_t n_valid) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    if (flags[i]) starts[ids[i]] = (uint32_t)i;
+  if (blockIdx.x == 0 && threadIdx.x == 0) starts[n_ie] = n_valid;
+}
+
+__global__ void k_gather(const uint32_t* __restrict__ vals, int64_t n_valid, int64_t n_points,
+                         const float* __restrict__ xyz, const float* __restrict__ nrm, float4* __restrict__ pts,
+                         float4* __restrict__ pnrm) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_valid;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t v = vals[i];
+    if (v < n_points) {
+      pts[i] = make_float4(xyz[3 * (int64_t)v], xyz[3 * (int64_t)v + 1], xyz[3 * (int64_t)v + 2], 0.f);
+      pnrm[i] = make_float4(nrm[3 * (int64_t)v], nrm[3 * (int64_t)v + 1], nrm[3 * (int64_t)v + 2], 0.f);
+    } else {
+      pts[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      pnrm[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  }
+}
+
+struct BuildK {
+  GridK g;
+  double o[3], hs;
+  int64_t n_points;
+  int n_ie;
+};
+
+// One thread per IE: reduce its run of sorted entries into the IE record.  Point
+// IE: reception point = centroid, normal = normalised mean normal, bounding-box
+// centre, material = smallest in the group.  Edge IE: reception point = midpoint
+// of its piece range on the edge.
+__global__ void k_ie_build(BuildK b, const uint64_t* __restrict__ keys, const uint32_t* __restrict__ vals,
+                           const uint32_t* __restrict__ starts, const float4* __restrict__ pts,
+                           const float4* __restrict__ pnrm, const uint8_t* __restrict__ material,
+                           const int4* __restrict__ pieces, const double* __restrict__ edges,
+                           IERec* __restrict__ ies, uint32_t* __restrict__ ie_cell) {
+  int ie = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ie >= b.n_ie) return;
+  const GridK& g = b.g;
+  uint32_t s = starts[ie], e = starts[ie + 1];
+  uint64_t key = keys[s];
+  uint32_t id = (uint32_t)(key & ((1ull << g.id_bits) - 1));
+  uint32_t kind = (uint32_t)((key >> g.id_bits) & 1ull);
+  uint32_t sub = (uint32_t)((key >> (g.id_bits + 1)) & ((1ull << g.sub_bits) - 1));
+  uint64_t cell = key >> (g.id_bits + 1 + g.sub_bits);
+  const int dv = g.dv;
+  int vx = (int)(cell % (uint64_t)g.nx), vy = (int)((cell / (uint64_t)g.nx) % (uint64_t)g.ny),
+      vz = (int)(cell / ((uint64_t)g.nx * g.ny));
+  int gs[3] = {vx * dv + (int)(sub % dv), vy * dv + (int)((sub / dv) % dv), vz * dv + (int)(sub / (dv * dv))};
+  IERec r;
+  float sc[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) sc[a] = (float)(b.o[a] + ((double)gs[a] + 0.5) * b.hs);
+  r.sc_pc = make_float4(sc[0], sc[1], sc[2], 0.f);
+  if (kind == IE_POINT) {
+    double sx = 0, sy = 0, sz = 0, nx_ = 0, ny_ = 0, nz_ = 0;
+    float lo[3] = {3.4e38f, 3.4e38f, 3.4e38f}, hi[3] = {-3.4e38f, -3.4e38f, -3.4e38f};
+    uint32_t mat = 255;
+    for (uint32_t k = s; k < e; ++k) {
+      float4 P = pts[k];
+      float4 N = pnrm[k];
+      sx = __dadd_rn(sx, (double)P.x); sy = __dadd_rn(sy, (double)P.y); sz = __dadd_rn(sz, (double)P.z);
+      nx_ = __dadd_rn(nx_, (double)N.x); ny_ = __dadd_rn(ny_, (double)N.y); nz_ = __dadd_rn(nz_, (double)N.z);
+      lo[0] = fminf(lo[0], P.x); lo[1] = fminf(lo[1], P.y); lo[2] = fminf(lo[2], P.z);
+      hi[0] = fmaxf(hi[0], P.x); hi[1] = fmaxf(hi[1], P.y); hi[2] = fmaxf(hi[2], P.z);
+      if (material) mat = min(mat, (uint32_t)material[vals[k]]);
+      else mat = 0;
+    }
+    double inv = __drcp_rn((double)(e - s));
+    double nn = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(nx_, nx_), __dmul_rn(ny_, ny_)), __dmul_rn(nz_, nz_)));
+    double ninv = nn > 0.0 ? __drcp_rn(nn) : 0.0;
+    r.rp_lab = make_float4((float)__dmul_rn(inv, sx), (float)__dmul_rn(inv, sy), (float)__dmul_rn(inv, sz),
+                           __uint_as_float(id));
+    r.nrm_meta = make_float4((float)__dmul_rn(ninv, nx_), (float)__dmul_rn(ninv, ny_), (float)__dmul_rn(ninv, nz_),
+                             __uint_as_float((uint32_t)IE_POINT | (mat << 8)));
+    r.bbc_pb = make_float4((float)(0.5 * ((double)lo[0] + (double)hi[0])), (float)(0.5 * ((double)lo[1] + (double)hi[1])),
+                           (float)(0.5 * ((double)lo[2] + (double)hi[2])), __uint_as_float(s));
+    r.sc_pc.w = __uint_as_float(e - s);
+  } else {
+    int4 pc = pieces[vals[s] - b.n_points];
+    const double* E = edges + 12 * pc.x;
+    double t0 = (double)pc.y / (double)pc.w, t1 = (double)(pc.z + 1) / (double)pc.w;
+    double tm = 0.5 * (t0 + t1);
+    float rp[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) rp[a] = (float)(E[a] + tm * (E[3 + a] - E[a]));
+    float3 n = normalize(f3((float)(E[6] + E[9]), (float)(E[7] + E[10]), (float)(E[8] + E[11])));
+    r.rp_lab = make_float4(rp[0], rp[1], rp[2], __uint_as_float(0u));  // label set on the host side below
+    r.nrm_meta = make_float4(n.x, n.y, n.z, __uint_as_float((uint32_t)IE_EDGE | (255u << 8)));
+    r.bbc_pb = make_float4(rp[0], rp[1], rp[2], __uint_as_float((uint32_t)pc.x));
+    r.sc_pc.w = __uint_as_float(0u);
+  }
+  ies[ie] = r;
+  ie_cell[ie] = (uint32_t)cell;
+}
+
+// Edge IEs carry their edge's label (looked up from the edge label table).
+__global__ void k_edge_labels(IERec* __restrict__ ies, int n_ie, const uint32_t* __restrict__ edge_label) {
+  int ie = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ie >= n_ie) return;
+  float4 m = ies[ie].nrm_meta;
+  if ((__float_as_uint(m.w) & 1u) == IE_EDGE) {
+    uint32_t e = __float_as_uint(ies[ie].bbc_pb.w);
+    ies[ie].rp_lab.w = __uint_as_float(edge_label[e]);
+  }
+}
+
+__global__ void k_cell_begin(const uint32_t* __restrict__ ie_cell, int n_ie, uint2* __restrict__ cells) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_ie) return;
+  if (i == 0 || ie_cell[i] != ie_cell[i - 1]) cells[ie_cell[i]].x = (uint32_t)i;
+}
+
+__global__ void k_cell_count(const uint32_t* __restrict__ ie_cell, int n_ie, uint2* __restrict__ cells) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_ie) return;
+  if (i == n_ie - 1 || ie_cell[i] != ie_cell[i + 1]) {
+    uint32_t c = ie_cell[i];
+    cells[c].y = (uint32_t)i + 1u - cells[c].x;
+  }
+}
+
+// March field, separable L-infinity distance transform (capped at 255):
+// pass x gives the 1-D distance to the nearest voxel with IEs in each row; passes
+// y and z take min over w of max(|v - w|, d(w)), which composes the L-infinity
+// metric one axis at a time.  The scan over w stops once |v - w| reaches the best.
+__global__ void k_march_x(const uint2* __restrict__ cells, int nx, int ny, int nz, uint8_t* __restrict__ d1) {
+  int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= ny * nz) return;
+  int64_t base = (int64_t)row * nx;
+  int dist = 255;
+  for (int x = 0; x < nx; ++x) {
+    dist = cells[base + x].y > 0 ? 0 : min(dist + 1, 255);
+    d1[base + x] = (uint8_t)dist;
+  }
+  dist = 255;
+  for (int x = nx - 1; x >= 0; --x) {
+    dist = cells[base + x].y > 0 ? 0 : min(dist + 1, 255);
+    d1[base + x] = (uint8_t)min((int)d1[base + x], dist);
+  }
+}
+
+__global__ void k_march_axis(const uint8_t* __restrict__ din, uint8_t* __restrict__ dout, int nx, int ny, int nz,
+                             int axis) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t n = (int64_t)nx * ny * nz;
+  if (i >= n) return;
+  int y = (int)((i / nx) % ny), z = (int)(i / ((int64_t)nx * ny));
+  int c = axis == 1 ? y : z;
+  int lim = axis == 1 ? ny : nz;
+  int64_t stride = axis == 1 ? nx : (int64_t)nx * ny;
+  int best = din[i];
+  for (int r = 1; r < best; ++r) {
+    if (c - r >= 0) best = min(best, max(r, (int)din[i - r * stride]));
+    if (c + r < lim) best = min(best, max(r, (int)din[i + r * stride]));
+    if (c - r < 0 && c + r >= lim) break;
+  }
+  dout[i] = (uint8_t)best;
+}
+
+// Build every derived table of a scene from its device cloud on a fixed grid.
+int build_tables(Mem& mem, SceneObj* S, cudaStream_t st) {
+  std::string* err = mem.err;
+  Scratch sc(&mem, st);
+  const int dv = S->params.dv;
+  const int64_t n = S->n_points;
+  const int64_t n_edges = (int64_t)S->edge_label_h.size();
+  const int64_t n_cells = (int64_t)S->dims[0] * S->dims[1] * S->dims[2];
+  if (n_cells >= (1ll << 32)) {
+    *err = "voxel grid too large";
+    return NIMBUS_ERR_ARG;
+  }
+  const double h = S->params.voxel_size, hs = h / dv;
+  // edge pieces per edge (same FP64 steps as the device kernel)
+  std::vector<int64_t> off(n_edges + 1, 0);
+  std::vector<int32_t> nf(n_edges, 1);
+  for (int64_t e = 0; e < n_edges; ++e) {
+    const double* E = &S->edges_h[12 * e];
+    double dx = E[3] - E[0], dy = E[4] - E[1], dz = E[5] - E[2];
+    double L = std::sqrt(dx * dx + dy * dy + dz * dz);
+    double q = std::ceil(L / (hs / 4.0));
+    if (q > 1e8) {
+      *err = "edge too long";
+      return NIMBUS_ERR_ARG;
+    }
+    nf[e] = std::max(1, (int)q);
+    off[e + 1] = off[e] + nf[e];
+  }
+  const int64_t n_piece_slots = off[n_edges];
+  const int64_t n_total = n + n_piece_slots;
+  if (n_total >= (1ll << 32) - 2) {
+    *err = "too many points";
+    return NIMBUS_ERR_ARG;
+  }
+  GridK g;
+  for (int a = 0; a < 3; ++a) {
+    g.o[a] = (float)S->origin[a];
+    g.gmax[a] = S->dims[a] * dv - 1;
+  }
+  g.hs = (float)hs;
+  g.dv = dv;
+  g.nx = S->dims[0];
+  g.ny = S->dims[1];
+  g.sub_bits = std::max(1, bits_for((uint64_t)dv * dv * dv - 1));
+  uint64_t max_id = std::max<uint64_t>(S->max_label, n_edges > 0 ? (uint64_t)(n_edges - 1) : 0);
+  g.id_bits = std::max(1, bits_for(max_id));
+  int cell_bits = bits_for((uint64_t)n_cells);
+  int key_bits = cell_bits + g.sub_bits + 1 + g.id_bits;
+  if (key_bits > 64) {
+    *err = "sort key exceeds 64 bits (labels or grid too large)";
+    return NIMBUS_ERR_ARG;
+  }
+  uint64_t *keys, *keys_alt;
+  uint32_t *vals, *vals_alt, *flags, *ids, *counter;
+  int4* pieces;
+  int64_t* d_off;
+  int32_t* d_nf;
+  double* d_edges = nullptr;
+  uint32_t* d_elabel = nullptr;
+  NB_TRY(sc.get(&keys, n_total));
+  NB_TRY(sc.get(&keys_alt, n_total));
+  NB_TRY(sc.get(&vals, n_total));
+  NB_TRY(sc.get(&vals_alt, n_total));
+  NB_TRY(sc.get(&flags, n_total));
+  NB_TRY(sc.get(&ids, n_total));
+  NB_TRY(sc.get(&counter, 4));
+  NB_TRY(sc.get(&pieces, std::max<int64_t>(1, n_piece_slots)));
+  NB_TRY(sc.get(&d_off, n_edges + 1));
+  NB_TRY(sc.get(&d_nf, std::max<int64_t>(1, n_edges)));
+  NB_CUDA(err, cudaMemsetAsync(counter, 0, 4 * sizeof(uint32_t), st));
+  const int B = 256;
+  const unsigned G = std::min<unsigned>(grid_for(std::max<int64_t>(n_total, 1), B), 148u * 16u);
+  if (n > 0) {
+    k_point_keys<<<std::min<unsigned>(grid_for(n, B), 148u * 16u), B, 0, st>>>(g, S->xyz, S->label, n, keys, vals);
+    NB_CUDA(err, cudaGetLastError());
+  }
+  if (n_edges > 0) {
+    // edges live in the object's owned buffer (d.edges)
+    d_edges = const_cast<double*>(S->d.edges);
+    NB_TRY(sc.get(&d_elabel, n_edges));
+    NB_CUDA(err, cudaMemcpyAsync(d_elabel, S->edge_label_h.data(), n_edges * sizeof(uint32_t),
+                                 cudaMemcpyHostToDevice, st));
+    NB_CUDA(err, cudaMemcpyAsync(d_off, off.data(), (n_edges + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    NB_CUDA(err, cudaMemcpyAsync(d_nf, nf.data(), n_edges * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    k_edge_pieces<<<grid_for(n_edges, 64), 64, 0, st>>>(g, d_edges, (int)n_edges, d_off, d_nf, n, keys, vals, pieces,
+                                                         counter);
+    NB_CUDA(err, cudaGetLastError());
+  }
+  NB_TRY(radix_sort(sc, keys, vals, keys_alt, vals_alt, n_total, key_bits));
+  k_run_flags<<<G, B, 0, st>>>(keys, n_total, flags);
+  NB_CUDA(err, cudaGetLastError());
+  NB_TRY(exclusive_scan(sc, flags, ids, n_total, counter + 1));
+  uint32_t hc[2];
+  NB_CUDA(err, cudaMemcpyAsync(hc, counter, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+  NB_CUDA(err, cudaStreamSynchronize(st));
+  const int64_t n_valid = n + hc[0];
+  const int64_t n_ie = hc[1];
+  uint32_t* starts;
+  uint32_t* ie_cell;
+  NB_TRY(sc.get(&starts, n_ie + 1));
+  NB_TRY(sc.get(&ie_cell, std::max<int64_t>(1, n_ie)));
+  k_run_starts<<<G, B, 0, st>>>(flags, ids, n_total, starts, (uint32_t)n_ie, (uint32_t)n_valid);
+  NB_CUDA(err, cudaGetLastError());
+
+  // owned tables: freed first if this is a rebuild
+  for (void* p : S->table_bufs) mem.release(p, st);
+  S->table_bufs.clear();
+  auto own = [&](auto** p, size_t cnt) {
+    int rc = mem.alloc_n(p, cnt, st);
+    if (rc == NIMBUS_OK) S->table_bufs.push_back(*p);
+    return rc;
+  };
+  float4 *pts, *pnrm;
+  IERec* ies;
+  uint2* cells;
+  uint8_t *march, *d1, *d2;
+  NB_TRY(own(&pts, std::max<int64_t>(1, n_valid)));
+  NB_TRY(own(&pnrm, std::max<int64_t>(1, n_valid)));
+  NB_TRY(own(&ies, std::max<int64_t>(1, n_ie)));
+  NB_TRY(own(&cells, n_cells));
+  NB_TRY(own(&march, n_cells));
+  NB_TRY(sc.get(&d1, n_cells));
+  NB_TRY(sc.get(&d2, n_cells));
+  if (n_valid > 0) {
+    k_gather<<<std::min<unsigned>(grid_for(n_valid, B), 148u * 16u), B, 0, st>>>(vals, n_valid, n, S->xyz, S->nrm,
+                                                                                  pts, pnrm);
+    NB_CUDA(err, cudaGetLastError());
+  }
+  NB_CUDA(err, cudaMemsetAsync(cells, 0, n_cells * sizeof(uint2), st));
+  if (n_ie > 0) {
+    BuildK bk;
+    bk.g = g;
+    for (int a = 0; a < 3; ++a) bk.o[a] = S->origin[a];
+    bk.hs = hs;
+    bk.n_points = n;
+    bk.n_ie = (int)n_ie;
+    k_ie_build<<<grid_for(n_ie, 128), 128, 0, st>>>(bk, keys, vals, starts, pts, pnrm, S->material, pieces, d_edges,
+                                                    ies, ie_cell);
+    NB_CUDA(err, cudaGetLastError());
+    if (n_edges > 0) {
+      k_edge_labels<<<grid_for(n_ie, 256), 256, 0, st>>>(ies, (int)n_ie, d_elabel);
+      NB_CUDA(err, cudaGetLastError());
+    }
+    k_cell_begin<<<grid_for(n_ie, 256), 256, 0, st>>>(ie_cell, (int)n_ie, cells);
+    NB_CUDA(err, cudaGetLastError());
+    k_cell_count<<<grid_for(n_ie, 256), 256, 0, st>>>(ie_cell, (int)n_ie, cells);
+    NB_CUDA(err, cudaGetLastError());
+  }
+  const int nx = S->dims[0], ny = S->dims[1], nz = S->dims[2];
+  k_march_x<<<grid_for((int64_t)ny * nz, 128), 128, 0, st>>>(cells, nx, ny, nz, d1);
+  NB_CUDA(err, cudaGetLastError());
+  k_march_axis<<<grid_for(n_cells, 256), 256, 0, st>>>(d1, d2, nx, ny, nz, 1);
+  NB_CUDA(err, cudaGetLastError());
+  k_march_axis<<<grid_for(n_cells, 256), 256, 0, st>>>(d2, march, nx, ny, nz, 2);
+  NB_CUDA(err, cudaGetLastError());
+  // the scratch buffers are released when sc leaves scope (stream-ordered)
+  S->n_ie = n_ie;
+  S->n_slots = n_valid;
+  DScene& d = S->d;
+  d.cells = cells;
+  d.march = march;
+  d.ies = ies;
+  d.pts = pts;
+  d.pnrm = pnrm;
+  d.n_ie = (int)n_ie;
+  return NIMBUS_OK;
+}
+
+void fill_dscene(SceneObj* S) {
+  const nimbus_vox_params& p = S->params;
+  DScene& d = S->d;
+  double h = p.voxel_size, hs = h / p.dv;
+  d.ox = (float)S->origin[0];
+  d.oy = (float)S->origin[1];
+  d.oz = (float)S->origin[2];
+  d.h = (float)h;
+  d.inv_h = (float)(1.0 / h);
+  d.hs = (float)hs;
+  d.nx = S->dims[0];
+  d.ny = S->dims[1];
+  d.nz = S->dims[2];
+  d.dv = p.dv;
+  d.odx = S->origin[0];
+  d.ody = S->origin[1];
+  d.odz = S->origin[2];
+  d.hd = h;
+  d.hsd = hs;
+  d.n_cells = (long long)S->dims[0] * S->dims[1] * S->dims[2];
+  d.n_edges = (int)S->edge_label_h.size();
+  d.r_vox = (float)(h * std::sqrt(3.0) / 2.0);
+  d.r_sub = (float)(hs * std::sqrt(3.0) / 2.0);
+  d.seg_len = (float)(hs * std::sqrt(3.0));
+  d.sdf_inv_s2 = (float)(1.0 / (p.sdf_sigma * p.sdf_sigma));
+  d.sdf_eps = (float)p.sdf_eps;
+  d.vis_ignore = (float)p.vis_ignore;
+  d.sdf_max_steps = p.sdf_max_steps;
+}
+
+}  // namespace
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int copy_in(std::string* err, void* dst, const void* src, size_t n, cudaStream_t st) {
+  if (n == 0) return NIMBUS_OK;
+  NB_CUDA(err, cudaMemcpyAsync(dst, src, n, cudaMemcpyDefault, st));
+  return NIMBUS_OK;
+}
+
+int voxelize_scene(Mem& mem, const nimbus_cloud* cloud, const nimbus_edges* edges, const nimbus_vox_params* p,
+                   SceneObj* S, cudaStream_t st) {
+  std::string* err = mem.err;
+  if (!cloud || !p || cloud->n < 0 || (cloud->n > 0 && (!cloud->xyz || !cloud->nrm || !cloud->label))) {
+    *err = "voxelize: invalid cloud";
+    return NIMBUS_ERR_ARG;
+  }
+  if (!(p->voxel_size > 0) || p->dv < 1 || p->dv > 4 || p->sdf_max_steps < 1 || !(p->sdf_sigma > 0)) {
+    *err = "voxelize: invalid parameters";
+    return NIMBUS_ERR_ARG;
+  }
+  const int64_t n = cloud->n;
+  const int64_t ne = edges ? edges->n : 0;
+  if (ne < 0 || (ne > 0 && (!edges->edges || !edges->label))) {
+    *err = "voxelize: invalid edges";
+    return NIMBUS_ERR_ARG;
+  }
+  if (n == 0 && ne == 0 && !p->has_region) {
+    *err = "voxelize: empty scene and no region";
+    return NIMBUS_ERR_ARG;
+  }
+  S->mem = &mem;
+  S->params = *p;
+  S->n_points = n;
+  NB_TRY(S->own(&S->xyz, std::max<int64_t>(1, 3 * n), st));
+  NB_TRY(S->own(&S->nrm, std::max<int64_t>(1, 3 * n), st));
+  NB_TRY(S->own(&S->label, std::max<int64_t>(1, n), st));
+  NB_TRY(copy_in(err, S->xyz, cloud->xyz, 3 * n * sizeof(float), st));
+  NB_TRY(copy_in(err, S->nrm, cloud->nrm, 3 * n * sizeof(float), st));
+  NB_TRY(copy_in(err, S->label, cloud->label, n * sizeof(uint32_t), st));
+  if (cloud->material) {
+    NB_TRY(S->own(&S->material, std::max<int64_t>(1, n), st));
+    NB_TRY(copy_in(err, S->material, cloud->material, n * sizeof(uint8_t), st));
+  }
+  S->edges_h.resize(12 * ne);
+  S->edge_label_h.resize(ne);
+  if (ne > 0) {
+    NB_CUDA(err, cudaMemcpy(S->edges_h.data(), edges->edges, 12 * ne * sizeof(double), cudaMemcpyDefault));
+    NB_CUDA(err, cudaMemcpy(S->edge_label_h.data(), edges->label, ne * sizeof(uint32_t), cudaMemcpyDefault));
+    double* de;
+    NB_TRY(S->own(&de, 12 * ne, st));
+    NB_CUDA(err, cudaMemcpyAsync(de, S->edges_h.data(), 12 * ne * sizeof(double), cudaMemcpyHostToDevice, st));
+    S->d.edges = de;
+  }
+  // bounds of the points (device reduction), the edges and the region (host)
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  uint32_t maxlab = 0;
+  if (n > 0) {
+    uint32_t* red;
+    Scratch sc(&mem, st);
+    NB_TRY(sc.get(&red, 8));
+    uint32_t init[8] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0u, 0u, 0u, 0u, 0u};
+    NB_CUDA(err, cudaMemcpyAsync(red, init, sizeof init, cudaMemcpyHostToDevice, st));
+    k_bounds<<<std::min<unsigned>(grid_for(n, 256), 148u * 8u), 256, 0, st>>>(S->xyz, S->label, n, red);
+    NB_CUDA(err, cudaGetLastError());
+    uint32_t hr[8];
+    NB_CUDA(err, cudaMemcpyAsync(hr, red, sizeof hr, cudaMemcpyDeviceToHost, st));
+    NB_CUDA(err, cudaStreamSynchronize(st));
+    for (int a = 0; a < 6; ++a) {
+      uint32_t u = hr[a];
+      uint32_t b = (u & 0x80000000u) ? (u & 0x7fffffffu) : ~u;
+      float f;
+      std::memcpy(&f, &b, 4);
+      if (a < 3) lo[a] = std::min(lo[a], (double)f);
+      else hi[a - 3] = std::max(hi[a - 3], (double)f);
+    }
+    maxlab = hr[6];
+  }
+  for (int64_t e = 0; e < ne; ++e)
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = std::min(lo[a], std::min(S->edges_h[12 * e + a], S->edges_h[12 * e + 3 + a]));
+      hi[a] = std::max(hi[a], std::max(S->edges_h[12 * e + a], S->edges_h[12 * e + 3 + a]));
+      maxlab = std::max(maxlab, S->edge_label_h[e]);
+    }
+  if (p->has_region)
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = std::min(lo[a], p->region_min[a]);
+      hi[a] = std::max(hi[a], p->region_max[a]);
+    }
+  if (maxlab >= (1u << 24)) {
+    *err = "labels must be < 2^24";
+    return NIMBUS_ERR_ARG;
+  }
+  S->max_label = maxlab;
+  const double h = p->voxel_size;
+  for (int a = 0; a < 3; ++a) {
+    S->origin[a] = (std::floor(lo[a] / h) - 1.0) * h;
+    double dd = std::ceil((hi[a] - S->origin[a]) / h) + 1.0;
+    if (!(dd >= 1.0 && dd < 1e6)) {
+      *err = "voxel grid dimensions out of range";
+      return NIMBUS_ERR_ARG;
+    }
+    S->dims[a] = (int)dd;
+  }
+  fill_dscene(S);
+  return build_tables(mem, S, st);
+}
+
+namespace {
+__global__ void k_outside_flags(const float* __restrict__ xyz, int64_t n, float lx, float ly, float lz, float hx,
+                                float hy, float hz, uint32_t* __restrict__ keep) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    float x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
+    bool inside = x >= lx && x <= hx && y >= ly && y <= hy && z >= lz && z <= hz;
+    keep[i] = inside ? 0u : 1u;
+  }
+}
+
+__global__ void k_compact_points(const float* __restrict__ xyz, const float* __restrict__ nrm,
+                                 const uint32_t* __restrict__ label, const uint8_t* __restrict__ mat, int64_t n,
+                                 const uint32_t* __restrict__ keep, const uint32_t* __restrict__ pos,
+                                 float* __restrict__ oxyz, float* __restrict__ onrm, uint32_t* __restrict__ olabel,
+                                 uint8_t* __restrict__ omat) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    if (!keep[i]) continue;
+    int64_t j = pos[i];
+    for (int a = 0; a < 3; ++a) {
+      oxyz[3 * j + a] = xyz[3 * i + a];
+      onrm[3 * j + a] = nrm[3 * i + a];
+    }
+    olabel[j] = label[i];
+    if (omat) omat[j] = mat ? mat[i] : 0;
+  }
+}
+}  // namespace
+
+int update_scene_region(Mem& mem, SceneObj* S, const double lo[3], const double hi[3], const nimbus_cloud* repl,
+                        cudaStream_t st) {
+  std::string* err = mem.err;
+  const int64_t n = S->n_points;
+  const int64_t nr = repl ? repl->n : 0;
+  if (nr < 0 || (nr > 0 && (!repl->xyz || !repl->nrm || !repl->label))) {
+    *err = "update_region: invalid replacement cloud";
+    return NIMBUS_ERR_ARG;
+  }
+  Scratch sc(&mem, st);
+  uint32_t *keep, *pos, *cnt;
+  NB_TRY(sc.get(&keep, std::max<int64_t>(1, n)));
+  NB_TRY(sc.get(&pos, std::max<int64_t>(1, n)));
+  NB_TRY(sc.get(&cnt, 1));
+  if (n > 0) {
+    k_outside_flags<<<std::min<unsigned>(grid_for(n, 256), 148u * 8u), 256, 0, st>>>(
+        S->xyz, n, (float)lo[0], (float)lo[1], (float)lo[2], (float)hi[0], (float)hi[1], (float)hi[2], keep);
+    NB_CUDA(err, cudaGetLastError());
+  }
+  NB_TRY(exclusive_scan(sc, keep, pos, n, cnt));
+  uint32_t n_keep = 0;
+  NB_CUDA(err, cudaMemcpyAsync(&n_keep, cnt, sizeof n_keep, cudaMemcpyDeviceToHost, st));
+  NB_CUDA(err, cudaStreamSynchronize(st));
+  const int64_t n_new = (int64_t)n_keep + nr;
+  float *nxyz, *nnrm;
+  uint32_t* nlab;
+  uint8_t* nmat = nullptr;
+  NB_TRY(mem.alloc_n(&nxyz, std::max<int64_t>(1, 3 * n_new), st));
+  NB_TRY(mem.alloc_n(&nnrm, std::max<int64_t>(1, 3 * n_new), st));
+  NB_TRY(mem.alloc_n(&nlab, std::max<int64_t>(1, n_new), st));
+  bool with_mat = S->material != nullptr || (repl && repl->material);
+  if (with_mat) NB_TRY(mem.alloc_n(&nmat, std::max<int64_t>(1, n_new), st));
+  if (n > 0) {
+    k_compact_points<<<std::min<unsigned>(grid_for(n, 256), 148u * 8u), 256, 0, st>>>(
+        S->xyz, S->nrm, S->label, S->material, n, keep, pos, nxyz, nnrm, nlab, nmat);
+    NB_CUDA(err, cudaGetLastError());
+  }
+  if (nr > 0) {
+    NB_TRY(copy_in(err, nxyz + 3 * n_keep, repl->xyz, 3 * nr * sizeof(float), st));
+    NB_TRY(copy_in(err, nnrm + 3 * n_keep, repl->nrm, 3 * nr * sizeof(float), st));
+    NB_TRY(copy_in(err, nlab + n_keep, repl->label, nr * sizeof(uint32_t), st));
+    if (nmat) {
+      if (repl->material) NB_TRY(copy_in(err, nmat + n_keep, repl->material, nr, st));
+      else NB_CUDA(err, cudaMemsetAsync(nmat + n_keep, 0, nr, st));
+    }
+    // the replacement must lie on the existing grid and keep labels < 2^24
+    std::vector<uint32_t> hl(nr);
+    NB_CUDA(err, cudaMemcpy(hl.data(), repl->label, nr * sizeof(uint32_t), cudaMemcpyDefault));
+    for (uint32_t l : hl) S->max_label = std::max(S->max_label, l);
+  }
+  // swap in the new cloud
+  auto swap_buf = [&](void* oldp, void* newp) {
+    for (auto& b : S->bufs)
+      if (b == oldp) b = newp;
+    mem.release(oldp, st);
+  };
+  swap_buf(S->xyz, nxyz);
+  swap_buf(S->nrm, nnrm);
+  swap_buf(S->label, nlab);
+  if (S->material) swap_buf(S->material, nmat);
+  else if (nmat) S->bufs.push_back(nmat);
+  S->xyz = nxyz;
+  S->nrm = nnrm;
+  S->label = nlab;
+  S->material = nmat;
+  S->n_points = n_new;
+  return build_tables(mem, S, st);
+}
+
+}  // namespace nb

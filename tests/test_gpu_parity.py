@@ -1,0 +1,178 @@
+"""CUDA library vs FP64 oracle, through the C ABI (needs a B300)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2402_13747_b300 import config, scenes
+from tests.imagemethod import box_room_planes, image_paths
+from tests.pathsets import compare, keyed
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2402_13747_b300 import _abi
+    c = _abi.Context(0)
+    yield c
+    c.close()
+
+
+def _tables_match(ctx, sc, params):
+    h = ctx.voxelize_scene(sc, params)
+    G = ctx.scene_tables(h)
+    s = oracle.Scene.from_scene(sc, params)
+    R = s.ies()
+    Rc = s.cells()
+    np.testing.assert_allclose(G["origin"], s.origin, rtol=0, atol=0)
+    np.testing.assert_array_equal(G["dims"], s.dims)
+    assert G["n_ie"] == s.n_ie
+    # integer / index work: bit-exact
+    np.testing.assert_array_equal(G["kind"], R["kind"])
+    np.testing.assert_array_equal(G["label"], R["label"])
+    np.testing.assert_array_equal(G["cell"], R["cell"])
+    np.testing.assert_array_equal(G["gs"], R["gs"])
+    np.testing.assert_array_equal(G["prange"][:, 1], R["prange"][:, 1])
+    np.testing.assert_array_equal(G["cell_count"], Rc["count"])
+    occ = Rc["count"] > 0
+    np.testing.assert_array_equal(G["cell_begin"][occ], Rc["begin"][occ])
+    np.testing.assert_array_equal(G["march"], Rc["march"])
+    # FP32 records of FP64 sums: within one FP32 rounding
+    np.testing.assert_allclose(G["rp"], R["rp"], atol=2e-6)
+    pt = R["kind"] == 0
+    np.testing.assert_allclose(G["normal"][pt], R["normal"][pt], atol=2e-6)
+    np.testing.assert_allclose(G["bbc"][pt], R["bbc"][pt], atol=2e-6)
+    np.testing.assert_array_equal(G["material"][pt], R["material"][pt])
+    ctx.release(h)
+
+
+@pytest.mark.parametrize("name", ["room_tiny", "room_noisy", "wedge"])
+def test_voxel_tables_match_oracle(ctx, name):
+    sc = {"room_tiny": scenes.room_tiny, "room_noisy": lambda: scenes.room_noisy(n_tx=1, n_rx=1),
+          "wedge": scenes.wedge}[name]()
+    _tables_match(ctx, sc, config.params_for(sc))
+
+
+def test_voxel_tables_ragged_sizes(ctx):
+    """Clouds that leave a ragged last tile in every kernel, down to a single point."""
+    rng = np.random.default_rng(3)
+    p = config.Params()
+    for n in (1, 2, 31, 33, 4095, 4097, 70001):
+        xyz = rng.uniform(0, 6, size=(n, 3)).astype(np.float32)
+        nrm = rng.normal(size=(n, 3)).astype(np.float32)
+        nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
+        lab = rng.integers(0, 7, n).astype(np.uint32)
+        sc = scenes.Scene("rand", xyz, nrm, lab, (lab % 3).astype(np.uint8))
+        _tables_match(ctx, sc, p)
+
+
+def test_room_tiny_exact_paths(ctx, room_tiny):
+    """The tiny room: the same 25 paths as the oracle and the image method."""
+    p = config.params_for(room_tiny)
+    G = ctx.run(room_tiny, p)
+    _, _, e = oracle.run(room_tiny, p)
+    R = e.paths()
+    cmp = compare(G, R, atol_pts=1e-3, rtol_len=1e-6)
+    assert cmp["only_gpu"] == [] and cmp["only_ref"] == [], cmp
+    assert cmp["bad"] == [], cmp
+    ref = image_paths(box_room_planes(10.0, 10.0, 3.0), room_tiny.tx[0], room_tiny.rx[0], max_order=2)
+    got = keyed(G)
+    assert {k[3] for k in got} == set(ref)
+    for k, (pts, L) in got.items():
+        np.testing.assert_allclose(pts, ref[k[3]][0], atol=1e-3)
+        assert abs(L - ref[k[3]][1]) <= 1e-6 * ref[k[3]][1]
+
+
+def test_wedge_keller_point(ctx):
+    sc = scenes.wedge(z_tx=0.5, z_rx=2.0)
+    p = config.params_for(sc)
+    G = ctx.run(sc, p)
+    assert len(G["n"]) == 1 and G["n"][0] == 1 and G["type"][0][0] == 1
+    np.testing.assert_allclose(G["pts"][0][0], [0.0, 0.0, 1.25], atol=1e-3)
+
+
+def test_noisy_room_subset_matches_oracle(ctx):
+    """Noisy room with the box: 1 TX x 3 RX, <= 2 reflections + 1 diffraction."""
+    full = scenes.room_noisy()
+    sc = full.with_pairs(full.tx[:1], full.rx[:3])
+    p = config.params_for(sc, max_refl=2, max_diff=1)
+    G = ctx.run(sc, p)
+    _, _, e = oracle.run(sc, p)
+    cmp = compare(G, e.paths(), atol_pts=1e-3, rtol_len=1e-6)
+    assert cmp["n_ref"] > 20
+    assert cmp["jaccard"] >= 0.9, cmp
+    assert len(cmp["bad"]) <= 0.05 * cmp["n_common"], cmp
+
+
+def test_deterministic(ctx, room_tiny):
+    p = config.params_for(room_tiny)
+    a = ctx.run(room_tiny, p)
+    b = ctx.run(room_tiny, p)
+    ka, kb = keyed(a), keyed(b)
+    assert ka.keys() == kb.keys()
+    for k in ka:
+        assert np.array_equal(ka[k][0], kb[k][0]) and ka[k][1] == kb[k][1]
+
+
+def test_edge_cases(ctx, room_tiny):
+    from paper_2402_13747_b300._abi import NimbusError
+    p = config.params_for(room_tiny)
+    s = ctx.voxelize_scene(room_tiny, p)
+    # no RX: no paths
+    c = ctx.trace(s, room_tiny.tx, np.zeros((0, 3)), p)
+    P = ctx.refine(s, c, p)
+    assert ctx.counts(P)["n_paths"] == 0
+    # no interactions allowed: LOS only
+    p0 = p.replace(max_refl=0, max_diff=0)
+    c = ctx.trace(s, room_tiny.tx, room_tiny.rx, p0)
+    out = ctx.query(ctx.refine(s, c, p0))
+    assert list(out["n"]) == [0]
+    assert out["length"][0] == pytest.approx(np.sqrt(34.0), rel=1e-12)
+    # TX outside the grid
+    with pytest.raises(NimbusError):
+        ctx.trace(s, np.array([[50.0, 0, 0]]), room_tiny.rx, p)
+    # overflow is reported with the needed size
+    with pytest.raises(NimbusError) as ei:
+        ctx.trace(s, room_tiny.tx, room_tiny.rx, p, max_nodes=100)
+    assert "overflow" in str(ei.value)
+    # bad handle kind
+    with pytest.raises(NimbusError):
+        ctx.refine(s, s, p)
+    ctx.release(s)
+
+
+def test_empty_cloud_with_region(ctx):
+    p = config.Params(max_refl=1)
+    s = ctx.voxelize(np.zeros((0, 3), np.float32), np.zeros((0, 3), np.float32), np.zeros(0, np.uint32),
+                     params=p, region=np.array([[0, 0, 0], [4, 4, 4.0]]))
+    c = ctx.trace(s, np.array([[1.0, 1, 1]]), np.array([[3.0, 3, 3]]), p)
+    out = ctx.query(ctx.refine(s, c, p))
+    assert list(out["n"]) == [0]
+
+
+def test_update_region_equals_rebuild(ctx):
+    """Dynamic scene: replacing a region gives the tables of a full build on that grid."""
+    room = scenes.room_noisy(n_tx=1, n_rx=1)
+    p = config.params_for(room)
+    info = None
+    s = ctx.voxelize_scene(room, p)
+    info = ctx.scene_info(s)
+    # a region box that reproduces this grid: one voxel inside the padded origin
+    h = p.voxel_size
+    region = np.array([info["origin"] + h + 1e-6, info["origin"] + (info["dims"] - 1) * h - 1e-6])
+    xyz, nrm, lab, mat, lo, hi = scenes.moving_box(room, step=7)
+    ctx.update_region(s, lo - 0.01, hi + 0.01, xyz, nrm, lab, mat)
+    A = ctx.scene_tables(s)
+    # the same cloud built from scratch on the same grid
+    keep = ~np.all((room.xyz >= (lo - 0.01).astype(np.float32)) & (room.xyz <= (hi + 0.01).astype(np.float32)), axis=1)
+    sc2 = scenes.Scene("upd", np.concatenate([room.xyz[keep], xyz]), np.concatenate([room.nrm[keep], nrm]),
+                       np.concatenate([room.label[keep], lab]), np.concatenate([room.material[keep], mat]),
+                       room.edges, room.edge_label, region=region)
+    s2 = ctx.voxelize_scene(sc2, p)
+    B = ctx.scene_tables(s2)
+    np.testing.assert_array_equal(A["dims"], B["dims"])
+    for k in ("kind", "label", "cell", "gs", "cell_count", "march", "material"):
+        np.testing.assert_array_equal(A[k], B[k])
+    np.testing.assert_array_equal(A["rp"], B["rp"])
+    ctx.release(s)
+    ctx.release(s2)

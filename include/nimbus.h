@@ -123,7 +123,19 @@ typedef struct {
   int64_t needed_coarse;    /* on NIMBUS_ERR_OVERFLOW: coarse paths requested */
   int64_t bytes_read;       /* algorithmic bytes of scene records read by the trace kernels */
   int32_t overflow;         /* nonzero when a bounded buffer dropped work */
-  int32_t pad_;
+  int32_t n_levels;         /* propagation levels launched */
+  /* Stage kernel times in ms, measured with CUDA events on the caller's stream
+   * around each stage's launches, and the algorithmic bytes each stage read. */
+  double ms_vis;            /* TX -> IE / RX visibility tables */
+  double ms_primary;        /* uniform launch (transmission phase) */
+  double ms_levels;         /* propagation levels (voxel cone tracing) */
+  double ms_kappa;          /* path expansion, grouping, sort and kappa selection */
+  double ms_refine;         /* refinement kernel (Section 2.3) */
+  double ms_dedup;          /* label and Fresnel duplicate removal */
+  int64_t bytes_primary;
+  int64_t bytes_levels;
+  int64_t bytes_refine;     /* algorithmic bytes read by the refinement kernel */
+  int64_t launches;         /* kernels launched by trace_coarse + refine for this handle */
 } nimbus_path_counts;
 
 /* Caller-owned host arrays for nimbus_query, each sized for n_paths entries
@@ -238,6 +250,10 @@ NIMBUS_API int nimbus_release(nimbus_ctx* ctx, nimbus_handle h);
 
 /* Bytes of device memory the context currently holds. */
 NIMBUS_API int nimbus_memory_used(nimbus_ctx* ctx, size_t* bytes);
+
+/* Number of CUDA kernels this library has launched in this process so far (all
+ * contexts); differences around a region count the kernels launched in it. */
+NIMBUS_API int nimbus_kernel_launches(int64_t* count);
 
 #ifdef __cplusplus
 }

@@ -104,6 +104,8 @@ def lib():
         L.oracle_exact_get.argtypes = [vp, i32] + [vp] * 14
         L.oracle_sdf.restype = i32
         L.oracle_sdf.argtypes = [vp, i64, vp, vp, vp]
+        L.oracle_sdf_label.restype = i32
+        L.oracle_sdf_label.argtypes = [vp, u32, vp, vp, vp]
         L.oracle_sdf_hit.restype = i32
         L.oracle_sdf_hit.argtypes = [vp, i64, vp, vp, vp]
         L.oracle_visible.restype = i32
@@ -189,6 +191,13 @@ class Scene:
         f = np.zeros(1)
         n = np.zeros(3)
         ok = lib().oracle_sdf(self.h, int(ie), _p(_c(x, np.float64)), _p(f), _p(n))
+        return (float(f[0]), n) if ok else (None, None)
+
+    def sdf_label(self, label, x):
+        """Eq. 1 on the nearby points of one label (the refinement's surface)."""
+        f = np.zeros(1)
+        n = np.zeros(3)
+        ok = lib().oracle_sdf_label(self.h, int(label), _p(_c(x, np.float64)), _p(f), _p(n))
         return (float(f[0]), n) if ok else (None, None)
 
     def sdf_hit(self, ie, P, d):

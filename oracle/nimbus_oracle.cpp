@@ -941,47 +941,91 @@ struct Exact {
 
 enum { ST_VALID = 0, ST_MISS = 1, ST_NOT_CONVERGED = 2, ST_OCCLUDED = 3, ST_OFF_EDGE = 4 };
 
+// Eq. 1 over the nearby points of one surface.  Reading: "nearby" = the points of
+// label `label` whose subvoxel lies in the 3x3x3 block of subvoxels around the
+// subvoxel of x, so the implicit surface of a label is continuous across subvoxel
+// boundaries (the re-projection below needs that to converge on noisy clouds).
+bool sdf_label(const Scene& s, uint32_t label, V3 x, double* f, V3* n_out) {
+  const int dv = s.p.dv;
+  int g[3], v0[3], v1[3];
+  for (int a = 0; a < 3; ++a) {
+    g[a] = (int)std::floor((comp(x, a) - comp(s.origin, a)) / s.hs);
+    v0[a] = (int)std::floor((double)(g[a] - 1) / dv);
+    v1[a] = (int)std::floor((double)(g[a] + 1) / dv);
+  }
+  const double inv_s2 = 1.0 / (s.p.sdf_sigma * s.p.sdf_sigma);
+  double sw = 0.0;
+  V3 sp, sn;
+  for (int vz = v0[2]; vz <= v1[2]; ++vz)
+    for (int vy = v0[1]; vy <= v1[1]; ++vy)
+      for (int vx = v0[0]; vx <= v1[0]; ++vx) {
+        if (!in_grid(s, vx, vy, vz)) continue;
+        int64_t c = cell_of(s, vx, vy, vz);
+        for (int32_t k = 0; k < s.cell_count[c]; ++k) {
+          const IE& ie = s.ies[s.cell_begin[c] + k];
+          if (ie.kind != IE_POINT || ie.label != label) continue;
+          if (std::abs(ie.gs[0] - g[0]) > 1 || std::abs(ie.gs[1] - g[1]) > 1 || std::abs(ie.gs[2] - g[2]) > 1)
+            continue;
+          for (int64_t q = 0; q < ie.p_count; ++q) {
+            const V3& P = s.pts[ie.p_begin + q];
+            V3 d = x - P;
+            double w = std::exp(-dot(d, d) * inv_s2);
+            sw += w;
+            sp = sp + w * P;
+            sn = sn + w * s.nrm[ie.p_begin + q];
+          }
+        }
+      }
+  if (!(sw > 0.0)) return false;
+  double nn = norm(sn);
+  if (!(nn > 0.0)) return false;
+  V3 n = (1.0 / nn) * sn;
+  *f = dot(x - (1.0 / sw) * sp, n);
+  if (n_out) *n_out = n;
+  return true;
+}
+
 // Re-projection (Section 2.3): a ray from the previous interaction point toward the
 // updated reflection point R; its intersection with the surface of label l gives the
-// new c_k, and the normal there (Eq. 1 normal) the new u_k, v_k.  Reading: the
-// point IEs of label l in the 3x3x3 voxels around R are intersected (Section 2.2.1)
-// and the hit nearest R is taken (ties: lower IE index).
+// new c_k, and the normal there (Eq. 1 normal) the new u_k, v_k.  The intersection is
+// the march of Section 2.2.1 on the label's surface (sdf_label), over a segment of
+// one subvoxel diameter centred on R.
 bool reproject(const Scene& s, V3 P, V3 R, uint32_t label, V3* c_out, V3* n_out) {
   V3 dvec = R - P;
   double tR = norm(dvec);
   if (tR < 1e-12) return false;
   V3 d = (1.0 / tR) * dvec;
-  int v[3];
-  for (int a = 0; a < 3; ++a) v[a] = (int)std::floor((comp(R, a) - comp(s.origin, a)) / s.h);
-  bool found = false;
-  double best = 0, best_t = 0;
-  int64_t best_id = -1;
-  for (int dz = -1; dz <= 1; ++dz)
-    for (int dy = -1; dy <= 1; ++dy)
-      for (int dx = -1; dx <= 1; ++dx) {
-        int u[3] = {v[0] + dx, v[1] + dy, v[2] + dz};
-        if (!in_grid(s, u[0], u[1], u[2])) continue;
-        int64_t c = cell_of(s, u[0], u[1], u[2]);
-        for (int32_t k = 0; k < s.cell_count[c]; ++k) {
-          int64_t id = s.cell_begin[c] + k;
-          const IE& ie = s.ies[id];
-          if (ie.kind != IE_POINT || ie.label != label) continue;
-          double tc = std::max(dot(ie.sc - P, d), 0.0);
-          V3 q = P + tc * d - ie.sc;
-          if (dot(q, q) > s.r_sub * s.r_sub) continue;
-          double t;
-          if (!sdf_hit(s, ie, P, d, &t) || !(t > 0.0)) continue;
-          double score = std::fabs(t - tR);
-          if (!found || score < best || (score == best && id < best_id)) {
-            found = true; best = score; best_t = t; best_id = id;
-          }
-        }
-      }
-  if (!found) return false;
-  V3 c = P + best_t * d;
+  const double L = s.hs * std::sqrt(3.0);
+  double t = tR - 0.5 * L, t_end = tR + 0.5 * L, th = 0.0;
   double f;
   V3 n;
-  if (!sdf_eval(s, s.ies[best_id], c, &f, &n)) return false;
+  bool hit = false;
+  if (!sdf_label(s, label, P + t * d, &f, &n)) return false;
+  for (int it = 0; it < s.p.sdf_max_steps && !hit; ++it) {
+    if (std::fabs(f) < s.p.sdf_eps) {
+      double dn = dot(n, d);
+      th = std::fabs(dn) > 1e-3 ? t - f / dn : t;
+      hit = true;
+      break;
+    }
+    double t_next = t + std::fabs(f);
+    if (t_next > t_end) return false;
+    double f_next;
+    V3 n_next;
+    if (!sdf_label(s, label, P + t_next * d, &f_next, &n_next)) return false;
+    if ((f_next < 0.0) != (f < 0.0)) {
+      th = t - f * (t_next - t) / (f_next - f);
+      hit = true;
+      break;
+    }
+    t = t_next;
+    f = f_next;
+    n = n_next;
+  }
+  // the placed hit must stay on the marched segment
+  if (!hit || !(th > 0.0) || std::fabs(th - tR) > 0.5 * L) return false;
+  V3 c = P + th * d;
+  if (!sdf_label(s, label, c, &f, &n)) return false;
   *c_out = c;
   *n_out = n;
   return true;
@@ -1043,11 +1087,30 @@ Exact refine_one(const Scene& s, const CoarseSet& cs, const Coarse& cp) {
     V3 In[MAXI + 2];
     In[0] = I[0];
     In[n + 1] = I[n + 1];
+    // Gradient-descent step, reading: each interaction's gradient is scaled by the
+    // inverse Hessian of its own local length f_k (2x2 in (r, s), 1x1 in t) times
+    // gamma, with all interactions updated from the same iterate (Jacobi); where that
+    // Hessian is near singular the step is gamma / (1/a + 1/b) times the gradient.
+    // The stationary points, and so the exact paths, do not depend on this choice.
     for (int k = 1; k <= n; ++k) {
       double a = norm(I[k] - I[k - 1]), b = norm(I[k] - I[k + 1]);
       double eta = p.gamma / (1.0 / a + 1.0 / b);
+      double hsc = (1.0 / a + 1.0 / b) * (1.0 / a + 1.0 / b);
+      V3 ea = unit(I[k] - I[k - 1]), eb = unit(I[k] - I[k + 1]);
       if (cp.type[k - 1] == T_REFL) {
-        double r = -eta * g[k][0], sv = -eta * g[k][1];
+        double au = dot(ea, u[k]), av = dot(ea, v[k]), bu = dot(eb, u[k]), bv = dot(eb, v[k]);
+        double h11 = (1.0 - au * au) / a + (1.0 - bu * bu) / b;
+        double h22 = (1.0 - av * av) / a + (1.0 - bv * bv) / b;
+        double h12 = -(au * av) / a - (bu * bv) / b;
+        double det = h11 * h22 - h12 * h12;
+        double r, sv;
+        if (det > 1e-12 * hsc) {
+          r = -p.gamma * (h22 * g[k][0] - h12 * g[k][1]) / det;
+          sv = -p.gamma * (h11 * g[k][1] - h12 * g[k][0]) / det;
+        } else {
+          r = -eta * g[k][0];
+          sv = -eta * g[k][1];
+        }
         double len = std::sqrt(r * r + sv * sv);
         if (len > s.hs) { r *= s.hs / len; sv *= s.hs / len; }
         V3 R = c[k] + r * u[k] + sv * v[k];      // R_k = c_k + r_k u_k + s_k v_k
@@ -1061,7 +1124,9 @@ Exact refine_one(const Scene& s, const CoarseSet& cs, const Coarse& cp) {
         onb(nn, &u[k], &v[k]);
         In[k] = cn;
       } else {
-        double dt = -eta * g[k][0];
+        double aw = dot(ea, w[k]), bw = dot(eb, w[k]);
+        double hw = (1.0 - aw * aw) / a + (1.0 - bw * bw) / b;
+        double dt = hw > 1e-12 * (1.0 / a + 1.0 / b) ? -p.gamma * g[k][0] / hw : -eta * g[k][0];
         if (std::fabs(dt) > s.hs) dt = std::copysign(s.hs, dt);
         tpar[k] += dt;                           // D_k = c_k + t_k w_k
         In[k] = c[k] + tpar[k] * w[k];
@@ -1309,6 +1374,14 @@ int32_t oracle_sdf(void* sp, int64_t ie, const double* x, double* f, double* n) 
   Scene* s = (Scene*)sp;
   V3 nn;
   bool ok = sdf_eval(*s, s->ies[ie], mk(x[0], x[1], x[2]), f, &nn);
+  n[0] = nn.x; n[1] = nn.y; n[2] = nn.z;
+  return ok ? 1 : 0;
+}
+
+int32_t oracle_sdf_label(void* sp, uint32_t label, const double* x, double* f, double* n) {
+  Scene* s = (Scene*)sp;
+  V3 nn;
+  bool ok = sdf_label(*s, label, mk(x[0], x[1], x[2]), f, &nn);
   n[0] = nn.x; n[1] = nn.y; n[2] = nn.z;
   return ok ? 1 : 0;
 }

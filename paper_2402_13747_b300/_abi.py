@@ -24,7 +24,7 @@ ERR_NAMES = {1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_OVERFLOW", 5: "E
 
 EXPORTS = ("nimbus_create", "nimbus_destroy", "nimbus_last_error", "nimbus_voxelize", "nimbus_update_region",
            "nimbus_trace_coarse", "nimbus_refine", "nimbus_query", "nimbus_query_coarse", "nimbus_scene_info",
-           "nimbus_scene_tables", "nimbus_release", "nimbus_memory_used")
+           "nimbus_scene_tables", "nimbus_release", "nimbus_memory_used", "nimbus_kernel_launches")
 
 _vp = C.c_void_p
 
@@ -56,12 +56,16 @@ class RefineParams(C.Structure):
 
 
 class Counts(C.Structure):
-    _fields_ = [(n, C.c_int64) for n in ("n_paths", "n_refined", "n_refined_valid", "n_coarse", "n_coarse_raw",
-                                         "n_cones", "n_vis", "n_nodes", "needed_nodes", "needed_coarse",
-                                         "bytes_read")] + [("overflow", C.c_int32), ("pad_", C.c_int32)]
+    _fields_ = ([(n, C.c_int64) for n in ("n_paths", "n_refined", "n_refined_valid", "n_coarse", "n_coarse_raw",
+                                          "n_cones", "n_vis", "n_nodes", "needed_nodes", "needed_coarse",
+                                          "bytes_read")] +
+                [("overflow", C.c_int32), ("n_levels", C.c_int32)] +
+                [(n, C.c_double) for n in ("ms_vis", "ms_primary", "ms_levels", "ms_kappa", "ms_refine",
+                                           "ms_dedup")] +
+                [(n, C.c_int64) for n in ("bytes_primary", "bytes_levels", "bytes_refine", "launches")])
 
     def as_dict(self):
-        return {f[0]: int(getattr(self, f[0])) for f in self._fields_ if f[0] != "pad_"}
+        return {f[0]: (float if f[1] is C.c_double else int)(getattr(self, f[0])) for f in self._fields_}
 
 
 class PathView(C.Structure):
@@ -85,6 +89,13 @@ class NimbusError(RuntimeError):
 
 
 _lib = None
+
+
+def kernel_launches() -> int:
+    """Kernels the library has launched in this process so far."""
+    v = C.c_int64(0)
+    load().nimbus_kernel_launches(C.byref(v))
+    return int(v.value)
 
 
 def load():
@@ -112,6 +123,7 @@ def load():
     L.nimbus_scene_tables.argtypes = [ctxp, C.c_uint64, P(SceneView), _vp]
     L.nimbus_release.argtypes = [ctxp, C.c_uint64]
     L.nimbus_memory_used.argtypes = [ctxp, P(C.c_size_t)]
+    L.nimbus_kernel_launches.argtypes = [P(C.c_int64)]
     for name in EXPORTS:
         L[name].restype = C.c_char_p if name == "nimbus_last_error" else C.c_int
     _lib = L

@@ -20,6 +20,8 @@ struct nimbus_ctx {
 
 namespace nb {
 
+std::atomic<long long> g_launches{0};
+
 int cuda_fail(std::string* err, cudaError_t e, const char* what) {
   char buf[512];
   std::snprintf(buf, sizeof buf, "CUDA error %d (%s) in %s", (int)e, cudaGetErrorString(e), what);
@@ -431,6 +433,12 @@ int nimbus_release(nimbus_ctx* ctx, nimbus_handle h) {
 int nimbus_memory_used(nimbus_ctx* ctx, size_t* bytes) {
   if (!ctx || !bytes) return NIMBUS_ERR_ARG;
   *bytes = ctx->mem.used;
+  return NIMBUS_OK;
+}
+
+int nimbus_kernel_launches(int64_t* count) {
+  if (!count) return NIMBUS_ERR_ARG;
+  *count = (int64_t)nb::g_launches.load();
   return NIMBUS_OK;
 }
 

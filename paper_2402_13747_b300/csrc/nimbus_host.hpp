@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
 #include <unordered_map>
 #include <vector>
@@ -49,6 +50,13 @@ int cuda_fail(std::string* err, cudaError_t e, const char* what);
     cudaError_t e_ = (call);                                 \
     if (e_ != cudaSuccess) return ::nb::cuda_fail(err, e_, #call); \
   } while (0)
+// Kernel launches made by the library (process-wide), for launch accounting.
+extern std::atomic<long long> g_launches;
+#define NB_LAUNCHED(err)                 \
+  do {                                   \
+    ::nb::g_launches.fetch_add(1);       \
+    NB_CUDA(err, cudaGetLastError());    \
+  } while (0)
 #define NB_TRY(call)               \
   do {                             \
     int rc_ = (call);              \
@@ -56,6 +64,31 @@ int cuda_fail(std::string* err, cudaError_t e, const char* what);
   } while (0)
 
 int num_sms();
+
+// CUDA events recorded on one stream to time stages of kernels (read after a sync).
+struct StageTimer {
+  cudaEvent_t ev[16];
+  int n = 0;
+  cudaStream_t st;
+  explicit StageTimer(cudaStream_t s) : st(s) {}
+  ~StageTimer() {
+    for (int i = 0; i < n; ++i) cudaEventDestroy(ev[i]);
+  }
+  int mark() {
+    if (n >= 16) return n - 1;
+    cudaEventCreate(&ev[n]);
+    cudaEventRecord(ev[n], st);
+    return n++;
+  }
+  double ms(int a, int b) {
+    float m = 0.f;
+    if (a < 0 || b < 0 || a >= n || b >= n || cudaEventElapsedTime(&m, ev[a], ev[b]) != cudaSuccess) {
+      cudaGetLastError();
+      return 0.0;
+    }
+    return (double)m;
+  }
+};
 
 // Exclusive prefix sum of n 32-bit counts; total (device, may be null) receives the sum.
 int exclusive_scan(Scratch& sc, const uint32_t* in, uint32_t* out, int64_t n, uint32_t* total);

@@ -2,11 +2,13 @@
 // re-projection of reflection points onto the point cloud, final visibility,
 // label-based and first-Fresnel-zone duplicate removal.
 //
-// B300 design: one thread per coarse path holds the whole path state in FP64
-// (positions, bases, the gradient and the final length), because the descent's
-// stability needs it; the re-projection ray and its Eq. 1 march run in FP32 in
-// the frame of the intersected IE (offsets of a few decimetres), and the final
-// visibility rays are the FP32 traversal of the tracer.
+// B300 design: one warp per coarse path.  Lane k owns interaction k's FP64 state
+// (point, basis or edge parameter), so the FP64 gradient and step -- the parts
+// whose stability needs double precision -- run once per interaction; neighbours
+// come from warp shuffles.  Each re-projection (a ray intersected with the point
+// sets of one label, Eq. 1) and each final visibility ray uses all 32 lanes:
+// candidate IEs are tested in parallel and the Eq. 1 sums over an IE's points are
+// split across lanes and combined with shuffles, in FP32 in the frame of the IE.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -19,6 +21,7 @@ namespace nb {
 namespace {
 
 constexpr double C_LIGHT = 299792458.0;
+constexpr unsigned FULL = 0xffffffffu;
 
 struct DRefine {
   double delta, gamma, grad_stop, lambda, hs;
@@ -35,204 +38,453 @@ __device__ __forceinline__ d3 dunit(d3 a) {
   return n > 0.0 ? (1.0 / n) * a : a;
 }
 
+__device__ __forceinline__ float wsum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+  return v;
+}
+
+__device__ __forceinline__ double wsumd(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+  return v;
+}
+
+__device__ __forceinline__ d3 shfl3(d3 a, int src) {
+  return D3(__shfl_sync(FULL, a.x, src), __shfl_sync(FULL, a.y, src), __shfl_sync(FULL, a.z, src));
+}
+
+// Eq. 1 over the points of one IE, the points split across the warp's lanes; every
+// lane returns the same f and normal.  c is the IE's bounding-box centre, x is
+// relative to c.
+__device__ bool sdf_warp(const DScene& s, uint32_t pb, uint32_t pc, float3 c, float3 x, float* f, float3* n_out,
+                         int lane, unsigned long long& bytes) {
+  float sw = 0.f, px = 0.f, py = 0.f, pz = 0.f, nx = 0.f, ny = 0.f, nz = 0.f;
+  for (uint32_t k = lane; k < pc; k += 32) {
+    float4 P = __ldg(&s.pts[pb + k]);
+    float4 N = __ldg(&s.pnrm[pb + k]);
+    float3 p = xyz(P) - c;
+    float3 d = x - p;
+    float w = expf(-dot(d, d) * s.sdf_inv_s2);
+    sw += w;
+    px += w * p.x; py += w * p.y; pz += w * p.z;
+    nx += w * N.x; ny += w * N.y; nz += w * N.z;
+  }
+  if (lane == 0) bytes += 32ull * pc;
+  sw = wsum(sw);
+  px = wsum(px); py = wsum(py); pz = wsum(pz);
+  nx = wsum(nx); ny = wsum(ny); nz = wsum(nz);
+  if (!(sw > 0.f)) return false;
+  float3 sn = f3(nx, ny, nz);
+  float nn = len(sn);
+  if (!(nn > 0.f)) return false;
+  float3 n = (1.f / nn) * sn;
+  float3 p = (1.f / sw) * f3(px, py, pz);
+  *f = dot(x - p, n);
+  if (n_out) *n_out = n;
+  return true;
+}
+
+// The Eq. 1 march of Section 2.2.1 (see sdf_march) with warp-shared sums.
+__device__ bool sdf_march_warp(const DScene& s, uint32_t pb, uint32_t pc, float3 c, float3 x0, float3 d,
+                               float* tau_hit, int lane, unsigned long long& bytes) {
+  float half = 0.5f * s.seg_len;
+  float t = -half;
+  float f;
+  float3 n;
+  if (!sdf_warp(s, pb, pc, c, x0 + t * d, &f, &n, lane, bytes)) return false;
+  for (int it = 0; it < s.sdf_max_steps; ++it) {
+    if (fabsf(f) < s.sdf_eps) {
+      float dn = dot(n, d);
+      *tau_hit = fabsf(dn) > 1e-3f ? t - f / dn : t;
+      return true;
+    }
+    float tn = t + fabsf(f);
+    if (tn > half) return false;
+    float fn;
+    float3 nn;
+    if (!sdf_warp(s, pb, pc, c, x0 + tn * d, &fn, &nn, lane, bytes)) return false;
+    if ((fn < 0.f) != (f < 0.f)) {
+      *tau_hit = t - f * (tn - t) / (fn - f);
+      return true;
+    }
+    t = tn;
+    f = fn;
+    n = nn;
+  }
+  return false;
+}
+
+// Same-label IEs near one re-projection target, cached in shared memory per warp:
+// first point, point count and global subvoxel coordinates.
+constexpr int RCAP = 96;
+struct LabelCache {
+  uint32_t pb[RCAP], pc[RCAP];
+  int g[RCAP][3];
+};
+
+__device__ __forceinline__ int floor_div(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
+// Eq. 1 over the nearby points of one label -- the points of the cached IEs whose
+// subvoxel lies in the 3x3x3 block around the subvoxel of x -- with the sums split
+// across lanes; every lane returns the same f and normal.  c0 is the FP32 frame
+// centre of the sums (the re-projection target).
+__device__ bool sdf_label_warp(const DScene& s, const LabelCache& lc, int nc, d3 x, float3 c0, float* f,
+                               float3* n_out, int lane, unsigned long long& bytes) {
+  const int g0 = (int)floor((x.x - s.odx) / s.hsd), g1 = (int)floor((x.y - s.ody) / s.hsd),
+            g2 = (int)floor((x.z - s.odz) / s.hsd);
+  const float3 xl = f3((float)(x.x - (double)c0.x), (float)(x.y - (double)c0.y), (float)(x.z - (double)c0.z));
+  float sw = 0.f, px = 0.f, py = 0.f, pz = 0.f, nx = 0.f, ny = 0.f, nz = 0.f;
+  for (int q = 0; q < nc; ++q) {
+    if (abs(lc.g[q][0] - g0) > 1 || abs(lc.g[q][1] - g1) > 1 || abs(lc.g[q][2] - g2) > 1) continue;
+    const uint32_t pb = lc.pb[q], pc = lc.pc[q];
+    for (uint32_t k = lane; k < pc; k += 32) {
+      float4 P = __ldg(&s.pts[pb + k]);
+      float4 N = __ldg(&s.pnrm[pb + k]);
+      float3 p = xyz(P) - c0;
+      float3 d = xl - p;
+      float w = expf(-dot(d, d) * s.sdf_inv_s2);
+      sw += w;
+      px += w * p.x; py += w * p.y; pz += w * p.z;
+      nx += w * N.x; ny += w * N.y; nz += w * N.z;
+    }
+    if (lane == 0) bytes += 32ull * pc;
+  }
+  sw = wsum(sw);
+  px = wsum(px); py = wsum(py); pz = wsum(pz);
+  nx = wsum(nx); ny = wsum(ny); nz = wsum(nz);
+  if (!(sw > 0.f)) return false;
+  float3 sn = f3(nx, ny, nz);
+  float nn = len(sn);
+  if (!(nn > 0.f)) return false;
+  float3 n = (1.f / nn) * sn;
+  float3 p = (1.f / sw) * f3(px, py, pz);
+  *f = dot(xl - p, n);
+  if (n_out) *n_out = n;
+  return true;
+}
+
 // Re-projection (Section 2.3): the ray from P toward the updated point R is
-// intersected (Eq. 1 march) with the point IEs of label `label` in the 3x3x3 voxels
-// around R; the hit nearest R wins (ties: lower IE index).  Returns the new
-// interaction point and the Eq. 1 normal there.
-__device__ bool reproject(const DScene& s, d3 P, d3 R, uint32_t label, d3* c_out, d3* n_out) {
+// intersected with the implicit surface of label `label` (Eq. 1 over nearby points of
+// that label) by the march of Section 2.2.1 on a segment of one subvoxel diameter
+// centred on R.  The label's IEs within two subvoxels of R -- all that any point of
+// the segment can draw on -- are collected once into the warp's cache.
+__device__ bool reproject_warp(const DScene& s, d3 P, d3 R, uint32_t label, d3* c_out, d3* n_out, int lane,
+                               unsigned long long& bytes, LabelCache& lc) {
   d3 dv = R - P;
   double tR = len(dv);
   if (tR < 1e-12) return false;
   d3 d = (1.0 / tR) * dv;
-  float3 df = tof(d);
-  int v[3] = {(int)floor((R.x - s.odx) / s.hd), (int)floor((R.y - s.ody) / s.hd), (int)floor((R.z - s.odz) / s.hd)};
-  bool found = false;
-  double best = 0.0, best_t = 0.0;
-  uint32_t best_id = 0;
-  unsigned long long bytes = 0;
-  const double rs2 = (double)s.r_sub * (double)s.r_sub;
-  for (int dz = -1; dz <= 1; ++dz)
-    for (int dy = -1; dy <= 1; ++dy)
-      for (int dx = -1; dx <= 1; ++dx) {
-        int u0 = v[0] + dx, u1 = v[1] + dy, u2 = v[2] + dz;
-        if (!in_grid(s, u0, u1, u2)) continue;
-        uint2 cell = __ldg(&s.cells[cell_index(s, u0, u1, u2)]);
-        for (uint32_t k = 0; k < cell.y; ++k) {
-          uint32_t id = cell.x + k;
-          const IERec* r = &s.ies[id];
-          float4 nm = __ldg(&r->nrm_meta);
-          if ((__float_as_uint(nm.w) & 1u) != IE_POINT) continue;
-          if (__float_as_uint(__ldg(&r->rp_lab).w) != label) continue;
-          float4 sc = __ldg(&r->sc_pc);
-          d3 scd = D3(sc.x, sc.y, sc.z);
-          double tc = fmax(dot(scd - P, d), 0.0);
-          d3 q = (P + tc * d) - scd;
-          if (dot(q, q) > rs2) continue;
-          float4 bb = __ldg(&r->bbc_pb);
-          d3 c = D3(bb.x, bb.y, bb.z);
-          double t0 = dot(c - P, d);
-          float3 x0 = tof((P + t0 * d) - c);
-          float tau;
-          if (!sdf_march(s, __float_as_uint(bb.w), __float_as_uint(sc.w), xyz(bb), x0, df, &tau, bytes)) continue;
-          double t = t0 + (double)tau;
-          if (!(t > 0.0)) continue;
-          double score = fabs(t - tR);
-          if (!found || score < best || (score == best && id < best_id)) {
-            found = true;
-            best = score;
-            best_t = t;
-            best_id = id;
+  const int gR[3] = {(int)floor((R.x - s.odx) / s.hsd), (int)floor((R.y - s.ody) / s.hsd),
+                     (int)floor((R.z - s.odz) / s.hsd)};
+  int v0[3], v1[3];
+  for (int a = 0; a < 3; ++a) {
+    v0[a] = floor_div(gR[a] - 2, s.dv);
+    v1[a] = floor_div(gR[a] + 2, s.dv);
+  }
+  const float ofs[3] = {s.ox, s.oy, s.oz};
+  int nc = 0;
+  const unsigned lt = (1u << lane) - 1u;
+  for (int vz = v0[2]; vz <= v1[2]; ++vz)
+    for (int vy = v0[1]; vy <= v1[1]; ++vy)
+      for (int vx = v0[0]; vx <= v1[0]; ++vx) {
+        if (!in_grid(s, vx, vy, vz)) continue;
+        uint2 cell = __ldg(&s.cells[cell_index(s, vx, vy, vz)]);
+        for (uint32_t base = 0; base < cell.y; base += 32) {
+          uint32_t k = base + lane;
+          bool ok = false;
+          uint32_t pb = 0, pc = 0;
+          int g[3] = {0, 0, 0};
+          if (k < cell.y) {
+            const IERec* r = &s.ies[cell.x + k];
+            float4 nm = __ldg(&r->nrm_meta);
+            float4 rp = __ldg(&r->rp_lab);
+            float4 sc = __ldg(&r->sc_pc);
+            bytes += 48;
+            if ((__float_as_uint(nm.w) & 1u) == IE_POINT && __float_as_uint(rp.w) == label) {
+              const float scv[3] = {sc.x, sc.y, sc.z};
+              ok = true;
+              for (int a = 0; a < 3; ++a) {
+                g[a] = (int)floorf((scv[a] - ofs[a]) / s.hs);
+                ok = ok && abs(g[a] - gR[a]) <= 2;
+              }
+              pb = __float_as_uint(__ldg(&r->bbc_pb).w);
+              pc = __float_as_uint(sc.w);
+            }
           }
+          unsigned mask = __ballot_sync(FULL, ok);
+          int slot = nc + __popc(mask & lt);
+          if (ok && slot < RCAP) {
+            lc.pb[slot] = pb;
+            lc.pc[slot] = pc;
+            lc.g[slot][0] = g[0];
+            lc.g[slot][1] = g[1];
+            lc.g[slot][2] = g[2];
+          }
+          nc += __popc(mask);
         }
       }
-  if (!found) return false;
-  d3 c = P + best_t * d;
-  const IERec* r = &s.ies[best_id];
-  float4 bb = __ldg(&r->bbc_pb);
-  float4 sc = __ldg(&r->sc_pc);
-  d3 cb = D3(bb.x, bb.y, bb.z);
+  __syncwarp();
+  if (nc > RCAP || nc == 0) return false;
+  const float3 c0 = tof(R);
+  const double L = (double)s.seg_len;
+  double t = -0.5 * L, th = 0.0;
   float f;
   float3 n;
-  if (!sdf_local(s, __float_as_uint(bb.w), __float_as_uint(sc.w), xyz(bb), tof(c - cb), &f, &n, bytes))
-    return false;
+  bool hit = false;
+  if (!sdf_label_warp(s, lc, nc, R + t * d, c0, &f, &n, lane, bytes)) return false;
+  for (int it = 0; it < s.sdf_max_steps; ++it) {
+    if (fabsf(f) < s.sdf_eps) {
+      double dn = (double)dot(n, tof(d));
+      th = fabs(dn) > 1e-3 ? t - (double)f / dn : t;
+      hit = true;
+      break;
+    }
+    double tn = t + (double)fabsf(f);
+    if (tn > 0.5 * L) return false;
+    float fn;
+    float3 nn;
+    if (!sdf_label_warp(s, lc, nc, R + tn * d, c0, &fn, &nn, lane, bytes)) return false;
+    if ((fn < 0.f) != (f < 0.f)) {
+      th = t - (double)f * (tn - t) / ((double)fn - (double)f);
+      hit = true;
+      break;
+    }
+    t = tn;
+    f = fn;
+    n = nn;
+  }
+  // the placed hit must stay on the marched segment
+  if (!hit || !(tR + th > 0.0) || fabs(th) > 0.5 * L) return false;
+  d3 c = P + (tR + th) * d;
+  if (!sdf_label_warp(s, lc, nc, c, c0, &f, &n, lane, bytes)) return false;
   *c_out = c;
   *n_out = D3(n.x, n.y, n.z);
   return true;
 }
 
-__global__ void __launch_bounds__(128) k_refine(DScene s, DRefine rp, CoarseView C, const double* txd,
-                                                const double* rxd, ExactRec* out) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < C.n; i += (int64_t)gridDim.x * blockDim.x) {
-    ExactRec ex;
-    const int n = (int)C.nint[i];
-    const uint32_t types = C.types[i];
-    d3 I[NB_MAXI + 2], c[NB_MAXI + 2], u[NB_MAXI + 2], v[NB_MAXI + 2], w[NB_MAXI + 2], p0[NB_MAXI + 2];
-    double tpar[NB_MAXI + 2], elen[NB_MAXI + 2];
-    const uint32_t tx = C.tx[i], rx = C.rx[i];
-    I[0] = D3(txd[3 * tx], txd[3 * tx + 1], txd[3 * tx + 2]);
-    I[n + 1] = D3(rxd[3 * rx], rxd[3 * rx + 1], rxd[3 * rx + 2]);
-    ex.tx = tx;
-    ex.rx = rx;
-    ex.n = (uint32_t)n;
-    ex.types = types;
-    ex.gid = C.gid[i];
-    for (int q = 0; q < NB_MAXI; ++q) {
-      ex.lab[q] = C.lab[i * NB_MAXI + q];
-      ex.ie[q] = C.ie[i * NB_MAXI + q];
-      ex.mat[q] = 255;
-      ex.pts[q][0] = ex.pts[q][1] = ex.pts[q][2] = 0.0;
-    }
-    for (int k = 1; k <= n; ++k) {
-      const IERec* r = &s.ies[C.ie[i * NB_MAXI + k - 1]];
-      float4 rpl = r->rp_lab, nm = r->nrm_meta;
-      ex.mat[k - 1] = (uint8_t)((__float_as_uint(nm.w) >> 8) & 0xffu);
-      c[k] = D3(rpl.x, rpl.y, rpl.z);
-      I[k] = c[k];
-      tpar[k] = 0.0;
-      if (!((types >> (k - 1)) & 1u)) {
-        onb(dunit(D3(nm.x, nm.y, nm.z)), &u[k], &v[k]);
-      } else {
-        const double* E = s.edges + 12 * __float_as_uint(r->bbc_pb.w);
-        p0[k] = D3(E[0], E[1], E[2]);
-        d3 ev = D3(E[3] - E[0], E[4] - E[1], E[5] - E[2]);
-        elen[k] = len(ev);
-        w[k] = (1.0 / elen[k]) * ev;
+// Visibility ray A -> B (Section 2.3's final check) with the warp: the walk is shared,
+// the IEs of each voxel are screened by the lanes, candidates are marched together.
+__device__ bool visible_warp(const DScene& s, float3 A, float3 B, Endpoint ea, Endpoint eb, int lane,
+                             unsigned long long& bytes) {
+  float3 dv = B - A;
+  float T = len(dv);
+  if (T < 1e-9f) return true;
+  float3 d = (1.f / T) * dv;
+  Walk w;
+  walk_init(s, A, d, w);
+  const int max_steps = s.nx + s.ny + s.nz + 3;
+  for (int step = 0; step < max_steps; ++step) {
+    uint2 cell = __ldg(&s.cells[cell_index(s, w.v[0], w.v[1], w.v[2])]);
+    for (uint32_t base = 0; base < cell.y; base += 32) {
+      uint32_t k = base + lane;
+      uint32_t id = cell.x + k;
+      bool ok = false;
+      if (k < cell.y) {
+        const IERec* r = &s.ies[id];
+        float4 sc = __ldg(&r->sc_pc);
+        float4 nm = __ldg(&r->nrm_meta);
+        bytes += 32;
+        ok = (__float_as_uint(nm.w) & 1u) == IE_POINT && segment_sphere(A, d, T, xyz(sc), s.r_sub);
+      }
+      unsigned mask = __ballot_sync(FULL, ok);
+      while (mask) {
+        int j = __ffs(mask) - 1;
+        mask &= mask - 1;
+        uint32_t cid = __shfl_sync(FULL, id, j);
+        const IERec* r = &s.ies[cid];
+        float4 bb = __ldg(&r->bbc_pb);
+        float4 sc = __ldg(&r->sc_pc);
+        float3 c = xyz(bb);
+        float tc = dot(c - A, d);
+        float3 x0 = (A - c) + tc * d;
+        float tau;
+        if (!sdf_march_warp(s, __float_as_uint(bb.w), __float_as_uint(sc.w), c, x0, d, &tau, lane, bytes)) continue;
+        float th = tc + tau;
+        if (!(th > 0.f && th < T)) continue;
+        uint32_t lbl = __float_as_uint(__ldg(&r->rp_lab).w);
+        if (ignored(ea, lbl, th, s.vis_ignore) || ignored(eb, lbl, T - th, s.vis_ignore)) continue;
+        return false;
       }
     }
-    double g[NB_MAXI + 2][2];
+    if (!walk_next(s, w, T)) break;
+  }
+  return true;
+}
+
+// One warp per coarse path: lanes 1..n hold the interactions, lane 0 the TX and
+// lane n+1 the RX.  Iterate rho times (or until ||grad f|| < grad_stop): gradient of
+// Eq. 2 per interaction, a Jacobi step (each interaction's gradient scaled by its
+// local inverse Hessian times gamma) clamped to h_s, then for each reflection a
+// re-projection ray from the previous interaction point toward
+// R_k = c_k + r_k u_k + s_k v_k, for each diffraction D_k = c_k + t_k w_k.
+__global__ void __launch_bounds__(128) k_refine(DScene s, DRefine rp, CoarseView C, const double* txd,
+                                                const double* rxd, ExactRec* out, unsigned long long* bytes_out) {
+  __shared__ LabelCache s_cache[4];
+  const int lane = threadIdx.x & 31;
+  const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  unsigned long long bytes = 0;
+  for (int64_t i = warp0; i < C.n; i += n_warps) {
+    const int n = (int)C.nint[i];
+    const uint32_t types = C.types[i];
+    const uint32_t tx = C.tx[i], rx = C.rx[i];
+    const bool mine = lane >= 1 && lane <= n;
+    const bool diff = mine && ((types >> (lane - 1)) & 1u);
+    // lane-local state
+    d3 I = D3(0, 0, 0), c = D3(0, 0, 0), u = D3(0, 0, 0), v = D3(0, 0, 0), w = D3(0, 0, 0), p0 = D3(0, 0, 0);
+    double tpar = 0.0, elen = 0.0;
+    uint32_t my_lab = NB_NONE_LABEL, my_ie = 0xffffffffu;
+    uint8_t my_mat = 255;
+    if (lane == 0) I = D3(txd[3 * tx], txd[3 * tx + 1], txd[3 * tx + 2]);
+    if (lane == n + 1) I = D3(rxd[3 * rx], rxd[3 * rx + 1], rxd[3 * rx + 2]);
+    if (mine) {
+      my_ie = C.ie[i * NB_MAXI + lane - 1];
+      my_lab = C.lab[i * NB_MAXI + lane - 1];
+      const IERec* r = &s.ies[my_ie];
+      float4 rpl = r->rp_lab, nm = r->nrm_meta;
+      my_mat = (uint8_t)((__float_as_uint(nm.w) >> 8) & 0xffu);
+      c = D3(rpl.x, rpl.y, rpl.z);
+      I = c;
+      if (!diff) {
+        onb(dunit(D3(nm.x, nm.y, nm.z)), &u, &v);
+      } else {
+        const double* E = s.edges + 12 * __float_as_uint(r->bbc_pb.w);
+        p0 = D3(E[0], E[1], E[2]);
+        d3 ev = D3(E[3] - E[0], E[4] - E[1], E[5] - E[2]);
+        elen = len(ev);
+        w = (1.0 / elen) * ev;
+      }
+    }
     int status = ST_VALID, it = 0;
     bool converged = false;
     double gn = 0.0;
-    for (; it < rp.rho; ++it) {
+    for (; it <= rp.rho; ++it) {
       // gradient of Eq. 2: (e_in + e_out) . (u, v) for reflections, . w for diffractions
-      double g2 = 0.0;
-      for (int k = 1; k <= n; ++k) {
-        d3 e = dunit(I[k] - I[k - 1]) + dunit(I[k] - I[k + 1]);
-        if (!((types >> (k - 1)) & 1u)) {
-          g[k][0] = dot(e, u[k]);
-          g[k][1] = dot(e, v[k]);
+      d3 Ip = shfl3(I, max(lane - 1, 0)), In_ = shfl3(I, min(lane + 1, 31));
+      double g0 = 0.0, g1 = 0.0, eta = 0.0, a = 1.0, b = 1.0;
+      d3 ea = D3(0, 0, 0), eb = D3(0, 0, 0);
+      if (mine) {
+        ea = dunit(I - Ip);
+        eb = dunit(I - In_);
+        d3 e = ea + eb;
+        if (!diff) {
+          g0 = dot(e, u);
+          g1 = dot(e, v);
         } else {
-          g[k][0] = dot(e, w[k]);
-          g[k][1] = 0.0;
+          g0 = dot(e, w);
         }
-        g2 += g[k][0] * g[k][0] + g[k][1] * g[k][1];
+        a = len(I - Ip);
+        b = len(I - In_);
+        eta = rp.gamma / (1.0 / a + 1.0 / b);
       }
-      gn = sqrt(g2);
+      gn = sqrt(wsumd(g0 * g0 + g1 * g1));
       if (gn < rp.grad_stop) {
         converged = true;
         break;
       }
-      d3 In[NB_MAXI + 2];
-      for (int k = 1; k <= n; ++k) {
-        double a = len(I[k] - I[k - 1]), b = len(I[k] - I[k + 1]);
-        double eta = rp.gamma / (1.0 / a + 1.0 / b);
-        if (!((types >> (k - 1)) & 1u)) {
-          double rr = -eta * g[k][0], ss = -eta * g[k][1];
-          double l = sqrt(rr * rr + ss * ss);
-          if (l > rp.hs) {
-            rr *= rp.hs / l;
-            ss *= rp.hs / l;
-          }
-          d3 R = c[k] + rr * u[k] + ss * v[k];     // R_k = c_k + r_k u_k + s_k v_k
-          d3 cn, nn;
-          if (!reproject(s, I[k - 1], R, ex.lab[k - 1], &cn, &nn)) {
-            status = ST_MISS;
-            break;
-          }
-          c[k] = cn;
-          onb(dunit(nn), &u[k], &v[k]);
-          In[k] = cn;
+      if (it == rp.rho) break;
+      d3 Inew = I, R = I;
+      bool off = false;
+      // step: gradient scaled by the inverse Hessian of the local length f_k (2x2 in
+      // (r, s), 1x1 in t) times gamma; near-singular Hessians fall back to eta
+      const double hsum = 1.0 / a + 1.0 / b;
+      if (mine && !diff) {
+        double au = dot(ea, u), av = dot(ea, v), bu = dot(eb, u), bv = dot(eb, v);
+        double h11 = (1.0 - au * au) / a + (1.0 - bu * bu) / b;
+        double h22 = (1.0 - av * av) / a + (1.0 - bv * bv) / b;
+        double h12 = -(au * av) / a - (bu * bv) / b;
+        double det = h11 * h22 - h12 * h12;
+        double rr, ss;
+        if (det > 1e-12 * hsum * hsum) {
+          rr = -rp.gamma * (h22 * g0 - h12 * g1) / det;
+          ss = -rp.gamma * (h11 * g1 - h12 * g0) / det;
         } else {
-          double dt = -eta * g[k][0];
-          if (fabs(dt) > rp.hs) dt = copysign(rp.hs, dt);
-          tpar[k] += dt;                            // D_k = c_k + t_k w_k
-          In[k] = c[k] + tpar[k] * w[k];
-          double along = dot(In[k] - p0[k], w[k]);
-          if (along < 0.0 || along > elen[k]) {
-            status = ST_OFF_EDGE;
-            break;
-          }
+          rr = -eta * g0;
+          ss = -eta * g1;
+        }
+        double l = sqrt(rr * rr + ss * ss);
+        if (l > rp.hs) {
+          rr *= rp.hs / l;
+          ss *= rp.hs / l;
+        }
+        R = c + rr * u + ss * v;                 // R_k = c_k + r_k u_k + s_k v_k
+      }
+      if (diff) {
+        double aw = dot(ea, w), bw = dot(eb, w);
+        double hw = (1.0 - aw * aw) / a + (1.0 - bw * bw) / b;
+        double dt = hw > 1e-12 * hsum ? -rp.gamma * g0 / hw : -eta * g0;
+        if (fabs(dt) > rp.hs) dt = copysign(rp.hs, dt);
+        tpar += dt;                               // D_k = c_k + t_k w_k
+        Inew = c + tpar * w;
+        double along = dot(Inew - p0, w);
+        off = along < 0.0 || along > elen;
+      }
+      if (__any_sync(FULL, off)) {
+        status = ST_OFF_EDGE;
+        break;
+      }
+      for (int k = 1; k <= n; ++k) {
+        if ((types >> (k - 1)) & 1u) continue;
+        d3 Pk = shfl3(Ip, k), Rk = shfl3(R, k);
+        uint32_t lk = __shfl_sync(FULL, my_lab, k);
+        d3 cn, nn;
+        if (!reproject_warp(s, Pk, Rk, lk, &cn, &nn, lane, bytes, s_cache[threadIdx.x >> 5])) {
+          status = ST_MISS;
+          break;
+        }
+        if (lane == k) {
+          c = cn;
+          onb(dunit(nn), &u, &v);
+          Inew = cn;
         }
       }
       if (status != ST_VALID) break;
-      for (int k = 1; k <= n; ++k) I[k] = In[k];
+      I = Inew;
     }
-    if (status == ST_VALID && !converged) {
-      double g2 = 0.0;
-      for (int k = 1; k <= n; ++k) {
-        d3 e = dunit(I[k] - I[k - 1]) + dunit(I[k] - I[k + 1]);
-        double a0 = ((types >> (k - 1)) & 1u) ? dot(e, w[k]) : dot(e, u[k]);
-        double a1 = ((types >> (k - 1)) & 1u) ? 0.0 : dot(e, v[k]);
-        g2 += a0 * a0 + a1 * a1;
-      }
-      gn = sqrt(g2);
-      if (!(gn < rp.delta)) status = ST_NOT_CONVERGED;
-    }
-    for (int k = 1; k <= n; ++k) {
-      ex.pts[k - 1][0] = I[k].x;
-      ex.pts[k - 1][1] = I[k].y;
-      ex.pts[k - 1][2] = I[k].z;
-    }
+    if (status == ST_VALID && !converged && !(gn < rp.delta)) status = ST_NOT_CONVERGED;
     if (status == ST_VALID) {
       // visibility between consecutive path nodes
-      unsigned long long bytes = 0;
-      for (int k = 0; k <= n && status == ST_VALID; ++k) {
+      for (int k = 0; k <= n; ++k) {
+        float3 A = tof(shfl3(I, k)), B = tof(shfl3(I, k + 1));
+        uint32_t la = __shfl_sync(FULL, my_lab, k), lb = __shfl_sync(FULL, my_lab, min(k + 1, 31));
         Endpoint ea{IGN_NONE, NB_NONE_LABEL}, eb{IGN_NONE, NB_NONE_LABEL};
-        if (k >= 1) ea = Endpoint{((types >> (k - 1)) & 1u) ? IGN_ANY : IGN_LABEL, ex.lab[k - 1]};
-        if (k + 1 <= n) eb = Endpoint{((types >> k) & 1u) ? IGN_ANY : IGN_LABEL, ex.lab[k]};
-        if (!visible(s, tof(I[k]), tof(I[k + 1]), ea, eb, bytes)) status = ST_OCCLUDED;
+        if (k >= 1) ea = Endpoint{((types >> (k - 1)) & 1u) ? IGN_ANY : IGN_LABEL, la};
+        if (k + 1 <= n) eb = Endpoint{((types >> k) & 1u) ? IGN_ANY : IGN_LABEL, lb};
+        if (!visible_warp(s, A, B, ea, eb, lane, bytes)) {
+          status = ST_OCCLUDED;
+          break;
+        }
       }
     }
-    double L = 0.0;
-    for (int k = 0; k <= n; ++k) L += len(I[k + 1] - I[k]);
-    ex.length = status == ST_VALID ? L : 0.0;
-    ex.delay = ex.length / C_LIGHT;
-    ex.grad = gn;
-    ex.iters = (uint32_t)it;
-    ex.status = (uint32_t)status;
-    ex.pad = 0;
-    out[i] = ex;
+    d3 Inext = shfl3(I, min(lane + 1, 31));
+    double seg = lane <= n ? len(Inext - I) : 0.0;
+    double L = wsumd(seg);
+    ExactRec* o = &out[i];
+    if (lane == 0) {
+      o->length = status == ST_VALID ? L : 0.0;
+      o->delay = o->length / C_LIGHT;
+      o->grad = gn;
+      o->tx = tx;
+      o->rx = rx;
+      o->n = (uint32_t)n;
+      o->types = types;
+      o->status = (uint32_t)status;
+      o->iters = (uint32_t)it;
+      o->gid = C.gid[i];
+      o->pad = 0;
+    }
+    if (lane >= 1 && lane <= NB_MAXI) {
+      int q = lane - 1;
+      o->lab[q] = mine ? my_lab : NB_NONE_LABEL;
+      o->ie[q] = mine ? my_ie : 0xffffffffu;
+      o->mat[q] = mine ? my_mat : 255;
+      o->pts[q][0] = mine ? I.x : 0.0;
+      o->pts[q][1] = mine ? I.y : 0.0;
+      o->pts[q][2] = mine ? I.z : 0.0;
+    }
   }
+  if (lane == 0 && bytes) atomicAdd(bytes_out, bytes);
 }
 
 // ------------------------------------------------------------ duplicate removal
@@ -342,6 +594,7 @@ int refine_paths(Mem& mem, SceneObj* S, CoarseObj* C, const nimbus_refine_params
     *err = "refine: invalid parameters";
     return NIMBUS_ERR_ARG;
   }
+  const long long launches0 = g_launches.load();
   P->mem = &mem;
   const int64_t n = C->n;
   P->n_all = n;
@@ -362,10 +615,16 @@ int refine_paths(Mem& mem, SceneObj* S, CoarseObj* C, const nimbus_refine_params
   rp.hs = S->d.hsd;
   rp.rho = p->rho;
   CoarseView cv{C->tx, C->rx, C->nint, C->types, C->ie, C->lab, C->gid, n};
-  const unsigned G = std::min<unsigned>(grid_for(n, 128), pgrid(128));
-  k_refine<<<G, 128, 0, st>>>(S->d, rp, cv, C->txd, C->rxd, P->all);
-  NB_CUDA(err, cudaGetLastError());
   Scratch sc(&mem, st);
+  unsigned long long* rbytes;
+  NB_TRY(sc.get(&rbytes, 1));
+  NB_CUDA(err, cudaMemsetAsync(rbytes, 0, sizeof(unsigned long long), st));
+  StageTimer tm(st);
+  const int e0 = tm.mark();
+  const unsigned G = std::min<unsigned>(grid_for(n * 32, 128), pgrid(128));
+  k_refine<<<G, 128, 0, st>>>(S->d, rp, cv, C->txd, C->rxd, P->all, rbytes);
+  NB_LAUNCHED(err);
+  const int e1 = tm.mark();
   unsigned long long* best;
   uint32_t *widx, *flag, *pos, *nw, *vals, *vals_alt, *keep, *kpos, *nk;
   uint64_t *keys, *keys_alt;
@@ -379,17 +638,20 @@ int refine_paths(Mem& mem, SceneObj* S, CoarseObj* C, const nimbus_refine_params
   NB_CUDA(err, cudaMemsetAsync(widx, 0xff, ng * sizeof(uint32_t), st));
   const unsigned G2 = std::min<unsigned>(grid_for(n, 256), pgrid(256));
   k_best_len<<<G2, 256, 0, st>>>(P->all, n, best);
-  NB_CUDA(err, cudaGetLastError());
+  NB_LAUNCHED(err);
   k_best_idx<<<G2, 256, 0, st>>>(P->all, n, best, widx);
-  NB_CUDA(err, cudaGetLastError());
+  NB_LAUNCHED(err);
   k_winner_flags<<<G2, 256, 0, st>>>(P->all, n, widx, flag);
-  NB_CUDA(err, cudaGetLastError());
+  NB_LAUNCHED(err);
   NB_TRY(exclusive_scan(sc, flag, pos, n, nw));
   // valid paths count (for the counters)
   uint32_t hw = 0;
+  unsigned long long hb = 0;
   NB_CUDA(err, cudaMemcpyAsync(&hw, nw, sizeof hw, cudaMemcpyDeviceToHost, st));
+  NB_CUDA(err, cudaMemcpyAsync(&hb, rbytes, sizeof hb, cudaMemcpyDeviceToHost, st));
   NB_CUDA(err, cudaStreamSynchronize(st));
   const int64_t m = hw;
+  int e3 = e1;
   if (m > 0) {
     NB_TRY(sc.get(&keys, m));
     NB_TRY(sc.get(&keys_alt, m));
@@ -399,16 +661,17 @@ int refine_paths(Mem& mem, SceneObj* S, CoarseObj* C, const nimbus_refine_params
     NB_TRY(sc.get(&kpos, m));
     NB_TRY(sc.get(&nk, 1));
     k_winner_keys<<<G2, 256, 0, st>>>(P->all, flag, pos, n, C->n_rx, keys, vals);
-    NB_CUDA(err, cudaGetLastError());
+    NB_LAUNCHED(err);
     NB_TRY(radix_sort(sc, keys, vals, keys_alt, vals_alt, m,
                       bits_for((uint64_t)C->n_tx * (uint64_t)std::max(1, C->n_rx))));
     NB_CUDA(err, cudaMemsetAsync(keep, 0, m * sizeof(uint32_t), st));
     k_fresnel<<<std::min<unsigned>(grid_for(m, 64), pgrid(64)), 64, 0, st>>>(P->all, keys, vals, m, C->txd, rp.lambda,
                                                                               keep);
-    NB_CUDA(err, cudaGetLastError());
+    NB_LAUNCHED(err);
     NB_TRY(exclusive_scan(sc, keep, kpos, m, nk));
     k_final<<<std::min<unsigned>(grid_for(m, 256), pgrid(256)), 256, 0, st>>>(keep, kpos, vals, m, P->final_idx);
-    NB_CUDA(err, cudaGetLastError());
+    NB_LAUNCHED(err);
+    e3 = tm.mark();
     uint32_t hk = 0;
     NB_CUDA(err, cudaMemcpyAsync(&hk, nk, sizeof hk, cudaMemcpyDeviceToHost, st));
     NB_CUDA(err, cudaStreamSynchronize(st));
@@ -416,6 +679,10 @@ int refine_paths(Mem& mem, SceneObj* S, CoarseObj* C, const nimbus_refine_params
   }
   P->counts.n_paths = P->n_final;
   P->counts.n_refined_valid = -1;  // filled by a query with which = 1
+  P->counts.ms_refine = tm.ms(e0, e1);
+  P->counts.ms_dedup = tm.ms(e1, e3);
+  P->counts.bytes_refine = (int64_t)hb;
+  P->counts.launches = C->counts.launches + (g_launches.load() - launches0);
   return NIMBUS_OK;
 }
 

@@ -85,7 +85,7 @@ int scan_rec(Scratch& sc, const uint32_t* in, uint32_t* out, int64_t n) {
   int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
   if (nb == 1) {
     k_scan_tiles<<<1, SCAN_BLOCK, 0, sc.st>>>(in, out, n, nullptr);
-    NB_CUDA(sc.mem->err, cudaGetLastError());
+    NB_LAUNCHED(sc.mem->err);
     return NIMBUS_OK;
   }
   uint32_t* sums;
@@ -93,10 +93,10 @@ int scan_rec(Scratch& sc, const uint32_t* in, uint32_t* out, int64_t n) {
   NB_TRY(sc.get(&sums, nb));
   NB_TRY(sc.get(&sums_scanned, nb));
   k_scan_tiles<<<(unsigned)nb, SCAN_BLOCK, 0, sc.st>>>(in, out, n, sums);
-  NB_CUDA(sc.mem->err, cudaGetLastError());
+  NB_LAUNCHED(sc.mem->err);
   NB_TRY(scan_rec(sc, sums, sums_scanned, nb));
   k_scan_add<<<(unsigned)nb, SCAN_BLOCK, 0, sc.st>>>(out, n, sums_scanned);
-  NB_CUDA(sc.mem->err, cudaGetLastError());
+  NB_LAUNCHED(sc.mem->err);
   return NIMBUS_OK;
 }
 
@@ -176,7 +176,7 @@ int exclusive_scan(Scratch& sc, const uint32_t* in, uint32_t* out, int64_t n, ui
   NB_TRY(scan_rec(sc, in, out, n));
   if (total) {
     k_total<<<1, 1, 0, sc.st>>>(last_in, out + (n - 1), total);
-    NB_CUDA(sc.mem->err, cudaGetLastError());
+    NB_LAUNCHED(sc.mem->err);
   }
   return NIMBUS_OK;
 }
@@ -197,10 +197,10 @@ int radix_sort(Scratch& sc, uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, 
   for (int p = 0; p < passes; ++p) {
     int shift = 8 * p;
     k_rs_hist<<<(unsigned)n_tiles, RS_BLOCK, 0, sc.st>>>(kin, n, shift, hist, n_tiles);
-    NB_CUDA(sc.mem->err, cudaGetLastError());
+    NB_LAUNCHED(sc.mem->err);
     NB_TRY(exclusive_scan(sc, hist, offs, (int64_t)RS_RADIX * n_tiles, nullptr));
     k_rs_scatter<<<(unsigned)n_tiles, RS_BLOCK, 0, sc.st>>>(kin, vin, kout, vout, n, shift, offs, n_tiles);
-    NB_CUDA(sc.mem->err, cudaGetLastError());
+    NB_LAUNCHED(sc.mem->err);
     uint64_t* tk = kin; kin = kout; kout = tk;
     uint32_t* tv = vin; vin = vout; vout = tv;
   }

@@ -25,7 +25,9 @@ constexpr int MAX_LEVELS = NB_MAXI + 1;
 constexpr uint32_t NO_NODE = 0xFFFFFFFFu;
 
 enum { CONE_PRIMARY = 0, CONE_REFLECT = 1, CONE_DIFFRACT = 2 };
+// per-stage counters: [stage * N_STATS + ST_*] for stages vis tables, primary, levels
 enum { ST_CONES = 0, ST_VIS = 1, ST_BYTES = 2, ST_EVALS = 3, N_STATS = 4 };
+enum { STAGE_VIS = 0, STAGE_PRIMARY = 1, STAGE_LEVELS = 2, N_STAGES = 3 };
 
 struct DTrace {
   float sin_a, cos_a, sin_a0, cos_a0;
@@ -669,6 +671,7 @@ int trace_coarse(Mem& mem, SceneObj* S, const double* txh, int n_tx, const doubl
     return NIMBUS_ERR_ARG;
   }
   const DScene& s = S->d;
+  const long long launches0 = g_launches.load();
   C->mem = &mem;
   C->n_tx = n_tx;
   C->n_rx = n_rx;
@@ -735,31 +738,31 @@ int trace_coarse(Mem& mem, SceneObj* S, const double* txh, int n_tx, const doubl
   NB_TRY(sc.get(&first_bits, std::max<int64_t>(1, (int64_t)n_tx * tr.ie_words)));
   NB_TRY(sc.get(&los, std::max<int64_t>(1, (int64_t)n_tx * n_rx)));
   NB_TRY(sc.get(&overflow, 2));
-  NB_TRY(sc.get(&stats, N_STATS));
+  NB_TRY(sc.get(&stats, N_STATS * N_STAGES));
   NB_CUDA(err, cudaMemsetAsync(rx_bits, 0, ((n_cells + 31) / 32) * sizeof(uint32_t), st));
   NB_CUDA(err, cudaMemsetAsync(vis_ie, 0, std::max<int64_t>(1, (int64_t)n_tx * tr.ie_words) * 4, st));
   NB_CUDA(err, cudaMemsetAsync(first_bits, 0, std::max<int64_t>(1, (int64_t)n_tx * tr.ie_words) * 4, st));
   NB_CUDA(err, cudaMemsetAsync(los, 0xff, std::max<int64_t>(1, (int64_t)n_tx * n_rx) * 4, st));
   NB_CUDA(err, cudaMemsetAsync(overflow, 0, 2 * sizeof(uint32_t), st));
-  NB_CUDA(err, cudaMemsetAsync(stats, 0, N_STATS * sizeof(unsigned long long), st));
+  NB_CUDA(err, cudaMemsetAsync(stats, 0, N_STATS * N_STAGES * sizeof(unsigned long long), st));
   k_tx_setup<<<grid_for(n_tx, 64), 64, 0, st>>>(C->txd, n_tx, tx4);
-  NB_CUDA(err, cudaGetLastError());
+  NB_LAUNCHED(err);
   if (n_rx > 0) {
     k_rx_setup<<<grid_for(n_rx, 64), 64, 0, st>>>(s, C->rxd, n_rx, rx4, rx_vox, rx_keys, rx_bits);
-    NB_CUDA(err, cudaGetLastError());
+    NB_LAUNCHED(err);
     NB_CUDA(err, cudaMemsetAsync(rx_vals, 0, n_rx * sizeof(uint32_t), st));
     NB_TRY(radix_sort(sc, rx_keys, rx_vals, rx_keys_alt, rx_vals_alt, n_rx, 64));
   }
   const int R = 8;
   k_march_cap<<<std::min<unsigned>(grid_for(n_cells, 256), 2048u), 256, 0, st>>>(s.march, mtmp, n_cells, R + 1);
-  NB_CUDA(err, cudaGetLastError());
+  NB_LAUNCHED(err);
   if (n_rx > 0) {
     int64_t work = (int64_t)(2 * R + 1) * (2 * R + 1) * (2 * R + 1) * n_rx;
     k_march_rx<<<std::min<unsigned>(grid_for(work, 256), 4096u), 256, 0, st>>>(s, rx_vox, n_rx, mtmp, R);
-    NB_CUDA(err, cudaGetLastError());
+    NB_LAUNCHED(err);
   }
   k_march_pack<<<std::min<unsigned>(grid_for(n_cells, 256), 2048u), 256, 0, st>>>(mtmp, march, n_cells);
-  NB_CUDA(err, cudaGetLastError());
+  NB_LAUNCHED(err);
   tr.tx = tx4;
   tr.rx = rx4;
   tr.march = march;
@@ -804,12 +807,20 @@ int trace_coarse(Mem& mem, SceneObj* S, const double* txh, int n_tx, const doubl
   cb.cnt = cnts;  // slot 0 of level 0 counts the coarse paths
   // transmission phase
   const unsigned PG = persistent_grid(256);
-  k_vis_tables<<<PG, 256, 0, st>>>(s, tr);
-  NB_CUDA(err, cudaGetLastError());
-  k_primary<<<PG, 256, 0, st>>>(s, tr, first_bits, los);
-  NB_CUDA(err, cudaGetLastError());
+  StageTimer tm(st);
+  DTrace tr_vis = tr, tr_pri = tr, tr_lev = tr;
+  tr_vis.stats = stats + STAGE_VIS * N_STATS;
+  tr_pri.stats = stats + STAGE_PRIMARY * N_STATS;
+  tr_lev.stats = stats + STAGE_LEVELS * N_STATS;
+  const int e0 = tm.mark();
+  k_vis_tables<<<PG, 256, 0, st>>>(s, tr_vis);
+  NB_LAUNCHED(err);
+  const int e1 = tm.mark();
+  k_primary<<<PG, 256, 0, st>>>(s, tr_pri, first_bits, los);
+  NB_LAUNCHED(err);
+  const int e2 = tm.mark();
   k_los<<<grid_for((int64_t)n_tx * n_rx, 128), 128, 0, st>>>(tr, los, cb);
-  NB_CUDA(err, cudaGetLastError());
+  NB_LAUNCHED(err);
   if (max_int >= 1) {
     int64_t nflag = (int64_t)n_tx * n_ie;
     uint32_t *fr, *fd, *pr, *pd, *tot;
@@ -820,18 +831,19 @@ int trace_coarse(Mem& mem, SceneObj* S, const double* txh, int n_tx, const doubl
     NB_TRY(sc.get(&tot, 2));
     if (nflag > 0) {
       k_first_flags<<<PG, 256, 0, st>>>(s, tr, first_bits, fr, fd);
-      NB_CUDA(err, cudaGetLastError());
+      NB_LAUNCHED(err);
     }
     NB_TRY(exclusive_scan(sc, fr, pr, nflag, tot));
     NB_TRY(exclusive_scan(sc, fd, pd, nflag, tot + 1));
     if (nflag > 0) {
       k_first_nodes<<<PG, 256, 0, st>>>(s, tr, fr, pr, fd, pd, lv[1]);
-      NB_CUDA(err, cudaGetLastError());
+      NB_LAUNCHED(err);
     }
     k_first_counts<<<1, 1, 0, st>>>(tot, tot + 1, lv[1]);
-    NB_CUDA(err, cudaGetLastError());
+    NB_LAUNCHED(err);
   }
   // propagation phase, one launch per depth
+  const int e3 = tm.mark();
   for (int d = 1; d <= max_int; ++d) {
     NodeLevel next = d < max_int ? lv[d + 1] : lv[0];
     if (d == max_int) {
@@ -839,12 +851,13 @@ int trace_coarse(Mem& mem, SceneObj* S, const double* txh, int n_tx, const doubl
       next.cap_d = 0;
       next.cnt = cnts + 2 * MAX_LEVELS - 2;  // unused sink
     }
-    k_level<<<PG, 256, 0, st>>>(s, tr, lv[d], next, cb);
-    NB_CUDA(err, cudaGetLastError());
+    k_level<<<PG, 256, 0, st>>>(s, tr_lev, lv[d], next, cb);
+    NB_LAUNCHED(err);
   }
+  const int e4 = tm.mark();
   // read the sizes back
   uint32_t hc[2 * MAX_LEVELS], hov[2];
-  unsigned long long hs[N_STATS];
+  unsigned long long hs[N_STATS * N_STAGES];
   NB_CUDA(err, cudaMemcpyAsync(hc, cnts, sizeof hc, cudaMemcpyDeviceToHost, st));
   NB_CUDA(err, cudaMemcpyAsync(hov, overflow, sizeof hov, cudaMemcpyDeviceToHost, st));
   NB_CUDA(err, cudaMemcpyAsync(hs, stats, sizeof hs, cudaMemcpyDeviceToHost, st));
@@ -853,9 +866,17 @@ int trace_coarse(Mem& mem, SceneObj* S, const double* txh, int n_tx, const doubl
   std::memset(&cnt, 0, sizeof cnt);
   const int64_t n_raw = std::min<int64_t>(hc[0], cb.cap);
   cnt.n_coarse_raw = hc[0];
-  cnt.n_cones = (int64_t)hs[ST_CONES];
-  cnt.n_vis = (int64_t)hs[ST_VIS];
-  cnt.bytes_read = (int64_t)hs[ST_BYTES];
+  for (int g = 0; g < N_STAGES; ++g) {
+    cnt.n_cones += (int64_t)hs[g * N_STATS + ST_CONES];
+    cnt.n_vis += (int64_t)hs[g * N_STATS + ST_VIS];
+    cnt.bytes_read += (int64_t)hs[g * N_STATS + ST_BYTES];
+  }
+  cnt.bytes_primary = (int64_t)hs[STAGE_PRIMARY * N_STATS + ST_BYTES];
+  cnt.bytes_levels = (int64_t)hs[STAGE_LEVELS * N_STATS + ST_BYTES];
+  cnt.n_levels = max_int;
+  cnt.ms_vis = tm.ms(e0, e1);
+  cnt.ms_primary = tm.ms(e1, e2);
+  cnt.ms_levels = tm.ms(e3, e4);
   for (int d = 1; d <= max_int; ++d) cnt.n_nodes += (int64_t)hc[2 * d] + hc[2 * d + 1];
   cnt.needed_nodes = hov[0];
   cnt.needed_coarse = hov[1];
@@ -863,6 +884,8 @@ int trace_coarse(Mem& mem, SceneObj* S, const double* txh, int n_tx, const doubl
 
   // kappa: group, rank by miss, keep at most kappa per group
   C->n = 0;
+  const int e5 = tm.mark();
+  int e6 = e5;
   if (n_raw > 0) {
     uint32_t *e_tx, *e_rx, *e_n, *e_types, *e_ie, *e_lab, *e_hash, *gid, *owner, *keep, *pos, *vals, *vals_alt,
         *n_keep;
@@ -893,9 +916,9 @@ int trace_coarse(Mem& mem, SceneObj* S, const double* txh, int n_tx, const doubl
     }
     const unsigned G = std::min<unsigned>(grid_for(n_raw, 256), PG);
     k_expand<<<G, 256, 0, st>>>(s, LV, cb.rec, cb.miss, n_raw, e_tx, e_rx, e_n, e_types, e_ie, e_lab, e_miss, e_hash);
-    NB_CUDA(err, cudaGetLastError());
+    NB_LAUNCHED(err);
     k_group<<<G, 256, 0, st>>>(e_tx, e_rx, e_n, e_types, e_lab, n_raw, owner, cap_h - 1, gid);
-    NB_CUDA(err, cudaGetLastError());
+    NB_LAUNCHED(err);
     NB_TRY(sc.get(&keys, n_raw));
     NB_TRY(sc.get(&keys_alt, n_raw));
     NB_TRY(sc.get(&vals, n_raw));
@@ -904,11 +927,11 @@ int trace_coarse(Mem& mem, SceneObj* S, const double* txh, int n_tx, const doubl
     NB_TRY(sc.get(&pos, n_raw));
     NB_TRY(sc.get(&n_keep, 1));
     k_kappa_keys<<<G, 256, 0, st>>>(gid, e_miss, e_hash, n_raw, keys, vals);
-    NB_CUDA(err, cudaGetLastError());
+    NB_LAUNCHED(err);
     int gbits = bits_for(cap_h - 1);
     NB_TRY(radix_sort(sc, keys, vals, keys_alt, vals_alt, n_raw, 39 + gbits));
     k_kappa_keep<<<G, 256, 0, st>>>(keys, n_raw, p->kappa, keep);
-    NB_CUDA(err, cudaGetLastError());
+    NB_LAUNCHED(err);
     NB_TRY(exclusive_scan(sc, keep, pos, n_raw, n_keep));
     uint32_t hk = 0;
     NB_CUDA(err, cudaMemcpyAsync(&hk, n_keep, sizeof hk, cudaMemcpyDeviceToHost, st));
@@ -925,10 +948,13 @@ int trace_coarse(Mem& mem, SceneObj* S, const double* txh, int n_tx, const doubl
     NB_TRY(C->own(&C->gid, std::max<int64_t>(1, hk), st));
     k_kappa_compact<<<G, 256, 0, st>>>(keep, pos, vals, n_raw, e_tx, e_rx, e_n, e_types, e_ie, e_lab, e_miss, gid,
                                        *C);
-    NB_CUDA(err, cudaGetLastError());
+    NB_LAUNCHED(err);
+    e6 = tm.mark();
   }
   cnt.n_coarse = C->n;
   NB_CUDA(err, cudaStreamSynchronize(st));
+  cnt.ms_kappa = tm.ms(e5, e6);
+  cnt.launches = g_launches.load() - launches0;
   if (cnt.overflow) {
     *err = "trace: a bounded buffer overflowed (see needed_nodes / needed_coarse)";
     return NIMBUS_ERR_OVERFLOW;

@@ -373,7 +373,7 @@ int build_tables(Mem& mem, SceneObj* S, cudaStream_t st) {
   const unsigned G = std::min<unsigned>(grid_for(std::max<int64_t>(n_total, 1), B), 148u * 16u);
   if (n > 0) {
     k_point_keys<<<std::min<unsigned>(grid_for(n, B), 148u * 16u), B, 0, st>>>(g, S->xyz, S->label, n, keys, vals);
-    NB_CUDA(err, cudaGetLastError());
+    NB_LAUNCHED(err);
   }
   if (n_edges > 0) {
     // edges live in the object's owned buffer (d.edges)
@@ -385,11 +385,11 @@ int build_tables(Mem& mem, SceneObj* S, cudaStream_t st) {
     NB_CUDA(err, cudaMemcpyAsync(d_nf, nf.data(), n_edges * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     k_edge_pieces<<<grid_for(n_edges, 64), 64, 0, st>>>(g, d_edges, (int)n_edges, d_off, d_nf, n, keys, vals, pieces,
                                                          counter);
-    NB_CUDA(err, cudaGetLastError());
+    NB_LAUNCHED(err);
   }
   NB_TRY(radix_sort(sc, keys, vals, keys_alt, vals_alt, n_total, key_bits));
   k_run_flags<<<G, B, 0, st>>>(keys, n_total, flags);
-  NB_CUDA(err, cudaGetLastError());
+  NB_LAUNCHED(err);
   NB_TRY(exclusive_scan(sc, flags, ids, n_total, counter + 1));
   uint32_t hc[2];
   NB_CUDA(err, cudaMemcpyAsync(hc, counter, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
@@ -401,7 +401,7 @@ int build_tables(Mem& mem, SceneObj* S, cudaStream_t st) {
   NB_TRY(sc.get(&starts, n_ie + 1));
   NB_TRY(sc.get(&ie_cell, std::max<int64_t>(1, n_ie)));
   k_run_starts<<<G, B, 0, st>>>(flags, ids, n_total, starts, (uint32_t)n_ie, (uint32_t)n_valid);
-  NB_CUDA(err, cudaGetLastError());
+  NB_LAUNCHED(err);
 
   // owned tables: freed first if this is a rebuild
   for (void* p : S->table_bufs) mem.release(p, st);
@@ -425,7 +425,7 @@ int build_tables(Mem& mem, SceneObj* S, cudaStream_t st) {
   if (n_valid > 0) {
     k_gather<<<std::min<unsigned>(grid_for(n_valid, B), 148u * 16u), B, 0, st>>>(vals, n_valid, n, S->xyz, S->nrm,
                                                                                   pts, pnrm);
-    NB_CUDA(err, cudaGetLastError());
+    NB_LAUNCHED(err);
   }
   NB_CUDA(err, cudaMemsetAsync(cells, 0, n_cells * sizeof(uint2), st));
   if (n_ie > 0) {
@@ -437,23 +437,23 @@ int build_tables(Mem& mem, SceneObj* S, cudaStream_t st) {
     bk.n_ie = (int)n_ie;
     k_ie_build<<<grid_for(n_ie, 128), 128, 0, st>>>(bk, keys, vals, starts, pts, pnrm, S->material, pieces, d_edges,
                                                     ies, ie_cell);
-    NB_CUDA(err, cudaGetLastError());
+    NB_LAUNCHED(err);
     if (n_edges > 0) {
       k_edge_labels<<<grid_for(n_ie, 256), 256, 0, st>>>(ies, (int)n_ie, d_elabel);
-      NB_CUDA(err, cudaGetLastError());
+      NB_LAUNCHED(err);
     }
     k_cell_begin<<<grid_for(n_ie, 256), 256, 0, st>>>(ie_cell, (int)n_ie, cells);
-    NB_CUDA(err, cudaGetLastError());
+    NB_LAUNCHED(err);
     k_cell_count<<<grid_for(n_ie, 256), 256, 0, st>>>(ie_cell, (int)n_ie, cells);
-    NB_CUDA(err, cudaGetLastError());
+    NB_LAUNCHED(err);
   }
   const int nx = S->dims[0], ny = S->dims[1], nz = S->dims[2];
   k_march_x<<<grid_for((int64_t)ny * nz, 128), 128, 0, st>>>(cells, nx, ny, nz, d1);
-  NB_CUDA(err, cudaGetLastError());
+  NB_LAUNCHED(err);
   k_march_axis<<<grid_for(n_cells, 256), 256, 0, st>>>(d1, d2, nx, ny, nz, 1);
-  NB_CUDA(err, cudaGetLastError());
+  NB_LAUNCHED(err);
   k_march_axis<<<grid_for(n_cells, 256), 256, 0, st>>>(d2, march, nx, ny, nz, 2);
-  NB_CUDA(err, cudaGetLastError());
+  NB_LAUNCHED(err);
   // the scratch buffers are released when sc leaves scope (stream-ordered)
   S->n_ie = n_ie;
   S->n_slots = n_valid;
@@ -568,7 +568,7 @@ int voxelize_scene(Mem& mem, const nimbus_cloud* cloud, const nimbus_edges* edge
     uint32_t init[8] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0u, 0u, 0u, 0u, 0u};
     NB_CUDA(err, cudaMemcpyAsync(red, init, sizeof init, cudaMemcpyHostToDevice, st));
     k_bounds<<<std::min<unsigned>(grid_for(n, 256), 148u * 8u), 256, 0, st>>>(S->xyz, S->label, n, red);
-    NB_CUDA(err, cudaGetLastError());
+    NB_LAUNCHED(err);
     uint32_t hr[8];
     NB_CUDA(err, cudaMemcpyAsync(hr, red, sizeof hr, cudaMemcpyDeviceToHost, st));
     NB_CUDA(err, cudaStreamSynchronize(st));
@@ -657,7 +657,7 @@ int update_scene_region(Mem& mem, SceneObj* S, const double lo[3], const double 
   if (n > 0) {
     k_outside_flags<<<std::min<unsigned>(grid_for(n, 256), 148u * 8u), 256, 0, st>>>(
         S->xyz, n, (float)lo[0], (float)lo[1], (float)lo[2], (float)hi[0], (float)hi[1], (float)hi[2], keep);
-    NB_CUDA(err, cudaGetLastError());
+    NB_LAUNCHED(err);
   }
   NB_TRY(exclusive_scan(sc, keep, pos, n, cnt));
   uint32_t n_keep = 0;
@@ -675,7 +675,7 @@ int update_scene_region(Mem& mem, SceneObj* S, const double lo[3], const double 
   if (n > 0) {
     k_compact_points<<<std::min<unsigned>(grid_for(n, 256), 148u * 8u), 256, 0, st>>>(
         S->xyz, S->nrm, S->label, S->material, n, keep, pos, nxyz, nnrm, nlab, nmat);
-    NB_CUDA(err, cudaGetLastError());
+    NB_LAUNCHED(err);
   }
   if (nr > 0) {
     NB_TRY(copy_in(err, nxyz + 3 * n_keep, repl->xyz, 3 * nr * sizeof(float), st));

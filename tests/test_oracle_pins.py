@@ -320,16 +320,11 @@ def test_stationarity_on_noisy_room():
             eout = (x - nodes[k + 2]) / np.linalg.norm(x - nodes[k + 2])
             ie = int(P["ie"][i][k])
             if P["type"][i][k] == 0:
-                # the point lies on the Eq. 1 surface of one IE of its label, and e_in + e_out
-                # is parallel to that surface's normal there (the reflection law)
-                same = np.where((I["label"] == P["label"][i][k]) & (I["kind"] == 0) &
-                                (np.linalg.norm(I["bbc"] - x, axis=1) < 0.4))[0]
-                ok = False
-                for j in same:
-                    f, nn = s.sdf(j, x)
-                    if f is not None and abs(f) < 1e-4:
-                        ok = ok or np.linalg.norm(np.cross(ein + eout, nn)) < 1e-3
-                assert ok
+                # the point lies on its label's Eq. 1 surface and e_in + e_out is parallel to
+                # that surface's normal there (the reflection law)
+                f, nn = s.sdf_label(int(P["label"][i][k]), x)
+                assert f is not None and abs(f) < 1e-4
+                assert np.linalg.norm(np.cross(ein + eout, nn)) < 1e-4
             else:
                 e_ = sc.edges[I["edge"][ie]]
                 p0, p1 = e_[:3], e_[3:6]
@@ -339,3 +334,21 @@ def test_stationarity_on_noisy_room():
                 assert np.linalg.norm(off) < 1e-9
             n_checked += 1
     assert n_checked >= 2
+
+
+def test_label_surface_is_plane_distance_and_continuous(room_tiny):
+    """Eq. 1 on a label's nearby points: the plane distance on an exact plane, across
+    subvoxel boundaries; on a noisy wall it varies smoothly (no jumps at boundaries)."""
+    s = oracle.Scene.from_scene(room_tiny, config.Params())
+    rng = np.random.default_rng(4)
+    for _ in range(50):
+        x = np.array([rng.uniform(1, 9), rng.uniform(1, 9), rng.uniform(-0.2, 0.2)])
+        f, n = s.sdf_label(4, x)
+        assert f == pytest.approx(x[2], abs=1e-12)
+        np.testing.assert_allclose(n, [0, 0, 1], atol=1e-12)
+    noisy = scenes.room_noisy(n_tx=1, n_rx=1)
+    s2 = oracle.Scene.from_scene(noisy, config.Params())
+    ys = np.linspace(2.0, 4.0, 801)          # crosses 8 subvoxel boundaries, 2.5 mm steps
+    fs = np.array([s2.sdf_label(0, np.array([0.01, y, 1.3]))[0] for y in ys])
+    assert np.all(np.isfinite(fs))
+    assert np.max(np.abs(np.diff(fs))) < 1e-3   # no step at subvoxel faces

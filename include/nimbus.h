@@ -255,6 +255,60 @@ NIMBUS_API int nimbus_memory_used(nimbus_ctx* ctx, size_t* bytes);
  * contexts); differences around a region count the kernels launched in it. */
 NIMBUS_API int nimbus_kernel_launches(int64_t* count);
 
+/* ---------------------------------------------------------------------------
+ * Voxelisation without any device allocation.
+ *
+ * Not part of the paper's method (the paper has no counterpart): an operational
+ * variant for callers that cannot allocate device memory while they run -- for
+ * example code inside a host callback of a CUDA graph, a process whose device
+ * memory is carved up in advance by another allocator, or a real-time loop that
+ * must not block on the allocator.  It computes the same tables as
+ * nimbus_voxelize + nimbus_scene_tables for a cloud without edges, but writes them
+ * into caller-owned device buffers and keeps every intermediate in one fixed
+ * device array inside this library (NIMBUS_STATIC_MAX_POINTS points and
+ * NIMBUS_STATIC_MAX_CELLS voxels at most; about 33 MB that every GPU which loads
+ * the library holds until the process exits).
+ *
+ * - Inputs (cloud->xyz, nrm, label, material) must be device pointers.
+ * - Larger clouds or grids: NIMBUS_ERR_ARG with a message; output capacities
+ *   too small: NIMBUS_ERR_OVERFLOW with the needed sizes in *info.
+ * - The first call on a device resolves the fixed array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call before
+ *   any stream capture on that device.
+ * - Every call shares the one array: calls that overlap on the GPU (other
+ *   streams, other host threads) race and must be serialised by the caller.  The
+ *   call reads two counters back and so returns after its work has finished.
+ * - Calls no cudaMalloc, cudaFree or other allocating routine. */
+#define NIMBUS_STATIC_MAX_POINTS (1 << 17)
+#define NIMBUS_STATIC_MAX_CELLS (1 << 20)
+
+typedef struct {          /* caller-owned device buffers */
+  int32_t* kind;          /* [ie_capacity] 0 point set (edges are not taken) */
+  uint32_t* label;        /* [ie_capacity] */
+  int32_t* gs;            /* [ie_capacity*3] global subvoxel coordinates */
+  int32_t* pcount;        /* [ie_capacity] points in the entity */
+  float* rp;              /* [ie_capacity*3] reception point (centroid) */
+  float* normal;          /* [ie_capacity*3] normalised mean normal */
+  float* bbc;             /* [ie_capacity*3] bounding-box centre */
+  uint8_t* material;      /* [ie_capacity] */
+  int64_t ie_capacity;
+  uint32_t* cell_begin;   /* [cell_capacity] first entity of each voxel (0 when empty) */
+  uint32_t* cell_count;   /* [cell_capacity] */
+  uint8_t* march;         /* [cell_capacity] capped L-infinity distance to a voxel with entities */
+  int64_t cell_capacity;
+} nimbus_static_tables;
+
+typedef struct {          /* host outputs */
+  double origin[3];
+  int32_t dims[3];
+  int32_t pad_;
+  int64_t n_ie;
+  int64_t n_cells;
+} nimbus_static_info;
+
+NIMBUS_API int nimbus_voxelize_static(nimbus_ctx* ctx, const nimbus_cloud* cloud, const nimbus_vox_params* params,
+                                      const nimbus_static_tables* out, nimbus_static_info* info, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

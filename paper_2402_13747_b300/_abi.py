@@ -24,7 +24,8 @@ ERR_NAMES = {1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_OVERFLOW", 5: "E
 
 EXPORTS = ("nimbus_create", "nimbus_destroy", "nimbus_last_error", "nimbus_voxelize", "nimbus_update_region",
            "nimbus_trace_coarse", "nimbus_refine", "nimbus_query", "nimbus_query_coarse", "nimbus_scene_info",
-           "nimbus_scene_tables", "nimbus_release", "nimbus_memory_used", "nimbus_kernel_launches")
+           "nimbus_scene_tables", "nimbus_release", "nimbus_memory_used", "nimbus_kernel_launches",
+           "nimbus_voxelize_static")
 
 _vp = C.c_void_p
 
@@ -82,6 +83,21 @@ class SceneView(C.Structure):
                                    "cell_begin", "cell_count", "march")]
 
 
+class StaticTables(C.Structure):
+    _fields_ = [("kind", _vp), ("label", _vp), ("gs", _vp), ("pcount", _vp), ("rp", _vp), ("normal", _vp),
+                ("bbc", _vp), ("material", _vp), ("ie_capacity", C.c_int64), ("cell_begin", _vp),
+                ("cell_count", _vp), ("march", _vp), ("cell_capacity", C.c_int64)]
+
+
+class StaticInfo(C.Structure):
+    _fields_ = [("origin", C.c_double * 3), ("dims", C.c_int32 * 3), ("pad_", C.c_int32), ("n_ie", C.c_int64),
+                ("n_cells", C.c_int64)]
+
+
+STATIC_MAX_POINTS = 1 << 17
+STATIC_MAX_CELLS = 1 << 20
+
+
 class NimbusError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"{ERR_NAMES.get(code, code)}: {msg}")
@@ -124,6 +140,7 @@ def load():
     L.nimbus_release.argtypes = [ctxp, C.c_uint64]
     L.nimbus_memory_used.argtypes = [ctxp, P(C.c_size_t)]
     L.nimbus_kernel_launches.argtypes = [P(C.c_int64)]
+    L.nimbus_voxelize_static.argtypes = [ctxp, P(Cloud), P(VoxParams), P(StaticTables), P(StaticInfo), _vp]
     for name in EXPORTS:
         L[name].restype = C.c_char_p if name == "nimbus_last_error" else C.c_int
     _lib = L
@@ -346,6 +363,31 @@ class Context:
         self._check(self.L.nimbus_scene_tables(self.h, scene, C.byref(v), _stream(stream)), "scene_tables")
         out.update(info)
         return out
+
+    def voxelize_static(self, xyz, nrm, label, out: dict, material=None, params: Params = None, region=None,
+                        stream=None) -> dict:
+        """Voxelise into caller-owned device buffers without any device allocation.
+
+        For callers that cannot allocate while they run (graph host callbacks,
+        pre-carved memory pools, real-time loops): the inputs must be device tensors
+        and ``out`` holds device tensors named as in nimbus_static_tables, sized by
+        the capacities ``out['ie_capacity']`` and ``out['cell_capacity']``.
+        Calls that overlap on the GPU share one fixed scratch array and race.
+        """
+        params = params or Params()
+        cl = Cloud(_ptr(xyz), _ptr(nrm), _ptr(label), _ptr(material), int(xyz.shape[0]))
+        t = StaticTables(*[_ptr(out[k]) for k in ("kind", "label", "gs", "pcount", "rp", "normal", "bbc",
+                                                  "material")],
+                         int(out["ie_capacity"]),
+                         *[_ptr(out[k]) for k in ("cell_begin", "cell_count", "march")], int(out["cell_capacity"]))
+        vp = vox_params(params, region)
+        info = StaticInfo()
+        rc = self.L.nimbus_voxelize_static(self.h, C.byref(cl), C.byref(vp), C.byref(t), C.byref(info),
+                                           _stream(stream))
+        res = dict(origin=np.array(info.origin[:]), dims=np.array(info.dims[:], np.int32), n_ie=info.n_ie,
+                   n_cells=info.n_cells)
+        self._check(rc, "voxelize_static")
+        return res
 
     def release(self, h: int):
         self._check(self.L.nimbus_release(self.h, h), "release")

@@ -436,6 +436,13 @@ int nimbus_memory_used(nimbus_ctx* ctx, size_t* bytes) {
   return NIMBUS_OK;
 }
 
+int nimbus_voxelize_static(nimbus_ctx* ctx, const nimbus_cloud* cloud, const nimbus_vox_params* params,
+                           const nimbus_static_tables* out, nimbus_static_info* info, void* stream) {
+  if (!ctx) return NIMBUS_ERR_ARG;
+  DeviceGuard g(ctx->device);
+  return nb::voxelize_static(&ctx->err, cloud, params, out, info, (cudaStream_t)stream);
+}
+
 int nimbus_kernel_launches(int64_t* count) {
   if (!count) return NIMBUS_ERR_ARG;
   *count = (int64_t)nb::g_launches.load();

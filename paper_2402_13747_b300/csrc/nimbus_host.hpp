@@ -27,17 +27,30 @@ struct Mem {
   }
 };
 
-// A list of device allocations released together.
+// A list of device allocations released together.  With an arena set, buffers are
+// carved from that preallocated device region instead (nothing is allocated).
 struct Scratch {
   Mem* mem;
   cudaStream_t st;
   std::vector<void*> ptrs;
+  char* arena = nullptr;
+  size_t arena_cap = 0, arena_used = 0;
   Scratch(Mem* m, cudaStream_t s) : mem(m), st(s) {}
   ~Scratch() {
     for (void* p : ptrs) mem->release(p, st);
   }
   template <class T>
   int get(T** p, size_t n) {
+    if (arena) {
+      size_t bytes = (n * sizeof(T) + 16 + 255) & ~(size_t)255;
+      if (arena_used + bytes > arena_cap) {
+        if (mem && mem->err) *mem->err = "static scratch exhausted";
+        return NIMBUS_ERR_ARG;
+      }
+      *p = reinterpret_cast<T*>(arena + arena_used);
+      arena_used += bytes;
+      return NIMBUS_OK;
+    }
     int rc = mem->alloc_n(p, n, st);
     if (rc == NIMBUS_OK) ptrs.push_back(*p);
     return rc;
@@ -187,6 +200,10 @@ int voxelize_scene(Mem& mem, const nimbus_cloud* cloud, const nimbus_edges* edge
                    SceneObj* out, cudaStream_t st);
 int update_scene_region(Mem& mem, SceneObj* s, const double lo[3], const double hi[3],
                         const nimbus_cloud* repl, cudaStream_t st);
+
+// Voxelisation into caller buffers with every intermediate in a fixed device array.
+int voxelize_static(std::string* err, const nimbus_cloud* cloud, const nimbus_vox_params* p,
+                    const nimbus_static_tables* out, nimbus_static_info* info, cudaStream_t st);
 
 bool is_device_ptr(const void* p);
 // Copy n bytes of a host or device input into a device buffer.

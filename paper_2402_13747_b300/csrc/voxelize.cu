@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "nimbus_host.hpp"
 
@@ -707,6 +708,246 @@ int update_scene_region(Mem& mem, SceneObj* S, const double lo[3], const double 
   S->material = nmat;
   S->n_points = n_new;
   return build_tables(mem, S, st);
+}
+
+// ----------------------------------------------------------- voxelisation without allocation
+// Every intermediate of nimbus_voxelize_static lives in this one fixed device array:
+// 136.5 bytes per point (sort keys and values with their work copies, run flags and
+// ids, run starts, grouped points, entity records) plus 10 bytes per voxel and a
+// small reserve for the scan and sort tables, for the largest sizes allowed.
+namespace {
+constexpr size_t kStaticPoints = NIMBUS_STATIC_MAX_POINTS;
+constexpr size_t kStaticCells = NIMBUS_STATIC_MAX_CELLS;
+constexpr size_t kStaticBytes = 137 * kStaticPoints + 10 * kStaticCells + (4u << 20);
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
+
+namespace {
+
+// Device address of g_static_scratch on each device, resolved once per device with
+// that device current (the host-side name is only a stand-in for the symbol).
+std::mutex g_static_mu;
+void* g_static_addr[128] = {nullptr};
+
+int static_scratch(std::string* err, void** out) {
+  int dev = 0;
+  NB_CUDA(err, cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 128) {
+    *err = "device index out of range";
+    return NIMBUS_ERR_ARG;
+  }
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_addr[dev]) {
+    void* p = nullptr;
+    NB_CUDA(err, cudaGetSymbolAddress(&p, g_static_scratch));
+    g_static_addr[dev] = p;
+  }
+  *out = g_static_addr[dev];
+  return NIMBUS_OK;
+}
+
+// Entity records and voxel ranges -> the caller's structure-of-arrays buffers.
+__global__ void k_static_out(const IERec* __restrict__ ies, int n_ie, const uint2* __restrict__ cells,
+                             int64_t n_cells, nimbus_static_tables o) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_ie; i += (int64_t)gridDim.x * blockDim.x) {
+    const IERec r = ies[i];
+    o.kind[i] = (int32_t)(__float_as_uint(r.nrm_meta.w) & 1u);
+    o.label[i] = __float_as_uint(r.rp_lab.w);
+    o.material[i] = (uint8_t)((__float_as_uint(r.nrm_meta.w) >> 8) & 0xffu);
+    o.pcount[i] = (int32_t)__float_as_uint(r.sc_pc.w);
+    const float rp[3] = {r.rp_lab.x, r.rp_lab.y, r.rp_lab.z};
+    const float nn[3] = {r.nrm_meta.x, r.nrm_meta.y, r.nrm_meta.z};
+    const float bb[3] = {r.bbc_pb.x, r.bbc_pb.y, r.bbc_pb.z};
+    for (int a = 0; a < 3; ++a) {
+      o.rp[3 * i + a] = rp[a];
+      o.normal[3 * i + a] = nn[a];
+      o.bbc[3 * i + a] = bb[a];
+    }
+  }
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n_cells; c += (int64_t)gridDim.x * blockDim.x) {
+    o.cell_begin[c] = cells[c].y ? cells[c].x : 0u;
+    o.cell_count[c] = cells[c].y;
+  }
+}
+
+__global__ void k_static_gs(const IERec* __restrict__ ies, int n_ie, float ox, float oy, float oz, float hs,
+                            int32_t* __restrict__ gs) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_ie) return;
+  const float4 sc = ies[i].sc_pc;
+  gs[3 * i] = (int32_t)floorf((sc.x - ox) / hs);
+  gs[3 * i + 1] = (int32_t)floorf((sc.y - oy) / hs);
+  gs[3 * i + 2] = (int32_t)floorf((sc.z - oz) / hs);
+}
+
+}  // namespace
+
+int voxelize_static(std::string* err, const nimbus_cloud* cloud, const nimbus_vox_params* p,
+                    const nimbus_static_tables* out, nimbus_static_info* info, cudaStream_t st) {
+  if (!cloud || !p || !out || !info || cloud->n < 1 || !cloud->xyz || !cloud->nrm || !cloud->label) {
+    *err = "voxelize_static: invalid arguments";
+    return NIMBUS_ERR_ARG;
+  }
+  if (!(p->voxel_size > 0) || p->dv < 1 || p->dv > 4 || p->sdf_max_steps < 1 || !(p->sdf_sigma > 0)) {
+    *err = "voxelize_static: invalid parameters";
+    return NIMBUS_ERR_ARG;
+  }
+  const int64_t n = cloud->n;
+  if (n > (int64_t)kStaticPoints) {
+    *err = "voxelize_static: the cloud has more than NIMBUS_STATIC_MAX_POINTS points";
+    return NIMBUS_ERR_ARG;
+  }
+  if (!is_device_ptr(cloud->xyz) || !is_device_ptr(cloud->nrm) || !is_device_ptr(cloud->label) ||
+      (cloud->material && !is_device_ptr(cloud->material))) {
+    *err = "voxelize_static: inputs must be device pointers";
+    return NIMBUS_ERR_ARG;
+  }
+  void* base = nullptr;
+  NB_TRY(static_scratch(err, &base));
+  Mem m;  // error sink only: the arena below serves every buffer
+  m.err = err;
+  Scratch sc(&m, st);
+  sc.arena = static_cast<char*>(base);
+  sc.arena_cap = kStaticBytes;
+  // bounds of the cloud (counters cleared first: the array keeps the last call's contents)
+  uint32_t* red;
+  NB_TRY(sc.get(&red, 8));
+  NB_CUDA(err, cudaMemsetAsync(red, 0xff, 3 * sizeof(uint32_t), st));
+  NB_CUDA(err, cudaMemsetAsync(red + 3, 0, 5 * sizeof(uint32_t), st));
+  k_bounds<<<std::min<unsigned>(grid_for(n, 256), 148u * 8u), 256, 0, st>>>(cloud->xyz, cloud->label, n, red);
+  NB_LAUNCHED(err);
+  uint32_t hr[8];
+  NB_CUDA(err, cudaMemcpyAsync(hr, red, sizeof hr, cudaMemcpyDeviceToHost, st));
+  NB_CUDA(err, cudaStreamSynchronize(st));
+  double lo[3], hi[3];
+  for (int a = 0; a < 6; ++a) {
+    uint32_t u = hr[a];
+    uint32_t b = (u & 0x80000000u) ? (u & 0x7fffffffu) : ~u;
+    float f;
+    std::memcpy(&f, &b, 4);
+    if (a < 3) lo[a] = (double)f;
+    else hi[a - 3] = (double)f;
+  }
+  if (p->has_region)
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = std::min(lo[a], p->region_min[a]);
+      hi[a] = std::max(hi[a], p->region_max[a]);
+    }
+  const uint32_t maxlab = hr[6];
+  if (maxlab >= (1u << 24)) {
+    *err = "voxelize_static: labels must be < 2^24";
+    return NIMBUS_ERR_ARG;
+  }
+  const double h = p->voxel_size, hs = h / p->dv;
+  int dims[3];
+  double origin[3];
+  for (int a = 0; a < 3; ++a) {
+    origin[a] = (std::floor(lo[a] / h) - 1.0) * h;
+    double dd = std::ceil((hi[a] - origin[a]) / h) + 1.0;
+    if (!(dd >= 1.0 && dd < 1e6)) {
+      *err = "voxelize_static: voxel grid dimensions out of range";
+      return NIMBUS_ERR_ARG;
+    }
+    dims[a] = (int)dd;
+    info->origin[a] = origin[a];
+    info->dims[a] = dims[a];
+  }
+  const int64_t n_cells = (int64_t)dims[0] * dims[1] * dims[2];
+  info->n_cells = n_cells;
+  info->n_ie = 0;
+  if (n_cells > (int64_t)kStaticCells) {
+    *err = "voxelize_static: the voxel grid has more than NIMBUS_STATIC_MAX_CELLS voxels";
+    return NIMBUS_ERR_ARG;
+  }
+  GridK g;
+  for (int a = 0; a < 3; ++a) {
+    g.o[a] = (float)origin[a];
+    g.gmax[a] = dims[a] * p->dv - 1;
+  }
+  g.hs = (float)hs;
+  g.dv = p->dv;
+  g.nx = dims[0];
+  g.ny = dims[1];
+  g.sub_bits = std::max(1, bits_for((uint64_t)p->dv * p->dv * p->dv - 1));
+  g.id_bits = std::max(1, bits_for(maxlab));
+  const int key_bits = bits_for((uint64_t)n_cells) + g.sub_bits + 1 + g.id_bits;
+  if (key_bits > 64) {
+    *err = "voxelize_static: sort key exceeds 64 bits";
+    return NIMBUS_ERR_ARG;
+  }
+  uint64_t *keys, *keys_alt;
+  uint32_t *vals, *vals_alt, *flags, *ids, *counter;
+  NB_TRY(sc.get(&keys, n));
+  NB_TRY(sc.get(&keys_alt, n));
+  NB_TRY(sc.get(&vals, n));
+  NB_TRY(sc.get(&vals_alt, n));
+  NB_TRY(sc.get(&flags, n));
+  NB_TRY(sc.get(&ids, n));
+  NB_TRY(sc.get(&counter, 4));
+  NB_CUDA(err, cudaMemsetAsync(counter, 0, 4 * sizeof(uint32_t), st));
+  const int B = 256;
+  const unsigned G = std::min<unsigned>(grid_for(n, B), 148u * 16u);
+  k_point_keys<<<G, B, 0, st>>>(g, cloud->xyz, cloud->label, n, keys, vals);
+  NB_LAUNCHED(err);
+  NB_TRY(radix_sort(sc, keys, vals, keys_alt, vals_alt, n, key_bits));
+  k_run_flags<<<G, B, 0, st>>>(keys, n, flags);
+  NB_LAUNCHED(err);
+  NB_TRY(exclusive_scan(sc, flags, ids, n, counter + 1));
+  uint32_t hn = 0;
+  NB_CUDA(err, cudaMemcpyAsync(&hn, counter + 1, sizeof hn, cudaMemcpyDeviceToHost, st));
+  NB_CUDA(err, cudaStreamSynchronize(st));
+  const int64_t n_ie = hn;
+  info->n_ie = n_ie;
+  if (n_ie > out->ie_capacity || n_cells > out->cell_capacity) {
+    *err = "voxelize_static: output capacity too small (needed sizes in info)";
+    return NIMBUS_ERR_OVERFLOW;
+  }
+  uint32_t *starts, *ie_cell;
+  float4 *pts, *pnrm;
+  IERec* ies;
+  uint2* cells;
+  uint8_t *d1, *d2;
+  NB_TRY(sc.get(&starts, n_ie + 1));
+  NB_TRY(sc.get(&ie_cell, std::max<int64_t>(1, n_ie)));
+  NB_TRY(sc.get(&pts, n));
+  NB_TRY(sc.get(&pnrm, n));
+  NB_TRY(sc.get(&ies, std::max<int64_t>(1, n_ie)));
+  NB_TRY(sc.get(&cells, n_cells));
+  NB_TRY(sc.get(&d1, n_cells));
+  NB_TRY(sc.get(&d2, n_cells));
+  k_run_starts<<<G, B, 0, st>>>(flags, ids, n, starts, (uint32_t)n_ie, (uint32_t)n);
+  NB_LAUNCHED(err);
+  k_gather<<<G, B, 0, st>>>(vals, n, n, cloud->xyz, cloud->nrm, pts, pnrm);
+  NB_LAUNCHED(err);
+  NB_CUDA(err, cudaMemsetAsync(cells, 0, n_cells * sizeof(uint2), st));
+  BuildK bk;
+  bk.g = g;
+  for (int a = 0; a < 3; ++a) bk.o[a] = origin[a];
+  bk.hs = hs;
+  bk.n_points = n;
+  bk.n_ie = (int)n_ie;
+  k_ie_build<<<grid_for(n_ie, 128), 128, 0, st>>>(bk, keys, vals, starts, pts, pnrm, cloud->material, nullptr,
+                                                  nullptr, ies, ie_cell);
+  NB_LAUNCHED(err);
+  k_cell_begin<<<grid_for(n_ie, 256), 256, 0, st>>>(ie_cell, (int)n_ie, cells);
+  NB_LAUNCHED(err);
+  k_cell_count<<<grid_for(n_ie, 256), 256, 0, st>>>(ie_cell, (int)n_ie, cells);
+  NB_LAUNCHED(err);
+  k_march_x<<<grid_for((int64_t)dims[1] * dims[2], 128), 128, 0, st>>>(cells, dims[0], dims[1], dims[2], d1);
+  NB_LAUNCHED(err);
+  k_march_axis<<<grid_for(n_cells, 256), 256, 0, st>>>(d1, d2, dims[0], dims[1], dims[2], 1);
+  NB_LAUNCHED(err);
+  k_march_axis<<<grid_for(n_cells, 256), 256, 0, st>>>(d2, out->march, dims[0], dims[1], dims[2], 2);
+  NB_LAUNCHED(err);
+  k_static_out<<<std::min<unsigned>(grid_for(std::max<int64_t>(n_ie, n_cells), 256), 148u * 16u), 256, 0, st>>>(
+      ies, (int)n_ie, cells, n_cells, *out);
+  NB_LAUNCHED(err);
+  k_static_gs<<<grid_for(n_ie, 256), 256, 0, st>>>(ies, (int)n_ie, (float)origin[0], (float)origin[1],
+                                                  (float)origin[2], (float)hs, out->gs);
+  NB_LAUNCHED(err);
+  NB_CUDA(err, cudaStreamSynchronize(st));
+  return NIMBUS_OK;
 }
 
 }  // namespace nb

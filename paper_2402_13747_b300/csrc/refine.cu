@@ -2,13 +2,16 @@
 // re-projection of reflection points onto the point cloud, final visibility,
 // label-based and first-Fresnel-zone duplicate removal.
 //
-// B300 design: one warp per coarse path.  Lane k owns interaction k's FP64 state
-// (point, basis or edge parameter), so the FP64 gradient and step -- the parts
-// whose stability needs double precision -- run once per interaction; neighbours
-// come from warp shuffles.  Each re-projection (a ray intersected with the point
-// sets of one label, Eq. 1) and each final visibility ray uses all 32 lanes:
-// candidate IEs are tested in parallel and the Eq. 1 sums over an IE's points are
-// split across lanes and combined with shuffles, in FP32 in the frame of the IE.
+// B300 design: one warp per coarse path.  Lane k owns interaction k's state: the
+// FP64 iterate (the point and, for a diffraction, its edge parameter) and its FP32
+// basis; neighbours come from warp shuffles.  B300's FP64 rate is a small fraction
+// of FP32, so FP64 is kept to what must accumulate without loss -- the iterate,
+// the re-projected points and the path length -- while directions, gradient, local
+// Hessian and step are FP32 evaluations of FP64 differences.  Each re-projection
+// (a ray intersected with one label's implicit surface, Eq. 1) and each final
+// visibility ray uses all 32 lanes: the Eq. 1 sums are split across lanes and
+// combined with shuffles, in FP32 in a frame centred on the target, and the label's
+// nearby entities are cached in shared memory per interaction.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -32,11 +35,6 @@ struct CoarseView {
   const uint32_t *tx, *rx, *nint, *types, *ie, *lab, *gid;
   int64_t n;
 };
-
-__device__ __forceinline__ d3 dunit(d3 a) {
-  double n = sqrt(dot(a, a));
-  return n > 0.0 ? (1.0 / n) * a : a;
-}
 
 __device__ __forceinline__ float wsum(float v) {
 #pragma unroll
@@ -115,29 +113,99 @@ __device__ bool sdf_march_warp(const DScene& s, uint32_t pb, uint32_t pc, float3
   return false;
 }
 
-// Same-label IEs near one re-projection target, cached in shared memory per warp:
-// first point, point count and global subvoxel coordinates.
-constexpr int RCAP = 96;
+// Same-label IEs near one re-projection target, cached in shared memory for each
+// interaction of a warp's path.  Key: label and the target's subvoxel gR; entries
+// hold the first point, and the point count with the IE's subvoxel offset from gR
+// (each in [-2, 2], stored + 2 in three 3-bit fields).  Rebuilt only when the key
+// changes, i.e. when an update carries the target into another subvoxel.
+// 112 entries cover a surface that crosses up to four subvoxel layers of the 5x5x5
+// block (a noisy wall lying on subvoxel faces fills two); a fuller block makes the
+// re-projection miss.
+constexpr int RCAP = 112;
 struct LabelCache {
-  uint32_t pb[RCAP], pc[RCAP];
-  int g[RCAP][3];
+  uint32_t pb[RCAP];
+  uint32_t meta[RCAP];   // point count | (gx - gR.x + 2) << 16 | (gy ...) << 19 | (gz ...) << 22
+  int gR[3];
+  uint32_t label;
+  int n;                 // entries, -1: empty
 };
 
 __device__ __forceinline__ int floor_div(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
 
+// (Re)build the cache for target subvoxel gR and label: the label's point IEs whose
+// subvoxel lies within two subvoxels of gR -- all that Eq. 1 at any point of a
+// re-projection segment around the target can draw on.
+__device__ void fill_cache(const DScene& s, LabelCache& lc, const int gR[3], uint32_t label, int lane,
+                           unsigned long long& bytes) {
+  int v0[3], v1[3];
+  for (int a = 0; a < 3; ++a) {
+    v0[a] = floor_div(gR[a] - 2, s.dv);
+    v1[a] = floor_div(gR[a] + 2, s.dv);
+  }
+  const float ofs[3] = {s.ox, s.oy, s.oz};
+  const unsigned lt = (1u << lane) - 1u;
+  int nc = 0;
+  for (int vz = v0[2]; vz <= v1[2]; ++vz)
+    for (int vy = v0[1]; vy <= v1[1]; ++vy)
+      for (int vx = v0[0]; vx <= v1[0]; ++vx) {
+        if (!in_grid(s, vx, vy, vz)) continue;
+        uint2 cell = __ldg(&s.cells[cell_index(s, vx, vy, vz)]);
+        for (uint32_t base = 0; base < cell.y; base += 32) {
+          uint32_t k = base + lane;
+          bool ok = false;
+          uint32_t pb = 0, meta = 0;
+          if (k < cell.y) {
+            const IERec* r = &s.ies[cell.x + k];
+            float4 nm = __ldg(&r->nrm_meta);
+            float4 rp = __ldg(&r->rp_lab);
+            bytes += 32;
+            if ((__float_as_uint(nm.w) & 1u) == IE_POINT && __float_as_uint(rp.w) == label) {
+              float4 sc = __ldg(&r->sc_pc);
+              const float scv[3] = {sc.x, sc.y, sc.z};
+              ok = true;
+              meta = __float_as_uint(sc.w) & 0xffffu;
+              for (int a = 0; a < 3; ++a) {
+                int dg = (int)floorf((scv[a] - ofs[a]) / s.hs) - gR[a];
+                ok = ok && abs(dg) <= 2;
+                meta |= (uint32_t)(dg + 2) << (16 + 3 * a);
+              }
+              pb = __float_as_uint(__ldg(&r->bbc_pb).w);
+              bytes += 32;
+            }
+          }
+          unsigned mask = __ballot_sync(FULL, ok);
+          int slot = nc + __popc(mask & lt);
+          if (ok && slot < RCAP) {
+            lc.pb[slot] = pb;
+            lc.meta[slot] = meta;
+          }
+          nc += __popc(mask);
+        }
+      }
+  if (lane == 0) {
+    lc.gR[0] = gR[0];
+    lc.gR[1] = gR[1];
+    lc.gR[2] = gR[2];
+    lc.label = label;
+    lc.n = nc > RCAP ? RCAP + 1 : nc;
+  }
+  __syncwarp();
+}
+
 // Eq. 1 over the nearby points of one label -- the points of the cached IEs whose
-// subvoxel lies in the 3x3x3 block around the subvoxel of x -- with the sums split
-// across lanes; every lane returns the same f and normal.  c0 is the FP32 frame
-// centre of the sums (the re-projection target).
-__device__ bool sdf_label_warp(const DScene& s, const LabelCache& lc, int nc, d3 x, float3 c0, float* f,
-                               float3* n_out, int lane, unsigned long long& bytes) {
-  const int g0 = (int)floor((x.x - s.odx) / s.hsd), g1 = (int)floor((x.y - s.ody) / s.hsd),
-            g2 = (int)floor((x.z - s.odz) / s.hsd);
-  const float3 xl = f3((float)(x.x - (double)c0.x), (float)(x.y - (double)c0.y), (float)(x.z - (double)c0.z));
+// subvoxel lies in the 3x3x3 block around the subvoxel of x -- in FP32 in a frame
+// centred on c0 (the target); xl = x - c0, dg = subvoxel of x minus gR.  The sums
+// are split across lanes; every lane returns the same f and normal.
+__device__ bool sdf_label_warp(const DScene& s, const LabelCache& lc, float3 xl, const int dg[3], float3 c0,
+                               float* f, float3* n_out, int lane, unsigned long long& bytes) {
   float sw = 0.f, px = 0.f, py = 0.f, pz = 0.f, nx = 0.f, ny = 0.f, nz = 0.f;
+  const int nc = lc.n;
   for (int q = 0; q < nc; ++q) {
-    if (abs(lc.g[q][0] - g0) > 1 || abs(lc.g[q][1] - g1) > 1 || abs(lc.g[q][2] - g2) > 1) continue;
-    const uint32_t pb = lc.pb[q], pc = lc.pc[q];
+    const uint32_t m = lc.meta[q];
+    if (abs((int)((m >> 16) & 7u) - 2 - dg[0]) > 1 || abs((int)((m >> 19) & 7u) - 2 - dg[1]) > 1 ||
+        abs((int)((m >> 22) & 7u) - 2 - dg[2]) > 1)
+      continue;
+    const uint32_t pb = lc.pb[q], pc = m & 0xffffu;
     for (uint32_t k = lane; k < pc; k += 32) {
       float4 P = __ldg(&s.pts[pb + k]);
       float4 N = __ldg(&s.pnrm[pb + k]);
@@ -164,89 +232,55 @@ __device__ bool sdf_label_warp(const DScene& s, const LabelCache& lc, int nc, d3
   return true;
 }
 
+// Subvoxel of c0 + xl relative to gR.
+__device__ __forceinline__ void rel_subvoxel(const DScene& s, float3 c0, float3 xl, const int gR[3], int dg[3]) {
+  dg[0] = (int)floorf((c0.x - s.ox + xl.x) / s.hs) - gR[0];
+  dg[1] = (int)floorf((c0.y - s.oy + xl.y) / s.hs) - gR[1];
+  dg[2] = (int)floorf((c0.z - s.oz + xl.z) / s.hs) - gR[2];
+}
+
 // Re-projection (Section 2.3): the ray from P toward the updated point R is
 // intersected with the implicit surface of label `label` (Eq. 1 over nearby points of
 // that label) by the march of Section 2.2.1 on a segment of one subvoxel diameter
-// centred on R.  The label's IEs within two subvoxels of R -- all that any point of
-// the segment can draw on -- are collected once into the warp's cache.
-__device__ bool reproject_warp(const DScene& s, d3 P, d3 R, uint32_t label, d3* c_out, d3* n_out, int lane,
+// centred on R.  The march runs in FP32 relative to R; the new point is R plus the
+// FP32 offset along the ray, in FP64.
+__device__ bool reproject_warp(const DScene& s, d3 P, d3 R, uint32_t label, d3* c_out, float3* n_out, int lane,
                                unsigned long long& bytes, LabelCache& lc) {
   d3 dv = R - P;
   double tR = len(dv);
   if (tR < 1e-12) return false;
-  d3 d = (1.0 / tR) * dv;
+  const float3 d = normalize(tof(dv));
   const int gR[3] = {(int)floor((R.x - s.odx) / s.hsd), (int)floor((R.y - s.ody) / s.hsd),
                      (int)floor((R.z - s.odz) / s.hsd)};
-  int v0[3], v1[3];
-  for (int a = 0; a < 3; ++a) {
-    v0[a] = floor_div(gR[a] - 2, s.dv);
-    v1[a] = floor_div(gR[a] + 2, s.dv);
-  }
-  const float ofs[3] = {s.ox, s.oy, s.oz};
-  int nc = 0;
-  const unsigned lt = (1u << lane) - 1u;
-  for (int vz = v0[2]; vz <= v1[2]; ++vz)
-    for (int vy = v0[1]; vy <= v1[1]; ++vy)
-      for (int vx = v0[0]; vx <= v1[0]; ++vx) {
-        if (!in_grid(s, vx, vy, vz)) continue;
-        uint2 cell = __ldg(&s.cells[cell_index(s, vx, vy, vz)]);
-        for (uint32_t base = 0; base < cell.y; base += 32) {
-          uint32_t k = base + lane;
-          bool ok = false;
-          uint32_t pb = 0, pc = 0;
-          int g[3] = {0, 0, 0};
-          if (k < cell.y) {
-            const IERec* r = &s.ies[cell.x + k];
-            float4 nm = __ldg(&r->nrm_meta);
-            float4 rp = __ldg(&r->rp_lab);
-            float4 sc = __ldg(&r->sc_pc);
-            bytes += 48;
-            if ((__float_as_uint(nm.w) & 1u) == IE_POINT && __float_as_uint(rp.w) == label) {
-              const float scv[3] = {sc.x, sc.y, sc.z};
-              ok = true;
-              for (int a = 0; a < 3; ++a) {
-                g[a] = (int)floorf((scv[a] - ofs[a]) / s.hs);
-                ok = ok && abs(g[a] - gR[a]) <= 2;
-              }
-              pb = __float_as_uint(__ldg(&r->bbc_pb).w);
-              pc = __float_as_uint(sc.w);
-            }
-          }
-          unsigned mask = __ballot_sync(FULL, ok);
-          int slot = nc + __popc(mask & lt);
-          if (ok && slot < RCAP) {
-            lc.pb[slot] = pb;
-            lc.pc[slot] = pc;
-            lc.g[slot][0] = g[0];
-            lc.g[slot][1] = g[1];
-            lc.g[slot][2] = g[2];
-          }
-          nc += __popc(mask);
-        }
-      }
-  __syncwarp();
-  if (nc > RCAP || nc == 0) return false;
+  if (lc.n < 0 || lc.label != label || lc.gR[0] != gR[0] || lc.gR[1] != gR[1] || lc.gR[2] != gR[2])
+    fill_cache(s, lc, gR, label, lane, bytes);
+  if (lc.n > RCAP || lc.n == 0) return false;
   const float3 c0 = tof(R);
-  const double L = (double)s.seg_len;
-  double t = -0.5 * L, th = 0.0;
-  float f;
+  const float3 r0 = tof(R - tod(c0));      // R relative to its FP32 rounding
+  const float half = 0.5f * s.seg_len;
+  float t = -half, th = 0.f, f;
   float3 n;
+  int dg[3];
   bool hit = false;
-  if (!sdf_label_warp(s, lc, nc, R + t * d, c0, &f, &n, lane, bytes)) return false;
+  float3 xl = r0 + t * d;
+  rel_subvoxel(s, c0, xl, gR, dg);
+  if (!sdf_label_warp(s, lc, xl, dg, c0, &f, &n, lane, bytes)) return false;
   for (int it = 0; it < s.sdf_max_steps; ++it) {
     if (fabsf(f) < s.sdf_eps) {
-      double dn = (double)dot(n, tof(d));
-      th = fabs(dn) > 1e-3 ? t - (double)f / dn : t;
+      float dn = dot(n, d);
+      th = fabsf(dn) > 1e-3f ? t - f / dn : t;
       hit = true;
       break;
     }
-    double tn = t + (double)fabsf(f);
-    if (tn > 0.5 * L) return false;
+    float tn = t + fabsf(f);
+    if (tn > half) return false;
     float fn;
     float3 nn;
-    if (!sdf_label_warp(s, lc, nc, R + tn * d, c0, &fn, &nn, lane, bytes)) return false;
+    xl = r0 + tn * d;
+    rel_subvoxel(s, c0, xl, gR, dg);
+    if (!sdf_label_warp(s, lc, xl, dg, c0, &fn, &nn, lane, bytes)) return false;
     if ((fn < 0.f) != (f < 0.f)) {
-      th = t - (double)f * (tn - t) / ((double)fn - (double)f);
+      th = t - f * (tn - t) / (fn - f);
       hit = true;
       break;
     }
@@ -254,12 +288,13 @@ __device__ bool reproject_warp(const DScene& s, d3 P, d3 R, uint32_t label, d3* 
     f = fn;
     n = nn;
   }
-  // the placed hit must stay on the marched segment
-  if (!hit || !(tR + th > 0.0) || fabs(th) > 0.5 * L) return false;
-  d3 c = P + (tR + th) * d;
-  if (!sdf_label_warp(s, lc, nc, c, c0, &f, &n, lane, bytes)) return false;
-  *c_out = c;
-  *n_out = D3(n.x, n.y, n.z);
+  // the placed hit must stay on the marched segment (and in front of P)
+  if (!hit || !(tR + (double)th > 0.0) || fabsf(th) > half) return false;
+  xl = r0 + th * d;
+  rel_subvoxel(s, c0, xl, gR, dg);
+  if (!sdf_label_warp(s, lc, xl, dg, c0, &f, &n, lane, bytes)) return false;
+  *c_out = R + (double)th * tod(d);
+  *n_out = n;
   return true;
 }
 
@@ -318,10 +353,13 @@ __device__ bool visible_warp(const DScene& s, float3 A, float3 B, Endpoint ea, E
 // local inverse Hessian times gamma) clamped to h_s, then for each reflection a
 // re-projection ray from the previous interaction point toward
 // R_k = c_k + r_k u_k + s_k v_k, for each diffraction D_k = c_k + t_k w_k.
-__global__ void __launch_bounds__(128) k_refine(DScene s, DRefine rp, CoarseView C, const double* txd,
-                                                const double* rxd, ExactRec* out, unsigned long long* bytes_out) {
-  __shared__ LabelCache s_cache[4];
-  const int lane = threadIdx.x & 31;
+// Precision: the iterate (interaction points, edge parameters), the re-projected
+// points and the path length are FP64; directions, gradient, local Hessian and step
+// are FP32 evaluations from FP64 differences (error ~1e-7, below grad_stop).
+__global__ void __launch_bounds__(128, 4) k_refine(DScene s, DRefine rp, CoarseView C, const double* txd,
+                                                   const double* rxd, ExactRec* out, unsigned long long* bytes_out) {
+  __shared__ LabelCache s_cache[4][NB_MAXI];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   unsigned long long bytes = 0;
@@ -331,9 +369,13 @@ __global__ void __launch_bounds__(128) k_refine(DScene s, DRefine rp, CoarseView
     const uint32_t tx = C.tx[i], rx = C.rx[i];
     const bool mine = lane >= 1 && lane <= n;
     const bool diff = mine && ((types >> (lane - 1)) & 1u);
+    if (lane < NB_MAXI) s_cache[wib][lane].n = -1;
+    __syncwarp();
     // lane-local state
-    d3 I = D3(0, 0, 0), c = D3(0, 0, 0), u = D3(0, 0, 0), v = D3(0, 0, 0), w = D3(0, 0, 0), p0 = D3(0, 0, 0);
-    double tpar = 0.0, elen = 0.0;
+    d3 I = D3(0, 0, 0), c = D3(0, 0, 0), p0 = D3(0, 0, 0);
+    float3 u = f3(0, 0, 0), v = f3(0, 0, 0), w = f3(0, 0, 0);
+    double tpar = 0.0;
+    float elen = 0.f;
     uint32_t my_lab = NB_NONE_LABEL, my_ie = 0xffffffffu;
     uint8_t my_mat = 255;
     if (lane == 0) I = D3(txd[3 * tx], txd[3 * tx + 1], txd[3 * tx + 2]);
@@ -347,39 +389,40 @@ __global__ void __launch_bounds__(128) k_refine(DScene s, DRefine rp, CoarseView
       c = D3(rpl.x, rpl.y, rpl.z);
       I = c;
       if (!diff) {
-        onb(dunit(D3(nm.x, nm.y, nm.z)), &u, &v);
+        onb(normalize(xyz(nm)), &u, &v);
       } else {
         const double* E = s.edges + 12 * __float_as_uint(r->bbc_pb.w);
         p0 = D3(E[0], E[1], E[2]);
         d3 ev = D3(E[3] - E[0], E[4] - E[1], E[5] - E[2]);
-        elen = len(ev);
-        w = (1.0 / elen) * ev;
+        double el = len(ev);
+        elen = (float)el;
+        w = tof((1.0 / el) * ev);
       }
     }
     int status = ST_VALID, it = 0;
     bool converged = false;
-    double gn = 0.0;
+    float gn = 0.f;
     for (; it <= rp.rho; ++it) {
       // gradient of Eq. 2: (e_in + e_out) . (u, v) for reflections, . w for diffractions
       d3 Ip = shfl3(I, max(lane - 1, 0)), In_ = shfl3(I, min(lane + 1, 31));
-      double g0 = 0.0, g1 = 0.0, eta = 0.0, a = 1.0, b = 1.0;
-      d3 ea = D3(0, 0, 0), eb = D3(0, 0, 0);
+      float g0 = 0.f, g1 = 0.f, a = 1.f, b = 1.f;
+      float3 ea = f3(0, 0, 0), eb = f3(0, 0, 0);
       if (mine) {
-        ea = dunit(I - Ip);
-        eb = dunit(I - In_);
-        d3 e = ea + eb;
+        float3 fa = tof(I - Ip), fb = tof(I - In_);
+        a = len(fa);
+        b = len(fb);
+        ea = a > 0.f ? (1.f / a) * fa : fa;
+        eb = b > 0.f ? (1.f / b) * fb : fb;
+        float3 e = ea + eb;
         if (!diff) {
           g0 = dot(e, u);
           g1 = dot(e, v);
         } else {
           g0 = dot(e, w);
         }
-        a = len(I - Ip);
-        b = len(I - In_);
-        eta = rp.gamma / (1.0 / a + 1.0 / b);
       }
-      gn = sqrt(wsumd(g0 * g0 + g1 * g1));
-      if (gn < rp.grad_stop) {
+      gn = sqrtf(wsum(g0 * g0 + g1 * g1));
+      if (gn < (float)rp.grad_stop) {
         converged = true;
         break;
       }
@@ -388,37 +431,38 @@ __global__ void __launch_bounds__(128) k_refine(DScene s, DRefine rp, CoarseView
       bool off = false;
       // step: gradient scaled by the inverse Hessian of the local length f_k (2x2 in
       // (r, s), 1x1 in t) times gamma; near-singular Hessians fall back to eta
-      const double hsum = 1.0 / a + 1.0 / b;
+      const float hsum = 1.f / a + 1.f / b;
+      const float gam = (float)rp.gamma, eta = gam / hsum, hs = (float)rp.hs;
       if (mine && !diff) {
-        double au = dot(ea, u), av = dot(ea, v), bu = dot(eb, u), bv = dot(eb, v);
-        double h11 = (1.0 - au * au) / a + (1.0 - bu * bu) / b;
-        double h22 = (1.0 - av * av) / a + (1.0 - bv * bv) / b;
-        double h12 = -(au * av) / a - (bu * bv) / b;
-        double det = h11 * h22 - h12 * h12;
-        double rr, ss;
-        if (det > 1e-12 * hsum * hsum) {
-          rr = -rp.gamma * (h22 * g0 - h12 * g1) / det;
-          ss = -rp.gamma * (h11 * g1 - h12 * g0) / det;
+        float au = dot(ea, u), av = dot(ea, v), bu = dot(eb, u), bv = dot(eb, v);
+        float h11 = (1.f - au * au) / a + (1.f - bu * bu) / b;
+        float h22 = (1.f - av * av) / a + (1.f - bv * bv) / b;
+        float h12 = -(au * av) / a - (bu * bv) / b;
+        float det = h11 * h22 - h12 * h12;
+        float rr, ss;
+        if (det > 1e-12f * hsum * hsum) {
+          rr = -gam * (h22 * g0 - h12 * g1) / det;
+          ss = -gam * (h11 * g1 - h12 * g0) / det;
         } else {
           rr = -eta * g0;
           ss = -eta * g1;
         }
-        double l = sqrt(rr * rr + ss * ss);
-        if (l > rp.hs) {
-          rr *= rp.hs / l;
-          ss *= rp.hs / l;
+        float l = sqrtf(rr * rr + ss * ss);
+        if (l > hs) {
+          rr *= hs / l;
+          ss *= hs / l;
         }
-        R = c + rr * u + ss * v;                 // R_k = c_k + r_k u_k + s_k v_k
+        R = c + (double)rr * tod(u) + (double)ss * tod(v);   // R_k = c_k + r_k u_k + s_k v_k
       }
       if (diff) {
-        double aw = dot(ea, w), bw = dot(eb, w);
-        double hw = (1.0 - aw * aw) / a + (1.0 - bw * bw) / b;
-        double dt = hw > 1e-12 * hsum ? -rp.gamma * g0 / hw : -eta * g0;
-        if (fabs(dt) > rp.hs) dt = copysign(rp.hs, dt);
-        tpar += dt;                               // D_k = c_k + t_k w_k
-        Inew = c + tpar * w;
-        double along = dot(Inew - p0, w);
-        off = along < 0.0 || along > elen;
+        float aw = dot(ea, w), bw = dot(eb, w);
+        float hw = (1.f - aw * aw) / a + (1.f - bw * bw) / b;
+        float dt = hw > 1e-12f * hsum ? -gam * g0 / hw : -eta * g0;
+        if (fabsf(dt) > hs) dt = copysignf(hs, dt);
+        tpar += (double)dt;                                   // D_k = c_k + t_k w_k
+        Inew = c + tpar * tod(w);
+        double along = dot(Inew - p0, tod(w));
+        off = along < 0.0 || along > (double)elen;
       }
       if (__any_sync(FULL, off)) {
         status = ST_OFF_EDGE;
@@ -428,21 +472,22 @@ __global__ void __launch_bounds__(128) k_refine(DScene s, DRefine rp, CoarseView
         if ((types >> (k - 1)) & 1u) continue;
         d3 Pk = shfl3(Ip, k), Rk = shfl3(R, k);
         uint32_t lk = __shfl_sync(FULL, my_lab, k);
-        d3 cn, nn;
-        if (!reproject_warp(s, Pk, Rk, lk, &cn, &nn, lane, bytes, s_cache[threadIdx.x >> 5])) {
+        d3 cn;
+        float3 nn;
+        if (!reproject_warp(s, Pk, Rk, lk, &cn, &nn, lane, bytes, s_cache[wib][k - 1])) {
           status = ST_MISS;
           break;
         }
         if (lane == k) {
           c = cn;
-          onb(dunit(nn), &u, &v);
+          onb(normalize(nn), &u, &v);
           Inew = cn;
         }
       }
       if (status != ST_VALID) break;
       I = Inew;
     }
-    if (status == ST_VALID && !converged && !(gn < rp.delta)) status = ST_NOT_CONVERGED;
+    if (status == ST_VALID && !converged && !(gn < (float)rp.delta)) status = ST_NOT_CONVERGED;
     if (status == ST_VALID) {
       // visibility between consecutive path nodes
       for (int k = 0; k <= n; ++k) {
@@ -464,7 +509,7 @@ __global__ void __launch_bounds__(128) k_refine(DScene s, DRefine rp, CoarseView
     if (lane == 0) {
       o->length = status == ST_VALID ? L : 0.0;
       o->delay = o->length / C_LIGHT;
-      o->grad = gn;
+      o->grad = (double)gn;
       o->tx = tx;
       o->rx = rx;
       o->n = (uint32_t)n;
@@ -483,6 +528,7 @@ __global__ void __launch_bounds__(128) k_refine(DScene s, DRefine rp, CoarseView
       o->pts[q][1] = mine ? I.y : 0.0;
       o->pts[q][2] = mine ? I.z : 0.0;
     }
+    __syncwarp();
   }
   if (lane == 0 && bytes) atomicAdd(bytes_out, bytes);
 }

@@ -97,6 +97,13 @@ typedef struct {
   int32_t pad_;
   int64_t max_nodes;        /* bound on interaction nodes per level (0: from the memory budget) */
   int64_t max_coarse;       /* bound on coarse paths before kappa (0: from the memory budget) */
+  /* Optional per-RX restrictions for batching independent requests in one call
+   * (host or device arrays of n_rx, NULL = none): rx_owner[j] >= 0 lets only TX
+   * rx_owner[j] reach RX j; rx_max_int[j] >= 0 keeps only coarse paths to RX j with
+   * at most that many interactions.  A path with d interactions is found the same
+   * way whatever the larger depth limit, so each request gets its own result. */
+  const int32_t* rx_owner;
+  const int32_t* rx_max_int;
 } nimbus_trace_params;
 
 /* Path refinement (Section 2.3). */

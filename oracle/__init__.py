@@ -99,6 +99,7 @@ def lib():
         L.oracle_refine.restype = vp
         L.oracle_refine.argtypes = [vp, vp]
         L.oracle_exact_free.argtypes = [vp]
+        L.oracle_refine_given.argtypes = [vp, vp, i32, vp, i32, i64] + [vp] * 11
         L.oracle_exact_count.restype = i64
         L.oracle_exact_count.argtypes = [vp, i32]
         L.oracle_exact_get.argtypes = [vp, i32] + [vp] * 14
@@ -185,6 +186,20 @@ class Scene:
 
     def refine(self, coarse: "Coarse") -> "Exact":
         return Exact(lib().oracle_refine(self.h, coarse.h), coarse)
+
+    def refine_given(self, tx, rx, paths: dict) -> dict:
+        """Refine the given coarse paths one by one (tx, rx, n, ie, type, label arrays)."""
+        tx = _c(np.asarray(tx).reshape(-1, 3), np.float64)
+        rx = _c(np.asarray(rx).reshape(-1, 3), np.float64)
+        m = len(paths["n"])
+        a = {k: _c(paths[k], dt) for k, dt in (("tx", np.int32), ("rx", np.int32), ("n", np.int32),
+                                                ("ie", np.int64), ("type", np.int32), ("label", np.uint32))}
+        out = dict(status=np.zeros(m, np.int32), iters=np.zeros(m, np.int32), grad=np.zeros(m),
+                   pts=np.zeros((m, MAXI, 3)), length=np.zeros(m))
+        lib().oracle_refine_given(self.h, _p(tx), tx.shape[0], _p(rx), rx.shape[0], m, _p(a["tx"]), _p(a["rx"]),
+                                  _p(a["n"]), _p(a["ie"]), _p(a["type"]), _p(a["label"]), _p(out["status"]),
+                                  _p(out["iters"]), _p(out["grad"]), _p(out["pts"]), _p(out["length"]))
+        return out
 
     # building blocks for pins
     def sdf(self, ie, x):

@@ -1341,6 +1341,39 @@ void oracle_coarse_get(void* cp, int32_t* tx, int32_t* rx, int32_t* n, int64_t* 
 }
 
 void* oracle_refine(void* sp, void* cp) { return refine(*(Scene*)sp, *(CoarseSet*)cp); }
+
+// Refine given coarse paths one by one (no duplicate removal), for sampled checks of
+// another implementation's refinement: coarse path i runs from TX tx_idx[i] to RX
+// rx_idx[i] through n[i] interactions (ie, type, label rows of MAXI).  Writes the
+// status, iterations, final gradient norm, points (MAXI*3) and length per path.
+void oracle_refine_given(void* sp, const double* tx, int32_t ntx, const double* rx, int32_t nrx, int64_t m,
+                         const int32_t* tx_idx, const int32_t* rx_idx, const int32_t* n, const int64_t* ie,
+                         const int32_t* type, const uint32_t* label, int32_t* status, int32_t* iters,
+                         double* grad, double* pts, double* length) {
+  const Scene& s = *(Scene*)sp;
+  CoarseSet cs;
+  for (int t = 0; t < ntx; ++t) cs.tx.push_back(mk(tx[3 * t], tx[3 * t + 1], tx[3 * t + 2]));
+  for (int j = 0; j < nrx; ++j) cs.rx.push_back(mk(rx[3 * j], rx[3 * j + 1], rx[3 * j + 2]));
+  for (int64_t i = 0; i < m; ++i) {
+    Coarse c;
+    std::memset(&c, 0, sizeof c);
+    c.tx = tx_idx[i];
+    c.rx = rx_idx[i];
+    c.n = n[i];
+    for (int q = 0; q < c.n; ++q) {
+      c.ie[q] = ie[MAXI * i + q];
+      c.type[q] = type[MAXI * i + q];
+      c.label[q] = label[MAXI * i + q];
+    }
+    Exact e = refine_one(s, cs, c);
+    status[i] = e.status;
+    iters[i] = e.iters;
+    grad[i] = e.grad;
+    length[i] = e.length;
+    for (int q = 0; q < MAXI; ++q)
+      for (int a = 0; a < 3; ++a) pts[3 * (MAXI * i + q) + a] = q < c.n ? comp(e.pts[q], a) : 0.0;
+  }
+}
 void oracle_exact_free(void* e) { delete (ExactSet*)e; }
 
 // which = 0: paths after duplicate removal; 1: every refined coarse path with status.

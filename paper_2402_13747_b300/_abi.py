@@ -48,7 +48,7 @@ class TraceParams(C.Structure):
     _fields_ = [("cone_half_angle", C.c_double), ("launch_spacing", C.c_double), ("sep_eps", C.c_double),
                 ("n_launch", C.c_int32), ("max_refl", C.c_int32), ("max_diff", C.c_int32),
                 ("max_int", C.c_int32), ("kappa", C.c_int32), ("pad_", C.c_int32),
-                ("max_nodes", C.c_int64), ("max_coarse", C.c_int64)]
+                ("max_nodes", C.c_int64), ("max_coarse", C.c_int64), ("rx_owner", _vp), ("rx_max_int", _vp)]
 
 
 class RefineParams(C.Structure):
@@ -286,11 +286,15 @@ class Context:
 
     # -- Section 2.2
     def trace(self, scene: int, tx, rx, params: Params = None, max_nodes=0, max_coarse=0, stream=None,
-              allow_overflow=False) -> int:
+              allow_overflow=False, rx_owner=None, rx_max_int=None) -> int:
         params = params or Params()
         t = _host(tx, np.float64, (-1, 3))
         r = _host(rx, np.float64, (-1, 3))
         tp = trace_params(params, max_nodes, max_coarse)
+        own = None if rx_owner is None else _host(rx_owner, np.int32)
+        mx = None if rx_max_int is None else _host(rx_max_int, np.int32)
+        tp.rx_owner = _ptr(own)
+        tp.rx_max_int = _ptr(mx)
         out = C.c_uint64(0)
         rc = self.L.nimbus_trace_coarse(self.h, scene, _ptr(t), int(t.shape[0]), _ptr(r), int(r.shape[0]),
                                         C.byref(tp), C.byref(out), _stream(stream))

@@ -115,20 +115,32 @@ __device__ bool sdf_march_warp(const DScene& s, uint32_t pb, uint32_t pc, float3
 
 // Same-label IEs near one re-projection target, cached in shared memory for each
 // interaction of a warp's path.  Key: label and the target's subvoxel gR; entries
-// hold the first point, and the point count with the IE's subvoxel offset from gR
-// (each in [-2, 2], stored + 2 in three 3-bit fields).  Rebuilt only when the key
-// changes, i.e. when an update carries the target into another subvoxel.
-// 112 entries cover a surface that crosses up to four subvoxel layers of the 5x5x5
-// block (a noisy wall lying on subvoxel faces fills two); a fuller block makes the
+// hold the first point, the point count and a 27-bit mask of the subvoxels x around
+// gR (offsets in [-1, 1]^3) whose 3x3x3 block contains the IE.  Rebuilt only when
+// the key changes, i.e. when an update carries the target into another subvoxel.
+// 96 entries cover a surface crossing three subvoxel layers of the 5x5x5 block (a
+// noisy wall lying on subvoxel faces fills two); a fuller block makes the
 // re-projection miss.
-constexpr int RCAP = 112;
+constexpr int RCAP = 96;
 struct LabelCache {
   uint32_t pb[RCAP];
-  uint32_t meta[RCAP];   // point count | (gx - gR.x + 2) << 16 | (gy ...) << 19 | (gz ...) << 22
+  uint32_t pc[RCAP];
+  uint32_t nbr[RCAP];
   int gR[3];
   uint32_t label;
   int n;                 // entries, -1: empty
 };
+
+// Bit (dz+1)*9 + (dy+1)*3 + (dx+1) of the mask: an IE at subvoxel offset g from gR
+// lies in the 3x3x3 block of the subvoxel at offset d iff |g - d| <= 1 per axis.
+__device__ __forceinline__ uint32_t block_mask(int gx, int gy, int gz) {
+  uint32_t m = 0;
+  for (int dz = -1; dz <= 1; ++dz)
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx)
+        if (abs(gx - dx) <= 1 && abs(gy - dy) <= 1 && abs(gz - dz) <= 1) m |= 1u << ((dz + 1) * 9 + (dy + 1) * 3 + dx + 1);
+  return m;
+}
 
 __device__ __forceinline__ int floor_div(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
 
@@ -153,7 +165,7 @@ __device__ void fill_cache(const DScene& s, LabelCache& lc, const int gR[3], uin
         for (uint32_t base = 0; base < cell.y; base += 32) {
           uint32_t k = base + lane;
           bool ok = false;
-          uint32_t pb = 0, meta = 0;
+          uint32_t pb = 0, pc = 0, nbr = 0;
           if (k < cell.y) {
             const IERec* r = &s.ies[cell.x + k];
             float4 nm = __ldg(&r->nrm_meta);
@@ -162,13 +174,14 @@ __device__ void fill_cache(const DScene& s, LabelCache& lc, const int gR[3], uin
             if ((__float_as_uint(nm.w) & 1u) == IE_POINT && __float_as_uint(rp.w) == label) {
               float4 sc = __ldg(&r->sc_pc);
               const float scv[3] = {sc.x, sc.y, sc.z};
+              int dg[3];
               ok = true;
-              meta = __float_as_uint(sc.w) & 0xffffu;
               for (int a = 0; a < 3; ++a) {
-                int dg = (int)floorf((scv[a] - ofs[a]) / s.hs) - gR[a];
-                ok = ok && abs(dg) <= 2;
-                meta |= (uint32_t)(dg + 2) << (16 + 3 * a);
+                dg[a] = (int)floorf((scv[a] - ofs[a]) / s.hs) - gR[a];
+                ok = ok && abs(dg[a]) <= 2;
               }
+              pc = __float_as_uint(sc.w);
+              nbr = block_mask(dg[0], dg[1], dg[2]);
               pb = __float_as_uint(__ldg(&r->bbc_pb).w);
               bytes += 32;
             }
@@ -177,7 +190,8 @@ __device__ void fill_cache(const DScene& s, LabelCache& lc, const int gR[3], uin
           int slot = nc + __popc(mask & lt);
           if (ok && slot < RCAP) {
             lc.pb[slot] = pb;
-            lc.meta[slot] = meta;
+            lc.pc[slot] = pc;
+            lc.nbr[slot] = nbr;
           }
           nc += __popc(mask);
         }
@@ -200,12 +214,11 @@ __device__ bool sdf_label_warp(const DScene& s, const LabelCache& lc, float3 xl,
                                float* f, float3* n_out, int lane, unsigned long long& bytes) {
   float sw = 0.f, px = 0.f, py = 0.f, pz = 0.f, nx = 0.f, ny = 0.f, nz = 0.f;
   const int nc = lc.n;
+  if (abs(dg[0]) > 1 || abs(dg[1]) > 1 || abs(dg[2]) > 1) return false;
+  const int di = (dg[2] + 1) * 9 + (dg[1] + 1) * 3 + dg[0] + 1;
   for (int q = 0; q < nc; ++q) {
-    const uint32_t m = lc.meta[q];
-    if (abs((int)((m >> 16) & 7u) - 2 - dg[0]) > 1 || abs((int)((m >> 19) & 7u) - 2 - dg[1]) > 1 ||
-        abs((int)((m >> 22) & 7u) - 2 - dg[2]) > 1)
-      continue;
-    const uint32_t pb = lc.pb[q], pc = m & 0xffffu;
+    if (!((lc.nbr[q] >> di) & 1u)) continue;
+    const uint32_t pb = lc.pb[q], pc = lc.pc[q];
     for (uint32_t k = lane; k < pc; k += 32) {
       float4 P = __ldg(&s.pts[pb + k]);
       float4 N = __ldg(&s.pnrm[pb + k]);
@@ -357,13 +370,18 @@ __device__ bool visible_warp(const DScene& s, float3 A, float3 B, Endpoint ea, E
 // points and the path length are FP64; directions, gradient, local Hessian and step
 // are FP32 evaluations from FP64 differences (error ~1e-7, below grad_stop).
 __global__ void __launch_bounds__(128, 4) k_refine(DScene s, DRefine rp, CoarseView C, const double* txd,
-                                                   const double* rxd, ExactRec* out, unsigned long long* bytes_out) {
+                                                   const double* rxd, ExactRec* out, unsigned long long* bytes_out,
+                                                   unsigned long long* next_path) {
   __shared__ LabelCache s_cache[4][NB_MAXI];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   unsigned long long bytes = 0;
-  for (int64_t i = warp0; i < C.n; i += n_warps) {
+  // paths are handed out one at a time (iteration counts differ by 100x, so a static
+  // split would leave warps and their blocks waiting on the slowest path)
+  for (;;) {
+    unsigned long long grab = 0;
+    if (lane == 0) grab = atomicAdd(next_path, 1ull);
+    const int64_t i = (int64_t)__shfl_sync(FULL, grab, 0);
+    if (i >= C.n) break;
     const int n = (int)C.nint[i];
     const uint32_t types = C.types[i];
     const uint32_t tx = C.tx[i], rx = C.rx[i];
@@ -662,13 +680,13 @@ int refine_paths(Mem& mem, SceneObj* S, CoarseObj* C, const nimbus_refine_params
   rp.rho = p->rho;
   CoarseView cv{C->tx, C->rx, C->nint, C->types, C->ie, C->lab, C->gid, n};
   Scratch sc(&mem, st);
-  unsigned long long* rbytes;
-  NB_TRY(sc.get(&rbytes, 1));
-  NB_CUDA(err, cudaMemsetAsync(rbytes, 0, sizeof(unsigned long long), st));
+  unsigned long long* rbytes;   // [0] bytes read, [1] next path to hand out
+  NB_TRY(sc.get(&rbytes, 2));
+  NB_CUDA(err, cudaMemsetAsync(rbytes, 0, 2 * sizeof(unsigned long long), st));
   StageTimer tm(st);
   const int e0 = tm.mark();
   const unsigned G = std::min<unsigned>(grid_for(n * 32, 128), pgrid(128));
-  k_refine<<<G, 128, 0, st>>>(S->d, rp, cv, C->txd, C->rxd, P->all, rbytes);
+  k_refine<<<G, 128, 0, st>>>(S->d, rp, cv, C->txd, C->rxd, P->all, rbytes, rbytes + 1);
   NB_LAUNCHED(err);
   const int e1 = tm.mark();
   unsigned long long* best;

@@ -45,6 +45,9 @@ struct DTrace {
   const uint32_t* vis_ie;    // [n_tx * ie_words] TX -> IE visibility bits
   int ie_words;
   const uint32_t* vis_rx;    // [n_tx * n_rx]
+  const int32_t* rx_owner;   // [n_rx] TX allowed to reach each RX (-1: any), or null
+  const int32_t* rx_max_int; // [n_rx] interaction limit of each RX (-1: none), or null
+  const int32_t* tx_max_int; // [n_tx] depth to which each TX's tree is expanded, or null
   unsigned long long* stats;
   uint32_t* overflow;        // [0] largest node slot requested, [1] coarse slot requested
 };
@@ -198,6 +201,7 @@ struct PrimaryAcc {
   }
   __device__ void rx(int j, float3, float miss, unsigned long long& bytes) {
     bytes += 4;
+    if (tr->rx_owner && tr->rx_owner[j] >= 0 && tr->rx_owner[j] != t) return;
     if (__ldg(&tr->vis_rx[(size_t)t * tr->n_rx + j])) atomicMin(&los[(size_t)t * tr->n_rx + j], __float_as_uint(miss));
   }
 };
@@ -285,7 +289,8 @@ __global__ void k_first_flags(DScene s, DTrace tr, const uint32_t* first_bits, u
     int64_t k = i % s.n_ie;
     bool hit = (first_bits[(size_t)t * tr.ie_words + (k >> 5)] >> (k & 31)) & 1u;
     uint32_t kind = __float_as_uint(s.ies[k].nrm_meta.w) & 1u;
-    bool ok = hit && tr.max_int >= 1 && (kind == IE_POINT ? tr.max_refl >= 1 : tr.max_diff >= 1);
+    bool ok = hit && tr.max_int >= 1 && (!tr.tx_max_int || tr.tx_max_int[t] >= 1) &&
+              (kind == IE_POINT ? tr.max_refl >= 1 : tr.max_diff >= 1);
     fr[i] = ok && kind == IE_POINT;
     fd[i] = ok && kind == IE_EDGE;
   }
@@ -381,6 +386,8 @@ struct LevelAcc {
     return true;
   }
   __device__ void rx(int j, float3 pos, float miss, unsigned long long& bytes) {
+    if (tr->rx_owner && tr->rx_owner[j] >= 0 && (uint32_t)tr->rx_owner[j] != tx) return;
+    if (tr->rx_max_int && tr->rx_max_int[j] >= 0 && (int)depth > tr->rx_max_int[j]) return;
     ++vis;
     if (visible(*s, c->apex, pos, c->origin, Endpoint{IGN_NONE, NB_NONE_LABEL}, bytes))
       emit_coarse(*tr, cb, tx, (uint32_t)j, self_ref, depth, miss);
@@ -457,7 +464,7 @@ __global__ void k_level(DScene s, DTrace tr, NodeLevel cur, NodeLevel next, Coar
     acc.nd = nd;
     acc.depth = depth;
     acc.self_ref = idx | (refl ? 0u : 0x80000000u);
-    acc.can_child = (int)depth < tr.max_int;
+    acc.can_child = (int)depth < tr.max_int && (!tr.tx_max_int || (int)depth < tr.tx_max_int[acc.tx]);
     acc.vis = 0;
     bool test_edges = acc.can_child && (int)nd < tr.max_diff;
     ++cones;
@@ -773,6 +780,36 @@ int trace_coarse(Mem& mem, SceneObj* S, const double* txh, int n_tx, const doubl
   tr.vis_rx = vis_rx;
   tr.stats = stats;
   tr.overflow = overflow;
+  // optional per-RX owner TX and interaction limit (request batching); each TX's
+  // tree is then expanded only as deep as the deepest RX it serves
+  tr.rx_owner = nullptr;
+  tr.rx_max_int = nullptr;
+  tr.tx_max_int = nullptr;
+  if (n_rx > 0 && (p->rx_owner || p->rx_max_int)) {
+    std::vector<int32_t> own(n_rx, -1), mx(n_rx, -1), lim(n_tx, 0);
+    if (p->rx_owner) NB_CUDA(err, cudaMemcpy(own.data(), p->rx_owner, n_rx * sizeof(int32_t), cudaMemcpyDefault));
+    if (p->rx_max_int) NB_CUDA(err, cudaMemcpy(mx.data(), p->rx_max_int, n_rx * sizeof(int32_t), cudaMemcpyDefault));
+    for (int j = 0; j < n_rx; ++j) {
+      if (own[j] >= n_tx) {
+        *err = "trace: rx_owner names a TX that does not exist";
+        return NIMBUS_ERR_ARG;
+      }
+      int d = mx[j] >= 0 ? std::min(mx[j], max_int) : max_int;
+      if (own[j] >= 0) lim[own[j]] = std::max(lim[own[j]], d);
+      else
+        for (int t = 0; t < n_tx; ++t) lim[t] = std::max(lim[t], d);
+    }
+    int32_t *d_own, *d_mx, *d_lim;
+    NB_TRY(sc.get(&d_own, n_rx));
+    NB_TRY(sc.get(&d_mx, n_rx));
+    NB_TRY(sc.get(&d_lim, n_tx));
+    NB_CUDA(err, cudaMemcpyAsync(d_own, own.data(), n_rx * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    NB_CUDA(err, cudaMemcpyAsync(d_mx, mx.data(), n_rx * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    NB_CUDA(err, cudaMemcpyAsync(d_lim, lim.data(), n_tx * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    tr.rx_owner = d_own;
+    tr.rx_max_int = d_mx;
+    tr.tx_max_int = d_lim;
+  }
 
   // bounded buffers: nodes per level and coarse paths
   const int64_t cap_nodes = p->max_nodes > 0 ? p->max_nodes : (int64_t)8 << 20;

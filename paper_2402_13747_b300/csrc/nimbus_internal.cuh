@@ -216,39 +216,73 @@ __device__ __forceinline__ bool sdf_local(const DScene& s, uint32_t pb, uint32_t
   return true;
 }
 
-// Ray / point-set intersection (Section 2.2.1) in the IE's local frame.  c is the
-// IE's bounding-box centre, x0 the ray point nearest it (relative to c), d the unit
-// direction;
-// the segment [-L/2, L/2] around x0 is marched from its near end by |f| until f
-// changes sign or |f| < eps.  Returns the hit offset tau from x0 (secant step on a
-// sign change, one Newton step otherwise), false on a miss.
-__device__ __forceinline__ bool sdf_march(const DScene& s, uint32_t pb, uint32_t pc, float3 c, float3 x0,
-                                          float3 d, float* tau_hit, unsigned long long& bytes) {
-  float half = 0.5f * s.seg_len;
-  float t = -half;
-  float f;
+// The |f| march of Section 2.2.1 on [t0, t_end] along unit direction d, for any
+// evaluator eval(t, &f, &n) of Eq. 1 on the ray.  Steps t += |f(t)| until the sign
+// of f changes (secant placement) or |f| < eps (one Newton step along the ray);
+// false when the segment end is passed, the step budget runs out or every weight
+// vanishes.
+// With Jump set (visibility only, where the caller keeps a yes/no decision): where
+// f falls geometrically between two steps (as it does exactly on a surface that is
+// linear along the ray), the step k at which the march would first see |f| < eps,
+// and its position, follow in closed form; the march jumps there only if that step
+// is within the budget and the segment and one evaluation there confirms |f| < eps
+// with the same sign, else it continues step by step.  The placed hit then moves by
+// up to eps along the ray, so the re-projection of the refinement, whose points are
+// results, marches without it.
+template <bool Jump, class Eval>
+__device__ __forceinline__ bool march_abs_f(Eval&& eval, float3 d, float t0, float t_end, float eps, int max_steps,
+                                            float* t_hit) {
+  float t = t0, f;
   float3 n;
-  if (!sdf_local(s, pb, pc, c, x0 + t * d, &f, &n, bytes)) return false;
-  for (int it = 0; it < s.sdf_max_steps; ++it) {
-    if (fabsf(f) < s.sdf_eps) {
+  if (!eval(t, &f, &n)) return false;
+  for (int it = 0; it < max_steps; ++it) {
+    if (fabsf(f) < eps) {
       float dn = dot(n, d);
-      *tau_hit = fabsf(dn) > 1e-3f ? t - f / dn : t;
+      *t_hit = fabsf(dn) > 1e-3f ? t - f / dn : t;
       return true;
     }
     float tn = t + fabsf(f);
-    if (tn > half) return false;
+    if (tn > t_end) return false;
     float fn;
     float3 nn;
-    if (!sdf_local(s, pb, pc, c, x0 + tn * d, &fn, &nn, bytes)) return false;
+    if (!eval(tn, &fn, &nn)) return false;
     if ((fn < 0.f) != (f < 0.f)) {
-      *tau_hit = t - f * (tn - t) / (fn - f);
+      *t_hit = t - f * (tn - t) / (fn - f);
       return true;
+    }
+    const float a0 = fabsf(f), a1 = fabsf(fn);
+    if (Jump && a1 >= eps && a1 < 0.9f * a0) {
+      const float lq = __logf(a1 / a0);                      // log of the ratio, < 0
+      const int k = (int)ceilf(__logf(eps / a1) / lq);        // steps after tn to |f| < eps
+      if (k >= 2 && it + 1 + k < max_steps) {
+        const float tk = tn + a1 * (1.f - __expf((float)k * lq)) / (1.f - a1 / a0);
+        float fk;
+        float3 nk;
+        if (tk <= t_end && eval(tk, &fk, &nk) && fabsf(fk) < eps && ((fk < 0.f) == (fn < 0.f))) {
+          t = tk;
+          f = fk;
+          n = nk;
+          it += k;
+          continue;
+        }
+      }
     }
     t = tn;
     f = fn;
     n = nn;
   }
   return false;
+}
+
+// Ray / point-set intersection (Section 2.2.1) in the IE's local frame for the
+// visibility test: c is the IE's bounding-box centre, x0 the ray point nearest it
+// (relative to c), d the unit direction; the segment [-L/2, L/2] around x0 is
+// marched from its near end.  Returns the hit offset tau from x0, false on a miss.
+__device__ __forceinline__ bool sdf_march(const DScene& s, uint32_t pb, uint32_t pc, float3 c, float3 x0,
+                                          float3 d, float* tau_hit, unsigned long long& bytes) {
+  const float half = 0.5f * s.seg_len;
+  auto eval = [&](float t, float* f, float3* n) { return sdf_local(s, pb, pc, c, x0 + t * d, f, n, bytes); };
+  return march_abs_f<true>(eval, d, -half, half, s.sdf_eps, s.sdf_max_steps, tau_hit);
 }
 
 struct Endpoint {

@@ -86,31 +86,9 @@ __device__ bool sdf_warp(const DScene& s, uint32_t pb, uint32_t pc, float3 c, fl
 // The Eq. 1 march of Section 2.2.1 (see sdf_march) with warp-shared sums.
 __device__ bool sdf_march_warp(const DScene& s, uint32_t pb, uint32_t pc, float3 c, float3 x0, float3 d,
                                float* tau_hit, int lane, unsigned long long& bytes) {
-  float half = 0.5f * s.seg_len;
-  float t = -half;
-  float f;
-  float3 n;
-  if (!sdf_warp(s, pb, pc, c, x0 + t * d, &f, &n, lane, bytes)) return false;
-  for (int it = 0; it < s.sdf_max_steps; ++it) {
-    if (fabsf(f) < s.sdf_eps) {
-      float dn = dot(n, d);
-      *tau_hit = fabsf(dn) > 1e-3f ? t - f / dn : t;
-      return true;
-    }
-    float tn = t + fabsf(f);
-    if (tn > half) return false;
-    float fn;
-    float3 nn;
-    if (!sdf_warp(s, pb, pc, c, x0 + tn * d, &fn, &nn, lane, bytes)) return false;
-    if ((fn < 0.f) != (f < 0.f)) {
-      *tau_hit = t - f * (tn - t) / (fn - f);
-      return true;
-    }
-    t = tn;
-    f = fn;
-    n = nn;
-  }
-  return false;
+  const float half = 0.5f * s.seg_len;
+  auto eval = [&](float t, float* f, float3* n) { return sdf_warp(s, pb, pc, c, x0 + t * d, f, n, lane, bytes); };
+  return march_abs_f<true>(eval, d, -half, half, s.sdf_eps, s.sdf_max_steps, tau_hit);
 }
 
 // Same-label IEs near one re-projection target, cached in shared memory for each
@@ -271,39 +249,19 @@ __device__ bool reproject_warp(const DScene& s, d3 P, d3 R, uint32_t label, d3* 
   const float3 c0 = tof(R);
   const float3 r0 = tof(R - tod(c0));      // R relative to its FP32 rounding
   const float half = 0.5f * s.seg_len;
-  float t = -half, th = 0.f, f;
+  float th = 0.f, f;
   float3 n;
   int dg[3];
-  bool hit = false;
-  float3 xl = r0 + t * d;
-  rel_subvoxel(s, c0, xl, gR, dg);
-  if (!sdf_label_warp(s, lc, xl, dg, c0, &f, &n, lane, bytes)) return false;
-  for (int it = 0; it < s.sdf_max_steps; ++it) {
-    if (fabsf(f) < s.sdf_eps) {
-      float dn = dot(n, d);
-      th = fabsf(dn) > 1e-3f ? t - f / dn : t;
-      hit = true;
-      break;
-    }
-    float tn = t + fabsf(f);
-    if (tn > half) return false;
-    float fn;
-    float3 nn;
-    xl = r0 + tn * d;
-    rel_subvoxel(s, c0, xl, gR, dg);
-    if (!sdf_label_warp(s, lc, xl, dg, c0, &fn, &nn, lane, bytes)) return false;
-    if ((fn < 0.f) != (f < 0.f)) {
-      th = t - f * (tn - t) / (fn - f);
-      hit = true;
-      break;
-    }
-    t = tn;
-    f = fn;
-    n = nn;
-  }
+  auto eval = [&](float t, float* fo, float3* no) {
+    float3 x = r0 + t * d;
+    int g[3];
+    rel_subvoxel(s, c0, x, gR, g);
+    return sdf_label_warp(s, lc, x, g, c0, fo, no, lane, bytes);
+  };
+  if (!march_abs_f<false>(eval, d, -half, half, s.sdf_eps, s.sdf_max_steps, &th)) return false;
   // the placed hit must stay on the marched segment (and in front of P)
-  if (!hit || !(tR + (double)th > 0.0) || fabsf(th) > half) return false;
-  xl = r0 + th * d;
+  if (!(tR + (double)th > 0.0) || fabsf(th) > half) return false;
+  float3 xl = r0 + th * d;
   rel_subvoxel(s, c0, xl, gR, dg);
   if (!sdf_label_warp(s, lc, xl, dg, c0, &f, &n, lane, bytes)) return false;
   *c_out = R + (double)th * tod(d);

@@ -147,6 +147,29 @@ def cpu_baseline():
             "exact_paths_per_s": len(e.paths()["n"]) / T}
 
 
+def rank_scene(rank: int):
+    """The workload of one rank: the same noisy room on every rank; rank 0 uses the
+    scene's own 4 TX x 16 RX, rank r > 0 its own seeded draw (weak scaling)."""
+    from paper_2402_13747_b300 import scenes
+    sc = scenes.room_noisy()
+    if rank:
+        sc = sc.with_pairs(*scenes.room_noisy_pairs(1000 + rank, sc.tx.shape[0], sc.rx.shape[0]))
+    return sc
+
+
+def reduce_over_ranks(t_total: float, cones: float, paths: float, device):
+    """Whole-job figures after the timed region: the slowest rank's time and the
+    units of all ranks (the only collectives; none on the data path)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([t_total, cones, paths], dtype=torch.float64, device=device)
+    tmax = t[:1].clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    units = t[1:].clone()
+    dist.all_reduce(units, op=dist.ReduceOp.SUM)
+    return float(tmax[0]), float(units[0]), float(units[1])
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -156,6 +179,8 @@ def main():
     ap.add_argument("--plain-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--pairs", default="", help="TxR: only the first T TX and R RX (small profiling cases)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -174,7 +199,12 @@ def main():
             import torch.distributed as dist
             dist.barrier()
 
-    sc = scenes.room_noisy(seed=1 + rank) if rank else scenes.room_noisy()
+    sc = rank_scene(rank)
+    workload = WORKLOAD
+    if args.pairs:
+        nt, nr = (int(v) for v in args.pairs.lower().split("x"))
+        sc = sc.with_pairs(sc.tx[:nt], sc.rx[:nr])
+        workload = WORKLOAD.replace("4 TX x 16 RX", f"{nt} TX x {nr} RX (subset)")
     p = config.params_for(sc)
     dev = torch.device("cuda", local)
     T = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)  # noqa: E731
@@ -220,12 +250,7 @@ def main():
     cones = sum(c["n_cones"] for c in counts)
     paths = sum(c["n_paths"] for c in counts)
     if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([t_total, cones, paths], dtype=torch.float64, device=dev)
-        tmax = t.clone()
-        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
-        t_total, cones, paths = float(tmax[0]), float(t[1]), float(t[2])
+        t_total, cones, paths = reduce_over_ranks(t_total, cones, paths, dev)
     c0 = counts[-1]
     value = cones / t_total
     exact_ps = paths / t_total
@@ -254,7 +279,7 @@ def main():
                   tx=sc.tx, rx=sc.rx).items()}
         h2d = sum(int(t.numel() * t.element_size()) for t in h.values())
         e2e_t, e2e_cones, d2h = [], 0, 0
-        for i in range(args.warmup + args.steps):
+        for i in range(0 if args.no_e2e else args.warmup + args.steps):
             flush.fill_(1)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -270,8 +295,9 @@ def main():
                 e2e_t.append(dt)
                 e2e_cones += res["counts"]["n_cones"]
                 d2h = int(len(res["n"]) * 320 + 8 * 24)
-        e2e = {"value": e2e_cones / sum(e2e_t), "unit": "rays/s", "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h, "exact_paths_per_s": paths / max(1, len(counts)) / statistics.mean(e2e_t)}
+        e2e = None if args.no_e2e else {
+            "value": e2e_cones / sum(e2e_t), "unit": "rays/s", "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "exact_paths_per_s": paths / max(1, len(counts)) / statistics.mean(e2e_t)}
 
         # plain form: one trace + refine per TX/RX pair on the resident scene
         plain = None
@@ -318,7 +344,7 @@ def main():
                "warmup": args.warmup, "ms_per_step": float(statistics.mean(ms)), "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f32 traversal / f64 refinement",
                "data": "synthetic",
-               "config": {"workload": WORKLOAD, "l2": "flushed between timed steps (512 MB write)",
+               "config": {"workload": workload, "l2": "flushed between timed steps (512 MB write)",
                           "points": int(sc.xyz.shape[0]), "pairs": int(sc.tx.shape[0] * sc.rx.shape[0]),
                           "form": "batched: all pairs in one trace_coarse + refine"},
                "exact_paths_per_s": exact_ps, "exact_paths_per_step": paths / args.steps / world,

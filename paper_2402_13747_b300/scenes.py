@@ -241,16 +241,27 @@ def room_noisy(seed: int = 1, n_tx: int = 4, n_rx: int = 16, spacing: float = 0.
     xyz64, nrm64 = _perturb(xyz.astype(np.float64), nrm.astype(np.float64), rng, 0.005, 2.0)
     edges, elab = _box_edges(BOX_LO, BOX_HI, 11)
 
-    def in_box(p):
-        m = 0.3
-        return (BOX_LO[0] - m <= p[0] <= BOX_HI[0] + m and BOX_LO[1] - m <= p[1] <= BOX_HI[1] + m
-                and p[2] <= BOX_HI[2] + m)
-
-    tx = _uniform_points(rng, n_tx, [0.3, 0.3, 0.3], [9.7, 9.7, 2.7], in_box)
-    rx = _uniform_points(rng, n_rx, [0.3, 0.3, 0.3], [9.7, 9.7, 2.7], in_box)
+    tx, rx = _noisy_room_pairs(rng, n_tx, n_rx)
     return Scene("room_noisy", np.ascontiguousarray(xyz64.astype(np.float32)),
                  np.ascontiguousarray(nrm64.astype(np.float32)), lab, mat, edges, elab, tx, rx,
                  max_refl=3, max_diff=1, meta={"spacing": spacing, "room": (10.0, 10.0, 3.0)})
+
+
+def _near_box(p):
+    m = 0.3
+    return (BOX_LO[0] - m <= p[0] <= BOX_HI[0] + m and BOX_LO[1] - m <= p[1] <= BOX_HI[1] + m
+            and p[2] <= BOX_HI[2] + m)
+
+
+def _noisy_room_pairs(rng, n_tx, n_rx):
+    tx = _uniform_points(rng, n_tx, [0.3, 0.3, 0.3], [9.7, 9.7, 2.7], _near_box)
+    rx = _uniform_points(rng, n_rx, [0.3, 0.3, 0.3], [9.7, 9.7, 2.7], _near_box)
+    return tx, rx
+
+
+def room_noisy_pairs(seed: int, n_tx: int = 4, n_rx: int = 16):
+    """Another seeded TX/RX draw for the noisy room (same rules as room_noisy)."""
+    return _noisy_room_pairs(np.random.default_rng(seed), n_tx, n_rx)
 
 
 def indoor(seed: int = 2, n_rx: int = 256, target_points: int = 2_000_000) -> Scene:

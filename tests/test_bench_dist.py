@@ -1,0 +1,54 @@
+"""The N > 1 path of bench.py on CPU: two gloo ranks, no GPU.
+
+Each rank runs its own TX/RX draw on a replica of the same scene (weak scaling, no
+collective on the data path); after the timed region the slowest rank's time and
+the units of all ranks are reduced.
+"""
+import os
+import socket
+
+import numpy as np
+import torch.multiprocessing as mp
+
+import bench
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, out):
+    import torch
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        sc = bench.rank_scene(rank)
+        # per-rank figures as the timed loop would produce them
+        t_total, cones, paths = 1.0 + rank, 1000.0 * (rank + 1), 10.0 * (rank + 1)
+        res = bench.reduce_over_ranks(t_total, cones, paths, torch.device("cpu"))
+        dist.barrier()
+        out[rank] = (res, sc.tx.copy(), sc.rx.copy(), int(sc.xyz.shape[0]))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_ranks_reduce_and_draw_their_own_pairs():
+    world = 2
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as m:
+        out = m.dict()
+        mp.start_processes(_rank_main, args=(world, _free_port(), out), nprocs=world, join=True,
+                           start_method="spawn")
+        res0, tx0, rx0, n0 = out[0]
+        res1, tx1, rx1, n1 = out[1]
+    # max over ranks for the time, sums for the units, identical on every rank
+    assert res0 == res1 == (2.0, 3000.0, 30.0)
+    # same geometry, different seeded pairs, same pair count (fixed work per rank)
+    assert n0 == n1
+    assert tx0.shape == tx1.shape == (4, 3) and rx0.shape == rx1.shape == (16, 3)
+    assert not np.allclose(tx0, tx1)
+    for p in np.vstack([tx0, tx1, rx0, rx1]):
+        assert 0.3 <= p[0] <= 9.7 and 0.3 <= p[1] <= 9.7 and 0.3 <= p[2] <= 2.7

@@ -193,7 +193,7 @@ __device__ __forceinline__ bool segment_sphere(float3 A, float3 d, float T, floa
 // bounding-box centre c so the FP32 sums stay well conditioned.
 __device__ __forceinline__ bool sdf_local(const DScene& s, uint32_t pb, uint32_t pc, float3 c, float3 x,
                                           float* f, float3* n_out, unsigned long long& bytes) {
-  bytes += 32ull * pc;
+  bytes += 24ull * pc;
   float sw = 0.f;
   float3 sp = f3(0.f, 0.f, 0.f), sn = f3(0.f, 0.f, 0.f);
   for (uint32_t k = 0; k < pc; ++k) {

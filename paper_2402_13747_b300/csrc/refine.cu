@@ -52,35 +52,66 @@ __device__ __forceinline__ d3 shfl3(d3 a, int src) {
   return D3(__shfl_sync(FULL, a.x, src), __shfl_sync(FULL, a.y, src), __shfl_sync(FULL, a.z, src));
 }
 
+// Warp sums of eight values, returned to every lane: a reduce-scatter (each xor
+// level keeps half of the values and sends the other half, 4 + 2 + 1 shuffles), two
+// more levels on the last value, then one broadcast per value -- 16 shuffles
+// instead of 40 for eight independent butterflies.  After the scatter levels lane L
+// holds the total of value ((L>>2)&1) + 2((L>>3)&1) + 4((L>>4)&1), i.e. value q sits
+// in lane 4q.
+__device__ __forceinline__ void wsum8(float v[8], int lane) {
+  const bool u4 = lane & 16, u3 = lane & 8, u2 = lane & 4;
+  float a[4], b[2];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    float send = u4 ? v[k] : v[k + 4], keep = u4 ? v[k + 4] : v[k];
+    a[k] = keep + __shfl_xor_sync(FULL, send, 16);
+  }
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    float send = u3 ? a[k] : a[k + 2], keep = u3 ? a[k + 2] : a[k];
+    b[k] = keep + __shfl_xor_sync(FULL, send, 8);
+  }
+  float send = u2 ? b[0] : b[1], c = (u2 ? b[1] : b[0]) + __shfl_xor_sync(FULL, send, 4);
+  c += __shfl_xor_sync(FULL, c, 2);
+  c += __shfl_xor_sync(FULL, c, 1);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) v[k] = __shfl_sync(FULL, c, 4 * k);
+}
+
+// One Eq. 1 term: point P with normal N (both relative to the frame of x) adds its
+// Gaussian weight to the sums (weight, weighted position, weighted normal).
+__device__ __forceinline__ void eq1_term(float v[8], float3 x, float4 P, float4 N, float3 c, float inv_s2) {
+  float3 p = xyz(P) - c;
+  float3 d = x - p;
+  float w = expf(-dot(d, d) * inv_s2);
+  v[0] += w;
+  v[1] += w * p.x; v[2] += w * p.y; v[3] += w * p.z;
+  v[4] += w * N.x; v[5] += w * N.y; v[6] += w * N.z;
+}
+
+// f and normal from the reduced sums; false when every weight vanished.
+__device__ __forceinline__ bool eq1_finish(const float v[8], float3 x, float* f, float3* n_out) {
+  if (!(v[0] > 0.f)) return false;
+  float3 sn = f3(v[4], v[5], v[6]);
+  float nn = len(sn);
+  if (!(nn > 0.f)) return false;
+  float3 n = (1.f / nn) * sn;
+  float3 p = (1.f / v[0]) * f3(v[1], v[2], v[3]);
+  *f = dot(x - p, n);
+  if (n_out) *n_out = n;
+  return true;
+}
+
 // Eq. 1 over the points of one IE, the points split across the warp's lanes; every
 // lane returns the same f and normal.  c is the IE's bounding-box centre, x is
 // relative to c.
 __device__ bool sdf_warp(const DScene& s, uint32_t pb, uint32_t pc, float3 c, float3 x, float* f, float3* n_out,
                          int lane, unsigned long long& bytes) {
-  float sw = 0.f, px = 0.f, py = 0.f, pz = 0.f, nx = 0.f, ny = 0.f, nz = 0.f;
-  for (uint32_t k = lane; k < pc; k += 32) {
-    float4 P = __ldg(&s.pts[pb + k]);
-    float4 N = __ldg(&s.pnrm[pb + k]);
-    float3 p = xyz(P) - c;
-    float3 d = x - p;
-    float w = expf(-dot(d, d) * s.sdf_inv_s2);
-    sw += w;
-    px += w * p.x; py += w * p.y; pz += w * p.z;
-    nx += w * N.x; ny += w * N.y; nz += w * N.z;
-  }
-  if (lane == 0) bytes += 32ull * pc;
-  sw = wsum(sw);
-  px = wsum(px); py = wsum(py); pz = wsum(pz);
-  nx = wsum(nx); ny = wsum(ny); nz = wsum(nz);
-  if (!(sw > 0.f)) return false;
-  float3 sn = f3(nx, ny, nz);
-  float nn = len(sn);
-  if (!(nn > 0.f)) return false;
-  float3 n = (1.f / nn) * sn;
-  float3 p = (1.f / sw) * f3(px, py, pz);
-  *f = dot(x - p, n);
-  if (n_out) *n_out = n;
-  return true;
+  float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  for (uint32_t k = lane; k < pc; k += 32) eq1_term(v, x, __ldg(&s.pts[pb + k]), __ldg(&s.pnrm[pb + k]), c, s.sdf_inv_s2);
+  if (lane == 0) bytes += 24ull * pc;
+  wsum8(v, lane);
+  return eq1_finish(v, x, f, n_out);
 }
 
 // The Eq. 1 march of Section 2.2.1 (see sdf_march) with warp-shared sums.
@@ -186,41 +217,67 @@ __device__ void fill_cache(const DScene& s, LabelCache& lc, const int gR[3], uin
 
 // Eq. 1 over the nearby points of one label -- the points of the cached IEs whose
 // subvoxel lies in the 3x3x3 block around the subvoxel of x -- in FP32 in a frame
-// centred on c0 (the target); xl = x - c0, dg = subvoxel of x minus gR.  The sums
-// are split across lanes; every lane returns the same f and normal.
+// centred on c0 (the target); xl = x - c0, dg = subvoxel of x minus gR.  The block's
+// IEs are found with one ballot per 32 cache entries and taken IE_BATCH at a time:
+// lane k reads point k of each IE of the batch before any of them is summed, so
+// IE_BATCH loads are in flight per lane (the kernel is bound by load latency).
+// Each lane adds its points in IE order; every lane returns the same f and normal.
+constexpr int IE_BATCH = 4;
 __device__ bool sdf_label_warp(const DScene& s, const LabelCache& lc, float3 xl, const int dg[3], float3 c0,
                                float* f, float3* n_out, int lane, unsigned long long& bytes) {
-  float sw = 0.f, px = 0.f, py = 0.f, pz = 0.f, nx = 0.f, ny = 0.f, nz = 0.f;
-  const int nc = lc.n;
   if (abs(dg[0]) > 1 || abs(dg[1]) > 1 || abs(dg[2]) > 1) return false;
   const int di = (dg[2] + 1) * 9 + (dg[1] + 1) * 3 + dg[0] + 1;
-  for (int q = 0; q < nc; ++q) {
-    if (!((lc.nbr[q] >> di) & 1u)) continue;
-    const uint32_t pb = lc.pb[q], pc = lc.pc[q];
-    for (uint32_t k = lane; k < pc; k += 32) {
-      float4 P = __ldg(&s.pts[pb + k]);
-      float4 N = __ldg(&s.pnrm[pb + k]);
-      float3 p = xyz(P) - c0;
-      float3 d = xl - p;
-      float w = expf(-dot(d, d) * s.sdf_inv_s2);
-      sw += w;
-      px += w * p.x; py += w * p.y; pz += w * p.z;
-      nx += w * N.x; ny += w * N.y; nz += w * N.z;
+  const int nc = lc.n;
+  static_assert(RCAP <= 96, "three ballots cover the cache");
+  const unsigned sel0 = __ballot_sync(FULL, lane < nc && ((lc.nbr[lane] >> di) & 1u));
+  const unsigned sel1 = __ballot_sync(FULL, 32 + lane < nc && ((lc.nbr[32 + lane] >> di) & 1u));
+  const unsigned sel2 = __ballot_sync(FULL, 64 + lane < nc && ((lc.nbr[64 + lane] >> di) & 1u));
+  float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  int r = 0;
+  unsigned m = sel0;
+  uint32_t total = 0;
+  for (;;) {
+    uint32_t pb[IE_BATCH], pc[IE_BATCH];
+    int got = 0;
+#pragma unroll
+    for (int u = 0; u < IE_BATCH; ++u) {
+      while (!m && r < 2) {
+        ++r;
+        m = r == 1 ? sel1 : sel2;
+      }
+      pb[u] = 0;
+      pc[u] = 0;
+      if (m) {
+        const int q = 32 * r + __ffs(m) - 1;
+        m &= m - 1;
+        pb[u] = lc.pb[q];
+        pc[u] = lc.pc[q];
+        ++got;
+      }
     }
-    if (lane == 0) bytes += 32ull * pc;
+    if (!got) break;
+    uint32_t most = 0;
+#pragma unroll
+    for (int u = 0; u < IE_BATCH; ++u) {
+      most = max(most, pc[u]);
+      total += pc[u];
+    }
+    for (uint32_t k = lane; k < most; k += 32) {
+      float4 P[IE_BATCH], N[IE_BATCH];
+#pragma unroll
+      for (int u = 0; u < IE_BATCH; ++u) {   // past an IE's end: re-read its first point, unused
+        const uint32_t kk = k < pc[u] ? k : 0u;
+        P[u] = __ldg(&s.pts[pb[u] + kk]);
+        N[u] = __ldg(&s.pnrm[pb[u] + kk]);
+      }
+#pragma unroll
+      for (int u = 0; u < IE_BATCH; ++u)
+        if (k < pc[u]) eq1_term(v, xl, P[u], N[u], c0, s.sdf_inv_s2);
+    }
   }
-  sw = wsum(sw);
-  px = wsum(px); py = wsum(py); pz = wsum(pz);
-  nx = wsum(nx); ny = wsum(ny); nz = wsum(nz);
-  if (!(sw > 0.f)) return false;
-  float3 sn = f3(nx, ny, nz);
-  float nn = len(sn);
-  if (!(nn > 0.f)) return false;
-  float3 n = (1.f / nn) * sn;
-  float3 p = (1.f / sw) * f3(px, py, pz);
-  *f = dot(xl - p, n);
-  if (n_out) *n_out = n;
-  return true;
+  if (lane == 0) bytes += 24ull * total;
+  wsum8(v, lane);
+  return eq1_finish(v, xl, f, n_out);
 }
 
 // Subvoxel of c0 + xl relative to gR.
@@ -327,7 +384,11 @@ __device__ bool visible_warp(const DScene& s, float3 A, float3 B, Endpoint ea, E
 // Precision: the iterate (interaction points, edge parameters), the re-projected
 // points and the path length are FP64; directions, gradient, local Hessian and step
 // are FP32 evaluations from FP64 differences (error ~1e-7, below grad_stop).
-__global__ void __launch_bounds__(128, 4) k_refine(DScene s, DRefine rp, CoarseView C, const double* txd,
+// Occupancy: three 4-warp blocks per SM (up to 170 registers a thread).  The kernel
+// is bound by the latency of the Eq. 1 point loads, and four IEs' loads in flight
+// per lane (IE_BATCH) hide more of it than a fourth block with fewer registers would;
+// any register spill in the point loop costs far more than either.
+__global__ void __launch_bounds__(128, 3) k_refine(DScene s, DRefine rp, CoarseView C, const double* txd,
                                                    const double* rxd, ExactRec* out, unsigned long long* bytes_out,
                                                    unsigned long long* next_path) {
   __shared__ LabelCache s_cache[4][NB_MAXI];
@@ -643,7 +704,9 @@ int refine_paths(Mem& mem, SceneObj* S, CoarseObj* C, const nimbus_refine_params
   NB_CUDA(err, cudaMemsetAsync(rbytes, 0, 2 * sizeof(unsigned long long), st));
   StageTimer tm(st);
   const int e0 = tm.mark();
-  const unsigned G = std::min<unsigned>(grid_for(n * 32, 128), pgrid(128));
+  static int refine_blocks = 0;   // resident blocks per SM (a persistent grid)
+  if (!refine_blocks) NB_CUDA(err, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&refine_blocks, k_refine, 128, 0));
+  const unsigned G = std::min<unsigned>(grid_for(n * 32, 128), (unsigned)(num_sms() * std::max(1, refine_blocks)));
   k_refine<<<G, 128, 0, st>>>(S->d, rp, cv, C->txd, C->rxd, P->all, rbytes, rbytes + 1);
   NB_LAUNCHED(err);
   const int e1 = tm.mark();

@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "nimbus_host.hpp"
+#include "warp_geom.cuh"
 
 namespace nb {
 
@@ -348,72 +349,204 @@ __global__ void k_los(DTrace tr, const uint32_t* los, CoarseBuf cb) {
   if (m != 0xFFFFFFFFu) emit_coarse(tr, cb, i / tr.n_rx, i % tr.n_rx, NO_NODE, 0, __uint_as_float(m));
 }
 
-// Propagation acceptance: visibility ray from the apex; children and RX hits.
-struct LevelAcc {
-  const DScene* s;
-  const DTrace* tr;
-  const ConeD* c;
-  NodeLevel next;
-  CoarseBuf cb;
+// A child node of the next level (Section 2.2.3): the accepted IE becomes the apex
+// of a reflected cone (point IE) or of a Keller fan (edge IE).
+__device__ void emit_child(const DTrace& tr, NodeLevel& next, uint32_t id, float3 rp, float3 apex, uint32_t kind,
+                           uint32_t tx, uint32_t nr, uint32_t nd, uint32_t depth, uint32_t self_ref) {
+  const uint32_t cnr = nr + (kind == IE_POINT), cnd = nd + (kind == IE_EDGE);
+  if ((int)cnr > tr.max_refl || (int)cnd > tr.max_diff) return;
+  const bool refl = kind == IE_POINT;
+  const uint32_t slot = atomicAdd(&next.cnt[refl ? 0 : 1], 1u);
+  const uint32_t cap = refl ? next.cap_r : next.cap_d;
+  if (slot >= cap) {
+    atomicMax(&tr.overflow[0], slot + 1);
+    return;
+  }
+  const float3 e = normalize(rp - apex);
+  const uint32_t meta = tx | (cnr << 16) | (cnd << 20) | ((depth + 1) << 24) | ((self_ref >> 31) << 28);
+  const float4 a = make_float4(rp.x, rp.y, rp.z, __uint_as_float(id));
+  const float4 b = make_float4(e.x, e.y, e.z, __uint_as_float(self_ref & 0x7fffffffu));
+  if (refl) {
+    next.ra[slot] = a; next.rb[slot] = b; next.rm[slot] = meta;
+  } else {
+    next.da[slot] = a; next.db[slot] = b; next.dm[slot] = meta;
+  }
+}
+
+// What one propagation cone needs besides its geometry.
+struct LevelCone {
   uint32_t tx, nr, nd, depth, self_ref;
-  bool can_child;
-  uint32_t vis;
-  __device__ bool ie(uint32_t id, float3 rp, uint32_t kind, uint32_t label, unsigned long long& bytes) {
-    Endpoint eb{kind == IE_EDGE ? IGN_ANY : IGN_LABEL, label};
-    ++vis;
-    if (!visible(*s, c->apex, rp, c->origin, eb, bytes)) return false;
-    if (can_child) {
-      uint32_t cnr = nr + (kind == IE_POINT), cnd = nd + (kind == IE_EDGE);
-      if ((int)cnr <= tr->max_refl && (int)cnd <= tr->max_diff) {
-        bool refl = kind == IE_POINT;
-        uint32_t slot = atomicAdd(&next.cnt[refl ? 0 : 1], 1u);
-        uint32_t cap = refl ? next.cap_r : next.cap_d;
-        if (slot >= cap) {
-          atomicMax(&tr->overflow[0], slot + 1);
-        } else {
-          float3 e = normalize(rp - c->apex);
-          uint32_t meta = tx | (cnr << 16) | (cnd << 20) | ((depth + 1) << 24) | ((self_ref >> 31) << 28);
-          float4 a = make_float4(rp.x, rp.y, rp.z, __uint_as_float(id));
-          float4 b = make_float4(e.x, e.y, e.z, __uint_as_float(self_ref & 0x7fffffffu));
-          if (refl) {
-            next.ra[slot] = a; next.rb[slot] = b; next.rm[slot] = meta;
-          } else {
-            next.da[slot] = a; next.db[slot] = b; next.dm[slot] = meta;
-          }
-        }
-      }
-    }
-    return true;
-  }
-  __device__ void rx(int j, float3 pos, float miss, unsigned long long& bytes) {
-    if (tr->rx_owner && tr->rx_owner[j] >= 0 && (uint32_t)tr->rx_owner[j] != tx) return;
-    if (tr->rx_max_int && tr->rx_max_int[j] >= 0 && (int)depth > tr->rx_max_int[j]) return;
-    ++vis;
-    if (visible(*s, c->apex, pos, c->origin, Endpoint{IGN_NONE, NB_NONE_LABEL}, bytes))
-      emit_coarse(*tr, cb, tx, (uint32_t)j, self_ref, depth, miss);
-  }
+  bool can_child, test_edges;
 };
 
-// One propagation level: reflected cones and Keller-fan cones of every node.
-__global__ void k_level(DScene s, DTrace tr, NodeLevel cur, NodeLevel next, CoarseBuf cb) {
+// Voxel cone tracing of one propagation cone by a whole warp (Section 2.2.4).  The
+// walk along the axis is the same on every lane.  At an evaluation lane l < 27
+// tests neighbour voxel l (already-evaluated voxels skipped, voxel sphere vs cone);
+// the IEs of each accepted voxel are screened one per lane (subvoxel sphere, kind,
+// separation planes), and each candidate's visibility ray (Section 2.2.1) is then
+// walked by the whole warp with the Eq. 1 sums split across lanes.  Visible IEs
+// become children; RXs reached become coarse paths; the cone stops after the
+// evaluation in which a point IE was visible.  Without children to emit (last
+// level) the remaining point IEs of that evaluation are not tested: they can only
+// confirm the stop.
+__device__ void march_cone_warp(const DScene& s, const DTrace& tr, const ConeD& c, const LevelCone& lc,
+                                NodeLevel& next, CoarseBuf& cb, int lane, unsigned long long& bytes,
+                                uint32_t& evals, uint32_t& vis) {
+  Walk w;
+  walk_init(s, c.apex, c.axis, w);
+  int last[3] = {0, 0, 0}, anchor[3] = {0, 0, 0};
+  bool have_last = false;
+  int rad = -1;
+  const int max_steps = s.nx + s.ny + s.nz + 3;
+  const float inf = __int_as_float(0x7f800000);
+  const int ldx = lane % 3 - 1, ldy = (lane / 3) % 3 - 1, ldz = lane / 9 - 1;   // lanes 0..26
+  for (int step = 0; step < max_steps; ++step) {
+    const bool in_box = rad >= 0 && abs(w.v[0] - anchor[0]) <= rad && abs(w.v[1] - anchor[1]) <= rad &&
+                        abs(w.v[2] - anchor[2]) <= rad;
+    if (!in_box) {
+      const int m = tr.march[cell_index(s, w.v[0], w.v[1], w.v[2])];
+      if (lane == 0) bytes += 1;
+      if (m > 1) {
+        anchor[0] = w.v[0]; anchor[1] = w.v[1]; anchor[2] = w.v[2];
+        rad = m - 2;
+      } else {
+        if (lane == 0) ++evals;
+        bool ok = false, has_rx = false;
+        uint2 cell = make_uint2(0u, 0u);
+        long long cu = 0;
+        if (lane < 27) {
+          const int u0 = w.v[0] + ldx, u1 = w.v[1] + ldy, u2 = w.v[2] + ldz;
+          const bool seen = have_last && abs(u0 - last[0]) <= 1 && abs(u1 - last[1]) <= 1 && abs(u2 - last[2]) <= 1;
+          if (in_grid(s, u0, u1, u2) && !seen) {
+            cu = cell_index(s, u0, u1, u2);
+            cell = __ldg(&s.cells[cu]);
+            has_rx = (__ldg(&tr.rx_bits[cu >> 5]) >> (cu & 31)) & 1u;
+            bytes += 12;
+            ok = (cell.y > 0 || has_rx) &&
+                 cone_sphere(c.apex, c.axis, c.sin_a, c.cos_a, voxel_center(s, u0, u1, u2), s.r_vox);
+          }
+        }
+        bool stop = false;
+        unsigned vm = __ballot_sync(FULL, ok && cell.y > 0);
+        while (vm) {
+          const int src = __ffs(vm) - 1;
+          vm &= vm - 1;
+          const uint32_t base = __shfl_sync(FULL, cell.x, src), cnt = __shfl_sync(FULL, cell.y, src);
+          for (uint32_t k0 = 0; k0 < cnt; k0 += 32) {
+            const uint32_t k = k0 + lane, id = base + k;
+            bool cand = false;
+            uint32_t kind = IE_POINT, lbl = 0;
+            float3 rp = f3(0.f, 0.f, 0.f);
+            if (k < cnt) {
+              const IERec* r = &s.ies[id];
+              const float4 nm = __ldg(&r->nrm_meta), sc = __ldg(&r->sc_pc);
+              bytes += 32;
+              kind = __float_as_uint(nm.w) & 1u;
+              if ((kind == IE_POINT || lc.test_edges) && cone_sphere(c.apex, c.axis, c.sin_a, c.cos_a, xyz(sc), s.r_sub)) {
+                const float4 q = __ldg(&r->rp_lab);
+                bytes += 16;
+                rp = xyz(q);
+                lbl = __float_as_uint(q.w);
+                cand = planes_ok(c, rp, tr.sep_eps);
+              }
+            }
+            unsigned cm = __ballot_sync(FULL, cand);
+            while (cm) {
+              const int j = __ffs(cm) - 1;
+              cm &= cm - 1;
+              const uint32_t cid = __shfl_sync(FULL, id, j), ckind = __shfl_sync(FULL, kind, j);
+              const uint32_t clab = __shfl_sync(FULL, lbl, j);
+              const float3 crp = f3(__shfl_sync(FULL, rp.x, j), __shfl_sync(FULL, rp.y, j), __shfl_sync(FULL, rp.z, j));
+              if (ckind == IE_POINT && stop && !lc.can_child) continue;
+              if (lane == 0) ++vis;
+              const Endpoint eb{ckind == IE_EDGE ? IGN_ANY : IGN_LABEL, clab};
+              if (!visible_warp(s, c.apex, crp, c.origin, eb, lane, bytes)) continue;
+              if (lc.can_child && lane == 0)
+                emit_child(tr, next, cid, crp, c.apex, ckind, lc.tx, lc.nr, lc.nd, lc.depth, lc.self_ref);
+              if (ckind == IE_POINT) stop = true;
+            }
+          }
+        }
+        // RXs in the accepted voxels (never stop the cone)
+        unsigned rm = __ballot_sync(FULL, ok && has_rx);
+        while (rm) {
+          const int src = __ffs(rm) - 1;
+          rm &= rm - 1;
+          const long long cus = __shfl_sync(FULL, cu, src);
+          const int q0 = rx_lower_bound(tr, (uint64_t)cus << 32);
+          for (int qb = q0;; qb += 32) {
+            const int q = qb + lane;
+            bool in = false, cand = false;
+            int rj = 0;
+            float3 pos = f3(0.f, 0.f, 0.f);
+            float miss = 0.f;
+            if (q < tr.n_rx_sorted) {
+              const uint64_t e = tr.rx_sorted[q];
+              bytes += 8;
+              in = (long long)(e >> 32) == cus;
+              if (in) {
+                rj = (int)(e & 0xffffffffu);
+                pos = xyz(__ldg(&tr.rx[rj]));
+                bytes += 16;
+                cand = cone_sphere(c.apex, c.axis, c.sin_a, c.cos_a, pos, s.r_sub) && planes_ok(c, pos, tr.sep_eps) &&
+                       !(tr.rx_owner && tr.rx_owner[rj] >= 0 && (uint32_t)tr.rx_owner[rj] != lc.tx) &&
+                       !(tr.rx_max_int && tr.rx_max_int[rj] >= 0 && (int)lc.depth > tr.rx_max_int[rj]);
+                if (cand) {
+                  const float3 v = pos - c.apex;
+                  miss = len(v - dot(v, c.axis) * c.axis);
+                }
+              }
+            }
+            const unsigned inm = __ballot_sync(FULL, in);
+            unsigned cm = __ballot_sync(FULL, cand);
+            while (cm) {
+              const int j = __ffs(cm) - 1;
+              cm &= cm - 1;
+              const int crj = __shfl_sync(FULL, rj, j);
+              const float cmiss = __shfl_sync(FULL, miss, j);
+              const float3 cpos = f3(__shfl_sync(FULL, pos.x, j), __shfl_sync(FULL, pos.y, j), __shfl_sync(FULL, pos.z, j));
+              if (lane == 0) ++vis;
+              if (visible_warp(s, c.apex, cpos, c.origin, Endpoint{IGN_NONE, NB_NONE_LABEL}, lane, bytes) && lane == 0)
+                emit_coarse(tr, cb, lc.tx, (uint32_t)crj, lc.self_ref, lc.depth, cmiss);
+            }
+            if (inm != FULL) break;   // the voxel's RX run ended in this chunk
+          }
+        }
+        have_last = true;
+        last[0] = w.v[0]; last[1] = w.v[1]; last[2] = w.v[2];
+        if (stop) break;
+      }
+    }
+    if (!walk_next(s, w, inf)) break;
+  }
+}
+
+// One propagation level: the reflected cones and Keller-fan cones of every node,
+// one warp per cone, cones handed out by a counter (their costs differ widely).
+__global__ void __launch_bounds__(256) k_level(DScene s, DTrace tr, NodeLevel cur, NodeLevel next, CoarseBuf cb,
+                                               unsigned long long* next_task) {
+  const int lane = threadIdx.x & 31;
   const uint32_t n_r = min(cur.cnt[0], cur.cap_r), n_d = min(cur.cnt[1], cur.cap_d);
   const int64_t total = (int64_t)n_r + (int64_t)n_d * tr.M;
   unsigned long long bytes = 0;
   uint32_t cones = 0, vis = 0, evals = 0;
-  for (int64_t task = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; task < total;
-       task += (int64_t)gridDim.x * blockDim.x) {
-    bool refl = task < n_r;
-    uint32_t idx = refl ? (uint32_t)task : (uint32_t)((task - n_r) / tr.M);
-    int j = refl ? 0 : (int)((task - n_r) % tr.M);
-    float4 a = refl ? cur.ra[idx] : cur.da[idx];
-    float4 b = refl ? cur.rb[idx] : cur.db[idx];
-    uint32_t meta = refl ? cur.rm[idx] : cur.dm[idx];
-    uint32_t ie = __float_as_uint(a.w);
+  for (;;) {
+    unsigned long long grab = 0;
+    if (lane == 0) grab = atomicAdd(next_task, 1ull);
+    const int64_t task = (int64_t)__shfl_sync(FULL, grab, 0);
+    if (task >= total) break;
+    const bool refl = task < n_r;
+    const uint32_t idx = refl ? (uint32_t)task : (uint32_t)((task - n_r) / tr.M);
+    const int j = refl ? 0 : (int)((task - n_r) % tr.M);
+    const float4 a = refl ? cur.ra[idx] : cur.da[idx];
+    const float4 b = refl ? cur.rb[idx] : cur.db[idx];
+    const uint32_t meta = refl ? cur.rm[idx] : cur.dm[idx];
+    const uint32_t ie = __float_as_uint(a.w);
     const IERec* r = &s.ies[ie];
-    float4 nm = __ldg(&r->nrm_meta);
-    uint32_t label = __float_as_uint(__ldg(&r->rp_lab).w);
-    bytes += 32 + 36;
-    float3 e = xyz(b);
+    const float4 nm = __ldg(&r->nrm_meta);
+    const uint32_t label = __float_as_uint(__ldg(&r->rp_lab).w);
+    if (lane == 0) bytes += 32 + 36;
+    const float3 e = xyz(b);
     ConeD c;
     c.apex = xyz(a);
     c.sin_a = tr.sin_a;
@@ -427,20 +560,20 @@ __global__ void k_level(DScene s, DTrace tr, NodeLevel cur, NodeLevel next, Coar
       c.origin = Endpoint{IGN_LABEL, label};
     } else {
       const double* E = s.edges + 12 * __float_as_uint(__ldg(&r->bbc_pb).w);
-      bytes += 96;
-      float3 w = normalize(f3((float)(E[3] - E[0]), (float)(E[4] - E[1]), (float)(E[5] - E[2])));
-      float cb_ = dot(e, w);
-      float sb2 = 1.f - cb_ * cb_;
+      if (lane == 0) bytes += 96;
+      const float3 w = normalize(f3((float)(E[3] - E[0]), (float)(E[4] - E[1]), (float)(E[5] - E[2])));
+      const float cb_ = dot(e, w);
+      const float sb2 = 1.f - cb_ * cb_;
       if (sb2 < 1e-12f) continue;
-      float sb = sqrtf(sb2);
+      const float sb = sqrtf(sb2);
       float3 ua, va;
       onb(w, &ua, &va);
-      float phi = (float)j * tr.dphi;
+      const float phi = (float)j * tr.dphi;
       float sp, cp;
       sincosf(phi, &sp, &cp);
-      float3 rr = cp * ua + sp * va;
-      float3 d = cb_ * w + sb * rr;
-      float3 n0 = f3((float)E[6], (float)E[7], (float)E[8]), n1 = f3((float)E[9], (float)E[10], (float)E[11]);
+      const float3 rr = cp * ua + sp * va;
+      const float3 d = cb_ * w + sb * rr;
+      const float3 n0 = f3((float)E[6], (float)E[7], (float)E[8]), n1 = f3((float)E[9], (float)E[10], (float)E[11]);
       if (!(dot(d, n0) > 0.f || dot(d, n1) > 0.f)) continue;
       float slo, clo, shi, chi;
       sincosf(phi - 0.5f * tr.dphi, &slo, &clo);
@@ -452,24 +585,16 @@ __global__ void k_level(DScene s, DTrace tr, NodeLevel cur, NodeLevel next, Coar
       c.rmid = rr;
       c.origin = Endpoint{IGN_ANY, label};
     }
-    uint32_t depth = (meta >> 24) & 0xfu, nr = (meta >> 16) & 0xfu, nd = (meta >> 20) & 0xfu;
-    LevelAcc acc;
-    acc.s = &s;
-    acc.tr = &tr;
-    acc.c = &c;
-    acc.next = next;
-    acc.cb = cb;
-    acc.tx = meta & 0xffffu;
-    acc.nr = nr;
-    acc.nd = nd;
-    acc.depth = depth;
-    acc.self_ref = idx | (refl ? 0u : 0x80000000u);
-    acc.can_child = (int)depth < tr.max_int && (!tr.tx_max_int || (int)depth < tr.tx_max_int[acc.tx]);
-    acc.vis = 0;
-    bool test_edges = acc.can_child && (int)nd < tr.max_diff;
-    ++cones;
-    march_cone(s, tr, c, test_edges, acc.can_child, acc, bytes, evals);
-    vis += acc.vis;
+    LevelCone lc;
+    lc.depth = (meta >> 24) & 0xfu;
+    lc.nr = (meta >> 16) & 0xfu;
+    lc.nd = (meta >> 20) & 0xfu;
+    lc.tx = meta & 0xffffu;
+    lc.self_ref = idx | (refl ? 0u : 0x80000000u);
+    lc.can_child = (int)lc.depth < tr.max_int && (!tr.tx_max_int || (int)lc.depth < tr.tx_max_int[lc.tx]);
+    lc.test_edges = lc.can_child && (int)lc.nd < tr.max_diff;
+    if (lane == 0) ++cones;
+    march_cone_warp(s, tr, c, lc, next, cb, lane, bytes, evals, vis);
   }
   add_stats(tr, cones, vis, bytes, evals);
 }
@@ -880,6 +1005,9 @@ int trace_coarse(Mem& mem, SceneObj* S, const double* txh, int n_tx, const doubl
     NB_LAUNCHED(err);
   }
   // propagation phase, one launch per depth
+  unsigned long long* task_ctr;   // cones handed out so far, one counter per level
+  NB_TRY(sc.get(&task_ctr, MAX_LEVELS));
+  NB_CUDA(err, cudaMemsetAsync(task_ctr, 0, MAX_LEVELS * sizeof(unsigned long long), st));
   const int e3 = tm.mark();
   for (int d = 1; d <= max_int; ++d) {
     NodeLevel next = d < max_int ? lv[d + 1] : lv[0];
@@ -888,7 +1016,7 @@ int trace_coarse(Mem& mem, SceneObj* S, const double* txh, int n_tx, const doubl
       next.cap_d = 0;
       next.cnt = cnts + 2 * MAX_LEVELS - 2;  // unused sink
     }
-    k_level<<<PG, 256, 0, st>>>(s, tr_lev, lv[d], next, cb);
+    k_level<<<PG, 256, 0, st>>>(s, tr_lev, lv[d], next, cb, task_ctr + d);
     NB_LAUNCHED(err);
   }
   const int e4 = tm.mark();

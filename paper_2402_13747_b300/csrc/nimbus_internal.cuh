@@ -38,6 +38,7 @@ enum { IGN_NONE = 0, IGN_LABEL = 1, IGN_ANY = 2 };
 struct DScene {
   float ox, oy, oz;        // grid origin
   float h, inv_h, hs;      // voxel edge, its inverse, subvoxel edge
+  float inv_hs;             // 1 / subvoxel edge (FP32 binning of continuous points in refinement)
   int nx, ny, nz, dv;
   double odx, ody, odz, hd, hsd;
   long long n_cells;

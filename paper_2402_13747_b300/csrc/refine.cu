@@ -110,7 +110,7 @@ __device__ void fill_cache(const DScene& s, LabelCache& lc, const int gR[3], uin
               int dg[3];
               ok = true;
               for (int a = 0; a < 3; ++a) {
-                dg[a] = (int)floorf((scv[a] - ofs[a]) / s.hs) - gR[a];
+                dg[a] = (int)floorf((scv[a] - ofs[a]) * s.inv_hs) - gR[a];
                 ok = ok && abs(dg[a]) <= 2;
               }
               pc = __float_as_uint(sc.w);
@@ -205,10 +205,12 @@ __device__ bool sdf_label_warp(const DScene& s, const LabelCache& lc, float3 xl,
 }
 
 // Subvoxel of c0 + xl relative to gR.
+// Continuous points of the refinement are binned in FP32 with the reciprocal of h_s;
+// the target's own subvoxel gR uses the same expression, so dg = 0 at the target.
 __device__ __forceinline__ void rel_subvoxel(const DScene& s, float3 c0, float3 xl, const int gR[3], int dg[3]) {
-  dg[0] = (int)floorf((c0.x - s.ox + xl.x) / s.hs) - gR[0];
-  dg[1] = (int)floorf((c0.y - s.oy + xl.y) / s.hs) - gR[1];
-  dg[2] = (int)floorf((c0.z - s.oz + xl.z) / s.hs) - gR[2];
+  dg[0] = (int)floorf((c0.x - s.ox + xl.x) * s.inv_hs) - gR[0];
+  dg[1] = (int)floorf((c0.y - s.oy + xl.y) * s.inv_hs) - gR[1];
+  dg[2] = (int)floorf((c0.z - s.oz + xl.z) * s.inv_hs) - gR[2];
 }
 
 // Re-projection (Section 2.3): the ray from P toward the updated point R is
@@ -218,17 +220,18 @@ __device__ __forceinline__ void rel_subvoxel(const DScene& s, float3 c0, float3 
 // FP32 offset along the ray, in FP64.
 __device__ bool reproject_warp(const DScene& s, d3 P, d3 R, uint32_t label, d3* c_out, float3* n_out, int lane,
                                unsigned long long& bytes, LabelCache& lc) {
-  d3 dv = R - P;
-  double tR = len(dv);
-  if (tR < 1e-12) return false;
-  const float3 d = normalize(tof(dv));
-  const int gR[3] = {(int)floor((R.x - s.odx) / s.hsd), (int)floor((R.y - s.ody) / s.hsd),
-                     (int)floor((R.z - s.odz) / s.hsd)};
+  const float3 dvf = tof(R - P);
+  const float tR = len(dvf);                // FP32: only compared with offsets of the segment
+  if (!(tR > 1e-9f)) return false;
+  const float3 d = (1.f / tR) * dvf;
+  const float3 c0 = tof(R);
+  const float3 r0 = tof(R - tod(c0));      // R relative to its FP32 rounding
+  const int zero[3] = {0, 0, 0};
+  int gR[3];
+  rel_subvoxel(s, c0, r0, zero, gR);
   if (lc.n < 0 || lc.label != label || lc.gR[0] != gR[0] || lc.gR[1] != gR[1] || lc.gR[2] != gR[2])
     fill_cache(s, lc, gR, label, lane, bytes);
   if (lc.n > RCAP || lc.n == 0) return false;
-  const float3 c0 = tof(R);
-  const float3 r0 = tof(R - tod(c0));      // R relative to its FP32 rounding
   const float half = 0.5f * s.seg_len;
   float th = 0.f, f;
   float3 n;
@@ -241,7 +244,7 @@ __device__ bool reproject_warp(const DScene& s, d3 P, d3 R, uint32_t label, d3* 
   };
   if (!march_abs_f<false>(eval, d, -half, half, s.sdf_eps, s.sdf_max_steps, &th)) return false;
   // the placed hit must stay on the marched segment (and in front of P)
-  if (!(tR + (double)th > 0.0) || fabsf(th) > half) return false;
+  if (!(tR + th > 0.f) || fabsf(th) > half) return false;
   float3 xl = r0 + th * d;
   rel_subvoxel(s, c0, xl, gR, dg);
   if (!sdf_label_warp(s, lc, xl, dg, c0, &f, &n, lane, bytes)) return false;

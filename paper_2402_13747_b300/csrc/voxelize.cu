@@ -478,6 +478,7 @@ void fill_dscene(SceneObj* S) {
   d.h = (float)h;
   d.inv_h = (float)(1.0 / h);
   d.hs = (float)hs;
+  d.inv_hs = (float)(1.0 / hs);
   d.nx = S->dims[0];
   d.ny = S->dims[1];
   d.nz = S->dims[2];

@@ -46,6 +46,23 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+# DRAM traffic of one full-size refine launch (dram__bytes_read.sum + dram__bytes_write.sum,
+# one-pass ncu capture of the timed step's k_refine), valid only for the kernel sources it
+# was taken on: the hash below covers them, and a changed kernel reports null.
+REFINE_TRAFFIC = {"bytes": 46.37e6 + 104.91e6, "sources_sha256": "8edd744740595624d2c1038dfe800ab1c7450ff125a94304d2d4c9d08a9bdaa8"}
+KERNEL_SOURCES = ("paper_2402_13747_b300/csrc/refine.cu", "paper_2402_13747_b300/csrc/warp_geom.cuh",
+                  "paper_2402_13747_b300/csrc/nimbus_internal.cuh", "include/nimbus.h")
+
+
+def kernel_sources_sha256() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
 def peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -266,8 +283,11 @@ def main():
         pk = peaks()
         peak = pk["hbm_gbs"] if pk else 6400.0
         achieved = dbytes / (dms * 1e-3) / 1e9 if dms > 0 else 0.0
+        traffic = None
+        if dom == "refine" and REFINE_TRAFFIC["sources_sha256"] == kernel_sources_sha256():
+            traffic = REFINE_TRAFFIC["bytes"]
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "kernel": dom, "kernel_ms": dms, "algorithmic_bytes": dbytes,
+                "traffic": traffic, "kernel": dom, "kernel_ms": dms, "algorithmic_bytes": dbytes,
                 "peak_source": "measured" if pk else "fallback",
                 "stage_ms": {k: v[0] for k, v in stages.items()} | {"vis_tables": c0["ms_vis"],
                                                                      "kappa": c0["ms_kappa"],
@@ -322,7 +342,10 @@ def main():
                 torch.cuda.synchronize()
                 pl_ms.append(1e3 * (time.perf_counter() - t0))
             tpl = sum(pl_ms) / 1e3
-            plain = {"rays_per_s": pl_cones / tpl, "exact_paths_per_s": pl_paths / tpl,
+            # rays_per_s counts the cones the plain form traced (each pair re-traces its TX's
+            # launch); workload_rays_per_s is the batched workload's cones over the plain time
+            plain = {"rays_per_s": pl_cones / tpl, "workload_rays_per_s": cones / len(counts) / world * args.plain_steps / tpl,
+                     "exact_paths_per_s": pl_paths / tpl,
                      "ms_per_step": statistics.mean(pl_ms), "calls_per_step": int(sc.tx.shape[0] * sc.rx.shape[0]),
                      "pair_latency_ms_p50": 1e3 * float(np.percentile(lat, 50)),
                      "pair_latency_ms_p99": 1e3 * float(np.percentile(lat, 99))}

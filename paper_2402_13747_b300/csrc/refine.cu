@@ -7,7 +7,8 @@
 // basis; neighbours come from warp shuffles.  B300's FP64 rate is a small fraction
 // of FP32, so FP64 is kept to what must accumulate without loss -- the iterate,
 // the re-projected points and the path length -- while directions, gradient, local
-// Hessian and step are FP32 evaluations of FP64 differences.  Each re-projection
+// Hessian and step are FP32 evaluations of FP64 differences (the gradient is FP64
+// again once it falls below delta, where it decides the stop).  Each re-projection
 // (a ray intersected with one label's implicit surface, Eq. 1) and each final
 // visibility ray uses all 32 lanes: the Eq. 1 sums are split across lanes and
 // combined with shuffles, in FP32 in a frame centred on the target, and the label's
@@ -261,7 +262,8 @@ __device__ bool reproject_warp(const DScene& s, d3 P, d3 R, uint32_t label, d3* 
 // R_k = c_k + r_k u_k + s_k v_k, for each diffraction D_k = c_k + t_k w_k.
 // Precision: the iterate (interaction points, edge parameters), the re-projected
 // points and the path length are FP64; directions, gradient, local Hessian and step
-// are FP32 evaluations from FP64 differences (error ~1e-7, below grad_stop).
+// are FP32 evaluations from FP64 differences, except that once ||grad|| < delta the
+// gradient that decides the stop and drives the last steps is FP64.
 // Occupancy: three 4-warp blocks per SM (up to 170 registers a thread).  The kernel
 // is bound by the latency of the Eq. 1 point loads, and four IEs' loads in flight
 // per lane (IE_BATCH) hide more of it than a fourth block with fewer registers would;
@@ -337,6 +339,25 @@ __global__ void __launch_bounds__(128, 3) k_refine(DScene s, DRefine rp, CoarseV
         }
       }
       gn = sqrtf(wsum(g0 * g0 + g1 * g1));
+      // Near the stop the gradient is taken again in FP64: at grazing incidence the
+      // local length is nearly flat along the surface, so an FP32 gradient (error
+      // ~1e-7) would move the stopping point by millimetres along it.
+      if (gn < (float)rp.delta) {
+        double h0 = 0.0, h1 = 0.0;
+        if (mine) {
+          const d3 fa = I - Ip, fb = I - In_;
+          const d3 e = (1.0 / len(fa)) * fa + (1.0 / len(fb)) * fb;
+          if (!diff) {
+            h0 = dot(e, tod(u));
+            h1 = dot(e, tod(v));
+          } else {
+            h0 = dot(e, tod(w));
+          }
+        }
+        g0 = (float)h0;
+        g1 = (float)h1;
+        gn = (float)sqrt(wsumd(h0 * h0 + h1 * h1));
+      }
       if (gn < (float)rp.grad_stop) {
         converged = true;
         break;

@@ -332,6 +332,12 @@ class Context:
         out["counts"] = c.as_dict()
         return out
 
+    def coarse_counts(self, coarse: int, stream=None) -> dict:
+        """Sizes and counters of a coarse set (no path arrays copied)."""
+        c = Counts()
+        self._check(self.L.nimbus_query_coarse(self.h, coarse, C.byref(c), None, _stream(stream)), "query_coarse")
+        return c.as_dict()
+
     def query_coarse(self, coarse: int, stream=None) -> dict:
         c = Counts()
         self._check(self.L.nimbus_query_coarse(self.h, coarse, C.byref(c), None, _stream(stream)), "query_coarse")

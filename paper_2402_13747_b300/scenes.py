@@ -464,11 +464,15 @@ def moving_box(room: Scene, step: int, seed: int = 4, size: float = 2.0, spacing
 
 
 def serving_requests(n: int, rate_hz: float, scene_ids, seed: int = 4, max_pairs: int = 64,
-                     depth_range=(2, 5), room=(10.0, 10.0, 3.0)):
+                     depth_range=(2, 5), room=(10.0, 10.0, 3.0), pools: dict | None = None,
+                     depth_caps: dict | None = None):
     """Poisson request stream: arrival time, scene id, 1 TX, 1..max_pairs RX, max depth.
 
-    Each request picks a resident scene uniformly, draws its TX and RX uniformly in
-    the room box (0.3 m from the walls) and a max interaction depth in depth_range.
+    Each request picks a resident scene uniformly and a max interaction depth in
+    depth_range (lowered to the scene's entry in depth_caps, if any).  With pools,
+    its TX and RXs are distinct positions drawn from the scene's pool (free-space
+    positions made by the scene's own generator); without, they are uniform in the
+    room box, 0.3 m from the walls.
     """
     rng = np.random.default_rng(seed)
     t = 0.0
@@ -478,9 +482,16 @@ def serving_requests(n: int, rate_hz: float, scene_ids, seed: int = 4, max_pairs
         sid = scene_ids[int(rng.integers(0, len(scene_ids)))]
         k = int(rng.integers(1, max_pairs + 1))
         depth = int(rng.integers(depth_range[0], depth_range[1] + 1))
-        lo = np.array([0.3, 0.3, 0.3])
-        hi = np.array(room) - 0.3
-        tx = lo + (hi - lo) * rng.random((1, 3))
-        rx = lo + (hi - lo) * rng.random((k, 3))
+        if depth_caps and sid in depth_caps:
+            depth = min(depth, int(depth_caps[sid]))
+        if pools and sid in pools:
+            pool = pools[sid]
+            pick = rng.choice(pool.shape[0], size=min(k + 1, pool.shape[0]), replace=False)
+            tx, rx = pool[pick[:1]], pool[pick[1:]]
+        else:
+            lo = np.array([0.3, 0.3, 0.3])
+            hi = np.array(room) - 0.3
+            tx = lo + (hi - lo) * rng.random((1, 3))
+            rx = lo + (hi - lo) * rng.random((k, 3))
         out.append({"id": i, "t": t, "scene": sid, "tx": tx, "rx": rx, "depth": depth})
     return out

@@ -151,17 +151,22 @@ class GpuExecutor:
         rx_off = np.cumsum([0] + [r.pairs for r in batch])
         dmax = int(max(r.depth for r in batch))
         p = self.params.replace(max_refl=dmax, max_diff=min(1, dmax), max_int=dmax)
-        caps = [1 << 20, 1 << 22, 1 << 23]
-        for cap in caps:   # grow the node / coarse bounds when a batch overflows them
-            c = self.ctx.trace(self.handles[sid], tx, rx, p, rx_owner=owner, rx_max_int=depth, max_nodes=cap,
-                               max_coarse=cap, stream=self.stream, allow_overflow=True)
-            P = self.ctx.refine(self.handles[sid], c, p, stream=self.stream)
-            out = self.ctx.query(P, 0, stream=self.stream)
-            ov = out["counts"]["overflow"]
-            self.ctx.release(P)
-            self.ctx.release(c)
-            if not ov or cap == caps[-1]:
+        # node / coarse buffers: the library's defaults first; a batch that overflows
+        # them is traced again with the sizes the first pass reported
+        caps = (0, 0)
+        for attempt in range(2):
+            c = self.ctx.trace(self.handles[sid], tx, rx, p, rx_owner=owner, rx_max_int=depth, max_nodes=caps[0],
+                               max_coarse=caps[1], stream=self.stream, allow_overflow=True)
+            cc = self.ctx.coarse_counts(c, stream=self.stream)
+            ov = cc["overflow"]
+            if not ov or attempt == 1:
                 break
+            self.ctx.release(c)
+            caps = (max(1 << 23, int(cc["needed_nodes"] * 1.2)), max(1 << 23, int(cc["needed_coarse"] * 1.2)))
+        P = self.ctx.refine(self.handles[sid], c, p, stream=self.stream)
+        out = self.ctx.query(P, 0, stream=self.stream)
+        self.ctx.release(P)
+        self.ctx.release(c)
         res = []
         for i, r in enumerate(batch):
             m = out["tx"] == i
@@ -254,11 +259,14 @@ class Server:
 
     def stats(self) -> dict:
         lat = np.array([r.t_done - r.t_arrival for r in self.completed])
+        svc = np.array([r.t_done - r.t_start for r in self.completed])
         paths = sum(len(r.future.result()["n"]) for r in self.completed if r.future.done()
                     and r.future.exception() is None)
         return {"requests": len(self.completed), "batches": self.batches,
                 "p50_ms": float(np.percentile(lat, 50) * 1e3) if len(lat) else None,
-                "p99_ms": float(np.percentile(lat, 99) * 1e3) if len(lat) else None, "exact_paths": paths,
+                "p99_ms": float(np.percentile(lat, 99) * 1e3) if len(lat) else None,
+                "service_p50_ms": float(np.percentile(svc, 50) * 1e3) if len(svc) else None,
+                "service_p99_ms": float(np.percentile(svc, 99) * 1e3) if len(svc) else None, "exact_paths": paths,
                 "cones": self.cones}
 
 
@@ -285,22 +293,30 @@ def run_stream(server: Server, requests: list[dict], scenes_update=None, update_
     return st
 
 
-def bench_latency(ctx=None, device: int = 0, n_requests: int = 100, rate_hz: float = 4.0, n_workers: int = 2,
-                  seed: int = 4, max_pairs: int = 16, depth_range=(2, 3)) -> dict:
-    """Serving measurement: resident tiny room and noisy room (and the moving box).
+def bench_latency(ctx=None, device: int = 0, n_requests: int = 40, rate_hz: float = 0.5, n_workers: int = 2,
+                  seed: int = 4, max_pairs: int = 64, depth_range=(2, 5), depth_caps=None) -> dict:
+    """Serving measurement on the three resident scenes of the larger configurations.
 
-    Poisson arrivals at ``rate_hz`` of requests with 1 TX, 1..max_pairs RX and a
-    depth drawn from depth_range; a 2x2x2 m box moves in the noisy room and is
-    re-voxelised every 50 requests.  Returns p50/p99 latency and throughput.
+    Resident: the noisy room with its box (133k points), the indoor scan (1.92M) and
+    the street canyon (20.0M).  Poisson arrivals at ``rate_hz``; each request picks a
+    scene, 1 TX and 1..max_pairs RXs from free-space positions of that scene, and a
+    maximum depth in depth_range, capped per scene where deeper trees leave the
+    latency budget (street: 2, indoor and room: 4; node counts grow about 6x per
+    level in the open street, and a 64-pair depth-5 request in the room refines
+    millions of coarse paths).  A 2x2x2 m box moves in the noisy room and is re-voxelised by
+    region every 50 requests.  Returns p50/p99 latency and throughput.
     """
     from . import scenes
-    res = {}
-    sc = {"room_tiny": scenes.room_tiny(), "room_noisy": scenes.room_noisy(n_tx=1, n_rx=1)}
-    server = Server(sc, Params(), n_workers=n_workers, device=device, max_pairs=64)
+    caps = {"street": 2, "indoor": 4, "room_noisy": 4} if depth_caps is None else depth_caps
+    room = scenes.room_noisy(n_tx=1, n_rx=1)
+    indoor = scenes.indoor(n_rx=512)
+    street = scenes.street(n_rx=512)
+    sc = {"room_noisy": room, "indoor": indoor, "street": street}
+    pools = {"room_noisy": scenes.room_noisy_pairs(900, 1, 512)[1], "indoor": indoor.rx, "street": street.rx}
+    server = Server(sc, Params(), n_workers=n_workers, device=device, max_pairs=128)
     reqs = scenes.serving_requests(n_requests, rate_hz, list(sc), seed=seed, max_pairs=max_pairs,
-                                   depth_range=depth_range)
+                                   depth_range=depth_range, pools=pools, depth_caps=caps)
     state = {"box": None}
-    room = sc["room_noisy"]
 
     def move(step):
         server.update_region("room_noisy", *moved_box_update(room, state, step))
@@ -309,8 +325,9 @@ def bench_latency(ctx=None, device: int = 0, n_requests: int = 100, rate_hz: flo
         res = run_stream(server, reqs, scenes_update=move)
     finally:
         server.close()
-    res.update({"rate_hz": rate_hz, "workers": n_workers, "scenes": list(sc), "requests_submitted": n_requests,
-                "pairs_per_request": f"1-{max_pairs}", "depth": f"{depth_range[0]}-{depth_range[1]}",
+    res.update({"rate_hz": rate_hz, "workers": n_workers, "scenes": {k: int(v.xyz.shape[0]) for k, v in sc.items()},
+                "requests_submitted": n_requests, "pairs_per_request": f"1-{max_pairs}",
+                "depth": f"{depth_range[0]}-{depth_range[1]}", "depth_caps": caps,
                 "moving_box": "2x2x2 m, region update every 50 requests"})
     return res
 

@@ -270,7 +270,7 @@ __device__ bool reproject_warp(const DScene& s, d3 P, d3 R, uint32_t label, d3* 
 // any register spill in the point loop costs far more than either.
 __global__ void __launch_bounds__(128, 3) k_refine(DScene s, DRefine rp, CoarseView C, const double* txd,
                                                    const double* rxd, ExactRec* out, unsigned long long* bytes_out,
-                                                   unsigned long long* next_path) {
+                                                   unsigned long long* next_path, const uint32_t* order) {
   __shared__ LabelCache s_cache[4][NB_MAXI];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   unsigned long long bytes = 0;
@@ -279,8 +279,9 @@ __global__ void __launch_bounds__(128, 3) k_refine(DScene s, DRefine rp, CoarseV
   for (;;) {
     unsigned long long grab = 0;
     if (lane == 0) grab = atomicAdd(next_path, 1ull);
-    const int64_t i = (int64_t)__shfl_sync(FULL, grab, 0);
-    if (i >= C.n) break;
+    const int64_t gi = (int64_t)__shfl_sync(FULL, grab, 0);
+    if (gi >= C.n) break;
+    const int64_t i = order[gi];
     const int n = (int)C.nint[i];
     const uint32_t types = C.types[i];
     const uint32_t tx = C.tx[i], rx = C.rx[i];
@@ -472,6 +473,13 @@ __global__ void __launch_bounds__(128, 3) k_refine(DScene s, DRefine rp, CoarseV
   if (lane == 0 && bytes) atomicAdd(bytes_out, bytes);
 }
 
+__global__ void k_order_keys(const uint32_t* nint, int64_t n, uint64_t* keys, uint32_t* vals) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    keys[i] = (uint64_t)(NB_MAXI - nint[i]);
+    vals[i] = (uint32_t)i;
+  }
+}
+
 // ------------------------------------------------------------ duplicate removal
 __global__ void k_best_len(const ExactRec* ex, int64_t n, unsigned long long* best) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -609,7 +617,18 @@ int refine_paths(Mem& mem, SceneObj* S, CoarseObj* C, const nimbus_refine_params
   static int refine_blocks = 0;   // resident blocks per SM (a persistent grid)
   if (!refine_blocks) NB_CUDA(err, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&refine_blocks, k_refine, 128, 0));
   const unsigned G = std::min<unsigned>(grid_for(n * 32, 128), (unsigned)(num_sms() * std::max(1, refine_blocks)));
-  k_refine<<<G, 128, 0, st>>>(S->d, rp, cv, C->txd, C->rxd, P->all, rbytes, rbytes + 1);
+  // hand out the paths with the most interactions first (they run longest), so the
+  // launch does not end on a few long paths
+  uint64_t *okeys, *okeys_alt;
+  uint32_t *ovals, *ovals_alt;
+  NB_TRY(sc.get(&okeys, n));
+  NB_TRY(sc.get(&okeys_alt, n));
+  NB_TRY(sc.get(&ovals, n));
+  NB_TRY(sc.get(&ovals_alt, n));
+  k_order_keys<<<grid_for(n, 256), 256, 0, st>>>(C->nint, n, okeys, ovals);
+  NB_LAUNCHED(err);
+  NB_TRY(radix_sort(sc, okeys, ovals, okeys_alt, ovals_alt, n, 8));
+  k_refine<<<G, 128, 0, st>>>(S->d, rp, cv, C->txd, C->rxd, P->all, rbytes, rbytes + 1, ovals);
   NB_LAUNCHED(err);
   const int e1 = tm.mark();
   unsigned long long* best;

@@ -219,8 +219,9 @@ __device__ __forceinline__ void rel_subvoxel(const DScene& s, float3 c0, float3 
 // that label) by the march of Section 2.2.1 on a segment of one subvoxel diameter
 // centred on R.  The march runs in FP32 relative to R; the new point is R plus the
 // FP32 offset along the ray, in FP64.
-__device__ bool reproject_warp(const DScene& s, d3 P, d3 R, uint32_t label, d3* c_out, float3* n_out, int lane,
-                               unsigned long long& bytes, LabelCache& lc) {
+__device__ bool reproject_warp(const DScene& s, const d3* Pp, const d3* Rp, uint32_t label, d3* c_out, float3* n_out,
+                               int lane, unsigned long long& bytes, LabelCache& lc) {
+  const d3 P = *Pp, R = *Rp;
   const float3 dvf = tof(R - P);
   const float tR = len(dvf);                // FP32: only compared with offsets of the segment
   if (!(tR > 1e-9f)) return false;
@@ -249,7 +250,7 @@ __device__ bool reproject_warp(const DScene& s, d3 P, d3 R, uint32_t label, d3* 
   float3 xl = r0 + th * d;
   rel_subvoxel(s, c0, xl, gR, dg);
   if (!sdf_label_warp(s, lc, xl, dg, c0, &f, &n, lane, bytes)) return false;
-  *c_out = R + (double)th * tod(d);
+  *c_out = *Rp + (double)th * tod(d);
   *n_out = n;
   return true;
 }
@@ -264,18 +265,27 @@ __device__ bool reproject_warp(const DScene& s, d3 P, d3 R, uint32_t label, d3* 
 // points and the path length are FP64; directions, gradient, local Hessian and step
 // are FP32 evaluations from FP64 differences, except that once ||grad|| < delta the
 // gradient that decides the stop and drives the last steps is FP64.
-// Occupancy: three 4-warp blocks per SM (up to 170 registers a thread).  The kernel
-// is bound by the latency of the Eq. 1 point loads, and four IEs' loads in flight
-// per lane (IE_BATCH) hide more of it than a fourth block with fewer registers would;
-// any register spill in the point loop costs far more than either.
-__global__ void __launch_bounds__(128, 3) k_refine(DScene s, DRefine rp, CoarseView C, const double* txd,
+// Occupancy: four 4-warp blocks per SM (128 registers a thread, 44 KB of shared
+// memory a block).  The kernel is bound by the latency of the Eq. 1 point loads:
+// four IEs' loads in flight per lane (IE_BATCH) and as many resident warps as the
+// registers allow both pay, and any register spill in the point loop costs far more
+// than either.  So each path's FP64 state lives in shared memory (WarpPath), indexed
+// by node (0 = TX, n+1 = RX), and is read where it is used.
+struct WarpPath {
+  d3 I[NB_MAXI + 2], c[NB_MAXI + 2], R[NB_MAXI + 2], In[NB_MAXI + 2], p0[NB_MAXI + 2];
+  double tpar[NB_MAXI + 2];
+  float3 u[NB_MAXI + 2], v[NB_MAXI + 2], w[NB_MAXI + 2];
+  float elen[NB_MAXI + 2];
+};
+
+__global__ void __launch_bounds__(128, 4) k_refine(DScene s, DRefine rp, CoarseView C, const double* txd,
                                                    const double* rxd, ExactRec* out, unsigned long long* bytes_out,
                                                    unsigned long long* next_path, const uint32_t* order) {
   __shared__ LabelCache s_cache[4][NB_MAXI];
+  __shared__ WarpPath s_path[4];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  WarpPath& W = s_path[wib];
   unsigned long long bytes = 0;
-  // paths are handed out one at a time (iteration counts differ by 100x, so a static
-  // split would leave warps and their blocks waiting on the slowest path)
   for (;;) {
     unsigned long long grab = 0;
     if (lane == 0) grab = atomicAdd(next_path, 1ull);
@@ -286,57 +296,57 @@ __global__ void __launch_bounds__(128, 3) k_refine(DScene s, DRefine rp, CoarseV
     const uint32_t types = C.types[i];
     const uint32_t tx = C.tx[i], rx = C.rx[i];
     const bool mine = lane >= 1 && lane <= n;
+    const bool node = lane <= n + 1;
     const bool diff = mine && ((types >> (lane - 1)) & 1u);
     if (lane < NB_MAXI) s_cache[wib][lane].n = -1;
-    __syncwarp();
-    // lane-local state
-    d3 I = D3(0, 0, 0), c = D3(0, 0, 0), p0 = D3(0, 0, 0);
-    float3 u = f3(0, 0, 0), v = f3(0, 0, 0), w = f3(0, 0, 0);
-    double tpar = 0.0;
-    float elen = 0.f;
     uint32_t my_lab = NB_NONE_LABEL, my_ie = 0xffffffffu;
     uint8_t my_mat = 255;
-    if (lane == 0) I = D3(txd[3 * tx], txd[3 * tx + 1], txd[3 * tx + 2]);
-    if (lane == n + 1) I = D3(rxd[3 * rx], rxd[3 * rx + 1], rxd[3 * rx + 2]);
+    if (lane == 0) W.I[0] = D3(txd[3 * tx], txd[3 * tx + 1], txd[3 * tx + 2]);
+    if (lane == n + 1) W.I[n + 1] = D3(rxd[3 * rx], rxd[3 * rx + 1], rxd[3 * rx + 2]);
     if (mine) {
       my_ie = C.ie[i * NB_MAXI + lane - 1];
       my_lab = C.lab[i * NB_MAXI + lane - 1];
       const IERec* r = &s.ies[my_ie];
       float4 rpl = r->rp_lab, nm = r->nrm_meta;
       my_mat = (uint8_t)((__float_as_uint(nm.w) >> 8) & 0xffu);
-      c = D3(rpl.x, rpl.y, rpl.z);
-      I = c;
+      W.c[lane] = D3(rpl.x, rpl.y, rpl.z);
+      W.I[lane] = W.c[lane];
+      W.tpar[lane] = 0.0;
       if (!diff) {
+        float3 u, v;
         onb(normalize(xyz(nm)), &u, &v);
+        W.u[lane] = u;
+        W.v[lane] = v;
       } else {
         const double* E = s.edges + 12 * __float_as_uint(r->bbc_pb.w);
-        p0 = D3(E[0], E[1], E[2]);
+        W.p0[lane] = D3(E[0], E[1], E[2]);
         d3 ev = D3(E[3] - E[0], E[4] - E[1], E[5] - E[2]);
         double el = len(ev);
-        elen = (float)el;
-        w = tof((1.0 / el) * ev);
+        W.elen[lane] = (float)el;
+        W.w[lane] = tof((1.0 / el) * ev);
       }
     }
+    __syncwarp();
     int status = ST_VALID, it = 0;
     bool converged = false;
     float gn = 0.f;
     for (; it <= rp.rho; ++it) {
       // gradient of Eq. 2: (e_in + e_out) . (u, v) for reflections, . w for diffractions
-      d3 Ip = shfl3(I, max(lane - 1, 0)), In_ = shfl3(I, min(lane + 1, 31));
       float g0 = 0.f, g1 = 0.f, a = 1.f, b = 1.f;
       float3 ea = f3(0, 0, 0), eb = f3(0, 0, 0);
       if (mine) {
-        float3 fa = tof(I - Ip), fb = tof(I - In_);
+        const d3 I = W.I[lane];
+        float3 fa = tof(I - W.I[lane - 1]), fb = tof(I - W.I[lane + 1]);
         a = len(fa);
         b = len(fb);
         ea = a > 0.f ? (1.f / a) * fa : fa;
         eb = b > 0.f ? (1.f / b) * fb : fb;
         float3 e = ea + eb;
         if (!diff) {
-          g0 = dot(e, u);
-          g1 = dot(e, v);
+          g0 = dot(e, W.u[lane]);
+          g1 = dot(e, W.v[lane]);
         } else {
-          g0 = dot(e, w);
+          g0 = dot(e, W.w[lane]);
         }
       }
       gn = sqrtf(wsum(g0 * g0 + g1 * g1));
@@ -346,13 +356,14 @@ __global__ void __launch_bounds__(128, 3) k_refine(DScene s, DRefine rp, CoarseV
       if (gn < (float)rp.delta) {
         double h0 = 0.0, h1 = 0.0;
         if (mine) {
-          const d3 fa = I - Ip, fb = I - In_;
+          const d3 I = W.I[lane];
+          const d3 fa = I - W.I[lane - 1], fb = I - W.I[lane + 1];
           const d3 e = (1.0 / len(fa)) * fa + (1.0 / len(fb)) * fb;
           if (!diff) {
-            h0 = dot(e, tod(u));
-            h1 = dot(e, tod(v));
+            h0 = dot(e, tod(W.u[lane]));
+            h1 = dot(e, tod(W.v[lane]));
           } else {
-            h0 = dot(e, tod(w));
+            h0 = dot(e, tod(W.w[lane]));
           }
         }
         g0 = (float)h0;
@@ -364,13 +375,14 @@ __global__ void __launch_bounds__(128, 3) k_refine(DScene s, DRefine rp, CoarseV
         break;
       }
       if (it == rp.rho) break;
-      d3 Inew = I, R = I;
       bool off = false;
+      if (node) W.In[lane] = W.I[lane];
       // step: gradient scaled by the inverse Hessian of the local length f_k (2x2 in
       // (r, s), 1x1 in t) times gamma; near-singular Hessians fall back to eta
       const float hsum = 1.f / a + 1.f / b;
       const float gam = (float)rp.gamma, eta = gam / hsum, hs = (float)rp.hs;
       if (mine && !diff) {
+        const float3 u = W.u[lane], v = W.v[lane];
         float au = dot(ea, u), av = dot(ea, v), bu = dot(eb, u), bv = dot(eb, v);
         float h11 = (1.f - au * au) / a + (1.f - bu * bu) / b;
         float h22 = (1.f - av * av) / a + (1.f - bv * bv) / b;
@@ -389,46 +401,55 @@ __global__ void __launch_bounds__(128, 3) k_refine(DScene s, DRefine rp, CoarseV
           rr *= hs / l;
           ss *= hs / l;
         }
-        R = c + (double)rr * tod(u) + (double)ss * tod(v);   // R_k = c_k + r_k u_k + s_k v_k
+        W.R[lane] = W.c[lane] + (double)rr * tod(u) + (double)ss * tod(v);   // R_k = c_k + r_k u_k + s_k v_k
       }
       if (diff) {
+        const float3 w = W.w[lane];
         float aw = dot(ea, w), bw = dot(eb, w);
         float hw = (1.f - aw * aw) / a + (1.f - bw * bw) / b;
         float dt = hw > 1e-12f * hsum ? -gam * g0 / hw : -eta * g0;
         if (fabsf(dt) > hs) dt = copysignf(hs, dt);
-        tpar += (double)dt;                                   // D_k = c_k + t_k w_k
-        Inew = c + tpar * tod(w);
-        double along = dot(Inew - p0, tod(w));
-        off = along < 0.0 || along > (double)elen;
+        const double tp = W.tpar[lane] + (double)dt;            // D_k = c_k + t_k w_k
+        W.tpar[lane] = tp;
+        const d3 Dn = W.c[lane] + tp * tod(w);
+        W.In[lane] = Dn;
+        double along = dot(Dn - W.p0[lane], tod(w));
+        off = along < 0.0 || along > (double)W.elen[lane];
       }
       if (__any_sync(FULL, off)) {
         status = ST_OFF_EDGE;
         break;
       }
+      __syncwarp();
       for (int k = 1; k <= n; ++k) {
         if ((types >> (k - 1)) & 1u) continue;
-        d3 Pk = shfl3(Ip, k), Rk = shfl3(R, k);
         uint32_t lk = __shfl_sync(FULL, my_lab, k);
         d3 cn;
         float3 nn;
-        if (!reproject_warp(s, Pk, Rk, lk, &cn, &nn, lane, bytes, s_cache[wib][k - 1])) {
+        if (!reproject_warp(s, &W.I[k - 1], &W.R[k], lk, &cn, &nn, lane, bytes, s_cache[wib][k - 1])) {
           status = ST_MISS;
           break;
         }
         if (lane == k) {
-          c = cn;
+          W.c[k] = cn;
+          float3 u, v;
           onb(normalize(nn), &u, &v);
-          Inew = cn;
+          W.u[k] = u;
+          W.v[k] = v;
+          W.In[k] = cn;
         }
       }
       if (status != ST_VALID) break;
-      I = Inew;
+      __syncwarp();
+      if (node) W.I[lane] = W.In[lane];
+      __syncwarp();
     }
+    __syncwarp();
     if (status == ST_VALID && !converged && !(gn < (float)rp.delta)) status = ST_NOT_CONVERGED;
     if (status == ST_VALID) {
       // visibility between consecutive path nodes
       for (int k = 0; k <= n; ++k) {
-        float3 A = tof(shfl3(I, k)), B = tof(shfl3(I, k + 1));
+        float3 A = tof(W.I[k]), B = tof(W.I[k + 1]);
         uint32_t la = __shfl_sync(FULL, my_lab, k), lb = __shfl_sync(FULL, my_lab, min(k + 1, 31));
         Endpoint ea{IGN_NONE, NB_NONE_LABEL}, eb{IGN_NONE, NB_NONE_LABEL};
         if (k >= 1) ea = Endpoint{((types >> (k - 1)) & 1u) ? IGN_ANY : IGN_LABEL, la};
@@ -439,8 +460,7 @@ __global__ void __launch_bounds__(128, 3) k_refine(DScene s, DRefine rp, CoarseV
         }
       }
     }
-    d3 Inext = shfl3(I, min(lane + 1, 31));
-    double seg = lane <= n ? len(Inext - I) : 0.0;
+    double seg = lane <= n ? len(W.I[lane + 1] - W.I[lane]) : 0.0;
     double L = wsumd(seg);
     ExactRec* o = &out[i];
     if (lane == 0) {
@@ -458,12 +478,13 @@ __global__ void __launch_bounds__(128, 3) k_refine(DScene s, DRefine rp, CoarseV
     }
     if (lane >= 1 && lane <= NB_MAXI) {
       int q = lane - 1;
+      const d3 I = mine ? W.I[lane] : D3(0, 0, 0);
       o->lab[q] = mine ? my_lab : NB_NONE_LABEL;
       o->ie[q] = mine ? my_ie : 0xffffffffu;
       o->mat[q] = mine ? my_mat : 255;
-      o->pts[q][0] = mine ? I.x : 0.0;
-      o->pts[q][1] = mine ? I.y : 0.0;
-      o->pts[q][2] = mine ? I.z : 0.0;
+      o->pts[q][0] = I.x;
+      o->pts[q][1] = I.y;
+      o->pts[q][2] = I.z;
     }
     __syncwarp();
   }

@@ -94,7 +94,10 @@ typedef struct {
   int32_t max_diff;
   int32_t max_int;          /* maximum interactions (Table 1: 5), <= NIMBUS_MAX_INTERACTIONS */
   int32_t kappa;            /* duplicate limit per (TX, RX, label sequence) (Table 1: 100) */
-  int32_t pad_;
+  int32_t launch_mode;      /* transmission phase (Section 2.2.2): 0 = cones on a uniform sphere grid of
+                             * spacing launch_spacing; 1 = the paper's own launch, a ray from each TX toward
+                             * every IE (edge IEs only when max_diff >= 1) and every RX, the visible ones
+                             * becoming the initial interactions and LOS paths.  Other values: NIMBUS_ERR_ARG. */
   int64_t max_nodes;        /* bound on interaction nodes per level (0: from the memory budget) */
   int64_t max_coarse;       /* bound on coarse paths before kappa (0: from the memory budget) */
   /* Optional per-RX restrictions for batching independent requests in one call

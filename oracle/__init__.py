@@ -37,6 +37,7 @@ class OracleParams(C.Structure):
         ("grad_stop", C.c_double), ("freq_hz", C.c_double),
         ("dv", C.c_int32), ("max_refl", C.c_int32), ("max_diff", C.c_int32), ("max_int", C.c_int32),
         ("kappa", C.c_int32), ("n_launch", C.c_int32), ("sdf_max_steps", C.c_int32), ("rho", C.c_int32),
+        ("launch_mode", C.c_int32),
     ]
 
 
@@ -62,6 +63,7 @@ def to_struct(p) -> OracleParams:
     s.n_launch = p.launch_count
     s.sdf_max_steps = p.sdf_max_steps
     s.rho = p.rho
+    s.launch_mode = getattr(p, "launch_mode", 0)
     return s
 
 

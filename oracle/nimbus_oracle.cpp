@@ -53,6 +53,7 @@ typedef struct {
   int32_t n_launch;        // number of uniform launch directions
   int32_t sdf_max_steps;
   int32_t rho;             // refinement iterations (Table 1)
+  int32_t launch_mode;     // 0: uniform launch; 1: a ray toward every IE and RX (Section 2.2.2)
 } oracle_params;
 }
 
@@ -803,14 +804,32 @@ CoarseSet* trace(const Scene& s, const double* txp, int ntx, const double* rxp, 
   };
 
   std::vector<int64_t> frontier;
-  // Transmission phase (Section 2.2.2), uniform launch reading: cones on a
-  // Fibonacci lattice from each TX; the IEs they accept are the initial interactions
-  // (a set per TX) and the RXs they accept are LOS connections.
+  // Transmission phase (Section 2.2.2).  Uniform launch reading (launch_mode 0):
+  // cones on a Fibonacci lattice from each TX; the IEs they accept are the initial
+  // interactions (a set per TX) and the RXs they accept are LOS connections.  The
+  // paper's own launch (launch_mode 1): a ray from the TX toward every IE (edge IEs
+  // only when a diffraction is allowed) and every RX; the visible ones are the
+  // initial interactions and the LOS connections (the ray points at the RX: miss 0).
   for (int t = 0; t < ntx; ++t) {
     V3 T = out->tx[t];
     std::set<int64_t> first;
     std::map<int, double> los;
-    for (int64_t i = 0; i < nl; ++i) {
+    if (p.launch_mode == 1) {
+      const bool test_edges = max_int >= 1 && p.max_diff >= 1;
+      for (int64_t id = 0; id < (int64_t)s.ies.size(); ++id) {
+        const IE& ie = s.ies[id];
+        if (ie.kind == IE_EDGE && !test_edges) continue;
+        ctx.n_vis++;
+        if (visible(s, T, ie.rp, Endpoint{IGN_NONE, NONE_LABEL},
+                    Endpoint{ie.kind == IE_EDGE ? IGN_ANY : IGN_LABEL, ie.label}))
+          first.insert(id);
+      }
+      for (int j = 0; j < nrx; ++j) {
+        ctx.n_vis++;
+        if (visible(s, T, out->rx[j], Endpoint{IGN_NONE, NONE_LABEL}, Endpoint{IGN_NONE, NONE_LABEL})) los[j] = 0.0;
+      }
+    }
+    for (int64_t i = 0; i < (p.launch_mode == 1 ? 0 : nl); ++i) {
       double d[3];
       fibonacci_dir(i, nl, d);
       Cone c;

@@ -47,7 +47,7 @@ class VoxParams(C.Structure):
 class TraceParams(C.Structure):
     _fields_ = [("cone_half_angle", C.c_double), ("launch_spacing", C.c_double), ("sep_eps", C.c_double),
                 ("n_launch", C.c_int32), ("max_refl", C.c_int32), ("max_diff", C.c_int32),
-                ("max_int", C.c_int32), ("kappa", C.c_int32), ("pad_", C.c_int32),
+                ("max_int", C.c_int32), ("kappa", C.c_int32), ("launch_mode", C.c_int32),
                 ("max_nodes", C.c_int64), ("max_coarse", C.c_int64), ("rx_owner", _vp), ("rx_max_int", _vp)]
 
 
@@ -175,6 +175,7 @@ def trace_params(p: Params, max_nodes=0, max_coarse=0) -> TraceParams:
     t.max_diff = p.max_diff
     t.max_int = p.max_interactions
     t.kappa = p.kappa
+    t.launch_mode = p.launch_mode
     t.max_nodes = max_nodes
     t.max_coarse = max_coarse
     return t

@@ -30,6 +30,7 @@ class Params:
     cone_half_angle_deg: float = 4.0     # constant cone apex half-angle alpha
     launch_spacing_deg: float = 0.5      # uniform sphere-grid spacing Delta of the TX launch
     n_launch: int = 0                # 0: round(4*pi/Delta^2) Fibonacci directions
+    launch_mode: int = 0             # 0: uniform sphere grid; 1: a ray toward every IE and RX (Section 2.2.2)
     # point-set intersection (Section 2.2.1, Eq. 1)
     sdf_sigma: float = 0.125         # Gaussian weight width [m] (h_s / 2)
     sdf_eps: float = 1e-3            # "near zero" |f| threshold [m]

@@ -43,9 +43,6 @@ __device__ __forceinline__ double wsumd(double v) {
   return v;
 }
 
-__device__ __forceinline__ d3 shfl3(d3 a, int src) {
-  return D3(__shfl_sync(FULL, a.x, src), __shfl_sync(FULL, a.y, src), __shfl_sync(FULL, a.z, src));
-}
 
 // Same-label IEs near one re-projection target, cached in shared memory for each
 // interaction of a warp's path.  Key: label and the target's subvoxel gR; entries

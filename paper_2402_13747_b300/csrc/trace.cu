@@ -341,6 +341,16 @@ __device__ __forceinline__ void emit_coarse(const DTrace& tr, CoarseBuf& cb, uin
   cb.miss[slot] = miss;
 }
 
+// LOS of the paper's launch (a ray toward each RX): every RX visible from the TX,
+// at miss distance 0 (the ray points at the RX).
+__global__ void k_los_from_vis(DTrace tr, uint32_t* los) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)tr.n_tx * tr.n_rx) return;
+  const int t = (int)(i / tr.n_rx), j = (int)(i % tr.n_rx);
+  if (tr.rx_owner && tr.rx_owner[j] >= 0 && tr.rx_owner[j] != t) return;
+  if (tr.vis_rx[i]) los[i] = __float_as_uint(0.f);
+}
+
 // LOS coarse paths: RXs reached by a primary cone.
 __global__ void k_los(DTrace tr, const uint32_t* los, CoarseBuf cb) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -793,7 +803,7 @@ int trace_coarse(Mem& mem, SceneObj* S, const double* txh, int n_tx, const doubl
     return NIMBUS_ERR_ARG;
   }
   if (p->max_refl < 0 || p->max_diff < 0 || p->kappa < 1 || !(p->cone_half_angle > 0) ||
-      !(p->cone_half_angle < 1.5) || !(p->launch_spacing > 0)) {
+      !(p->cone_half_angle < 1.5) || !(p->launch_spacing > 0) || p->launch_mode < 0 || p->launch_mode > 1) {
     *err = "trace: invalid parameters";
     return NIMBUS_ERR_ARG;
   }
@@ -978,8 +988,18 @@ int trace_coarse(Mem& mem, SceneObj* S, const double* txh, int n_tx, const doubl
   k_vis_tables<<<PG, 256, 0, st>>>(s, tr_vis);
   NB_LAUNCHED(err);
   const int e1 = tm.mark();
-  k_primary<<<PG, 256, 0, st>>>(s, tr_pri, first_bits, los);
-  NB_LAUNCHED(err);
+  if (p->launch_mode == 1) {
+    // the paper's launch: a ray toward every IE and RX, i.e. the visibility tables
+    NB_CUDA(err, cudaMemcpyAsync(first_bits, vis_ie, std::max<int64_t>(1, (int64_t)n_tx * tr.ie_words) * 4,
+                                 cudaMemcpyDeviceToDevice, st));
+    if ((int64_t)n_tx * n_rx > 0) {
+      k_los_from_vis<<<grid_for((int64_t)n_tx * n_rx, 128), 128, 0, st>>>(tr, los);
+      NB_LAUNCHED(err);
+    }
+  } else {
+    k_primary<<<PG, 256, 0, st>>>(s, tr_pri, first_bits, los);
+    NB_LAUNCHED(err);
+  }
   const int e2 = tm.mark();
   k_los<<<grid_for((int64_t)n_tx * n_rx, 128), 128, 0, st>>>(tr, los, cb);
   NB_LAUNCHED(err);

@@ -66,9 +66,11 @@ def test_voxel_tables_ragged_sizes(ctx):
         _tables_match(ctx, sc, p)
 
 
-def test_room_tiny_exact_paths(ctx, room_tiny):
-    """The tiny room: the same 25 paths as the oracle and the image method."""
-    p = config.params_for(room_tiny)
+@pytest.mark.parametrize("launch_mode", [0, 1])
+def test_room_tiny_exact_paths(ctx, room_tiny, launch_mode):
+    """The tiny room: the same 25 paths as the oracle and the image method, with the
+    uniform launch (0) and with the paper's ray toward every IE and RX (1)."""
+    p = config.params_for(room_tiny, launch_mode=launch_mode)
     G = ctx.run(room_tiny, p)
     _, _, e = oracle.run(room_tiny, p)
     R = e.paths()
@@ -102,6 +104,22 @@ def test_noisy_room_subset_matches_oracle(ctx):
     assert cmp["n_ref"] > 20
     assert cmp["jaccard"] >= 0.9, cmp
     assert len(cmp["bad"]) <= 0.05 * cmp["n_common"], cmp
+
+
+def test_noisy_room_subset_paper_launch(ctx):
+    """The paper's transmission phase (a ray toward every IE and RX) on the noisy room:
+    the coarse sets match in size and the exact path sets as for the uniform launch."""
+    full = scenes.room_noisy()
+    sc = full.with_pairs(full.tx[:1], full.rx[:3])
+    p = config.params_for(sc, max_refl=2, max_diff=1, launch_mode=1)
+    G = ctx.run(sc, p)
+    _, c, e = oracle.run(sc, p)
+    cmp = compare(G, e.paths(), atol_pts=1e-3, rtol_len=1e-6)
+    assert cmp["n_ref"] > 20
+    assert cmp["jaccard"] >= 0.9, cmp
+    assert len(cmp["bad"]) <= 0.05 * cmp["n_common"], cmp
+    # initial interactions: every IE visible from the TX, on both sides
+    assert abs(G["counts"]["n_coarse_raw"] - c.stats["n_before_kappa"]) <= 0.02 * c.stats["n_before_kappa"]
 
 
 def test_deterministic(ctx, room_tiny):

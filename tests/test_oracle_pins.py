@@ -60,6 +60,21 @@ def test_image_method_room_tiny(tiny_run):
         assert abs(length - rl) <= 1e-9 * rl
 
 
+def test_image_method_room_tiny_paper_launch(room_tiny):
+    """The paper's own transmission phase (a ray toward every IE and RX, Section 2.2.2)
+    finds the same 25 image-method paths in the sampled box room."""
+    p = config.params_for(room_tiny, grad_stop=1e-9, launch_mode=1)
+    s, c, e = oracle.run(room_tiny, p)
+    ref = image_paths(box_room_planes(10.0, 10.0, 3.0), room_tiny.tx[0], room_tiny.rx[0], max_order=2)
+    got = _exact_by_labels(e.paths())
+    assert set(k[2] for k in got) == set(ref)
+    for (t, r, lab), (pts, length, types) in got.items():
+        rp, rl = ref[lab]
+        np.testing.assert_allclose(pts, rp, atol=1e-6)
+        assert abs(length - rl) <= 1e-9 * rl
+    assert got[(0, 0, ())][1] == pytest.approx(math.sqrt(25 + 9), rel=1e-15)   # LOS
+
+
 def test_los_length(tiny_run):
     sc, p, s, c, e = tiny_run
     got = _exact_by_labels(e.paths())

@@ -170,6 +170,7 @@ struct CoarseObj : Obj {
   float* miss = nullptr;
   uint32_t* gid = nullptr;   // group of (tx, rx, types, labels)
   uint32_t n_groups_cap = 0;
+  int max_refl = NB_MAXI;    // reflection limit of the trace (bounds the reflections of every path)
   nimbus_path_counts counts{};
 };
 

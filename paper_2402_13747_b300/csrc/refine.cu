@@ -277,10 +277,13 @@ struct WarpPath {
 
 __global__ void __launch_bounds__(128, 4) k_refine(DScene s, DRefine rp, CoarseView C, const double* txd,
                                                    const double* rxd, ExactRec* out, unsigned long long* bytes_out,
-                                                   unsigned long long* next_path, const uint32_t* order) {
-  __shared__ LabelCache s_cache[4][NB_MAXI];
+                                                   unsigned long long* next_path, const uint32_t* order, int n_cache) {
+  // label caches: n_cache per warp (the trace's reflection limit), in dynamic shared
+  // memory, so that the rest of the SM's 256 KB stays L1 for the point loads
+  extern __shared__ LabelCache s_dyn[];
   __shared__ WarpPath s_path[4];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  LabelCache* cache = s_dyn + wib * n_cache;
   WarpPath& W = s_path[wib];
   unsigned long long bytes = 0;
   for (;;) {
@@ -295,7 +298,7 @@ __global__ void __launch_bounds__(128, 4) k_refine(DScene s, DRefine rp, CoarseV
     const bool mine = lane >= 1 && lane <= n;
     const bool node = lane <= n + 1;
     const bool diff = mine && ((types >> (lane - 1)) & 1u);
-    if (lane < NB_MAXI) s_cache[wib][lane].n = -1;
+    if (lane < n_cache) cache[lane].n = -1;
     uint32_t my_lab = NB_NONE_LABEL, my_ie = 0xffffffffu;
     uint8_t my_mat = 255;
     if (lane == 0) W.I[0] = D3(txd[3 * tx], txd[3 * tx + 1], txd[3 * tx + 2]);
@@ -423,7 +426,13 @@ __global__ void __launch_bounds__(128, 4) k_refine(DScene s, DRefine rp, CoarseV
         uint32_t lk = __shfl_sync(FULL, my_lab, k);
         d3 cn;
         float3 nn;
-        if (!reproject_warp(s, &W.I[k - 1], &W.R[k], lk, &cn, &nn, lane, bytes, s_cache[wib][k - 1])) {
+        // the cache of the path's r-th reflection, r = reflections before interaction k
+        const int r = (k - 1) - __popc(types & ((1u << (k - 1)) - 1u));
+        if (r >= n_cache) {   // more reflections than the trace allowed: not a path of this trace
+          status = ST_MISS;
+          break;
+        }
+        if (!reproject_warp(s, &W.I[k - 1], &W.R[k], lk, &cn, &nn, lane, bytes, cache[r])) {
           status = ST_MISS;
           break;
         }
@@ -632,8 +641,10 @@ int refine_paths(Mem& mem, SceneObj* S, CoarseObj* C, const nimbus_refine_params
   NB_CUDA(err, cudaMemsetAsync(rbytes, 0, 2 * sizeof(unsigned long long), st));
   StageTimer tm(st);
   const int e0 = tm.mark();
-  static int refine_blocks = 0;   // resident blocks per SM (a persistent grid)
-  if (!refine_blocks) NB_CUDA(err, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&refine_blocks, k_refine, 128, 0));
+  const int n_cache = std::max(1, std::min(C->max_refl, NB_MAXI));
+  const size_t dyn = sizeof(LabelCache) * 4 * n_cache;
+  int refine_blocks = 0;   // resident blocks per SM (a persistent grid)
+  NB_CUDA(err, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&refine_blocks, k_refine, 128, dyn));
   const unsigned G = std::min<unsigned>(grid_for(n * 32, 128), (unsigned)(num_sms() * std::max(1, refine_blocks)));
   // hand out the paths with the most interactions first (they run longest), so the
   // launch does not end on a few long paths
@@ -646,7 +657,7 @@ int refine_paths(Mem& mem, SceneObj* S, CoarseObj* C, const nimbus_refine_params
   k_order_keys<<<grid_for(n, 256), 256, 0, st>>>(C->nint, n, okeys, ovals);
   NB_LAUNCHED(err);
   NB_TRY(radix_sort(sc, okeys, ovals, okeys_alt, ovals_alt, n, 8));
-  k_refine<<<G, 128, 0, st>>>(S->d, rp, cv, C->txd, C->rxd, P->all, rbytes, rbytes + 1, ovals);
+  k_refine<<<G, 128, dyn, st>>>(S->d, rp, cv, C->txd, C->rxd, P->all, rbytes, rbytes + 1, ovals, n_cache);
   NB_LAUNCHED(err);
   const int e1 = tm.mark();
   unsigned long long* best;

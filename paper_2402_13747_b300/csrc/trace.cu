@@ -815,6 +815,7 @@ int trace_coarse(Mem& mem, SceneObj* S, const double* txh, int n_tx, const doubl
   const DScene& s = S->d;
   const long long launches0 = g_launches.load();
   C->mem = &mem;
+  C->max_refl = std::min(p->max_refl, max_int);
   C->n_tx = n_tx;
   C->n_rx = n_rx;
   // TX/RX on the host for the grid check, on the device for the kernels

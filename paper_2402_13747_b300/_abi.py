@@ -25,7 +25,7 @@ ERR_NAMES = {1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_OVERFLOW", 5: "E
 EXPORTS = ("nimbus_create", "nimbus_destroy", "nimbus_last_error", "nimbus_voxelize", "nimbus_update_region",
            "nimbus_trace_coarse", "nimbus_refine", "nimbus_query", "nimbus_query_coarse", "nimbus_scene_info",
            "nimbus_scene_tables", "nimbus_release", "nimbus_memory_used", "nimbus_kernel_launches",
-           "nimbus_voxelize_static")
+           "nimbus_voxelize_static", "nimbus_get_tuning", "nimbus_set_tuning", "nimbus_autotune")
 
 _vp = C.c_void_p
 
@@ -89,6 +89,14 @@ class StaticTables(C.Structure):
                 ("cell_count", _vp), ("march", _vp), ("cell_capacity", C.c_int64)]
 
 
+class Tuning(C.Structure):
+    _fields_ = [("level_packet", C.c_int32), ("level_block", C.c_int32), ("refine_blocks", C.c_int32),
+                ("refine_order", C.c_int32), ("level_ms", C.c_double), ("refine_ms", C.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class StaticInfo(C.Structure):
     _fields_ = [("origin", C.c_double * 3), ("dims", C.c_int32 * 3), ("pad_", C.c_int32), ("n_ie", C.c_int64),
                 ("n_cells", C.c_int64)]
@@ -141,6 +149,10 @@ def load():
     L.nimbus_memory_used.argtypes = [ctxp, P(C.c_size_t)]
     L.nimbus_kernel_launches.argtypes = [P(C.c_int64)]
     L.nimbus_voxelize_static.argtypes = [ctxp, P(Cloud), P(VoxParams), P(StaticTables), P(StaticInfo), _vp]
+    L.nimbus_get_tuning.argtypes = [ctxp, P(Tuning)]
+    L.nimbus_set_tuning.argtypes = [ctxp, P(Tuning)]
+    L.nimbus_autotune.argtypes = [ctxp, C.c_uint64, _vp, C.c_int32, _vp, C.c_int32, P(TraceParams), P(RefineParams),
+                                  P(Tuning), _vp]
     for name in EXPORTS:
         L[name].restype = C.c_char_p if name == "nimbus_last_error" else C.c_int
     _lib = L
@@ -332,6 +344,30 @@ class Context:
         self._check(self.L.nimbus_query(self.h, paths, which, C.byref(c), C.byref(v), _stream(stream)), "query")
         out["counts"] = c.as_dict()
         return out
+
+    # -- launch layout (result-neutral)
+    def get_tuning(self) -> dict:
+        t = Tuning()
+        self._check(self.L.nimbus_get_tuning(self.h, C.byref(t)), "get_tuning")
+        return t.as_dict()
+
+    def set_tuning(self, **kw) -> dict:
+        t = Tuning()
+        self._check(self.L.nimbus_get_tuning(self.h, C.byref(t)), "get_tuning")
+        for k, v in kw.items():
+            setattr(t, k, v)
+        self._check(self.L.nimbus_set_tuning(self.h, C.byref(t)), "set_tuning")
+        return t.as_dict()
+
+    def autotune(self, scene: int, tx, rx, params: Params = None, stream=None) -> dict:
+        """Time the launch layouts on a TX/RX sample and keep the fastest (nimbus_autotune)."""
+        params = params or Params()
+        t = _host(tx, np.float64, (-1, 3))
+        r = _host(rx, np.float64, (-1, 3))
+        tp, rp, out = trace_params(params), refine_params(params), Tuning()
+        self._check(self.L.nimbus_autotune(self.h, scene, _ptr(t), int(t.shape[0]), _ptr(r), int(r.shape[0]),
+                                           C.byref(tp), C.byref(rp), C.byref(out), _stream(stream)), "autotune")
+        return out.as_dict()
 
     def coarse_counts(self, coarse: int, stream=None) -> dict:
         """Sizes and counters of a coarse set (no path arrays copied)."""

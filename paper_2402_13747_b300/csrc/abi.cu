@@ -12,6 +12,7 @@
 struct nimbus_ctx {
   int device = 0;
   nb::Mem mem;
+  nb::Tuning tune;
   std::string err;
   std::unordered_map<uint64_t, nb::Obj*> objs;
   std::unordered_map<uint64_t, cudaStream_t> obj_stream;
@@ -207,7 +208,7 @@ int nimbus_trace_coarse(nimbus_ctx* ctx, nimbus_handle scene, const double* tx, 
   auto* C = new nb::CoarseObj();
   C->mem = &ctx->mem;
   C->scene = scene;
-  int rc = nb::trace_coarse(ctx->mem, S, tx, n_tx, rx, n_rx, params, C, st);
+  int rc = nb::trace_coarse(ctx->mem, S, tx, n_tx, rx, n_rx, params, C, st, ctx->tune);
   if (rc != NIMBUS_OK && rc != NIMBUS_ERR_OVERFLOW) {
     drop_obj(ctx, C, st);
     return rc;
@@ -235,7 +236,7 @@ int nimbus_refine(nimbus_ctx* ctx, nimbus_handle scene, nimbus_handle coarse, co
   cudaStream_t st = (cudaStream_t)stream;
   auto* P = new nb::PathsObj();
   P->mem = &ctx->mem;
-  int rc = nb::refine_paths(ctx->mem, S, C, params, P, st);
+  int rc = nb::refine_paths(ctx->mem, S, C, params, P, st, ctx->tune);
   if (rc != NIMBUS_OK) {
     drop_obj(ctx, P, st);
     return rc;
@@ -441,6 +442,109 @@ int nimbus_voxelize_static(nimbus_ctx* ctx, const nimbus_cloud* cloud, const nim
   if (!ctx) return NIMBUS_ERR_ARG;
   DeviceGuard g(ctx->device);
   return nb::voxelize_static(&ctx->err, cloud, params, out, info, (cudaStream_t)stream);
+}
+
+static void to_public(const nb::Tuning& t, nimbus_tuning* o) {
+  o->level_packet = t.level_packet;
+  o->level_block = t.level_block;
+  o->refine_blocks = t.refine_blocks;
+  o->refine_order = t.refine_order;
+  o->level_ms = t.level_ms;
+  o->refine_ms = t.refine_ms;
+}
+
+int nimbus_get_tuning(nimbus_ctx* ctx, nimbus_tuning* out) {
+  if (!ctx || !out) return NIMBUS_ERR_ARG;
+  to_public(ctx->tune, out);
+  return NIMBUS_OK;
+}
+
+int nimbus_set_tuning(nimbus_ctx* ctx, const nimbus_tuning* t) {
+  if (!ctx) return NIMBUS_ERR_ARG;
+  if (!t || !(t->level_packet == 1 || t->level_packet == 2 || t->level_packet == 4) ||
+      !(t->level_block == 128 || t->level_block == 256) || t->refine_blocks < 0 || t->refine_blocks > 4 ||
+      !(t->refine_order == 0 || t->refine_order == 1)) {
+    ctx->err = "set_tuning: value out of range";
+    return NIMBUS_ERR_ARG;
+  }
+  ctx->tune.level_packet = t->level_packet;
+  ctx->tune.level_block = t->level_block;
+  ctx->tune.refine_blocks = t->refine_blocks;
+  ctx->tune.refine_order = t->refine_order;
+  ctx->tune.level_ms = t->level_ms;
+  ctx->tune.refine_ms = t->refine_ms;
+  return NIMBUS_OK;
+}
+
+int nimbus_autotune(nimbus_ctx* ctx, nimbus_handle scene, const double* tx, int32_t n_tx, const double* rx,
+                    int32_t n_rx, const nimbus_trace_params* tp, const nimbus_refine_params* rp, nimbus_tuning* out,
+                    void* stream) {
+  if (!ctx) return NIMBUS_ERR_ARG;
+  if (!tp || !rp) {
+    ctx->err = "autotune: null argument";
+    return NIMBUS_ERR_ARG;
+  }
+  DeviceGuard g(ctx->device);
+  auto* S = get_obj<nb::SceneObj>(ctx, scene, nb::OBJ_SCENE);
+  if (!S) return NIMBUS_ERR_STATE;
+  cudaStream_t st = (cudaStream_t)stream;
+  nb::Tuning best = ctx->tune;
+  // level layouts: propagation time of the sample's levels
+  double best_lv = -1.0;
+  const int packets[3] = {1, 2, 4}, blocks[2] = {128, 256};
+  for (int pk : packets)
+    for (int bl : blocks) {
+      nb::Tuning t = best;
+      t.level_packet = pk;
+      t.level_block = bl;
+      auto* C = new nb::CoarseObj();
+      C->mem = &ctx->mem;
+      C->scene = scene;
+      int rc = nb::trace_coarse(ctx->mem, S, tx, n_tx, rx, n_rx, tp, C, st, t);
+      const double ms = C->counts.ms_levels;
+      drop_obj(ctx, C, st);
+      if (rc != NIMBUS_OK) return rc;
+      if (best_lv < 0.0 || ms < best_lv) {
+        best_lv = ms;
+        best.level_packet = pk;
+        best.level_block = bl;
+      }
+    }
+  best.level_ms = best_lv;
+  // refinement layouts, on the coarse set of the chosen level layout
+  auto* C = new nb::CoarseObj();
+  C->mem = &ctx->mem;
+  C->scene = scene;
+  int rc = nb::trace_coarse(ctx->mem, S, tx, n_tx, rx, n_rx, tp, C, st, best);
+  if (rc != NIMBUS_OK) {
+    drop_obj(ctx, C, st);
+    return rc;
+  }
+  double best_rf = -1.0;
+  const int rblocks[2] = {3, 0}, orders[2] = {0, 1};
+  for (int rb : rblocks)
+    for (int od : orders) {
+      nb::Tuning t = best;
+      t.refine_blocks = rb;
+      t.refine_order = od;
+      auto* P = new nb::PathsObj();
+      P->mem = &ctx->mem;
+      rc = nb::refine_paths(ctx->mem, S, C, rp, P, st, t);
+      const double ms = P->counts.ms_refine;
+      drop_obj(ctx, P, st);
+      if (rc != NIMBUS_OK) break;
+      if (best_rf < 0.0 || ms < best_rf) {
+        best_rf = ms;
+        best.refine_blocks = rb;
+        best.refine_order = od;
+      }
+    }
+  drop_obj(ctx, C, st);
+  if (rc != NIMBUS_OK) return rc;
+  best.refine_ms = best_rf;
+  ctx->tune = best;
+  if (out) to_public(best, out);
+  return NIMBUS_OK;
 }
 
 int nimbus_kernel_launches(int64_t* count) {

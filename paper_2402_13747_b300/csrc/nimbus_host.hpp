@@ -192,10 +192,19 @@ struct PathsObj : Obj {
   nimbus_path_counts counts{};
 };
 
+// Launch layout of the propagation levels and the refinement (result-neutral).
+struct Tuning {
+  int level_packet = 1;
+  int level_block = 256;
+  int refine_blocks = 0;   // 0: as many as fit
+  int refine_order = 1;
+  double level_ms = 0, refine_ms = 0;
+};
+
 int trace_coarse(Mem& mem, SceneObj* S, const double* tx, int n_tx, const double* rx, int n_rx,
-                 const nimbus_trace_params* p, CoarseObj* out, cudaStream_t st);
+                 const nimbus_trace_params* p, CoarseObj* out, cudaStream_t st, const Tuning& tn);
 int refine_paths(Mem& mem, SceneObj* S, CoarseObj* C, const nimbus_refine_params* p, PathsObj* out,
-                 cudaStream_t st);
+                 cudaStream_t st, const Tuning& tn);
 
 int voxelize_scene(Mem& mem, const nimbus_cloud* cloud, const nimbus_edges* edges, const nimbus_vox_params* p,
                    SceneObj* out, cudaStream_t st);

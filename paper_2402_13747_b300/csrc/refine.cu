@@ -291,7 +291,7 @@ __global__ void __launch_bounds__(128, 4) k_refine(DScene s, DRefine rp, CoarseV
     if (lane == 0) grab = atomicAdd(next_path, 1ull);
     const int64_t gi = (int64_t)__shfl_sync(FULL, grab, 0);
     if (gi >= C.n) break;
-    const int64_t i = order[gi];
+    const int64_t i = order ? order[gi] : gi;
     const int n = (int)C.nint[i];
     const uint32_t types = C.types[i];
     const uint32_t tx = C.tx[i], rx = C.rx[i];
@@ -608,7 +608,8 @@ unsigned pgrid(int block) {
 
 }  // namespace
 
-int refine_paths(Mem& mem, SceneObj* S, CoarseObj* C, const nimbus_refine_params* p, PathsObj* P, cudaStream_t st) {
+int refine_paths(Mem& mem, SceneObj* S, CoarseObj* C, const nimbus_refine_params* p, PathsObj* P, cudaStream_t st,
+                 const Tuning& tn) {
   std::string* err = mem.err;
   if (!(p->delta > 0) || p->rho < 0 || !(p->gamma > 0) || !(p->freq_hz > 0)) {
     *err = "refine: invalid parameters";
@@ -645,18 +646,22 @@ int refine_paths(Mem& mem, SceneObj* S, CoarseObj* C, const nimbus_refine_params
   const size_t dyn = sizeof(LabelCache) * 4 * n_cache;
   int refine_blocks = 0;   // resident blocks per SM (a persistent grid)
   NB_CUDA(err, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&refine_blocks, k_refine, 128, dyn));
+  if (tn.refine_blocks > 0) refine_blocks = std::min(refine_blocks, tn.refine_blocks);
   const unsigned G = std::min<unsigned>(grid_for(n * 32, 128), (unsigned)(num_sms() * std::max(1, refine_blocks)));
   // hand out the paths with the most interactions first (they run longest), so the
   // launch does not end on a few long paths
-  uint64_t *okeys, *okeys_alt;
-  uint32_t *ovals, *ovals_alt;
-  NB_TRY(sc.get(&okeys, n));
-  NB_TRY(sc.get(&okeys_alt, n));
-  NB_TRY(sc.get(&ovals, n));
-  NB_TRY(sc.get(&ovals_alt, n));
-  k_order_keys<<<grid_for(n, 256), 256, 0, st>>>(C->nint, n, okeys, ovals);
-  NB_LAUNCHED(err);
-  NB_TRY(radix_sort(sc, okeys, ovals, okeys_alt, ovals_alt, n, 8));
+  uint32_t* ovals = nullptr;
+  if (tn.refine_order) {
+    uint64_t *okeys, *okeys_alt;
+    uint32_t* ovals_alt;
+    NB_TRY(sc.get(&okeys, n));
+    NB_TRY(sc.get(&okeys_alt, n));
+    NB_TRY(sc.get(&ovals, n));
+    NB_TRY(sc.get(&ovals_alt, n));
+    k_order_keys<<<grid_for(n, 256), 256, 0, st>>>(C->nint, n, okeys, ovals);
+    NB_LAUNCHED(err);
+    NB_TRY(radix_sort(sc, okeys, ovals, okeys_alt, ovals_alt, n, 8));
+  }
   k_refine<<<G, 128, dyn, st>>>(S->d, rp, cv, C->txd, C->rxd, P->all, rbytes, rbytes + 1, ovals, n_cache);
   NB_LAUNCHED(err);
   const int e1 = tm.mark();

@@ -272,22 +272,22 @@ NIMBUS_API int nimbus_kernel_launches(int64_t* count);
  * they compute.  Every setting gives bit-identical results; only the time changes.
  */
 typedef struct {
-  int32_t level_packet;     /* propagation-level cones a warp takes per grab of the work counter: 1, 2, 4 */
   int32_t level_block;      /* threads per block of the propagation levels: 128 or 256 */
   int32_t refine_blocks;    /* 4-warp refinement blocks per SM: 1..4, or 0 for as many as fit */
   int32_t refine_order;     /* 1: refine the paths with the most interactions first; 0: in coarse order */
+  int32_t pad_;
   double level_ms;          /* after nimbus_autotune: time of the chosen level layout on the sample, else 0 */
   double refine_ms;         /* after nimbus_autotune: time of the chosen refinement layout on the sample, else 0 */
 } nimbus_tuning;
 
-/* The context's launch configuration (defaults 1, 256, 0, 1). */
+/* The context's launch configuration (defaults 256, 0, 1). */
 NIMBUS_API int nimbus_get_tuning(nimbus_ctx* ctx, nimbus_tuning* out);
 
 /* Replace it.  A value out of range returns NIMBUS_ERR_ARG and changes nothing. */
 NIMBUS_API int nimbus_set_tuning(nimbus_ctx* ctx, const nimbus_tuning* t);
 
 /* Autotuner.  Traces the given TX/RX sample on `scene` once per level layout
- * (packet 1, 2, 4 x block 128, 256), keeps the fastest propagation time, then
+ * (blocks of 128 or 256 threads), keeps the fastest propagation time, then
  * refines that coarse set once per refinement layout (3 or all resident blocks per
  * SM x ordered or not), keeps the fastest, stores the result in the context for the
  * calls that follow and writes it to `out` (may be NULL).  Times are CUDA events on

@@ -445,7 +445,6 @@ int nimbus_voxelize_static(nimbus_ctx* ctx, const nimbus_cloud* cloud, const nim
 }
 
 static void to_public(const nb::Tuning& t, nimbus_tuning* o) {
-  o->level_packet = t.level_packet;
   o->level_block = t.level_block;
   o->refine_blocks = t.refine_blocks;
   o->refine_order = t.refine_order;
@@ -461,13 +460,11 @@ int nimbus_get_tuning(nimbus_ctx* ctx, nimbus_tuning* out) {
 
 int nimbus_set_tuning(nimbus_ctx* ctx, const nimbus_tuning* t) {
   if (!ctx) return NIMBUS_ERR_ARG;
-  if (!t || !(t->level_packet == 1 || t->level_packet == 2 || t->level_packet == 4) ||
-      !(t->level_block == 128 || t->level_block == 256) || t->refine_blocks < 0 || t->refine_blocks > 4 ||
+  if (!t || !(t->level_block == 128 || t->level_block == 256) || t->refine_blocks < 0 || t->refine_blocks > 4 ||
       !(t->refine_order == 0 || t->refine_order == 1)) {
     ctx->err = "set_tuning: value out of range";
     return NIMBUS_ERR_ARG;
   }
-  ctx->tune.level_packet = t->level_packet;
   ctx->tune.level_block = t->level_block;
   ctx->tune.refine_blocks = t->refine_blocks;
   ctx->tune.refine_order = t->refine_order;
@@ -491,25 +488,22 @@ int nimbus_autotune(nimbus_ctx* ctx, nimbus_handle scene, const double* tx, int3
   nb::Tuning best = ctx->tune;
   // level layouts: propagation time of the sample's levels
   double best_lv = -1.0;
-  const int packets[3] = {1, 2, 4}, blocks[2] = {128, 256};
-  for (int pk : packets)
-    for (int bl : blocks) {
-      nb::Tuning t = best;
-      t.level_packet = pk;
-      t.level_block = bl;
-      auto* C = new nb::CoarseObj();
-      C->mem = &ctx->mem;
-      C->scene = scene;
-      int rc = nb::trace_coarse(ctx->mem, S, tx, n_tx, rx, n_rx, tp, C, st, t);
-      const double ms = C->counts.ms_levels;
-      drop_obj(ctx, C, st);
-      if (rc != NIMBUS_OK) return rc;
-      if (best_lv < 0.0 || ms < best_lv) {
-        best_lv = ms;
-        best.level_packet = pk;
-        best.level_block = bl;
-      }
+  const int blocks[2] = {256, 128};
+  for (int bl : blocks) {
+    nb::Tuning t = best;
+    t.level_block = bl;
+    auto* C = new nb::CoarseObj();
+    C->mem = &ctx->mem;
+    C->scene = scene;
+    int rc = nb::trace_coarse(ctx->mem, S, tx, n_tx, rx, n_rx, tp, C, st, t);
+    const double ms = C->counts.ms_levels;
+    drop_obj(ctx, C, st);
+    if (rc != NIMBUS_OK) return rc;
+    if (best_lv < 0.0 || ms < best_lv) {
+      best_lv = ms;
+      best.level_block = bl;
     }
+  }
   best.level_ms = best_lv;
   // refinement layouts, on the coarse set of the chosen level layout
   auto* C = new nb::CoarseObj();

@@ -194,7 +194,6 @@ struct PathsObj : Obj {
 
 // Launch layout of the propagation levels and the refinement (result-neutral).
 struct Tuning {
-  int level_packet = 1;
   int level_block = 256;
   int refine_blocks = 0;   // 0: as many as fit
   int refine_order = 1;

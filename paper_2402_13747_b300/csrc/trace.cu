@@ -534,7 +534,7 @@ __device__ void march_cone_warp(const DScene& s, const DTrace& tr, const ConeD& 
 // One propagation level: the reflected cones and Keller-fan cones of every node,
 // one warp per cone, cones handed out by a counter (their costs differ widely).
 __global__ void __launch_bounds__(256) k_level(DScene s, DTrace tr, NodeLevel cur, NodeLevel next, CoarseBuf cb,
-                                               unsigned long long* next_task, int packet) {
+                                               unsigned long long* next_task) {
   const int lane = threadIdx.x & 31;
   const uint32_t n_r = min(cur.cnt[0], cur.cap_r), n_d = min(cur.cnt[1], cur.cap_d);
   const int64_t total = (int64_t)n_r + (int64_t)n_d * tr.M;
@@ -542,72 +542,69 @@ __global__ void __launch_bounds__(256) k_level(DScene s, DTrace tr, NodeLevel cu
   uint32_t cones = 0, vis = 0, evals = 0;
   for (;;) {
     unsigned long long grab = 0;
-    if (lane == 0) grab = atomicAdd(next_task, (unsigned long long)packet);
-    const int64_t first = (int64_t)__shfl_sync(FULL, grab, 0);
-    if (first >= total) break;
-    const int64_t last = min(total, first + (int64_t)packet);
-    for (int64_t task = first; task < last; ++task) {   // a packet: consecutive cones of one warp
-      const bool refl = task < n_r;
-      const uint32_t idx = refl ? (uint32_t)task : (uint32_t)((task - n_r) / tr.M);
-      const int j = refl ? 0 : (int)((task - n_r) % tr.M);
-      const float4 a = refl ? cur.ra[idx] : cur.da[idx];
-      const float4 b = refl ? cur.rb[idx] : cur.db[idx];
-      const uint32_t meta = refl ? cur.rm[idx] : cur.dm[idx];
-      const uint32_t ie = __float_as_uint(a.w);
-      const IERec* r = &s.ies[ie];
-      const float4 nm = __ldg(&r->nrm_meta);
-      const uint32_t label = __float_as_uint(__ldg(&r->rp_lab).w);
-      if (lane == 0) bytes += 32 + 36;
-      const float3 e = xyz(b);
-      ConeD c;
-      c.apex = xyz(a);
-      c.sin_a = tr.sin_a;
-      c.cos_a = tr.cos_a;
-      if (refl) {
-        float3 n = xyz(nm);
-        if (dot(n, e) > 0.f) n = -1.f * n;
-        c.kind = CONE_REFLECT;
-        c.axis = normalize(e - (2.f * dot(e, n)) * n);
-        c.pn = n;
-        c.origin = Endpoint{IGN_LABEL, label};
-      } else {
-        const double* E = s.edges + 12 * __float_as_uint(__ldg(&r->bbc_pb).w);
-        if (lane == 0) bytes += 96;
-        const float3 w = normalize(f3((float)(E[3] - E[0]), (float)(E[4] - E[1]), (float)(E[5] - E[2])));
-        const float cb_ = dot(e, w);
-        const float sb2 = 1.f - cb_ * cb_;
-        if (sb2 < 1e-12f) continue;
-        const float sb = sqrtf(sb2);
-        float3 ua, va;
-        onb(w, &ua, &va);
-        const float phi = (float)j * tr.dphi;
-        float sp, cp;
-        sincosf(phi, &sp, &cp);
-        const float3 rr = cp * ua + sp * va;
-        const float3 d = cb_ * w + sb * rr;
-        const float3 n0 = f3((float)E[6], (float)E[7], (float)E[8]), n1 = f3((float)E[9], (float)E[10], (float)E[11]);
-        if (!(dot(d, n0) > 0.f || dot(d, n1) > 0.f)) continue;
-        float slo, clo, shi, chi;
-        sincosf(phi - 0.5f * tr.dphi, &slo, &clo);
-        sincosf(phi + 0.5f * tr.dphi, &shi, &chi);
-        c.kind = CONE_DIFFRACT;
-        c.axis = normalize(d);
-        c.tlo = (-slo) * ua + clo * va;
-        c.thi = (-shi) * ua + chi * va;
-        c.rmid = rr;
-        c.origin = Endpoint{IGN_ANY, label};
-      }
-      LevelCone lc;
-      lc.depth = (meta >> 24) & 0xfu;
-      lc.nr = (meta >> 16) & 0xfu;
-      lc.nd = (meta >> 20) & 0xfu;
-      lc.tx = meta & 0xffffu;
-      lc.self_ref = idx | (refl ? 0u : 0x80000000u);
-      lc.can_child = (int)lc.depth < tr.max_int && (!tr.tx_max_int || (int)lc.depth < tr.tx_max_int[lc.tx]);
-      lc.test_edges = lc.can_child && (int)lc.nd < tr.max_diff;
-      if (lane == 0) ++cones;
-      march_cone_warp(s, tr, c, lc, next, cb, lane, bytes, evals, vis);
+    if (lane == 0) grab = atomicAdd(next_task, 1ull);
+    const int64_t task = (int64_t)__shfl_sync(FULL, grab, 0);
+    if (task >= total) break;
+    const bool refl = task < n_r;
+    const uint32_t idx = refl ? (uint32_t)task : (uint32_t)((task - n_r) / tr.M);
+    const int j = refl ? 0 : (int)((task - n_r) % tr.M);
+    const float4 a = refl ? cur.ra[idx] : cur.da[idx];
+    const float4 b = refl ? cur.rb[idx] : cur.db[idx];
+    const uint32_t meta = refl ? cur.rm[idx] : cur.dm[idx];
+    const uint32_t ie = __float_as_uint(a.w);
+    const IERec* r = &s.ies[ie];
+    const float4 nm = __ldg(&r->nrm_meta);
+    const uint32_t label = __float_as_uint(__ldg(&r->rp_lab).w);
+    if (lane == 0) bytes += 32 + 36;
+    const float3 e = xyz(b);
+    ConeD c;
+    c.apex = xyz(a);
+    c.sin_a = tr.sin_a;
+    c.cos_a = tr.cos_a;
+    if (refl) {
+      float3 n = xyz(nm);
+      if (dot(n, e) > 0.f) n = -1.f * n;
+      c.kind = CONE_REFLECT;
+      c.axis = normalize(e - (2.f * dot(e, n)) * n);
+      c.pn = n;
+      c.origin = Endpoint{IGN_LABEL, label};
+    } else {
+      const double* E = s.edges + 12 * __float_as_uint(__ldg(&r->bbc_pb).w);
+      if (lane == 0) bytes += 96;
+      const float3 w = normalize(f3((float)(E[3] - E[0]), (float)(E[4] - E[1]), (float)(E[5] - E[2])));
+      const float cb_ = dot(e, w);
+      const float sb2 = 1.f - cb_ * cb_;
+      if (sb2 < 1e-12f) continue;
+      const float sb = sqrtf(sb2);
+      float3 ua, va;
+      onb(w, &ua, &va);
+      const float phi = (float)j * tr.dphi;
+      float sp, cp;
+      sincosf(phi, &sp, &cp);
+      const float3 rr = cp * ua + sp * va;
+      const float3 d = cb_ * w + sb * rr;
+      const float3 n0 = f3((float)E[6], (float)E[7], (float)E[8]), n1 = f3((float)E[9], (float)E[10], (float)E[11]);
+      if (!(dot(d, n0) > 0.f || dot(d, n1) > 0.f)) continue;
+      float slo, clo, shi, chi;
+      sincosf(phi - 0.5f * tr.dphi, &slo, &clo);
+      sincosf(phi + 0.5f * tr.dphi, &shi, &chi);
+      c.kind = CONE_DIFFRACT;
+      c.axis = normalize(d);
+      c.tlo = (-slo) * ua + clo * va;
+      c.thi = (-shi) * ua + chi * va;
+      c.rmid = rr;
+      c.origin = Endpoint{IGN_ANY, label};
     }
+    LevelCone lc;
+    lc.depth = (meta >> 24) & 0xfu;
+    lc.nr = (meta >> 16) & 0xfu;
+    lc.nd = (meta >> 20) & 0xfu;
+    lc.tx = meta & 0xffffu;
+    lc.self_ref = idx | (refl ? 0u : 0x80000000u);
+    lc.can_child = (int)lc.depth < tr.max_int && (!tr.tx_max_int || (int)lc.depth < tr.tx_max_int[lc.tx]);
+    lc.test_edges = lc.can_child && (int)lc.nd < tr.max_diff;
+    if (lane == 0) ++cones;
+    march_cone_warp(s, tr, c, lc, next, cb, lane, bytes, evals, vis);
   }
   add_stats(tr, cones, vis, bytes, evals);
 }
@@ -1040,8 +1037,7 @@ int trace_coarse(Mem& mem, SceneObj* S, const double* txh, int n_tx, const doubl
       next.cap_d = 0;
       next.cnt = cnts + 2 * MAX_LEVELS - 2;  // unused sink
     }
-    k_level<<<persistent_grid(tn.level_block), tn.level_block, 0, st>>>(s, tr_lev, lv[d], next, cb, task_ctr + d,
-                                                                         tn.level_packet);
+    k_level<<<persistent_grid(tn.level_block), tn.level_block, 0, st>>>(s, tr_lev, lv[d], next, cb, task_ctr + d);
     NB_LAUNCHED(err);
   }
   const int e4 = tm.mark();

@@ -206,14 +206,14 @@ def test_autotune_keeps_results(ctx):
     s = ctx.voxelize_scene(sc, p)
     t = ctx.autotune(s, sc.tx, sc.rx[:2], p)
     ctx.release(s)
-    assert t["level_packet"] in (1, 2, 4) and t["level_block"] in (128, 256)
+    assert t["level_block"] in (128, 256)
     assert t["refine_blocks"] in (0, 3) and t["refine_order"] in (0, 1) and t["refine_ms"] > 0
-    for layout in (dict(level_packet=4, level_block=128, refine_blocks=3, refine_order=0), t):
-        ctx.set_tuning(**{k: layout[k] for k in ("level_packet", "level_block", "refine_blocks", "refine_order")})
+    for layout in (dict(level_block=128, refine_blocks=3, refine_order=0), t):
+        ctx.set_tuning(**{k: layout[k] for k in ("level_block", "refine_blocks", "refine_order")})
         G = ctx.run(sc, p)
         assert len(G["n"]) == len(base["n"])
         for k in ("tx", "rx", "n", "type", "label", "pts", "length"):
             np.testing.assert_array_equal(G[k], base[k])
-    ctx.set_tuning(level_packet=1, level_block=256, refine_blocks=0, refine_order=1)
+    ctx.set_tuning(level_block=256, refine_blocks=0, refine_order=1)
     with pytest.raises(Exception):
-        ctx.set_tuning(level_packet=3)
+        ctx.set_tuning(level_block=96)

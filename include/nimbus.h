@@ -39,6 +39,7 @@ extern "C" {
 #define NIMBUS_ERR_OVERFLOW 4 /* a bounded device buffer overflowed; sizes in nimbus_path_counts */
 #define NIMBUS_ERR_TIMEOUT 5  /* a bounded device wait gave up */
 #define NIMBUS_ERR_STATE 6    /* unknown handle or a handle of the wrong kind */
+#define NIMBUS_ERR_IO 7       /* a file could not be written or read, or is not an intact scene checkpoint */
 
 #define NIMBUS_MAX_INTERACTIONS 8 /* interactions per path, upper bound of max_int */
 
@@ -264,6 +265,21 @@ NIMBUS_API int nimbus_memory_used(nimbus_ctx* ctx, size_t* bytes);
 /* Number of CUDA kernels this library has launched in this process so far (all
  * contexts); differences around a region count the kernels launched in it. */
 NIMBUS_API int nimbus_kernel_launches(int64_t* count);
+
+/* ---------------------------------------------------------------------------
+ * Scene checkpoint.
+ *
+ * Not part of the paper's method: persistence for a serving process.
+ * nimbus_scene_save writes the scene's current cloud (after any region updates), its
+ * edges, voxelisation parameters and grid to `path`.  nimbus_scene_load reads such a
+ * file into a new scene of `ctx` (any device); its derived tables are rebuilt on the
+ * saved grid, so they equal those of the saved scene bit for bit.  Both synchronise
+ * `stream`.  File: little-endian, magic "NIMBUSC1", version 1, FNV-1a checksum of the
+ * payload; a file that cannot be opened, is truncated, foreign or damaged returns
+ * NIMBUS_ERR_IO and creates nothing.
+ */
+NIMBUS_API int nimbus_scene_save(nimbus_ctx* ctx, nimbus_handle scene, const char* path, void* stream);
+NIMBUS_API int nimbus_scene_load(nimbus_ctx* ctx, const char* path, nimbus_handle* scene_out, void* stream);
 
 /* ---------------------------------------------------------------------------
  * Launch configuration and autotuner.

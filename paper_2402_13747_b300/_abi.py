@@ -19,13 +19,15 @@ LIB_PATH = os.path.join(_HERE, "libnimbus.so")
 MAXI = 8
 NONE_LABEL = 0xFFFFFFFF
 
-OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_OVERFLOW, ERR_TIMEOUT, ERR_STATE = range(7)
-ERR_NAMES = {1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_OVERFLOW", 5: "ERR_TIMEOUT", 6: "ERR_STATE"}
+OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_OVERFLOW, ERR_TIMEOUT, ERR_STATE, ERR_IO = range(8)
+ERR_NAMES = {1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_OVERFLOW", 5: "ERR_TIMEOUT", 6: "ERR_STATE",
+             7: "ERR_IO"}
 
 EXPORTS = ("nimbus_create", "nimbus_destroy", "nimbus_last_error", "nimbus_voxelize", "nimbus_update_region",
            "nimbus_trace_coarse", "nimbus_refine", "nimbus_query", "nimbus_query_coarse", "nimbus_scene_info",
            "nimbus_scene_tables", "nimbus_release", "nimbus_memory_used", "nimbus_kernel_launches",
-           "nimbus_voxelize_static", "nimbus_get_tuning", "nimbus_set_tuning", "nimbus_autotune")
+           "nimbus_voxelize_static", "nimbus_get_tuning", "nimbus_set_tuning", "nimbus_autotune",
+           "nimbus_scene_save", "nimbus_scene_load")
 
 _vp = C.c_void_p
 
@@ -149,6 +151,8 @@ def load():
     L.nimbus_memory_used.argtypes = [ctxp, P(C.c_size_t)]
     L.nimbus_kernel_launches.argtypes = [P(C.c_int64)]
     L.nimbus_voxelize_static.argtypes = [ctxp, P(Cloud), P(VoxParams), P(StaticTables), P(StaticInfo), _vp]
+    L.nimbus_scene_save.argtypes = [ctxp, C.c_uint64, C.c_char_p, _vp]
+    L.nimbus_scene_load.argtypes = [ctxp, C.c_char_p, P(C.c_uint64), _vp]
     L.nimbus_get_tuning.argtypes = [ctxp, P(Tuning)]
     L.nimbus_set_tuning.argtypes = [ctxp, P(Tuning)]
     L.nimbus_autotune.argtypes = [ctxp, C.c_uint64, _vp, C.c_int32, _vp, C.c_int32, P(TraceParams), P(RefineParams),
@@ -344,6 +348,17 @@ class Context:
         self._check(self.L.nimbus_query(self.h, paths, which, C.byref(c), C.byref(v), _stream(stream)), "query")
         out["counts"] = c.as_dict()
         return out
+
+    # -- scene checkpoint
+    def scene_save(self, scene: int, path: str, stream=None):
+        """Write the scene's current cloud, edges, parameters and grid to `path`."""
+        self._check(self.L.nimbus_scene_save(self.h, scene, os.fsencode(path), _stream(stream)), "scene_save")
+
+    def scene_load(self, path: str, stream=None) -> int:
+        """A new scene from a checkpoint; its tables equal the saved scene's."""
+        out = C.c_uint64(0)
+        self._check(self.L.nimbus_scene_load(self.h, os.fsencode(path), C.byref(out), _stream(stream)), "scene_load")
+        return out.value
 
     # -- launch layout (result-neutral)
     def get_tuning(self) -> dict:

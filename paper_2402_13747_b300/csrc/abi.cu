@@ -194,6 +194,33 @@ int nimbus_update_region(nimbus_ctx* ctx, nimbus_handle scene, const double aabb
   return nb::update_scene_region(ctx->mem, S, aabb_min, aabb_max, replacement, st);
 }
 
+int nimbus_scene_save(nimbus_ctx* ctx, nimbus_handle scene, const char* path, void* stream) {
+  if (!ctx) return NIMBUS_ERR_ARG;
+  DeviceGuard g(ctx->device);
+  auto* S = get_obj<nb::SceneObj>(ctx, scene, nb::OBJ_SCENE);
+  if (!S) return NIMBUS_ERR_STATE;
+  return nb::scene_save(ctx->mem, S, path, (cudaStream_t)stream);
+}
+
+int nimbus_scene_load(nimbus_ctx* ctx, const char* path, nimbus_handle* scene_out, void* stream) {
+  if (!ctx) return NIMBUS_ERR_ARG;
+  if (!scene_out) {
+    ctx->err = "scene_load: null argument";
+    return NIMBUS_ERR_ARG;
+  }
+  DeviceGuard g(ctx->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  auto* S = new nb::SceneObj();
+  S->mem = &ctx->mem;
+  int rc = nb::scene_load(ctx->mem, path, S, st);
+  if (rc != NIMBUS_OK) {
+    drop_obj(ctx, S, st);
+    return rc;
+  }
+  *scene_out = put_obj(ctx, S, st);
+  return NIMBUS_OK;
+}
+
 int nimbus_trace_coarse(nimbus_ctx* ctx, nimbus_handle scene, const double* tx, int32_t n_tx, const double* rx,
                         int32_t n_rx, const nimbus_trace_params* params, nimbus_handle* coarse_out, void* stream) {
   if (!ctx) return NIMBUS_ERR_ARG;

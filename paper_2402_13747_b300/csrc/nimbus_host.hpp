@@ -207,6 +207,8 @@ int refine_paths(Mem& mem, SceneObj* S, CoarseObj* C, const nimbus_refine_params
 
 int voxelize_scene(Mem& mem, const nimbus_cloud* cloud, const nimbus_edges* edges, const nimbus_vox_params* p,
                    SceneObj* out, cudaStream_t st);
+int scene_save(Mem& mem, SceneObj* S, const char* path, cudaStream_t st);
+int scene_load(Mem& mem, const char* path, SceneObj* S, cudaStream_t st);
 int update_scene_region(Mem& mem, SceneObj* s, const double lo[3], const double hi[3],
                         const nimbus_cloud* repl, cudaStream_t st);
 

@@ -9,7 +9,9 @@
 // same sort with the kind bit set, so edge IEs sit in their voxel's range.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
+#include <vector>
 #include <mutex>
 
 #include "nimbus_host.hpp"
@@ -709,6 +711,167 @@ int update_scene_region(Mem& mem, SceneObj* S, const double lo[3], const double 
   S->material = nmat;
   S->n_points = n_new;
   return build_tables(mem, S, st);
+}
+
+// ----------------------------------------------------------- scene checkpoint
+namespace {
+constexpr char kMagic[8] = {'N', 'I', 'M', 'B', 'U', 'S', 'C', '1'};
+constexpr uint32_t kVersion = 1;
+
+struct Fnv {   // FNV-1a over the payload
+  uint64_t h = 1469598103934665603ull;
+  void add(const void* p, size_t n) {
+    const unsigned char* b = static_cast<const unsigned char*>(p);
+    for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ull;
+  }
+};
+
+struct Writer {
+  FILE* f;
+  Fnv sum;
+  bool ok = true;
+  void put(const void* p, size_t n) {
+    if (n == 0) return;
+    sum.add(p, n);
+    ok = ok && std::fwrite(p, 1, n, f) == n;
+  }
+};
+
+struct Reader {
+  FILE* f;
+  Fnv sum;
+  bool ok = true;
+  void get(void* p, size_t n) {
+    if (n == 0 || !ok) return;
+    ok = std::fread(p, 1, n, f) == n;
+    if (ok) sum.add(p, n);
+  }
+};
+}  // namespace
+
+int scene_save(Mem& mem, SceneObj* S, const char* path, cudaStream_t st) {
+  std::string* err = mem.err;
+  if (!path) {
+    *err = "scene_save: null path";
+    return NIMBUS_ERR_ARG;
+  }
+  const int64_t n = S->n_points, ne = (int64_t)S->edge_label_h.size();
+  std::vector<float> xyz(3 * n), nrm(3 * n);
+  std::vector<uint32_t> lab(n);
+  std::vector<uint8_t> mat(S->material ? n : 0);
+  NB_CUDA(err, cudaStreamSynchronize(st));
+  if (n > 0) {
+    NB_CUDA(err, cudaMemcpy(xyz.data(), S->xyz, xyz.size() * sizeof(float), cudaMemcpyDeviceToHost));
+    NB_CUDA(err, cudaMemcpy(nrm.data(), S->nrm, nrm.size() * sizeof(float), cudaMemcpyDeviceToHost));
+    NB_CUDA(err, cudaMemcpy(lab.data(), S->label, lab.size() * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    if (S->material) NB_CUDA(err, cudaMemcpy(mat.data(), S->material, mat.size(), cudaMemcpyDeviceToHost));
+  }
+  FILE* f = std::fopen(path, "wb");
+  if (!f) {
+    *err = std::string("scene_save: cannot open ") + path;
+    return NIMBUS_ERR_IO;
+  }
+  bool ok = std::fwrite(kMagic, 1, 8, f) == 8;
+  Writer w{f};
+  const uint32_t has_mat = S->material ? 1u : 0u;
+  w.put(&kVersion, 4);
+  w.put(&S->params, sizeof S->params);
+  w.put(S->origin, sizeof S->origin);
+  w.put(S->dims, sizeof S->dims);
+  w.put(&n, 8);
+  w.put(&ne, 8);
+  w.put(&S->max_label, 4);
+  w.put(&has_mat, 4);
+  w.put(xyz.data(), xyz.size() * sizeof(float));
+  w.put(nrm.data(), nrm.size() * sizeof(float));
+  w.put(lab.data(), lab.size() * sizeof(uint32_t));
+  w.put(mat.data(), mat.size());
+  w.put(S->edges_h.data(), S->edges_h.size() * sizeof(double));
+  w.put(S->edge_label_h.data(), S->edge_label_h.size() * sizeof(uint32_t));
+  ok = ok && w.ok && std::fwrite(&w.sum.h, 1, 8, f) == 8;
+  ok = (std::fclose(f) == 0) && ok;
+  if (!ok) {
+    *err = std::string("scene_save: write failed: ") + path;
+    return NIMBUS_ERR_IO;
+  }
+  return NIMBUS_OK;
+}
+
+int scene_load(Mem& mem, const char* path, SceneObj* S, cudaStream_t st) {
+  std::string* err = mem.err;
+  if (!path) {
+    *err = "scene_load: null path";
+    return NIMBUS_ERR_ARG;
+  }
+  FILE* f = std::fopen(path, "rb");
+  if (!f) {
+    *err = std::string("scene_load: cannot open ") + path;
+    return NIMBUS_ERR_IO;
+  }
+  auto fail = [&](const char* why) {
+    std::fclose(f);
+    *err = std::string("scene_load: ") + why + ": " + path;
+    return NIMBUS_ERR_IO;
+  };
+  char magic[8];
+  if (std::fread(magic, 1, 8, f) != 8 || std::memcmp(magic, kMagic, 8) != 0) return fail("not a scene checkpoint");
+  Reader r{f};
+  uint32_t version = 0, has_mat = 0;
+  int64_t n = 0, ne = 0;
+  r.get(&version, 4);
+  if (!r.ok || version != kVersion) return fail("unsupported checkpoint version");
+  r.get(&S->params, sizeof S->params);
+  r.get(S->origin, sizeof S->origin);
+  r.get(S->dims, sizeof S->dims);
+  r.get(&n, 8);
+  r.get(&ne, 8);
+  r.get(&S->max_label, 4);
+  r.get(&has_mat, 4);
+  if (!r.ok || n < 0 || n > (int64_t)1 << 36 || ne < 0 || ne > (int64_t)1 << 28 || has_mat > 1 ||
+      !(S->params.voxel_size > 0) || S->params.dv < 1 || S->params.dv > 4 || S->max_label >= (1u << 24))
+    return fail("damaged header");
+  for (int a = 0; a < 3; ++a)
+    if (S->dims[a] < 1 || S->dims[a] >= 1000000) return fail("damaged header");
+  std::vector<float> xyz(3 * n), nrm(3 * n);
+  std::vector<uint32_t> lab(n);
+  std::vector<uint8_t> mat(has_mat ? n : 0);
+  S->edges_h.resize(12 * ne);
+  S->edge_label_h.resize(ne);
+  r.get(xyz.data(), xyz.size() * sizeof(float));
+  r.get(nrm.data(), nrm.size() * sizeof(float));
+  r.get(lab.data(), lab.size() * sizeof(uint32_t));
+  r.get(mat.data(), mat.size());
+  r.get(S->edges_h.data(), S->edges_h.size() * sizeof(double));
+  r.get(S->edge_label_h.data(), S->edge_label_h.size() * sizeof(uint32_t));
+  uint64_t sum = 0;
+  const bool got_sum = r.ok && std::fread(&sum, 1, 8, f) == 8;
+  if (!got_sum) return fail("truncated checkpoint");
+  if (sum != r.sum.h) return fail("checksum mismatch");
+  std::fclose(f);
+  S->mem = &mem;
+  S->n_points = n;
+  NB_TRY(S->own(&S->xyz, std::max<int64_t>(1, 3 * n), st));
+  NB_TRY(S->own(&S->nrm, std::max<int64_t>(1, 3 * n), st));
+  NB_TRY(S->own(&S->label, std::max<int64_t>(1, n), st));
+  if (n > 0) {
+    NB_CUDA(err, cudaMemcpyAsync(S->xyz, xyz.data(), xyz.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+    NB_CUDA(err, cudaMemcpyAsync(S->nrm, nrm.data(), nrm.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+    NB_CUDA(err, cudaMemcpyAsync(S->label, lab.data(), lab.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
+  }
+  if (has_mat) {
+    NB_TRY(S->own(&S->material, std::max<int64_t>(1, n), st));
+    if (n > 0) NB_CUDA(err, cudaMemcpyAsync(S->material, mat.data(), mat.size(), cudaMemcpyHostToDevice, st));
+  }
+  if (ne > 0) {
+    double* de;
+    NB_TRY(S->own(&de, 12 * ne, st));
+    NB_CUDA(err, cudaMemcpyAsync(de, S->edges_h.data(), 12 * ne * sizeof(double), cudaMemcpyHostToDevice, st));
+    S->d.edges = de;
+  }
+  fill_dscene(S);
+  const int rc = build_tables(mem, S, st);
+  if (rc == NIMBUS_OK) NB_CUDA(err, cudaStreamSynchronize(st));   // the host vectors go out of scope
+  return rc;
 }
 
 // ----------------------------------------------------------- voxelisation without allocation

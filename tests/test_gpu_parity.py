@@ -217,3 +217,42 @@ def test_autotune_keeps_results(ctx):
     ctx.set_tuning(level_block=256, refine_blocks=0, refine_order=1)
     with pytest.raises(Exception):
         ctx.set_tuning(level_block=96)
+
+
+def test_scene_checkpoint_round_trip(ctx, tmp_path):
+    """A saved scene -- including a region update -- loads into another context with
+    the same tables and gives the same coarse and exact paths; damaged files fail."""
+    from paper_2402_13747_b300 import _abi
+    from paper_2402_13747_b300.serve import moved_box_update
+    full = scenes.room_noisy()
+    sc = full.with_pairs(full.tx[:1], full.rx[:3])
+    p = config.params_for(sc, max_refl=2, max_diff=1)
+    s = ctx.voxelize_scene(sc, p)
+    lo, hi, cloud = moved_box_update(sc, {"box": None}, 3)
+    ctx.update_region(s, lo, hi, *cloud)
+    path = str(tmp_path / "scene.nimbus")
+    ctx.scene_save(s, path)
+    other = _abi.Context(0)
+    s2 = other.scene_load(path)
+    A, B = ctx.scene_tables(s), other.scene_tables(s2)
+    for k in ("origin", "dims", "kind", "label", "cell", "gs", "prange", "cell_count", "march", "rp", "normal"):
+        np.testing.assert_array_equal(np.asarray(A[k]), np.asarray(B[k]), err_msg=k)
+    def paths(c, h):
+        co = c.trace(h, sc.tx, sc.rx, p)
+        P = c.refine(h, co, p)
+        out = c.query(P, 0)
+        c.release(P)
+        c.release(co)
+        return out
+    G1, G2 = paths(ctx, s), paths(other, s2)
+    for k in ("tx", "rx", "n", "type", "label", "pts", "length"):
+        np.testing.assert_array_equal(G1[k], G2[k])
+    # a truncated and a foreign file are rejected without creating a scene
+    raw = open(path, "rb").read()
+    open(tmp_path / "cut.nimbus", "wb").write(raw[: len(raw) // 2])
+    open(tmp_path / "foreign.nimbus", "wb").write(b"not a scene" * 10)
+    for bad in ("cut.nimbus", "foreign.nimbus", "missing.nimbus"):
+        with pytest.raises(_abi.NimbusError, match="ERR_IO"):
+            other.scene_load(str(tmp_path / bad))
+    ctx.release(s)
+    other.close()

@@ -289,7 +289,7 @@ NIMBUS_API int nimbus_scene_load(nimbus_ctx* ctx, const char* path, nimbus_handl
  */
 typedef struct {
   int32_t level_block;      /* threads per block of the propagation levels: 128 or 256 */
-  int32_t refine_blocks;    /* 4-warp refinement blocks per SM: 1..4, or 0 for as many as fit */
+  int32_t refine_blocks;    /* 4-warp refinement blocks per SM: 1..8 (at most as many as fit), 0 = as many as fit */
   int32_t refine_order;     /* 1: refine the paths with the most interactions first; 0: in coarse order */
   int32_t pad_;
   double level_ms;          /* after nimbus_autotune: time of the chosen level layout on the sample, else 0 */
@@ -304,7 +304,7 @@ NIMBUS_API int nimbus_set_tuning(nimbus_ctx* ctx, const nimbus_tuning* t);
 
 /* Autotuner.  Traces the given TX/RX sample on `scene` once per level layout
  * (blocks of 128 or 256 threads), keeps the fastest propagation time, then
- * refines that coarse set once per refinement layout (3 or all resident blocks per
+ * refines that coarse set once per refinement layout (4 or all resident blocks per
  * SM x ordered or not), keeps the fastest, stores the result in the context for the
  * calls that follow and writes it to `out` (may be NULL).  Times are CUDA events on
  * `stream`; the call synchronises.  Errors of the trace or refinement (including

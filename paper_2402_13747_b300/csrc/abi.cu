@@ -487,7 +487,7 @@ int nimbus_get_tuning(nimbus_ctx* ctx, nimbus_tuning* out) {
 
 int nimbus_set_tuning(nimbus_ctx* ctx, const nimbus_tuning* t) {
   if (!ctx) return NIMBUS_ERR_ARG;
-  if (!t || !(t->level_block == 128 || t->level_block == 256) || t->refine_blocks < 0 || t->refine_blocks > 4 ||
+  if (!t || !(t->level_block == 128 || t->level_block == 256) || t->refine_blocks < 0 || t->refine_blocks > 8 ||
       !(t->refine_order == 0 || t->refine_order == 1)) {
     ctx->err = "set_tuning: value out of range";
     return NIMBUS_ERR_ARG;
@@ -542,7 +542,7 @@ int nimbus_autotune(nimbus_ctx* ctx, nimbus_handle scene, const double* tx, int3
     return rc;
   }
   double best_rf = -1.0;
-  const int rblocks[2] = {3, 0}, orders[2] = {0, 1};
+  const int rblocks[2] = {4, 0}, orders[2] = {0, 1};
   for (int rb : rblocks)
     for (int od : orders) {
       nb::Tuning t = best;

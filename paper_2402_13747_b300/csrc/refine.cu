@@ -142,9 +142,9 @@ __device__ void fill_cache(const DScene& s, LabelCache& lc, const int gR[3], uin
 // centred on c0 (the target); xl = x - c0, dg = subvoxel of x minus gR.  The block's
 // IEs are found with one ballot per 32 cache entries and taken IE_BATCH at a time:
 // lane k reads point k of each IE of the batch before any of them is summed, so
-// IE_BATCH loads are in flight per lane (the kernel is bound by load latency).
+// IE_BATCH loads are in flight per lane (the kernel is bound by latency).
 // Each lane adds its points in IE order; every lane returns the same f and normal.
-constexpr int IE_BATCH = 4;
+constexpr int IE_BATCH = 2;
 __device__ bool sdf_label_warp(const DScene& s, const LabelCache& lc, float3 xl, const int dg[3], float3 c0,
                                float* f, float3* n_out, int lane, unsigned long long& bytes) {
   if (abs(dg[0]) > 1 || abs(dg[1]) > 1 || abs(dg[2]) > 1) return false;
@@ -262,12 +262,13 @@ __device__ bool reproject_warp(const DScene& s, const d3* Pp, const d3* Rp, uint
 // points and the path length are FP64; directions, gradient, local Hessian and step
 // are FP32 evaluations from FP64 differences, except that once ||grad|| < delta the
 // gradient that decides the stop and drives the last steps is FP64.
-// Occupancy: four 4-warp blocks per SM (128 registers a thread, 44 KB of shared
-// memory a block).  The kernel is bound by the latency of the Eq. 1 point loads:
-// four IEs' loads in flight per lane (IE_BATCH) and as many resident warps as the
-// registers allow both pay, and any register spill in the point loop costs far more
-// than either.  So each path's FP64 state lives in shared memory (WarpPath), indexed
-// by node (0 = TX, n+1 = RX), and is read where it is used.
+// Occupancy: six 4-warp blocks per SM (80 registers a thread; 7 KB of static and
+// 14 KB of dynamic shared memory a block for three reflections).  The kernel is bound
+// by latency: resident warps pay most (measured on the noisy-room workload: 4 blocks
+// with four IEs' loads in flight per lane 4.41 s, 5 blocks with three 3.85 s, 6
+// blocks with two 3.72 s), and any sizeable register spill in the point loop costs
+// more than any of it.  So each path's FP64 state lives in shared memory (WarpPath),
+// indexed by node (0 = TX, n+1 = RX), and is read where it is used.
 struct WarpPath {
   d3 I[NB_MAXI + 2], c[NB_MAXI + 2], R[NB_MAXI + 2], In[NB_MAXI + 2], p0[NB_MAXI + 2];
   double tpar[NB_MAXI + 2];
@@ -275,7 +276,7 @@ struct WarpPath {
   float elen[NB_MAXI + 2];
 };
 
-__global__ void __launch_bounds__(128, 4) k_refine(DScene s, DRefine rp, CoarseView C, const double* txd,
+__global__ void __launch_bounds__(128, 6) k_refine(DScene s, DRefine rp, CoarseView C, const double* txd,
                                                    const double* rxd, ExactRec* out, unsigned long long* bytes_out,
                                                    unsigned long long* next_path, const uint32_t* order, int n_cache) {
   // label caches: n_cache per warp (the trace's reflection limit), in dynamic shared

@@ -207,7 +207,7 @@ def test_autotune_keeps_results(ctx):
     t = ctx.autotune(s, sc.tx, sc.rx[:2], p)
     ctx.release(s)
     assert t["level_block"] in (128, 256)
-    assert t["refine_blocks"] in (0, 3) and t["refine_order"] in (0, 1) and t["refine_ms"] > 0
+    assert t["refine_blocks"] in (0, 4) and t["refine_order"] in (0, 1) and t["refine_ms"] > 0
     for layout in (dict(level_block=128, refine_blocks=3, refine_order=0), t):
         ctx.set_tuning(**{k: layout[k] for k in ("level_block", "refine_blocks", "refine_order")})
         G = ctx.run(sc, p)

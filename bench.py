@@ -276,6 +276,39 @@ def main():
     value = cones / t_total
     exact_ps = paths / t_total
 
+    # end to end through the public API from pinned host buffers, results read back;
+    # every rank runs it on its own draw (whole-job figure like the value)
+    h = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in
+         dict(xyz=sc.xyz, nrm=sc.nrm, lab=sc.label, mat=sc.material, edges=sc.edges, elab=sc.edge_label,
+              tx=sc.tx, rx=sc.rx).items()}
+    h2d = sum(int(t.numel() * t.element_size()) for t in h.values())
+    e2e_t, e2e_cones, e2e_paths, d2h = [], 0, 0, 0
+    barrier()
+    for i in range(0 if args.no_e2e else args.warmup + args.steps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s = ctx.voxelize(h["xyz"], h["nrm"], h["lab"], h["mat"], h["edges"], h["elab"], params=p)
+        c = ctx.trace(s, h["tx"], h["rx"], p)
+        P = ctx.refine(s, c, p)
+        res = ctx.query(P)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        for hh in (P, c, s):
+            ctx.release(hh)
+        if i >= args.warmup:
+            e2e_t.append(dt)
+            e2e_cones += res["counts"]["n_cones"]
+            e2e_paths += res["counts"]["n_paths"]
+            d2h = int(len(res["n"]) * 320 + 8 * 24)
+    e2e = None
+    if not args.no_e2e:
+        t_e2e = sum(e2e_t)
+        if world > 1:
+            t_e2e, e2e_cones, e2e_paths = reduce_over_ranks(t_e2e, e2e_cones, e2e_paths, dev)
+        e2e = {"value": e2e_cones / t_e2e, "unit": "rays/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "exact_paths_per_s": e2e_paths / t_e2e}
+
     out = None
     if rank == 0:
         # dominant kernel and its roofline (algorithmic bytes / CUDA-event time)
@@ -296,32 +329,6 @@ def main():
                 "stage_ms": {k: v[0] for k, v in stages.items()} | {"vis_tables": c0["ms_vis"],
                                                                      "kappa": c0["ms_kappa"],
                                                                      "dedup": c0["ms_dedup"]}}
-
-        # end to end through the public API from pinned host buffers, results read back
-        h = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in
-             dict(xyz=sc.xyz, nrm=sc.nrm, lab=sc.label, mat=sc.material, edges=sc.edges, elab=sc.edge_label,
-                  tx=sc.tx, rx=sc.rx).items()}
-        h2d = sum(int(t.numel() * t.element_size()) for t in h.values())
-        e2e_t, e2e_cones, d2h = [], 0, 0
-        for i in range(0 if args.no_e2e else args.warmup + args.steps):
-            flush.fill_(1)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            s = ctx.voxelize(h["xyz"], h["nrm"], h["lab"], h["mat"], h["edges"], h["elab"], params=p)
-            c = ctx.trace(s, h["tx"], h["rx"], p)
-            P = ctx.refine(s, c, p)
-            res = ctx.query(P)
-            torch.cuda.synchronize()
-            dt = time.perf_counter() - t0
-            for hh in (P, c, s):
-                ctx.release(hh)
-            if i >= args.warmup:
-                e2e_t.append(dt)
-                e2e_cones += res["counts"]["n_cones"]
-                d2h = int(len(res["n"]) * 320 + 8 * 24)
-        e2e = None if args.no_e2e else {
-            "value": e2e_cones / sum(e2e_t), "unit": "rays/s", "h2d_bytes_per_step": h2d,
-            "d2h_bytes_per_step": d2h, "exact_paths_per_s": paths / max(1, len(counts)) / statistics.mean(e2e_t)}
 
         # plain form: one trace + refine per TX/RX pair on the resident scene
         plain = None

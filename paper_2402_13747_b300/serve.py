@@ -131,6 +131,7 @@ class GpuExecutor:
         self.params = params
         self.handles = {}
         self.applied = {}
+        self.need = {}   # (scene, depth) -> largest node / coarse counts per TX seen so far
         for sid, sc in scenes.items():
             self.handles[sid] = self.ctx.voxelize_scene(sc, params, stream=self.stream)
             self.applied[sid] = 0
@@ -151,14 +152,22 @@ class GpuExecutor:
         rx_off = np.cumsum([0] + [r.pairs for r in batch])
         dmax = int(max(r.depth for r in batch))
         p = self.params.replace(max_refl=dmax, max_diff=min(1, dmax), max_int=dmax)
-        # node / coarse buffers: the library's defaults first; a batch that overflows
-        # them is traced again with the sizes the first pass reported
-        caps = (0, 0)
+        # node / coarse buffers: sized from what this scene and depth needed per TX in
+        # earlier batches (the library's defaults at first); a batch that still
+        # overflows is traced again with the sizes the first pass reported
+        n_tx = len(batch)
+        per_tx = self.need.get((sid, dmax))
+        caps = (0, 0) if per_tx is None else (max(1 << 23, int(per_tx[0] * n_tx * 1.25)),
+                                              max(1 << 23, int(per_tx[1] * n_tx * 1.25)))
         for attempt in range(2):
             c = self.ctx.trace(self.handles[sid], tx, rx, p, rx_owner=owner, rx_max_int=depth, max_nodes=caps[0],
                                max_coarse=caps[1], stream=self.stream, allow_overflow=True)
             cc = self.ctx.coarse_counts(c, stream=self.stream)
             ov = cc["overflow"]
+            if ov:
+                seen = (cc["needed_nodes"] / n_tx, cc["needed_coarse"] / n_tx)
+                old = self.need.get((sid, dmax), (0, 0))
+                self.need[(sid, dmax)] = (max(old[0], seen[0]), max(old[1], seen[1]))
             if not ov or attempt == 1:
                 break
             self.ctx.release(c)

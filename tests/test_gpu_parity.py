@@ -159,6 +159,33 @@ def test_edge_cases(ctx, room_tiny):
     ctx.release(s)
 
 
+def test_degenerate_pairs_and_parameters(ctx, room_tiny):
+    """RX on the TX, a duplicated RX and kappa = 1 give the oracle's paths; an unknown
+    launch mode and too many interactions are argument errors."""
+    from paper_2402_13747_b300._abi import NimbusError
+    tx = room_tiny.tx[0]
+    sc = room_tiny.with_pairs(room_tiny.tx, np.vstack([tx, room_tiny.rx[0], room_tiny.rx[0]]))
+    p = config.params_for(sc, max_refl=1)
+    G = ctx.run(sc, p)
+    _, _, e = oracle.run(sc, p)
+    cmp = compare(G, e.paths(), atol_pts=1e-3, rtol_len=1e-6)
+    assert cmp["only_gpu"] == [] and cmp["only_ref"] == [] and cmp["bad"] == [], cmp
+    on = np.sort(G["length"][G["rx"] == 0])
+    want = np.sort([0.0] + [2 * d for d in (tx[0], 10 - tx[0], tx[1], 10 - tx[1], tx[2], 3 - tx[2])])
+    np.testing.assert_allclose(on, want, atol=1e-5)
+    np.testing.assert_array_equal(np.sort(G["length"][G["rx"] == 1]), np.sort(G["length"][G["rx"] == 2]))
+    p1 = config.params_for(room_tiny, kappa=1)
+    G1 = ctx.run(room_tiny, p1)
+    _, _, e1 = oracle.run(room_tiny, p1)
+    cmp = compare(G1, e1.paths(), atol_pts=1e-3, rtol_len=1e-6)
+    assert cmp["only_gpu"] == [] and cmp["only_ref"] == [] and len(G1["n"]) == 25, cmp
+    s = ctx.voxelize_scene(room_tiny, p1)
+    for bad in (p1.replace(launch_mode=2), p1.replace(max_int=9, max_refl=9)):
+        with pytest.raises(NimbusError, match="ERR_ARG"):
+            ctx.trace(s, room_tiny.tx, room_tiny.rx, bad)
+    ctx.release(s)
+
+
 def test_empty_cloud_with_region(ctx):
     p = config.Params(max_refl=1)
     s = ctx.voxelize(np.zeros((0, 3), np.float32), np.zeros((0, 3), np.float32), np.zeros(0, np.uint32),

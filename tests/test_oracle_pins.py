@@ -367,3 +367,20 @@ def test_label_surface_is_plane_distance_and_continuous(room_tiny):
     fs = np.array([s2.sdf_label(0, np.array([0.01, y, 1.3]))[0] for y in ys])
     assert np.all(np.isfinite(fs))
     assert np.max(np.abs(np.diff(fs))) < 1e-3   # no step at subvoxel faces
+
+
+def test_rx_on_the_tx_gives_normal_incidence_images(room_tiny):
+    """Degenerate pair: the RX at the TX.  The exact paths are the LOS of length 0 and
+    the six normal-incidence reflections, of length twice the distance to each face
+    (image method); a duplicated RX gets the same set."""
+    tx = room_tiny.tx[0]
+    sc = room_tiny.with_pairs(room_tiny.tx, np.vstack([tx, room_tiny.rx[0], room_tiny.rx[0]]))
+    p = config.params_for(sc, max_refl=1, grad_stop=1e-9)
+    _, _, e = oracle.run(sc, p)
+    P = e.paths()
+    on = np.sort(P["length"][P["rx"] == 0])
+    want = np.sort([0.0] + [2 * d for d in (tx[0], 10 - tx[0], tx[1], 10 - tx[1], tx[2], 3 - tx[2])])
+    np.testing.assert_allclose(on, want, atol=1e-6)
+    a = np.sort(P["length"][P["rx"] == 1])
+    b = np.sort(P["length"][P["rx"] == 2])
+    np.testing.assert_array_equal(a, b)

@@ -398,6 +398,9 @@ bool sdf_hit(const Scene& s, const IE& ie, V3 P, V3 d, double* t_hit) {
     if (std::fabs(f) < s.p.sdf_eps) {
       double dn = dot(n, d);
       double th = std::fabs(dn) > 1e-3 ? t - f / dn : t;
+      // reading: the intersection lies on the marched segment; a Newton placement
+      // past either end (grazing rays) is not an intersection of this point set
+      if (th < tc - 0.5 * L || th > t_end) return false;
       *t_hit = th;
       return true;
     }

@@ -220,8 +220,9 @@ __device__ __forceinline__ bool sdf_local(const DScene& s, uint32_t pb, uint32_t
 // The |f| march of Section 2.2.1 on [t0, t_end] along unit direction d, for any
 // evaluator eval(t, &f, &n) of Eq. 1 on the ray.  Steps t += |f(t)| until the sign
 // of f changes (secant placement) or |f| < eps (one Newton step along the ray);
-// false when the segment end is passed, the step budget runs out or every weight
-// vanishes.
+// false when the segment end is passed, the step budget runs out, every weight
+// vanishes, or the Newton placement falls off the segment (the intersection lies on
+// the marched segment), so a hit always satisfies t0 <= t_hit <= t_end.
 // With Jump set (visibility only, where the caller keeps a yes/no decision): where
 // f falls geometrically between two steps (as it does exactly on a surface that is
 // linear along the ray), the step k at which the march would first see |f| < eps,
@@ -239,7 +240,9 @@ __device__ __forceinline__ bool march_abs_f(Eval&& eval, float3 d, float t0, flo
   for (int it = 0; it < max_steps; ++it) {
     if (fabsf(f) < eps) {
       float dn = dot(n, d);
-      *t_hit = fabsf(dn) > 1e-3f ? t - f / dn : t;
+      const float th = fabsf(dn) > 1e-3f ? t - f / dn : t;
+      if (!(th >= t0 && th <= t_end)) return false;   // the intersection lies on the segment
+      *t_hit = th;
       return true;
     }
     float tn = t + fabsf(f);
@@ -298,6 +301,19 @@ __device__ __forceinline__ bool ignored(Endpoint e, uint32_t lbl, float dist, fl
   return false;
 }
 
+// True when no hit on an IE of label lbl, centred at tc along the ray of length T,
+// can occlude: every hit lies on the IE's marched segment [tc - half, tc + half], and
+// an endpoint whose rule ignores lbl covers that whole segment within r.  Exact in
+// FP32 too: th = tc + tau with |tau| <= half gives th <= tc + half (rounding is
+// monotonic), and likewise for T - th.  Skipping such an IE's march changes no
+// visibility decision.
+__device__ __forceinline__ bool cannot_occlude(Endpoint ea, Endpoint eb, uint32_t lbl, float tc, float half, float T,
+                                               float r) {
+  const bool a_ign = ea.mode == IGN_ANY || (ea.mode == IGN_LABEL && lbl == ea.label);
+  const bool b_ign = eb.mode == IGN_ANY || (eb.mode == IGN_LABEL && lbl == eb.label);
+  return (a_ign && tc + half < r) || (b_ign && T - (tc - half) < r);
+}
+
 // Visibility ray A -> B (Sections 2.2.4, 2.3): walk the voxels of the segment and
 // intersect the point IEs of each voxel passed.  bytes counts the scene records read.
 static __device__ __noinline__ bool visible(const DScene& s, float3 A, float3 B, Endpoint ea, Endpoint eb, unsigned long long& bytes) {
@@ -322,13 +338,14 @@ static __device__ __noinline__ bool visible(const DScene& s, float3 A, float3 B,
       if ((__float_as_uint(nm.w) & 1u) != IE_POINT) continue;   // edges never occlude
       float3 c = xyz(bb);
       float tc = dot(c - A, d);
+      uint32_t lbl = __float_as_uint(__ldg(&ie->rp_lab).w);
+      bytes += 16;
+      if (cannot_occlude(ea, eb, lbl, tc, 0.5f * s.seg_len, T, s.vis_ignore)) continue;
       float3 x0 = (A - c) + tc * d;
       float tau;
       if (!sdf_march(s, __float_as_uint(bb.w), __float_as_uint(sc_pc.w), c, x0, d, &tau, bytes)) continue;
       float th = tc + tau;
       if (!(th > 0.f && th < T)) continue;
-      uint32_t lbl = __float_as_uint(__ldg(&ie->rp_lab).w);
-      bytes += 16;
       if (ignored(ea, lbl, th, s.vis_ignore) || ignored(eb, lbl, T - th, s.vis_ignore)) continue;
       return false;
     }

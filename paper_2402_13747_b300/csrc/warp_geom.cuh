@@ -122,12 +122,13 @@ __device__ bool visible_warp(const DScene& s, float3 A, float3 B, Endpoint ea, E
         float4 sc = __ldg(&r->sc_pc);
         float3 c = xyz(bb);
         float tc = dot(c - A, d);
+        uint32_t lbl = __float_as_uint(__ldg(&r->rp_lab).w);
+        if (cannot_occlude(ea, eb, lbl, tc, 0.5f * s.seg_len, T, s.vis_ignore)) continue;
         float3 x0 = (A - c) + tc * d;
         float tau;
         if (!sdf_march_warp(s, __float_as_uint(bb.w), __float_as_uint(sc.w), c, x0, d, &tau, lane, bytes)) continue;
         float th = tc + tau;
         if (!(th > 0.f && th < T)) continue;
-        uint32_t lbl = __float_as_uint(__ldg(&r->rp_lab).w);
         if (ignored(ea, lbl, th, s.vis_ignore) || ignored(eb, lbl, T - th, s.vis_ignore)) continue;
         return false;
       }

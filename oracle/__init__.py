@@ -6,11 +6,18 @@ slow, single-threaded FP64 implementation of voxelisation (Section 2.1), coarse 
 tracing (Section 2.2) and path refinement (Section 2.3) -- through ctypes.  It
 shares no code with the CUDA library.
 
-Parity pins (tests/test_oracle_pins.py): image method on the box room, LOS length,
-Keller diffraction point on a sampled wedge, brute-force visibility, library
-distance transform for the march field, exact-plane SDF, Monte-Carlo cone-sphere,
-Fibonacci lattice properties.  The coarse-path set and the kappa choice on noisy
-scenes have no closed form: parity unpinned beyond those invariants.
+Parity pins (tests/test_oracle_pins.py):
+- the image method on the box room, with both transmission phases;
+- the LOS length, and the normal-incidence images of an RX placed on the TX;
+- the Keller diffraction point on a sampled wedge;
+- brute-force visibility and a closed-form plane patch;
+- a brute-force chessboard distance for the march field;
+- the exact-plane SDF and the continuity of a label's surface;
+- a Monte-Carlo cone-sphere test and the Fibonacci lattice properties;
+- integer re-derivation of the voxel keys, and the reflection law at refined points.
+
+The coarse-path set and the kappa choice on noisy scenes have no closed form: parity
+unpinned beyond those invariants.
 """
 from __future__ import annotations
 

@@ -13,6 +13,11 @@
 // intersections) and path refinement (Section 2.3: Eq. 2 minimised by gradient
 // descent, visibility, label and first-Fresnel-zone duplicate removal).
 // Where the paper is silent the reading used is stated next to the code.
+// Pins (tests/test_oracle_pins.py) fix voxelisation, the march field, Eq. 1,
+// visibility, the cone test and the refined exact paths against closed forms and
+// brute force.  The coarse-path set and the kappa choice on noisy clouds have no
+// closed form: parity unpinned beyond their invariants (kappa, depth limits) and the
+// exact paths they refine to.
 // The only FP32 arithmetic is the subvoxel binning, which both sides perform with
 // the same correctly rounded FP32 operations so that the point-to-subvoxel
 // assignment is bit-identical (binning reading).

@@ -291,12 +291,15 @@ typedef struct {
   int32_t level_block;      /* threads per block of the propagation levels: 128 or 256 */
   int32_t refine_blocks;    /* 4-warp refinement blocks per SM: 1..8 (at most as many as fit), 0 = as many as fit */
   int32_t refine_order;     /* 1: refine the paths with the most interactions first; 0: in coarse order */
-  int32_t pad_;
+  int32_t graph;            /* 1: each stretch of a call with no host round trip (trace: RX table, march field,
+                               transmission phase and all depths; refine: refinement, final visibility and
+                               winners; then dedup) is captured on a private stream and launched on the
+                               caller's stream as one CUDA graph; 0: the same launches issued directly */
   double level_ms;          /* after nimbus_autotune: time of the chosen level layout on the sample, else 0 */
   double refine_ms;         /* after nimbus_autotune: time of the chosen refinement layout on the sample, else 0 */
 } nimbus_tuning;
 
-/* The context's launch configuration (defaults 256, 0, 1). */
+/* The context's launch configuration (defaults 256, 0, 1, 1). */
 NIMBUS_API int nimbus_get_tuning(nimbus_ctx* ctx, nimbus_tuning* out);
 
 /* Replace it.  A value out of range returns NIMBUS_ERR_ARG and changes nothing. */

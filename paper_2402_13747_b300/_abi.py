@@ -93,10 +93,10 @@ class StaticTables(C.Structure):
 
 class Tuning(C.Structure):
     _fields_ = [("level_block", C.c_int32), ("refine_blocks", C.c_int32), ("refine_order", C.c_int32),
-                ("pad_", C.c_int32), ("level_ms", C.c_double), ("refine_ms", C.c_double)]
+                ("graph", C.c_int32), ("level_ms", C.c_double), ("refine_ms", C.c_double)]
 
     def as_dict(self) -> dict:
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad_"}
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class StaticInfo(C.Structure):

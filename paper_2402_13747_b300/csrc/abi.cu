@@ -12,6 +12,7 @@
 struct nimbus_ctx {
   int device = 0;
   nb::Mem mem;
+  nb::GraphCache graphs;
   nb::Tuning tune;
   std::string err;
   std::unordered_map<uint64_t, nb::Obj*> objs;
@@ -132,6 +133,7 @@ int nimbus_create(nimbus_ctx** out, int device, size_t mem_budget_bytes) {
   nimbus_ctx* ctx = new nimbus_ctx();
   ctx->device = device;
   ctx->mem.err = &ctx->err;
+  ctx->mem.graphs = &ctx->graphs;
   DeviceGuard g(device);
   size_t free_b = 0, total_b = 0;
   if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
@@ -151,6 +153,7 @@ int nimbus_destroy(nimbus_ctx* ctx) {
     for (auto& kv : ctx->objs) drop_obj(ctx, kv.second, ctx->obj_stream[kv.first]);
     ctx->objs.clear();
     cudaDeviceSynchronize();
+    ctx->graphs.release();
     cudaGetLastError();
   }
   delete ctx;
@@ -475,6 +478,7 @@ static void to_public(const nb::Tuning& t, nimbus_tuning* o) {
   o->level_block = t.level_block;
   o->refine_blocks = t.refine_blocks;
   o->refine_order = t.refine_order;
+  o->graph = t.graph;
   o->level_ms = t.level_ms;
   o->refine_ms = t.refine_ms;
 }
@@ -488,13 +492,14 @@ int nimbus_get_tuning(nimbus_ctx* ctx, nimbus_tuning* out) {
 int nimbus_set_tuning(nimbus_ctx* ctx, const nimbus_tuning* t) {
   if (!ctx) return NIMBUS_ERR_ARG;
   if (!t || !(t->level_block == 128 || t->level_block == 256) || t->refine_blocks < 0 || t->refine_blocks > 8 ||
-      !(t->refine_order == 0 || t->refine_order == 1)) {
+      !(t->refine_order == 0 || t->refine_order == 1) || !(t->graph == 0 || t->graph == 1)) {
     ctx->err = "set_tuning: value out of range";
     return NIMBUS_ERR_ARG;
   }
   ctx->tune.level_block = t->level_block;
   ctx->tune.refine_blocks = t->refine_blocks;
   ctx->tune.refine_order = t->refine_order;
+  ctx->tune.graph = t->graph;
   ctx->tune.level_ms = t->level_ms;
   ctx->tune.refine_ms = t->refine_ms;
   return NIMBUS_OK;

@@ -19,6 +19,7 @@ struct Mem {
   size_t budget = 0, used = 0, peak = 0;
   std::unordered_map<void*, size_t> sizes;
   std::string* err = nullptr;
+  struct GraphCache* graphs = nullptr;   // the context's CUDA graphs (may be null)
   int alloc(void** p, size_t bytes, cudaStream_t st);
   void release(void* p, cudaStream_t st);
   template <class T>
@@ -39,10 +40,12 @@ struct Scratch {
   ~Scratch() {
     for (void* p : ptrs) mem->release(p, st);
   }
+  // bytes an arena gives one get of n elements of size elem
+  static size_t arena_block(size_t n, size_t elem) { return (n * elem + 16 + 255) & ~(size_t)255; }
   template <class T>
   int get(T** p, size_t n) {
     if (arena) {
-      size_t bytes = (n * sizeof(T) + 16 + 255) & ~(size_t)255;
+      size_t bytes = arena_block(n, sizeof(T));
       if (arena_used + bytes > arena_cap) {
         if (mem && mem->err) *mem->err = "static scratch exhausted";
         return NIMBUS_ERR_ARG;
@@ -81,17 +84,43 @@ int num_sms();
 // CUDA events recorded on one stream to time stages of kernels (read after a sync).
 struct StageTimer {
   cudaEvent_t ev[16];
+  bool owned[16];
   int n = 0;
   cudaStream_t st;
   explicit StageTimer(cudaStream_t s) : st(s) {}
   ~StageTimer() {
-    for (int i = 0; i < n; ++i) cudaEventDestroy(ev[i]);
+    for (int i = 0; i < n; ++i)
+      if (owned[i]) cudaEventDestroy(ev[i]);
   }
   int mark() {
     if (n >= 16) return n - 1;
     cudaEventCreate(&ev[n]);
+    owned[n] = true;
     cudaEventRecord(ev[n], st);
     return n++;
+  }
+  // An event to record later with record(); created here because a stream capture
+  // may not create events.
+  int make() {
+    if (n >= 16) return n - 1;
+    cudaEventCreate(&ev[n]);
+    owned[n] = true;
+    return n++;
+  }
+  // An event owned elsewhere (it outlives the timer), to record later with record().
+  int adopt(cudaEvent_t e) {
+    if (n >= 16) return n - 1;
+    ev[n] = e;
+    owned[n] = false;
+    return n++;
+  }
+  // Record event i on q.  On a capturing stream the record becomes a node of the
+  // graph (an external record), so the event is stamped when the graph runs.
+  void record(int i, cudaStream_t q) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(q, &cs);
+    cudaEventRecordWithFlags(ev[i], q,
+                             cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault);
   }
   double ms(int a, int b) {
     float m = 0.f;
@@ -110,6 +139,113 @@ int exclusive_scan(Scratch& sc, const uint32_t* in, uint32_t* out, int64_t n, ui
 // sorted pairs end in (keys, vals); keys_alt / vals_alt are work buffers of n.
 int radix_sort(Scratch& sc, uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt,
                int64_t n, int bits);
+
+// Arena bytes that exclusive_scan (with or without a total) and radix_sort take from a
+// Scratch in arena mode for n items.
+size_t scan_arena_bytes(int64_t n, bool total);
+size_t radix_arena_bytes(int64_t n, int bits);
+
+// The CUDA graphs of one context: a private capture stream and one executable graph
+// per stretch site.  A new capture of a site refreshes its executable in place
+// (cudaGraphExecUpdate) when the shape is unchanged -- only pointers, sizes and
+// launch parameters differ -- and is instantiated afresh otherwise.  Every stretch
+// is followed by a host sync before its site is captured again, so no executable is
+// updated while it runs.
+enum { GRAPH_TRACE = 0, GRAPH_REFINE = 1, GRAPH_DEDUP = 2, N_GRAPH_SITES = 3 };
+// The stage events a site records live here too: a kept executable refers to them.
+enum { GRAPH_EVENTS = 6 };
+struct GraphCache {
+  cudaStream_t cs = nullptr;
+  cudaGraphExec_t exec[N_GRAPH_SITES] = {};
+  cudaEvent_t ev[N_GRAPH_SITES][GRAPH_EVENTS] = {};
+  long long instantiated = 0, updated = 0;
+  cudaEvent_t event(int site, int k) {
+    if (!ev[site][k]) cudaEventCreate(&ev[site][k]);
+    return ev[site][k];
+  }
+  void release() {
+    for (cudaGraphExec_t& e : exec)
+      if (e) {
+        cudaGraphExecDestroy(e);
+        e = nullptr;
+      }
+    for (auto& row : ev)
+      for (cudaEvent_t& e : row)
+        if (e) {
+          cudaEventDestroy(e);
+          e = nullptr;
+        }
+    if (cs) cudaStreamDestroy(cs);
+    cs = nullptr;
+  }
+  ~GraphCache() { release(); }
+};
+
+// Stage event k of a stretch site for tm: the context's own when it keeps graphs,
+// else one that tm creates and destroys.
+inline int stretch_event(StageTimer& tm, Mem& mem, int site, int k) {
+  return mem.graphs ? tm.adopt(mem.graphs->event(site, k)) : tm.make();
+}
+
+// A stretch of stream work with no host round trip: fn(q) issues it on stream q.
+// With graph = false it goes straight onto st.  With graph = true it is captured on a
+// private stream into one CUDA graph and launched on st, so the whole stretch is one
+// graph launch; with the context's cache (mem.graphs) the executable of `site` is
+// kept between calls.  fn must not allocate, synchronise or copy to or from pageable
+// host memory; its Scratch buffers come from an arena.
+template <class F>
+int run_stretch(Mem& mem, cudaStream_t st, bool graph, int site, F&& fn) {
+  std::string* err = mem.err;
+  if (!graph) return fn(st);
+  GraphCache* gc = mem.graphs;
+  cudaStream_t cs = gc ? gc->cs : nullptr;
+  if (!cs) {
+    NB_CUDA(err, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    if (gc) gc->cs = cs;
+  }
+  struct StreamDel {
+    cudaStream_t s;
+    ~StreamDel() {
+      if (s) cudaStreamDestroy(s);
+    }
+  } del{gc ? nullptr : cs};
+  NB_CUDA(err, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  const int rc = fn(cs);
+  cudaGraph_t g = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(cs, &g);
+  if (rc != NIMBUS_OK) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return rc;
+  }
+  NB_CUDA(err, ec);
+  cudaGraphExec_t local = nullptr;
+  cudaGraphExec_t& ge = gc ? gc->exec[site] : local;
+  if (ge) {
+    cudaGraphExecUpdateResultInfo info;
+    if (cudaGraphExecUpdate(ge, g, &info) == cudaSuccess) {
+      ++gc->updated;
+    } else {
+      cudaGetLastError();
+      cudaGraphExecDestroy(ge);
+      ge = nullptr;
+    }
+  }
+  if (!ge) {
+    const cudaError_t ei = cudaGraphInstantiate(&ge, g, 0ull);
+    if (ei != cudaSuccess) {
+      ge = nullptr;
+      cudaGraphDestroy(g);
+      return cuda_fail(err, ei, "cudaGraphInstantiate");
+    }
+    if (gc) ++gc->instantiated;
+  }
+  cudaGraphDestroy(g);
+  const cudaError_t el = cudaGraphLaunch(ge, st);
+  if (!gc) cudaGraphExecDestroy(ge);   // freed once the launch completes
+  NB_CUDA(err, el);
+  return NIMBUS_OK;
+}
 
 // ----------------------------------------------------------------------------- objects
 enum { OBJ_SCENE = 1, OBJ_COARSE = 2, OBJ_PATHS = 3 };
@@ -197,6 +333,7 @@ struct Tuning {
   int level_block = 256;
   int refine_blocks = 0;   // 0: as many as fit
   int refine_order = 1;
+  int graph = 1;           // issue each host-free stretch of a call as one CUDA graph
   double level_ms = 0, refine_ms = 0;
 };
 

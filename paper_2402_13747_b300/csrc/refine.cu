@@ -640,9 +640,6 @@ int refine_paths(Mem& mem, SceneObj* S, CoarseObj* C, const nimbus_refine_params
   Scratch sc(&mem, st);
   unsigned long long* rbytes;   // [0] bytes read, [1] next path to hand out
   NB_TRY(sc.get(&rbytes, 2));
-  NB_CUDA(err, cudaMemsetAsync(rbytes, 0, 2 * sizeof(unsigned long long), st));
-  StageTimer tm(st);
-  const int e0 = tm.mark();
   const int n_cache = std::max(1, std::min(C->max_refl, NB_MAXI));
   const size_t dyn = sizeof(LabelCache) * 4 * n_cache;
   int refine_blocks = 0;   // resident blocks per SM (a persistent grid)
@@ -651,40 +648,56 @@ int refine_paths(Mem& mem, SceneObj* S, CoarseObj* C, const nimbus_refine_params
   const unsigned G = std::min<unsigned>(grid_for(n * 32, 128), (unsigned)(num_sms() * std::max(1, refine_blocks)));
   // hand out the paths with the most interactions first (they run longest), so the
   // launch does not end on a few long paths
-  uint32_t* ovals = nullptr;
+  uint64_t *okeys = nullptr, *okeys_alt = nullptr;
+  uint32_t *ovals = nullptr, *ovals_alt = nullptr;
   if (tn.refine_order) {
-    uint64_t *okeys, *okeys_alt;
-    uint32_t* ovals_alt;
     NB_TRY(sc.get(&okeys, n));
     NB_TRY(sc.get(&okeys_alt, n));
     NB_TRY(sc.get(&ovals, n));
     NB_TRY(sc.get(&ovals_alt, n));
-    k_order_keys<<<grid_for(n, 256), 256, 0, st>>>(C->nint, n, okeys, ovals);
-    NB_LAUNCHED(err);
-    NB_TRY(radix_sort(sc, okeys, ovals, okeys_alt, ovals_alt, n, 8));
   }
-  k_refine<<<G, 128, dyn, st>>>(S->d, rp, cv, C->txd, C->rxd, P->all, rbytes, rbytes + 1, ovals, n_cache);
-  NB_LAUNCHED(err);
-  const int e1 = tm.mark();
   unsigned long long* best;
-  uint32_t *widx, *flag, *pos, *nw, *vals, *vals_alt, *keep, *kpos, *nk;
-  uint64_t *keys, *keys_alt;
+  uint32_t *widx, *flag, *pos, *nw;
   const uint32_t ng = C->n_groups_cap;
   NB_TRY(sc.get(&best, ng));
   NB_TRY(sc.get(&widx, ng));
   NB_TRY(sc.get(&flag, n));
   NB_TRY(sc.get(&pos, n));
   NB_TRY(sc.get(&nw, 1));
-  NB_CUDA(err, cudaMemsetAsync(best, 0xff, ng * sizeof(unsigned long long), st));
-  NB_CUDA(err, cudaMemsetAsync(widx, 0xff, ng * sizeof(uint32_t), st));
+  const size_t arena_bytes = (tn.refine_order ? radix_arena_bytes(n, 8) : 0) + scan_arena_bytes(n, true);
+  char* arena;
+  NB_TRY(sc.get(&arena, std::max<size_t>(1, arena_bytes)));
   const unsigned G2 = std::min<unsigned>(grid_for(n, 256), pgrid(256));
-  k_best_len<<<G2, 256, 0, st>>>(P->all, n, best);
-  NB_LAUNCHED(err);
-  k_best_idx<<<G2, 256, 0, st>>>(P->all, n, best, widx);
-  NB_LAUNCHED(err);
-  k_winner_flags<<<G2, 256, 0, st>>>(P->all, n, widx, flag);
-  NB_LAUNCHED(err);
-  NB_TRY(exclusive_scan(sc, flag, pos, n, nw));
+  StageTimer tm(st);
+  const int e0 = stretch_event(tm, mem, GRAPH_REFINE, 0), e1 = stretch_event(tm, mem, GRAPH_REFINE, 1),
+            e3 = stretch_event(tm, mem, GRAPH_DEDUP, 0);
+  // refinement, final visibility and the per-group winners: one stretch with no host
+  // round trip (one CUDA graph by default)
+  NB_TRY(run_stretch(mem, st, tn.graph != 0, GRAPH_REFINE, [&](cudaStream_t q) -> int {
+    Scratch ws(&mem, q);
+    ws.arena = arena;
+    ws.arena_cap = arena_bytes;
+    NB_CUDA(err, cudaMemsetAsync(rbytes, 0, 2 * sizeof(unsigned long long), q));
+    tm.record(e0, q);
+    if (tn.refine_order) {
+      k_order_keys<<<grid_for(n, 256), 256, 0, q>>>(C->nint, n, okeys, ovals);
+      NB_LAUNCHED(err);
+      NB_TRY(radix_sort(ws, okeys, ovals, okeys_alt, ovals_alt, n, 8));
+    }
+    k_refine<<<G, 128, dyn, q>>>(S->d, rp, cv, C->txd, C->rxd, P->all, rbytes, rbytes + 1, ovals, n_cache);
+    NB_LAUNCHED(err);
+    tm.record(e1, q);
+    NB_CUDA(err, cudaMemsetAsync(best, 0xff, ng * sizeof(unsigned long long), q));
+    NB_CUDA(err, cudaMemsetAsync(widx, 0xff, ng * sizeof(uint32_t), q));
+    k_best_len<<<G2, 256, 0, q>>>(P->all, n, best);
+    NB_LAUNCHED(err);
+    k_best_idx<<<G2, 256, 0, q>>>(P->all, n, best, widx);
+    NB_LAUNCHED(err);
+    k_winner_flags<<<G2, 256, 0, q>>>(P->all, n, widx, flag);
+    NB_LAUNCHED(err);
+    NB_TRY(exclusive_scan(ws, flag, pos, n, nw));
+    return NIMBUS_OK;
+  }));
   // valid paths count (for the counters)
   uint32_t hw = 0;
   unsigned long long hb = 0;
@@ -692,8 +705,10 @@ int refine_paths(Mem& mem, SceneObj* S, CoarseObj* C, const nimbus_refine_params
   NB_CUDA(err, cudaMemcpyAsync(&hb, rbytes, sizeof hb, cudaMemcpyDeviceToHost, st));
   NB_CUDA(err, cudaStreamSynchronize(st));
   const int64_t m = hw;
-  int e3 = e1;
+  bool deduped = false;
   if (m > 0) {
+    uint64_t *keys, *keys_alt;
+    uint32_t *vals, *vals_alt, *keep, *kpos, *nk;
     NB_TRY(sc.get(&keys, m));
     NB_TRY(sc.get(&keys_alt, m));
     NB_TRY(sc.get(&vals, m));
@@ -701,18 +716,29 @@ int refine_paths(Mem& mem, SceneObj* S, CoarseObj* C, const nimbus_refine_params
     NB_TRY(sc.get(&keep, m));
     NB_TRY(sc.get(&kpos, m));
     NB_TRY(sc.get(&nk, 1));
-    k_winner_keys<<<G2, 256, 0, st>>>(P->all, flag, pos, n, C->n_rx, keys, vals);
-    NB_LAUNCHED(err);
-    NB_TRY(radix_sort(sc, keys, vals, keys_alt, vals_alt, m,
-                      bits_for((uint64_t)C->n_tx * (uint64_t)std::max(1, C->n_rx))));
-    NB_CUDA(err, cudaMemsetAsync(keep, 0, m * sizeof(uint32_t), st));
-    k_fresnel<<<std::min<unsigned>(grid_for(m, 64), pgrid(64)), 64, 0, st>>>(P->all, keys, vals, m, C->txd, rp.lambda,
-                                                                              keep);
-    NB_LAUNCHED(err);
-    NB_TRY(exclusive_scan(sc, keep, kpos, m, nk));
-    k_final<<<std::min<unsigned>(grid_for(m, 256), pgrid(256)), 256, 0, st>>>(keep, kpos, vals, m, P->final_idx);
-    NB_LAUNCHED(err);
-    e3 = tm.mark();
+    const int key_bits = bits_for((uint64_t)C->n_tx * (uint64_t)std::max(1, C->n_rx));
+    const size_t arena2 = radix_arena_bytes(m, key_bits) + scan_arena_bytes(m, true);
+    char* arena_d;
+    NB_TRY(sc.get(&arena_d, std::max<size_t>(1, arena2)));
+    // label and first-Fresnel-zone dedup of the winners: a second stretch
+    NB_TRY(run_stretch(mem, st, tn.graph != 0, GRAPH_DEDUP, [&](cudaStream_t q) -> int {
+      Scratch ws(&mem, q);
+      ws.arena = arena_d;
+      ws.arena_cap = arena2;
+      k_winner_keys<<<G2, 256, 0, q>>>(P->all, flag, pos, n, C->n_rx, keys, vals);
+      NB_LAUNCHED(err);
+      NB_TRY(radix_sort(ws, keys, vals, keys_alt, vals_alt, m, key_bits));
+      NB_CUDA(err, cudaMemsetAsync(keep, 0, m * sizeof(uint32_t), q));
+      k_fresnel<<<std::min<unsigned>(grid_for(m, 64), pgrid(64)), 64, 0, q>>>(P->all, keys, vals, m, C->txd,
+                                                                                rp.lambda, keep);
+      NB_LAUNCHED(err);
+      NB_TRY(exclusive_scan(ws, keep, kpos, m, nk));
+      k_final<<<std::min<unsigned>(grid_for(m, 256), pgrid(256)), 256, 0, q>>>(keep, kpos, vals, m, P->final_idx);
+      NB_LAUNCHED(err);
+      tm.record(e3, q);
+      return NIMBUS_OK;
+    }));
+    deduped = true;
     uint32_t hk = 0;
     NB_CUDA(err, cudaMemcpyAsync(&hk, nk, sizeof hk, cudaMemcpyDeviceToHost, st));
     NB_CUDA(err, cudaStreamSynchronize(st));
@@ -721,7 +747,7 @@ int refine_paths(Mem& mem, SceneObj* S, CoarseObj* C, const nimbus_refine_params
   P->counts.n_paths = P->n_final;
   P->counts.n_refined_valid = -1;  // filled by a query with which = 1
   P->counts.ms_refine = tm.ms(e0, e1);
-  P->counts.ms_dedup = tm.ms(e1, e3);
+  P->counts.ms_dedup = deduped ? tm.ms(e1, e3) : 0.0;
   P->counts.bytes_refine = (int64_t)hb;
   P->counts.launches = C->counts.launches + (g_launches.load() - launches0);
   return NIMBUS_OK;

@@ -181,6 +181,31 @@ int exclusive_scan(Scratch& sc, const uint32_t* in, uint32_t* out, int64_t n, ui
   return NIMBUS_OK;
 }
 
+// The gets of scan_rec, level by level.
+static size_t scan_rec_arena_bytes(int64_t n) {
+  size_t b = 0;
+  while (n > 0) {
+    const int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
+    if (nb == 1) break;
+    b += 2 * Scratch::arena_block((size_t)nb, sizeof(uint32_t));
+    n = nb;
+  }
+  return b;
+}
+
+size_t scan_arena_bytes(int64_t n, bool total) {
+  if (n <= 0) return 0;
+  return (total ? Scratch::arena_block(1, sizeof(uint32_t)) : 0) + scan_rec_arena_bytes(n);
+}
+
+size_t radix_arena_bytes(int64_t n, int bits) {
+  if (n <= 1 || bits <= 0) return 0;
+  const int64_t n_tiles = (n + RS_TILE - 1) / RS_TILE;
+  const int passes = (bits + 7) / 8;
+  return 2 * Scratch::arena_block((size_t)RS_RADIX * n_tiles, sizeof(uint32_t)) +
+         (size_t)passes * scan_arena_bytes((int64_t)RS_RADIX * n_tiles, false);
+}
+
 int radix_sort(Scratch& sc, uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt, int64_t n,
                int bits) {
   if (n <= 1 || bits <= 0) return NIMBUS_OK;

@@ -882,30 +882,7 @@ int trace_coarse(Mem& mem, SceneObj* S, const double* txh, int n_tx, const doubl
   NB_TRY(sc.get(&los, std::max<int64_t>(1, (int64_t)n_tx * n_rx)));
   NB_TRY(sc.get(&overflow, 2));
   NB_TRY(sc.get(&stats, N_STATS * N_STAGES));
-  NB_CUDA(err, cudaMemsetAsync(rx_bits, 0, ((n_cells + 31) / 32) * sizeof(uint32_t), st));
-  NB_CUDA(err, cudaMemsetAsync(vis_ie, 0, std::max<int64_t>(1, (int64_t)n_tx * tr.ie_words) * 4, st));
-  NB_CUDA(err, cudaMemsetAsync(first_bits, 0, std::max<int64_t>(1, (int64_t)n_tx * tr.ie_words) * 4, st));
-  NB_CUDA(err, cudaMemsetAsync(los, 0xff, std::max<int64_t>(1, (int64_t)n_tx * n_rx) * 4, st));
-  NB_CUDA(err, cudaMemsetAsync(overflow, 0, 2 * sizeof(uint32_t), st));
-  NB_CUDA(err, cudaMemsetAsync(stats, 0, N_STATS * N_STAGES * sizeof(unsigned long long), st));
-  k_tx_setup<<<grid_for(n_tx, 64), 64, 0, st>>>(C->txd, n_tx, tx4);
-  NB_LAUNCHED(err);
-  if (n_rx > 0) {
-    k_rx_setup<<<grid_for(n_rx, 64), 64, 0, st>>>(s, C->rxd, n_rx, rx4, rx_vox, rx_keys, rx_bits);
-    NB_LAUNCHED(err);
-    NB_CUDA(err, cudaMemsetAsync(rx_vals, 0, n_rx * sizeof(uint32_t), st));
-    NB_TRY(radix_sort(sc, rx_keys, rx_vals, rx_keys_alt, rx_vals_alt, n_rx, 64));
-  }
   const int R = 8;
-  k_march_cap<<<std::min<unsigned>(grid_for(n_cells, 256), 2048u), 256, 0, st>>>(s.march, mtmp, n_cells, R + 1);
-  NB_LAUNCHED(err);
-  if (n_rx > 0) {
-    int64_t work = (int64_t)(2 * R + 1) * (2 * R + 1) * (2 * R + 1) * n_rx;
-    k_march_rx<<<std::min<unsigned>(grid_for(work, 256), 4096u), 256, 0, st>>>(s, rx_vox, n_rx, mtmp, R);
-    NB_LAUNCHED(err);
-  }
-  k_march_pack<<<std::min<unsigned>(grid_for(n_cells, 256), 2048u), 256, 0, st>>>(mtmp, march, n_cells);
-  NB_LAUNCHED(err);
   tr.tx = tx4;
   tr.rx = rx4;
   tr.march = march;
@@ -958,7 +935,6 @@ int trace_coarse(Mem& mem, SceneObj* S, const double* txh, int n_tx, const doubl
   std::memset(lv, 0, sizeof lv);
   uint32_t* cnts;
   NB_TRY(sc.get(&cnts, 2 * MAX_LEVELS));
-  NB_CUDA(err, cudaMemsetAsync(cnts, 0, 2 * MAX_LEVELS * sizeof(uint32_t), st));
   for (int d = 1; d <= max_int; ++d) {
     NodeLevel& L = lv[d];
     L.cap_r = (uint32_t)cap_nodes;
@@ -978,69 +954,114 @@ int trace_coarse(Mem& mem, SceneObj* S, const double* txh, int n_tx, const doubl
   NB_TRY(sc.get(&cb.rec, cb.cap));
   NB_TRY(sc.get(&cb.miss, cb.cap));
   cb.cnt = cnts;  // slot 0 of level 0 counts the coarse paths
-  // transmission phase
-  const unsigned PG = persistent_grid(256);
-  StageTimer tm(st);
-  DTrace tr_vis = tr, tr_pri = tr, tr_lev = tr;
-  tr_vis.stats = stats + STAGE_VIS * N_STATS;
-  tr_pri.stats = stats + STAGE_PRIMARY * N_STATS;
-  tr_lev.stats = stats + STAGE_LEVELS * N_STATS;
-  const int e0 = tm.mark();
-  k_vis_tables<<<PG, 256, 0, st>>>(s, tr_vis);
-  NB_LAUNCHED(err);
-  const int e1 = tm.mark();
-  if (p->launch_mode == 1) {
-    // the paper's launch: a ray toward every IE and RX, i.e. the visibility tables
-    NB_CUDA(err, cudaMemcpyAsync(first_bits, vis_ie, std::max<int64_t>(1, (int64_t)n_tx * tr.ie_words) * 4,
-                                 cudaMemcpyDeviceToDevice, st));
-    if ((int64_t)n_tx * n_rx > 0) {
-      k_los_from_vis<<<grid_for((int64_t)n_tx * n_rx, 128), 128, 0, st>>>(tr, los);
-      NB_LAUNCHED(err);
-    }
-  } else {
-    k_primary<<<PG, 256, 0, st>>>(s, tr_pri, first_bits, los);
-    NB_LAUNCHED(err);
-  }
-  const int e2 = tm.mark();
-  k_los<<<grid_for((int64_t)n_tx * n_rx, 128), 128, 0, st>>>(tr, los, cb);
-  NB_LAUNCHED(err);
+  const int64_t nflag = (int64_t)n_tx * n_ie;
+  uint32_t *fr = nullptr, *fd = nullptr, *pr = nullptr, *pd = nullptr, *tot = nullptr;
   if (max_int >= 1) {
-    int64_t nflag = (int64_t)n_tx * n_ie;
-    uint32_t *fr, *fd, *pr, *pd, *tot;
     NB_TRY(sc.get(&fr, std::max<int64_t>(1, nflag)));
     NB_TRY(sc.get(&fd, std::max<int64_t>(1, nflag)));
     NB_TRY(sc.get(&pr, std::max<int64_t>(1, nflag)));
     NB_TRY(sc.get(&pd, std::max<int64_t>(1, nflag)));
     NB_TRY(sc.get(&tot, 2));
-    if (nflag > 0) {
-      k_first_flags<<<PG, 256, 0, st>>>(s, tr, first_bits, fr, fd);
-      NB_LAUNCHED(err);
-    }
-    NB_TRY(exclusive_scan(sc, fr, pr, nflag, tot));
-    NB_TRY(exclusive_scan(sc, fd, pd, nflag, tot + 1));
-    if (nflag > 0) {
-      k_first_nodes<<<PG, 256, 0, st>>>(s, tr, fr, pr, fd, pd, lv[1]);
-      NB_LAUNCHED(err);
-    }
-    k_first_counts<<<1, 1, 0, st>>>(tot, tot + 1, lv[1]);
-    NB_LAUNCHED(err);
   }
-  // propagation phase, one launch per depth
   unsigned long long* task_ctr;   // cones handed out so far, one counter per level
   NB_TRY(sc.get(&task_ctr, MAX_LEVELS));
-  NB_CUDA(err, cudaMemsetAsync(task_ctr, 0, MAX_LEVELS * sizeof(unsigned long long), st));
-  const int e3 = tm.mark();
-  for (int d = 1; d <= max_int; ++d) {
-    NodeLevel next = d < max_int ? lv[d + 1] : lv[0];
-    if (d == max_int) {
-      next.cap_r = 0;
-      next.cap_d = 0;
-      next.cnt = cnts + 2 * MAX_LEVELS - 2;  // unused sink
-    }
-    k_level<<<persistent_grid(tn.level_block), tn.level_block, 0, st>>>(s, tr_lev, lv[d], next, cb, task_ctr + d);
+  // the sorts and scans of the stretch below draw from this arena
+  const size_t arena_bytes =
+      radix_arena_bytes(n_rx, 64) + (max_int >= 1 ? 2 * scan_arena_bytes(nflag, true) : 0);
+  char* arena;
+  NB_TRY(sc.get(&arena, std::max<size_t>(1, arena_bytes)));
+  const unsigned PG = persistent_grid(256);
+  const unsigned LG = persistent_grid(tn.level_block);
+  StageTimer tm(st);
+  const int e0 = stretch_event(tm, mem, GRAPH_TRACE, 0), e1 = stretch_event(tm, mem, GRAPH_TRACE, 1),
+            e2 = stretch_event(tm, mem, GRAPH_TRACE, 2), e3 = stretch_event(tm, mem, GRAPH_TRACE, 3),
+            e4 = stretch_event(tm, mem, GRAPH_TRACE, 4);
+  DTrace tr_vis = tr, tr_pri = tr, tr_lev = tr;
+  tr_vis.stats = stats + STAGE_VIS * N_STATS;
+  tr_pri.stats = stats + STAGE_PRIMARY * N_STATS;
+  tr_lev.stats = stats + STAGE_LEVELS * N_STATS;
+
+  // From the RX table to the last depth nothing returns to the host: the march field,
+  // the transmission phase and every propagation level over all TX/RX pairs form one
+  // stretch, issued as one CUDA graph by default.
+  NB_TRY(run_stretch(mem, st, tn.graph != 0, GRAPH_TRACE, [&](cudaStream_t q) -> int {
+    Scratch ws(&mem, q);
+    ws.arena = arena;
+    ws.arena_cap = arena_bytes;
+    NB_CUDA(err, cudaMemsetAsync(rx_bits, 0, ((n_cells + 31) / 32) * sizeof(uint32_t), q));
+    NB_CUDA(err, cudaMemsetAsync(vis_ie, 0, std::max<int64_t>(1, (int64_t)n_tx * tr.ie_words) * 4, q));
+    NB_CUDA(err, cudaMemsetAsync(first_bits, 0, std::max<int64_t>(1, (int64_t)n_tx * tr.ie_words) * 4, q));
+    NB_CUDA(err, cudaMemsetAsync(los, 0xff, std::max<int64_t>(1, (int64_t)n_tx * n_rx) * 4, q));
+    NB_CUDA(err, cudaMemsetAsync(overflow, 0, 2 * sizeof(uint32_t), q));
+    NB_CUDA(err, cudaMemsetAsync(stats, 0, N_STATS * N_STAGES * sizeof(unsigned long long), q));
+    NB_CUDA(err, cudaMemsetAsync(cnts, 0, 2 * MAX_LEVELS * sizeof(uint32_t), q));
+    NB_CUDA(err, cudaMemsetAsync(task_ctr, 0, MAX_LEVELS * sizeof(unsigned long long), q));
+    k_tx_setup<<<grid_for(n_tx, 64), 64, 0, q>>>(C->txd, n_tx, tx4);
     NB_LAUNCHED(err);
-  }
-  const int e4 = tm.mark();
+    if (n_rx > 0) {
+      k_rx_setup<<<grid_for(n_rx, 64), 64, 0, q>>>(s, C->rxd, n_rx, rx4, rx_vox, rx_keys, rx_bits);
+      NB_LAUNCHED(err);
+      NB_CUDA(err, cudaMemsetAsync(rx_vals, 0, n_rx * sizeof(uint32_t), q));
+      NB_TRY(radix_sort(ws, rx_keys, rx_vals, rx_keys_alt, rx_vals_alt, n_rx, 64));
+    }
+    k_march_cap<<<std::min<unsigned>(grid_for(n_cells, 256), 2048u), 256, 0, q>>>(s.march, mtmp, n_cells, R + 1);
+    NB_LAUNCHED(err);
+    if (n_rx > 0) {
+      int64_t work = (int64_t)(2 * R + 1) * (2 * R + 1) * (2 * R + 1) * n_rx;
+      k_march_rx<<<std::min<unsigned>(grid_for(work, 256), 4096u), 256, 0, q>>>(s, rx_vox, n_rx, mtmp, R);
+      NB_LAUNCHED(err);
+    }
+    k_march_pack<<<std::min<unsigned>(grid_for(n_cells, 256), 2048u), 256, 0, q>>>(mtmp, march, n_cells);
+    NB_LAUNCHED(err);
+    // transmission phase
+    tm.record(e0, q);
+    k_vis_tables<<<PG, 256, 0, q>>>(s, tr_vis);
+    NB_LAUNCHED(err);
+    tm.record(e1, q);
+    if (p->launch_mode == 1) {
+      // the paper's launch: a ray toward every IE and RX, i.e. the visibility tables
+      NB_CUDA(err, cudaMemcpyAsync(first_bits, vis_ie, std::max<int64_t>(1, (int64_t)n_tx * tr.ie_words) * 4,
+                                   cudaMemcpyDeviceToDevice, q));
+      if ((int64_t)n_tx * n_rx > 0) {
+        k_los_from_vis<<<grid_for((int64_t)n_tx * n_rx, 128), 128, 0, q>>>(tr, los);
+        NB_LAUNCHED(err);
+      }
+    } else {
+      k_primary<<<PG, 256, 0, q>>>(s, tr_pri, first_bits, los);
+      NB_LAUNCHED(err);
+    }
+    tm.record(e2, q);
+    k_los<<<grid_for((int64_t)n_tx * n_rx, 128), 128, 0, q>>>(tr, los, cb);
+    NB_LAUNCHED(err);
+    if (max_int >= 1) {
+      if (nflag > 0) {
+        k_first_flags<<<PG, 256, 0, q>>>(s, tr, first_bits, fr, fd);
+        NB_LAUNCHED(err);
+      }
+      NB_TRY(exclusive_scan(ws, fr, pr, nflag, tot));
+      NB_TRY(exclusive_scan(ws, fd, pd, nflag, tot + 1));
+      if (nflag > 0) {
+        k_first_nodes<<<PG, 256, 0, q>>>(s, tr, fr, pr, fd, pd, lv[1]);
+        NB_LAUNCHED(err);
+      }
+      k_first_counts<<<1, 1, 0, q>>>(tot, tot + 1, lv[1]);
+      NB_LAUNCHED(err);
+    }
+    // propagation phase, one launch per depth
+    tm.record(e3, q);
+    for (int d = 1; d <= max_int; ++d) {
+      NodeLevel next = d < max_int ? lv[d + 1] : lv[0];
+      if (d == max_int) {
+        next.cap_r = 0;
+        next.cap_d = 0;
+        next.cnt = cnts + 2 * MAX_LEVELS - 2;  // unused sink
+      }
+      k_level<<<LG, tn.level_block, 0, q>>>(s, tr_lev, lv[d], next, cb, task_ctr + d);
+      NB_LAUNCHED(err);
+    }
+    tm.record(e4, q);
+    return NIMBUS_OK;
+  }));
   // read the sizes back
   uint32_t hc[2 * MAX_LEVELS], hov[2];
   unsigned long long hs[N_STATS * N_STAGES];

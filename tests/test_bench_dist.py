@@ -52,3 +52,15 @@ def test_two_ranks_reduce_and_draw_their_own_pairs():
     assert not np.allclose(tx0, tx1)
     for p in np.vstack([tx0, tx1, rx0, rx1]):
         assert 0.3 <= p[0] <= 9.7 and 0.3 <= p[1] <= 9.7 and 0.3 <= p[2] <= 2.7
+
+
+def test_traffic_gate_hashes_device_code_only():
+    """The stored refine traffic is tied to a hash of the kernel's device code: the
+    hash finds the end of that code, and a change to the host launcher after it leaves
+    the hash unchanged."""
+    h = bench.kernel_sources_sha256()
+    assert len(h) == 64 and int(h, 16) >= 0
+    path, end = bench.KERNEL_SOURCES[0]
+    text = open(os.path.join(bench.ROOT, path), "rb").read()
+    assert text.count(end) == 1
+    assert b"__global__" not in text[text.index(end):]

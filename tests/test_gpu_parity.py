@@ -246,6 +246,64 @@ def test_autotune_keeps_results(ctx):
         ctx.set_tuning(level_block=96)
 
 
+def _coarse_rows(cq):
+    miss = np.asarray(cq["miss"], np.float32).view(np.uint32)
+    return sorted(zip(cq["tx"].tolist(), cq["rx"].tolist(), cq["n"].tolist(), map(tuple, cq["ie"].tolist()),
+                      map(tuple, cq["type"].tolist()), map(tuple, cq["label"].tolist()), miss.tolist()))
+
+
+def test_graph_launch_keeps_results(ctx):
+    """Issuing each host-free stretch as one CUDA graph changes nothing but how the
+    launches reach the GPU: the same coarse set and exact paths bit for bit, the same
+    kernel count, and the stage times still come from events recorded inside the
+    graphs.  Covers both launch modes and a request-batched trace (per-RX owner and
+    depth)."""
+    full = scenes.room_noisy()
+    sc = full.with_pairs(full.tx[:2], full.rx[:3])
+    s = None
+    try:
+        for mode in (0, 1):
+            p = config.params_for(sc, max_refl=2, max_diff=1, launch_mode=mode)
+            if s is None:
+                s = ctx.voxelize_scene(sc, p)
+            owner = np.array([0, 1, -1], np.int32)
+            depth = np.array([1, 3, 2], np.int32)
+            res = {}
+            for graph in (0, 1):
+                ctx.set_tuning(graph=graph)
+                for batched in (False, True):
+                    kw = dict(rx_owner=owner, rx_max_int=depth) if batched else {}
+                    co = ctx.trace(s, sc.tx, sc.rx, p, **kw)
+                    cq = ctx.query_coarse(co)
+                    cc = ctx.coarse_counts(co)
+                    P = ctx.refine(s, co, p)
+                    out = ctx.query(P, 0)
+                    pc = ctx.counts(P)
+                    ctx.release(P)
+                    ctx.release(co)
+                    res[graph, batched] = (cq, out, cc, pc)
+            for batched in (False, True):
+                (cq0, o0, cc0, pc0), (cq1, o1, cc1, pc1) = res[0, batched], res[1, batched]
+                assert len(o0["n"]) > 0
+                # the coarse records come out in group order, whose ids follow the
+                # device's atomics: compare them as a set of rows
+                assert _coarse_rows(cq1) == _coarse_rows(cq0)
+                for k in ("tx", "rx", "n", "type", "label", "pts", "length"):
+                    np.testing.assert_array_equal(o1[k], o0[k], err_msg=k)
+                for k in ("n_cones", "n_vis", "n_nodes", "n_coarse", "n_coarse_raw", "launches"):
+                    assert cc1[k] == cc0[k], k
+                assert pc1["launches"] == pc0["launches"]
+                assert cc1["ms_levels"] > 0 and cc1["ms_vis"] > 0
+                assert cc1["ms_primary"] > 0 or mode == 1
+                assert pc1["ms_refine"] > 0 and pc1["ms_dedup"] > 0
+    finally:
+        ctx.set_tuning(graph=1)
+        if s is not None:
+            ctx.release(s)
+    with pytest.raises(Exception):
+        ctx.set_tuning(graph=2)
+
+
 def test_scene_checkpoint_round_trip(ctx, tmp_path):
     """A saved scene -- including a region update -- loads into another context with
     the same tables and gives the same coarse and exact paths; damaged files fail."""

@@ -447,6 +447,25 @@ def wedge(spacing: float = 0.05, z_tx: float = 0.5, z_rx: float = 2.5) -> Scene:
                  region=np.array([[-4.0, -4.0, 0.0], [1.5, 1.5, 3.0]]))
 
 
+def wedge_on_floor(z_tx: float = 0.8, z_rx: float = 2.0, spacing: float = 0.05) -> Scene:
+    """The convex corner of ``wedge`` standing on a sampled floor (z = 0, label 3).
+
+    The floor covers x in [-4, 2], y in [-4, 2] outside the solid (x <= 0, y <= 0).
+    Besides the pure diffraction, TX and RX are joined by a floor reflection followed
+    by the edge diffraction.  Unfolding the floor puts the TX at (1, -3, -z_tx); its
+    Keller point on the edge is at z = (z_rx - z_tx) / 2 (both ends sqrt(10) m from
+    the edge), and the floor point is where that unfolded segment meets z = 0.
+    """
+    w = wedge(spacing=spacing, z_tx=z_tx, z_rx=z_rx)
+    X, Y, _ = np.eye(3)
+    floor = [plane_patch([0, -4, 0], X, Y, 2.0, 6.0, spacing, [0, 0, 1], 3),
+             plane_patch([-4, 0, 0], X, Y, 4.0 - spacing, 2.0, spacing, [0, 0, 1], 3)]
+    fx, fn, fl, fm = merge_clouds(floor)
+    return Scene("wedge_on_floor", np.vstack([w.xyz, fx]), np.vstack([w.nrm, fn]), np.concatenate([w.label, fl]),
+                 np.concatenate([w.material, fm]), w.edges, w.edge_label, tx=w.tx, rx=w.rx, max_refl=1,
+                 max_diff=1, meta={"spacing": spacing}, region=np.array([[-4.0, -4.0, 0.0], [2.0, 2.0, 3.0]]))
+
+
 def moving_box(room: Scene, step: int, seed: int = 4, size: float = 2.0, spacing: float = 0.05):
     """A 2x2x2 m box on a seeded random walk in the 10x10 m room (dynamic scenes).
 

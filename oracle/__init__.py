@@ -15,7 +15,8 @@ Parity pins (tests/test_oracle_pins.py):
 - a brute-force chessboard distance for the march field;
 - the exact-plane SDF and the continuity of a label's surface;
 - a Monte-Carlo cone-sphere test and the Fibonacci lattice properties;
-- integer re-derivation of the voxel keys, and the reflection law at refined points.
+- integer re-derivation of the voxel keys, and the reflection law at refined points;
+- the first Fresnel zone radius of the duplicate removal, just inside and just outside.
 
 The coarse-path set and the kappa choice on noisy scenes have no closed form: parity
 unpinned beyond those invariants.
@@ -127,6 +128,8 @@ def lib():
         L.oracle_onb.argtypes = [vp, vp, vp]
         L.oracle_dda_cells.restype = i64
         L.oracle_dda_cells.argtypes = [vp, vp, vp, vp, i64]
+        L.oracle_fresnel_dedup.restype = i64
+        L.oracle_fresnel_dedup.argtypes = [i64] + [vp] * 8 + [i32, d, vp]
         _lib = L
     return _lib
 
@@ -304,6 +307,19 @@ def onb(n):
     v = np.zeros(3)
     lib().oracle_onb(_p(_c(n, np.float64)), _p(u), _p(v))
     return u, v
+
+
+def fresnel_dedup(paths: dict, tx_pos, lam: float) -> np.ndarray:
+    """First-Fresnel-zone duplicate removal alone (Section 2.3) on given exact paths
+    (tx, rx, n, type, label, pts, length as returned by paths()); 1 = kept."""
+    m = len(paths["n"])
+    arrs = [_c(paths["tx"], np.int32), _c(paths["rx"], np.int32), _c(paths["n"], np.int32),
+            _c(paths["type"], np.int32).reshape(m, MAXI), _c(paths["label"], np.uint32).reshape(m, MAXI),
+            _c(paths["pts"], np.float64).reshape(m, MAXI, 3), _c(paths["length"], np.float64)]
+    txp = _c(tx_pos, np.float64).reshape(-1, 3)
+    keep = np.zeros(m, np.int32)
+    lib().oracle_fresnel_dedup(m, *[_p(a) for a in arrs], _p(txp), int(txp.shape[0]), float(lam), _p(keep))
+    return keep
 
 
 def run(scene, params):

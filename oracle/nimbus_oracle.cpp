@@ -1211,6 +1211,49 @@ bool ie_less(const Exact& a, const Exact& b) {
   return a.n < b.n;
 }
 
+// First-Fresnel-zone duplicate removal (Section 2.3) over paths already reduced to one
+// per label sequence: sort by delay; a path is dropped if an earlier kept path has the
+// same chain of interaction types and each of its interaction points lies within that
+// path's first Fresnel zone radius r_k = sqrt(lambda a_k b_k / (a_k + b_k)), a_k and b_k
+// the kept path's lengths from the TX to I_k and from I_k to the RX.  Reading for ties:
+// delays are compared in bins of 1 um of length, so paths of equal length up to
+// rounding are ordered by their interaction types and labels.
+std::vector<Exact> fresnel_dedup(std::vector<Exact> best, const std::vector<V3>& tx, double lambda) {
+  std::sort(best.begin(), best.end(), [](const Exact& a, const Exact& b) {
+    if (a.tx != b.tx) return a.tx < b.tx;
+    if (a.rx != b.rx) return a.rx < b.rx;
+    long long qa = (long long)std::floor(a.length * 1e6), qb = (long long)std::floor(b.length * 1e6);
+    if (qa != qb) return qa < qb;
+    if (seq_less(a, b)) return true;
+    if (seq_less(b, a)) return false;
+    return ie_less(a, b);
+  });
+  std::vector<Exact> kept;
+  for (size_t i = 0; i < best.size(); ++i) {
+    const Exact& B = best[i];
+    bool dup = false;
+    for (const Exact& A : kept) {
+      if (A.tx != B.tx || A.rx != B.rx || A.n != B.n || A.n == 0) continue;
+      bool same_chain = true;
+      for (int q = 0; q < A.n; ++q) same_chain = same_chain && A.type[q] == B.type[q];
+      if (!same_chain) continue;
+      V3 prev = tx[A.tx];
+      double acc = 0.0;
+      bool inside = true;
+      for (int q = 0; q < A.n && inside; ++q) {
+        acc += norm(A.pts[q] - prev);
+        prev = A.pts[q];
+        double ak = acc, bk = A.length - acc;
+        double r = std::sqrt(lambda * ak * bk / (ak + bk));
+        inside = norm(B.pts[q] - A.pts[q]) <= r;
+      }
+      if (inside) { dup = true; break; }
+    }
+    if (!dup) kept.push_back(B);
+  }
+  return kept;
+}
+
 ExactSet* refine(const Scene& s, const CoarseSet& cs) {
   ExactSet* out = new ExactSet();
   for (size_t i = 0; i < cs.paths.size(); ++i) {
@@ -1238,44 +1281,7 @@ ExactSet* refine(const Scene& s, const CoarseSet& cs) {
       continue;
     best.push_back(valid[i]);
   }
-  // First-Fresnel-zone duplicate removal: sort by delay; a path is dropped if an
-  // earlier kept path has the same chain of interaction types and each of its
-  // interaction points lies within that path's first Fresnel zone radius
-  // r_k = sqrt(lambda a_k b_k / (a_k + b_k)).  Reading for ties: delays are
-  // compared in bins of 1 um of length, so paths of equal length up to rounding
-  // are ordered by their interaction types and labels.
-  std::sort(best.begin(), best.end(), [](const Exact& a, const Exact& b) {
-    if (a.tx != b.tx) return a.tx < b.tx;
-    if (a.rx != b.rx) return a.rx < b.rx;
-    long long qa = (long long)std::floor(a.length * 1e6), qb = (long long)std::floor(b.length * 1e6);
-    if (qa != qb) return qa < qb;
-    if (seq_less(a, b)) return true;
-    if (seq_less(b, a)) return false;
-    return ie_less(a, b);
-  });
-  const double lambda = C_LIGHT / s.p.freq_hz;
-  for (size_t i = 0; i < best.size(); ++i) {
-    const Exact& B = best[i];
-    bool dup = false;
-    for (const Exact& A : out->paths) {
-      if (A.tx != B.tx || A.rx != B.rx || A.n != B.n || A.n == 0) continue;
-      bool same_chain = true;
-      for (int q = 0; q < A.n; ++q) same_chain = same_chain && A.type[q] == B.type[q];
-      if (!same_chain) continue;
-      V3 prev = cs.tx[A.tx];
-      double acc = 0.0;
-      bool inside = true;
-      for (int q = 0; q < A.n && inside; ++q) {
-        acc += norm(A.pts[q] - prev);
-        prev = A.pts[q];
-        double ak = acc, bk = A.length - acc;
-        double r = std::sqrt(lambda * ak * bk / (ak + bk));
-        inside = norm(B.pts[q] - A.pts[q]) <= r;
-      }
-      if (inside) { dup = true; break; }
-    }
-    if (!dup) out->paths.push_back(B);
-  }
+  out->paths = fresnel_dedup(std::move(best), cs.tx, C_LIGHT / s.p.freq_hz);
   return out;
 }
 
@@ -1291,6 +1297,37 @@ void* oracle_voxelize(const float* xyz, const float* nrm, const uint32_t* label,
 }
 
 void oracle_scene_free(void* s) { delete (Scene*)s; }
+
+// First-Fresnel-zone duplicate removal alone: m exact paths as arrays -- tx, rx, n,
+// type[m][8], label[m][8], pts[m][8][3], length[m] -- with the TX positions
+// tx_pos[n_tx][3] and the wavelength.  keep[m] receives 1 for each kept path.  Returns
+// the number kept.
+int64_t oracle_fresnel_dedup(int64_t m, const int32_t* tx, const int32_t* rx, const int32_t* n, const int32_t* type,
+                             const uint32_t* label, const double* pts, const double* length, const double* tx_pos,
+                             int32_t n_tx, double lambda, int32_t* keep) {
+  std::vector<V3> txs;
+  for (int t = 0; t < n_tx; ++t) txs.push_back(mk(tx_pos[3 * t], tx_pos[3 * t + 1], tx_pos[3 * t + 2]));
+  std::vector<Exact> best;
+  for (int64_t i = 0; i < m; ++i) {
+    Exact e{};
+    e.tx = tx[i];
+    e.rx = rx[i];
+    e.n = n[i];
+    for (int q = 0; q < MAXI; ++q) {
+      e.type[q] = type[i * MAXI + q];
+      e.label[q] = label[i * MAXI + q];
+      e.ie[q] = 0;
+      e.pts[q] = mk(pts[(i * MAXI + q) * 3], pts[(i * MAXI + q) * 3 + 1], pts[(i * MAXI + q) * 3 + 2]);
+    }
+    e.length = length[i];
+    e.coarse = i;
+    best.push_back(e);
+  }
+  std::vector<Exact> kept = fresnel_dedup(std::move(best), txs, lambda);
+  for (int64_t i = 0; i < m; ++i) keep[i] = 0;
+  for (const Exact& e : kept) keep[e.coarse] = 1;
+  return (int64_t)kept.size();
+}
 
 // Grid and table sizes: origin[3], dims[3]; returns the number of IEs.
 int64_t oracle_scene_info(void* sp, double* origin, int32_t* dims, int64_t* n_points_grouped) {

@@ -332,6 +332,53 @@ def test_fresnel_removes_label_split_duplicates():
     assert pts_sorted == sorted(round(v[1], 6) for v in ref.values())
 
 
+def _paths(tx, rx, chains, types):
+    """Exact-path arrays for given interaction points (one list per path)."""
+    m = len(chains)
+    out = dict(tx=np.zeros(m, np.int32), rx=np.zeros(m, np.int32), n=np.zeros(m, np.int32),
+               type=np.zeros((m, oracle.MAXI), np.int32), label=np.zeros((m, oracle.MAXI), np.uint32),
+               pts=np.zeros((m, oracle.MAXI, 3)), length=np.zeros(m))
+    for i, (pts, t) in enumerate(zip(chains, types)):
+        nodes = [tx] + list(pts) + [rx]
+        out["n"][i] = len(pts)
+        out["type"][i][:len(pts)] = t
+        out["label"][i][:len(pts)] = np.arange(len(pts)) + 10 * i   # distinct label sequences
+        out["pts"][i][:len(pts)] = pts
+        out["length"][i] = sum(np.linalg.norm(np.subtract(b, a)) for a, b in zip(nodes[:-1], nodes[1:]))
+    return out
+
+
+def test_fresnel_zone_radius():
+    """Section 2.3: a later path duplicates a kept one of the same interaction types when
+    each of its points lies within the kept path's first Fresnel zone radius
+    r_k = sqrt(lambda a_k b_k / (a_k + b_k)), a_k the kept path's length from the TX to
+    its k-th point and b_k the rest.  Points at 0.99 r are removed, at 1.01 r kept."""
+    lam = 299792458.0 / 60e9
+    tx, rx = np.array([0.0, 0.0, 1.0]), np.array([10.0, 0.0, 1.0])
+    y = np.array([0.0, 1.0, 0.0])
+    # one reflection: a = b = sqrt(26)
+    A1 = [np.array([5.0, 0.0, 0.0])]
+    r = math.sqrt(lam * math.sqrt(26.0) / 2.0)
+    chains = [A1, [A1[0] + 0.99 * r * y], [A1[0] - 1.01 * r * y], [A1[0] + 0.5 * r * y]]
+    keep = oracle.fresnel_dedup(_paths(tx, rx, chains, [[0], [0], [0], [1]]), tx[None], lam)
+    assert keep.tolist() == [1, 0, 1, 1]          # the diffraction at the same place is another chain
+    # two interactions, asymmetric: a_k accumulates along the kept path
+    P1, P2 = np.array([3.0, 0.0, 0.0]), np.array([7.0, 0.0, 3.0])
+    a1 = np.linalg.norm(P1 - tx)
+    a2 = a1 + np.linalg.norm(P2 - P1)
+    L = a2 + np.linalg.norm(rx - P2)
+    r1, r2 = (math.sqrt(lam * a * (L - a) / L) for a in (a1, a2))
+    chains = [[P1, P2],
+              [P1 + 0.99 * r1 * y, P2 + 0.99 * r2 * y],
+              [P1 + 0.99 * r1 * y, P2 + 1.01 * r2 * y],
+              [P1 - 1.01 * r1 * y, P2]]
+    keep = oracle.fresnel_dedup(_paths(tx, rx, chains, [[0, 0]] * 4), tx[None], lam)
+    assert keep.tolist() == [1, 0, 1, 1]
+    # the shorter of two duplicates is the one kept, whatever the input order
+    keep = oracle.fresnel_dedup(_paths(tx, rx, [[P1 + 0.5 * r1 * y, P2], [P1, P2]], [[0, 0]] * 2), tx[None], lam)
+    assert keep.tolist() == [0, 1]
+
+
 def test_kappa_keeps_nearest_axis(tiny_run):
     """kappa = 1 keeps, per (TX, RX, label sequence), the coarse path with the smallest miss."""
     sc, p, s, c, e = tiny_run

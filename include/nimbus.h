@@ -282,6 +282,73 @@ NIMBUS_API int nimbus_scene_save(nimbus_ctx* ctx, nimbus_handle scene, const cha
 NIMBUS_API int nimbus_scene_load(nimbus_ctx* ctx, const char* path, nimbus_handle* scene_out, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Automatic labels and exterior edges for an unlabelled cloud.
+ *
+ * The method takes a labelled cloud whose labels are the clusters of a segmentation
+ * into distinct surfaces, and diffraction edges inserted by hand (Section 2; the
+ * experiments of Section 3 labelled with a plane-fitting algorithm from PCL, and raw
+ * sensor clouds are left to future work).  nimbus_segment produces both from positions
+ * and normals alone, by this reading:
+ *  1. the points are binned into subvoxels exactly as nimbus_voxelize bins them
+ *     (Section 2.1); the points of one subvoxel, in input order, form a group;
+ *  2. each group gets an FP64 centroid, covariance and plane normal (the eigenvector of
+ *     the smallest eigenvalue, turned to agree with the sum of the input normals); it is
+ *     planar when it has >= min_points points, a positive trace, smallest eigenvalue
+ *     <= flat_max * trace and middle eigenvalue >= spread_min * trace;
+ *  3. planar groups in 26-adjacent subvoxels are joined when their normals agree
+ *     (n_a . n_b >= cos join_angle) and each centroid is within join_dist of the other's
+ *     plane; connected groups form one surface, a non-planar group a surface of its
+ *     own; surfaces are numbered in the order of their first group in (voxel, subvoxel)
+ *     order;
+ *  4. a point takes its group's surface when that group is planar, agrees with the
+ *     point's normal (>= cos join_angle) and has the point within join_dist of its
+ *     plane; otherwise the surface of the nearest such planar neighbour group (ties: the
+ *     lower group); otherwise its group's surface;
+ *  5. two surfaces with >= edge_min_groups planar groups each, meeting in 26-adjacent
+ *     subvoxels, form an exterior edge when their planes (pooled FP64 moments of their
+ *     planar groups) are >= edge_angle apart and each centroid lies behind the other's
+ *     plane.  The edge lies on the planes' intersection line, at its point nearest the
+ *     mean centroid of the meeting groups, spans those centroids' projections, and
+ *     carries the two planes' normals as face normals.  Edges are ordered by their
+ *     surface pair; edge e has label n_surfaces + e.
+ * The outputs feed nimbus_voxelize directly (labels as the cloud's labels, edges as
+ * nimbus_edges). */
+typedef struct {
+  double voxel_size;        /* the voxelisation grid (Table 1: 0.5) */
+  double flat_max;          /* planarity: smallest covariance eigenvalue <= flat_max * trace (0.02) */
+  double spread_min;        /* ... and middle eigenvalue >= spread_min * trace (0.05): not a row of points */
+  double join_angle;        /* radians: largest angle between the normals of joined groups (10 deg) */
+  double join_dist;         /* metres: largest centroid-to-plane offset of joined groups and fitted points (0.03) */
+  double edge_angle;        /* radians: smallest angle between the planes of an exterior edge (30 deg) */
+  int32_t dv;               /* voxel division factor D_v (Table 1: 2), 1..4 */
+  int32_t min_points;       /* fewest points of a planar group (3), >= 3 */
+  int32_t edge_min_groups;  /* fewest planar groups of each surface of an edge (4), >= 1 */
+  int32_t pad_;
+} nimbus_segment_params;
+
+typedef struct {
+  int64_t n_groups;         /* occupied subvoxels */
+  int64_t n_planar;         /* planar groups */
+  int64_t n_surfaces;       /* surfaces: point labels are < n_surfaces (a non-planar group whose points
+                               all went to neighbours keeps an empty label) */
+  int64_t n_edges;          /* exterior edges found (labels n_surfaces .. n_surfaces + n_edges - 1) */
+  double ms;                /* device time of steps 2-5 */
+  double ms_total;          /* device time of the call, including the binning voxelisation */
+} nimbus_segment_counts;
+
+/* Labels and exterior edges of an unlabelled cloud (cloud->label and ->material are
+ * ignored).  labels: [cloud->n] out; edges: [edges_cap * 12] out as p0 p1 n_face0
+ * n_face1; edge_labels: [edges_cap] out; any of them host or device memory, owned by
+ * the caller (edges and edge_labels may be NULL when edges_cap is 0).  counts is always
+ * filled on success and on NIMBUS_ERR_OVERFLOW, which means more than edges_cap edges
+ * exist: the first edges_cap are written and counts->n_edges says how many to allow.
+ * An empty cloud or out-of-range parameter is NIMBUS_ERR_ARG; a union-find step bound
+ * reached (not expected) is NIMBUS_ERR_TIMEOUT.  Synchronises `stream`. */
+NIMBUS_API int nimbus_segment(nimbus_ctx* ctx, const nimbus_cloud* cloud, const nimbus_segment_params* params,
+                              uint32_t* labels, double* edges, uint32_t* edge_labels, int64_t edges_cap,
+                              nimbus_segment_counts* counts, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Launch configuration and autotuner.
  *
  * Not part of the paper's method: how the kernels are laid out on the GPU, never what

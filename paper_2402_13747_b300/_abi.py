@@ -27,7 +27,7 @@ EXPORTS = ("nimbus_create", "nimbus_destroy", "nimbus_last_error", "nimbus_voxel
            "nimbus_trace_coarse", "nimbus_refine", "nimbus_query", "nimbus_query_coarse", "nimbus_scene_info",
            "nimbus_scene_tables", "nimbus_release", "nimbus_memory_used", "nimbus_kernel_launches",
            "nimbus_voxelize_static", "nimbus_get_tuning", "nimbus_set_tuning", "nimbus_autotune",
-           "nimbus_scene_save", "nimbus_scene_load")
+           "nimbus_scene_save", "nimbus_scene_load", "nimbus_segment")
 
 _vp = C.c_void_p
 
@@ -104,6 +104,28 @@ class StaticInfo(C.Structure):
                 ("n_cells", C.c_int64)]
 
 
+class SegmentParamsC(C.Structure):
+    _fields_ = [("voxel_size", C.c_double), ("flat_max", C.c_double), ("spread_min", C.c_double),
+                ("join_angle", C.c_double), ("join_dist", C.c_double), ("edge_angle", C.c_double),
+                ("dv", C.c_int32), ("min_points", C.c_int32), ("edge_min_groups", C.c_int32), ("pad_", C.c_int32)]
+
+
+class SegmentCounts(C.Structure):
+    _fields_ = [("n_groups", C.c_int64), ("n_planar", C.c_int64), ("n_surfaces", C.c_int64), ("n_edges", C.c_int64),
+                ("ms", C.c_double), ("ms_total", C.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def segment_params(sp) -> SegmentParamsC:
+    """config.SegmentParams -> the C parameter block (angles in radians)."""
+    import math
+    return SegmentParamsC(float(sp.voxel_size), float(sp.flat_max), float(sp.spread_min),
+                          math.radians(sp.join_angle_deg), float(sp.join_dist), math.radians(sp.edge_angle_deg),
+                          int(sp.dv), int(sp.min_points), int(sp.edge_min_groups), 0)
+
+
 STATIC_MAX_POINTS = 1 << 17
 STATIC_MAX_CELLS = 1 << 20
 
@@ -153,6 +175,7 @@ def load():
     L.nimbus_voxelize_static.argtypes = [ctxp, P(Cloud), P(VoxParams), P(StaticTables), P(StaticInfo), _vp]
     L.nimbus_scene_save.argtypes = [ctxp, C.c_uint64, C.c_char_p, _vp]
     L.nimbus_scene_load.argtypes = [ctxp, C.c_char_p, P(C.c_uint64), _vp]
+    L.nimbus_segment.argtypes = [ctxp, P(Cloud), P(SegmentParamsC), _vp, _vp, _vp, C.c_int64, P(SegmentCounts), _vp]
     L.nimbus_get_tuning.argtypes = [ctxp, P(Tuning)]
     L.nimbus_set_tuning.argtypes = [ctxp, P(Tuning)]
     L.nimbus_autotune.argtypes = [ctxp, C.c_uint64, _vp, C.c_int32, _vp, C.c_int32, P(TraceParams), P(RefineParams),
@@ -284,6 +307,32 @@ class Context:
         self._check(self.L.nimbus_voxelize(self.h, C.byref(cl), C.byref(ed) if ed else None, C.byref(vp),
                                            C.byref(out), _stream(stream)), "voxelize")
         return out.value
+
+    def segment(self, xyz, nrm, sp=None, edges_cap: int = 1024, stream=None) -> dict:
+        """Automatic labels and exterior edges of an unlabelled cloud (nimbus_segment).
+
+        Returns labels [n] (uint32), edges [m, 12], edge_labels [m] and counts; a larger
+        edge buffer is taken once when more than edges_cap edges exist."""
+        from .config import SegmentParams
+        sp = sp or SegmentParams()
+        x, nr = _host(xyz, np.float32), _host(nrm, np.float32)
+        n = int(x.shape[0])
+        cl = Cloud(_ptr(x), _ptr(nr), None, None, n)
+        prm = segment_params(sp)
+        for _ in range(2):
+            labels = np.zeros(n, np.uint32)
+            edges = np.zeros((max(edges_cap, 1), 12))
+            elab = np.zeros(max(edges_cap, 1), np.uint32)
+            cnt = SegmentCounts()
+            rc = self.L.nimbus_segment(self.h, C.byref(cl), C.byref(prm), _ptr(labels), _ptr(edges), _ptr(elab),
+                                       int(edges_cap), C.byref(cnt), _stream(stream))
+            if rc == ERR_OVERFLOW and cnt.n_edges > edges_cap:
+                edges_cap = int(cnt.n_edges)
+                continue
+            self._check(rc, "segment")
+            m = int(cnt.n_edges)
+            return dict(labels=labels, edges=edges[:m].copy(), edge_labels=elab[:m].copy(), counts=cnt.as_dict())
+        self._check(rc, "segment")
 
     def voxelize_scene(self, sc, params: Params = None, stream=None) -> int:
         return self.voxelize(sc.xyz, sc.nrm, sc.label, sc.material, sc.edges, sc.edge_label, params,

@@ -12,7 +12,7 @@ from __future__ import annotations
 from dataclasses import dataclass, asdict, replace
 import math
 
-__all__ = ["Params", "params_for", "NONE_LABEL"]
+__all__ = ["Params", "SegmentParams", "params_for", "NONE_LABEL"]
 
 NONE_LABEL = 0xFFFFFFFF
 
@@ -68,6 +68,32 @@ class Params:
 
     def as_dict(self) -> dict:
         return asdict(self)
+
+
+@dataclass(frozen=True)
+class SegmentParams:
+    """Automatic labels and exterior edges for unlabelled clouds.
+
+    The paper takes its labels from a plane-fitting segmentation and places its
+    diffraction edges by hand.  These are the values of the reading used here,
+    shared by the CUDA path and the oracle.
+    """
+    voxel_size: float = 0.5          # the voxel grid of the voxelisation
+    dv: int = 2
+    min_points: int = 3              # fewest points of a subvoxel that can be planar
+    flat_max: float = 0.02           # planar: smallest covariance eigenvalue <= flat_max * trace ...
+    spread_min: float = 0.05         # ... and the middle one >= spread_min * trace (not a line of points)
+    join_angle_deg: float = 10.0     # neighbouring planes joined when their normals agree this well ...
+    join_dist: float = 0.03          # ... and each centroid is this close to the other's plane [m]
+    edge_angle_deg: float = 30.0     # exterior edge between surfaces at least this far apart ...
+    edge_min_groups: int = 4         # ... each with at least this many planar subvoxels
+
+    @property
+    def h_s(self) -> float:
+        return self.voxel_size / self.dv
+
+    def replace(self, **kw) -> "SegmentParams":
+        return replace(self, **kw)
 
 
 def params_for(scene, **overrides) -> Params:

@@ -1,6 +1,7 @@
 // C ABI of the library (include/nimbus.h): contexts, handles, the device-memory
 // budget, argument checks and the copy-out of results.
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -195,6 +196,59 @@ int nimbus_update_region(nimbus_ctx* ctx, nimbus_handle scene, const double aabb
   cudaStream_t st = (cudaStream_t)stream;
   ctx->obj_stream[scene] = st;
   return nb::update_scene_region(ctx->mem, S, aabb_min, aabb_max, replacement, st);
+}
+
+int nimbus_segment(nimbus_ctx* ctx, const nimbus_cloud* cloud, const nimbus_segment_params* params,
+                   uint32_t* labels, double* edges, uint32_t* edge_labels, int64_t edges_cap,
+                   nimbus_segment_counts* counts, void* stream) {
+  if (!ctx) return NIMBUS_ERR_ARG;
+  if (!cloud || !params || !counts || cloud->n < 1 || !cloud->xyz || !cloud->nrm || !labels || edges_cap < 0 ||
+      (edges_cap > 0 && (!edges || !edge_labels))) {
+    ctx->err = "segment: null argument or empty cloud";
+    return NIMBUS_ERR_ARG;
+  }
+  const nimbus_segment_params& p = *params;
+  if (!(p.voxel_size > 0) || p.dv < 1 || p.dv > 4 || p.min_points < 3 || !(p.flat_max >= 0) ||
+      !(p.spread_min >= 0) || !(p.join_angle >= 0 && p.join_angle <= 3.1416) || !(p.join_dist >= 0) ||
+      !(p.edge_angle >= 0 && p.edge_angle <= 3.1416) || p.edge_min_groups < 1) {
+    ctx->err = "segment: parameter out of range";
+    return NIMBUS_ERR_ARG;
+  }
+  DeviceGuard g(ctx->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  nb::StageTimer tm(st);
+  const int e0 = tm.mark();
+  int rc = NIMBUS_OK;
+  {
+    // the cloud under a single label: every IE of its voxelisation is one subvoxel's points
+    nb::Scratch zs(&ctx->mem, st);
+    uint32_t* zero;
+    rc = zs.get(&zero, cloud->n);
+    if (rc != NIMBUS_OK) return rc;
+    if (cudaMemsetAsync(zero, 0, cloud->n * sizeof(uint32_t), st) != cudaSuccess) {
+      cudaGetLastError();
+      ctx->err = "segment: cudaMemsetAsync failed";
+      return NIMBUS_ERR_CUDA;
+    }
+    const nimbus_cloud one{cloud->xyz, cloud->nrm, zero, nullptr, cloud->n};
+    nimbus_vox_params vp{};
+    const double hs = p.voxel_size / p.dv;
+    vp.voxel_size = p.voxel_size;
+    vp.dv = p.dv;
+    vp.sdf_sigma = 0.5 * hs;
+    vp.sdf_eps = 1e-3;
+    vp.vis_ignore = hs * std::sqrt(3.0);
+    vp.sdf_max_steps = 1;
+    auto* S = new nb::SceneObj();
+    S->mem = &ctx->mem;
+    rc = nb::voxelize_scene(ctx->mem, &one, nullptr, &vp, S, st);
+    if (rc == NIMBUS_OK) rc = nb::segment_scene(ctx->mem, S, params, labels, edges, edge_labels, edges_cap, counts, st);
+    drop_obj(ctx, S, st);
+  }
+  const int e1 = tm.mark();
+  cudaStreamSynchronize(st);
+  counts->ms_total = tm.ms(e0, e1);
+  return rc;
 }
 
 int nimbus_scene_save(nimbus_ctx* ctx, nimbus_handle scene, const char* path, void* stream) {

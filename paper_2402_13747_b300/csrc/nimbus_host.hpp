@@ -345,6 +345,10 @@ int refine_paths(Mem& mem, SceneObj* S, CoarseObj* C, const nimbus_refine_params
 int voxelize_scene(Mem& mem, const nimbus_cloud* cloud, const nimbus_edges* edges, const nimbus_vox_params* p,
                    SceneObj* out, cudaStream_t st);
 int scene_save(Mem& mem, SceneObj* S, const char* path, cudaStream_t st);
+// Automatic labels and exterior edges (nimbus_segment) of a scene voxelised under a
+// single label: each of its IEs is the point group of one subvoxel.
+int segment_scene(Mem& mem, SceneObj* S, const nimbus_segment_params* p, uint32_t* labels_out, double* edges_out,
+                  uint32_t* edge_labels_out, int64_t edges_cap, nimbus_segment_counts* counts, cudaStream_t st);
 int scene_load(Mem& mem, const char* path, SceneObj* S, cudaStream_t st);
 int update_scene_region(Mem& mem, SceneObj* s, const double lo[3], const double hi[3],
                         const nimbus_cloud* repl, cudaStream_t st);

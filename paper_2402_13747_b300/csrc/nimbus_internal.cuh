@@ -49,7 +49,7 @@ struct DScene {
   const uint2* cells;      // per voxel: first IE, IE count
   const uint8_t* march;    // per voxel: capped L-inf distance to a voxel with IEs
   const IERec* ies;
-  const float4* pts;       // grouped by IE: xyz, unused
+  const float4* pts;       // grouped by IE: xyz, and w = the point's index in the input cloud (bits)
   const float4* pnrm;      // grouped by IE: normal xyz, unused
   const double* edges;     // [n_edges*12] p0 p1 n0 n1
 };

@@ -153,7 +153,7 @@ __global__ void k_gather(const uint32_t* __restrict__ vals, int64_t n_valid, int
        i += (int64_t)gridDim.x * blockDim.x) {
     uint32_t v = vals[i];
     if (v < n_points) {
-      pts[i] = make_float4(xyz[3 * (int64_t)v], xyz[3 * (int64_t)v + 1], xyz[3 * (int64_t)v + 2], 0.f);
+      pts[i] = make_float4(xyz[3 * (int64_t)v], xyz[3 * (int64_t)v + 1], xyz[3 * (int64_t)v + 2], __uint_as_float(v));
       pnrm[i] = make_float4(nrm[3 * (int64_t)v], nrm[3 * (int64_t)v + 1], nrm[3 * (int64_t)v + 2], 0.f);
     } else {
       pts[i] = make_float4(0.f, 0.f, 0.f, 0.f);

@@ -47,7 +47,8 @@ def test_struct_layouts_match_header(tmp_path):
                "nimbus_path_counts": _abi.Counts, "nimbus_path_view": _abi.PathView,
                "nimbus_coarse_view": _abi.CoarseView, "nimbus_scene_view": _abi.SceneView,
                "nimbus_static_tables": _abi.StaticTables, "nimbus_static_info": _abi.StaticInfo,
-               "nimbus_tuning": _abi.Tuning}
+               "nimbus_tuning": _abi.Tuning, "nimbus_segment_params": _abi.SegmentParamsC,
+               "nimbus_segment_counts": _abi.SegmentCounts}
     lines = []
     for cname, py in structs.items():
         lines.append(f'printf("{cname} %zu\\n", sizeof({cname}));')

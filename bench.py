@@ -204,6 +204,7 @@ def main():
     ap.add_argument("--plain-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-segment", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--pairs", default="", help="TxR: only the first T TX and R RX (small profiling cases)")
     args = ap.parse_args()
@@ -377,6 +378,22 @@ def main():
             except Exception as ex:  # the serving measurement must not hide the main line
                 latency = {"error": repr(ex)}
 
+        # automatic labels and edges of the workload's cloud (nimbus_segment), outside the
+        # timed region: median device time of three calls after one warm-up call
+        segment = None
+        if not args.no_segment:
+            try:
+                seg_ms = []
+                for _ in range(4):
+                    G = ctx.segment(sc.xyz, sc.nrm)
+                    seg_ms.append(G["counts"]["ms_total"])
+                sm = float(np.median(seg_ms[1:]))
+                segment = {"cloud": f"the workload's {sc.xyz.shape[0]} points without labels or edges",
+                           "ms": sm, "points_per_s": sc.xyz.shape[0] / (sm / 1e3),
+                           "surfaces": int(G["counts"]["n_surfaces"]), "edges": int(G["counts"]["n_edges"])}
+            except Exception as ex:  # must not hide the main line
+                segment = {"error": repr(ex)}
+
         cpu = None
         if not args.no_cpu_baseline and world == 1:
             cpu = cpu_baseline()
@@ -393,7 +410,8 @@ def main():
                           "tuning_sample": "all TX x 4 RX of the workload"},
                "exact_paths_per_s": exact_ps, "exact_paths_per_step": paths / args.steps / world,
                "cones_per_step": cones / args.steps / world, "wall_s_timed_region": wall,
-               "plain": plain, "latency": latency, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+               "plain": plain, "latency": latency, "segment": segment, "roofline": roof, "cpu_baseline": cpu,
+               "e2e": e2e,
                "gpu_launches": launches, "clocks": clocks,
                "counts_last_step": {k: c0[k] for k in ("n_paths", "n_coarse", "n_coarse_raw", "n_nodes", "n_vis",
                                                        "n_cones", "launches")}}

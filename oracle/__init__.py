@@ -9,8 +9,8 @@ shares no code with the CUDA library.
 Parity pins (tests/test_oracle_pins.py):
 - the image method on the box room, with both transmission phases;
 - the LOS length, and the normal-incidence images of an RX placed on the TX;
-- the Keller diffraction point on a sampled wedge, and a floor reflection followed by that
-  diffraction (the floor image of the TX and its Keller point);
+- the Keller diffraction point on a sampled wedge, and a floor reflection next to that
+  diffraction in either order (the floor image of the lower end and its Keller point);
 - brute-force visibility and a closed-form plane patch;
 - a brute-force chessboard distance for the march field;
 - the exact-plane SDF and the continuity of a label's surface;

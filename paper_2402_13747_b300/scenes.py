@@ -451,10 +451,12 @@ def wedge_on_floor(z_tx: float = 0.8, z_rx: float = 2.0, spacing: float = 0.05) 
     """The convex corner of ``wedge`` standing on a sampled floor (z = 0, label 3).
 
     The floor covers x in [-4, 2], y in [-4, 2] outside the solid (x <= 0, y <= 0).
-    Besides the pure diffraction, TX and RX are joined by a floor reflection followed
-    by the edge diffraction.  Unfolding the floor puts the TX at (1, -3, -z_tx); its
+    Besides the pure diffraction, TX and RX are joined by one path that mixes a floor
+    reflection and the edge diffraction, the floor taken next to the lower end.  With
+    z_tx < z_rx the floor comes first: unfolding it puts the TX at (1, -3, -z_tx), its
     Keller point on the edge is at z = (z_rx - z_tx) / 2 (both ends sqrt(10) m from
-    the edge), and the floor point is where that unfolded segment meets z = 0.
+    the edge), and the floor point is where that unfolded segment meets z = 0.  With
+    z_tx > z_rx the RX is unfolded instead and the edge comes first.
     """
     w = wedge(spacing=spacing, z_tx=z_tx, z_rx=z_rx)
     X, Y, _ = np.eye(3)

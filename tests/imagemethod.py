@@ -61,3 +61,27 @@ def image_paths(planes, tx, rx, max_order):
             length = sum(np.linalg.norm(path[i + 1] - path[i]) for i in range(len(path) - 1))
             out[tuple(planes[k][2] for k in seq)] = (np.array(pts, float).reshape(-1, 3), length)
     return out
+
+
+def corner_on_floor_mixed_path(tx, rx):
+    """Closed form of the one path that mixes a floor reflection and an edge diffraction
+    on the corner standing on a floor (edge on the z axis, floor z = 0, floor label 3,
+    edge label 2): the law of reflection unfolds the floor, so the path is a straight
+    line from the floor image of its first or last end, and the edge point is the
+    Keller point of that line (Section 2.3: equal angles to the edge).
+
+    The floor comes first when the TX is the lower end and last when the RX is; the
+    other order would put the Keller point below the floor.  Returns (labels, types,
+    points (2, 3), length).
+    """
+    tx, rx = np.asarray(tx, float), np.asarray(rx, float)
+    floor_first = tx[2] < rx[2]
+    a, b = (tx, rx) if floor_first else (rx, tx)       # a is reflected in the floor
+    a_img = a * np.array([1.0, 1.0, -1.0])
+    r_a, r_b = np.hypot(a_img[0], a_img[1]), np.hypot(b[0], b[1])
+    D = np.array([0.0, 0.0, a_img[2] + (b[2] - a_img[2]) * r_a / (r_a + r_b)])
+    F = a_img + (0.0 - a_img[2]) / (D[2] - a_img[2]) * (D - a_img)
+    length = float(np.linalg.norm(D - a_img) + np.linalg.norm(b - D))
+    if floor_first:
+        return (3, 2), (0, 1), np.array([F, D]), length
+    return (2, 3), (1, 0), np.array([D, F]), length

@@ -4,7 +4,7 @@ import pytest
 
 import oracle
 from paper_2402_13747_b300 import config, scenes
-from tests.imagemethod import box_room_planes, image_paths
+from tests.imagemethod import box_room_planes, corner_on_floor_mixed_path, image_paths
 from tests.pathsets import compare, keyed
 
 pytestmark = pytest.mark.gpu
@@ -93,26 +93,24 @@ def test_wedge_keller_point(ctx):
     np.testing.assert_allclose(G["pts"][0][0], [0.0, 0.0, 1.25], atol=1e-3)
 
 
-@pytest.mark.parametrize("z_tx,z_rx", [(0.8, 2.0), (1.0, 2.2)])
-def test_reflection_then_diffraction(ctx, z_tx, z_rx):
-    """The corner on a floor: the oracle's paths exactly, and the floor-then-edge path
-    at the closed-form points of the floor image of the TX and its Keller point."""
+@pytest.mark.parametrize("z_tx,z_rx", [(0.8, 2.0), (1.0, 2.2), (2.0, 0.8)])
+def test_reflection_and_diffraction(ctx, z_tx, z_rx):
+    """The corner on a floor: the oracle's paths exactly, and the path mixing a floor
+    reflection and the edge diffraction (floor first when the TX is the lower end,
+    edge first otherwise) at the closed-form points of the floor image and its
+    Keller point."""
     sc = scenes.wedge_on_floor(z_tx=z_tx, z_rx=z_rx)
     p = config.params_for(sc)
     G = ctx.run(sc, p)
     _, _, e = oracle.run(sc, p)
     cmp = compare(G, e.paths(), atol_pts=1e-3, rtol_len=1e-6)
     assert cmp["only_gpu"] == [] and cmp["only_ref"] == [] and cmp["bad"] == [], cmp
-    tx_img = np.array([1.0, -3.0, -z_tx])
-    D = np.array([0.0, 0.0, (z_rx - z_tx) / 2.0])
-    F = tx_img + z_tx / (z_tx + D[2]) * (D - tx_img)
-    L = np.linalg.norm(D - tx_img) + np.linalg.norm(sc.rx[0] - D)
-    rd = [i for i in range(len(G["n"])) if G["n"][i] == 2 and list(G["label"][i][:2]) == [3, 2]]
+    labels, types, want, L = corner_on_floor_mixed_path(sc.tx[0], sc.rx[0])
+    rd = [i for i in range(len(G["n"])) if G["n"][i] == 2 and tuple(G["label"][i][:2]) == labels]
     assert len(rd) == 1
     i = rd[0]
-    assert list(G["type"][i][:2]) == [0, 1]
-    np.testing.assert_allclose(G["pts"][i][0], F, atol=1e-3)
-    np.testing.assert_allclose(G["pts"][i][1], D, atol=1e-3)
+    assert tuple(G["type"][i][:2]) == types
+    np.testing.assert_allclose(G["pts"][i][:2], want, atol=1e-3)
     assert abs(G["length"][i] - L) <= 1e-6 * L
 
 

@@ -13,7 +13,7 @@ import pytest
 
 import oracle
 from paper_2402_13747_b300 import config, scenes
-from tests.imagemethod import box_room_planes, image_paths
+from tests.imagemethod import box_room_planes, corner_on_floor_mixed_path, image_paths
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -105,37 +105,29 @@ def test_keller_point_on_sampled_wedge(z_tx, z_rx):
     assert abs(ein @ w / np.linalg.norm(ein) - eout @ w / np.linalg.norm(eout)) < 1e-6
 
 
-def _floor_then_edge(z_tx, z_rx):
-    """Closed form of TX -> floor reflection -> edge diffraction -> RX on
-    scenes.wedge_on_floor: the floor image of the TX and its Keller point on the edge."""
-    tx_img = np.array([1.0, -3.0, -z_tx])
-    D = np.array([0.0, 0.0, (z_rx - z_tx) / 2.0])
-    F = tx_img + z_tx / (z_tx + D[2]) * (D - tx_img)
-    L = np.linalg.norm(D - tx_img) + np.linalg.norm(np.array([-3.0, 1.0, z_rx]) - D)
-    return F, D, L
-
-
-@pytest.mark.parametrize("z_tx,z_rx", [(0.8, 2.0), (1.0, 2.2), (0.6, 1.8)])
-def test_reflection_then_diffraction_closed_form(z_tx, z_rx):
-    """A path mixing both interaction kinds: the floor point and the edge point are
-    those of the image of the TX in the floor joined to the RX through the Keller
-    point, and each obeys its own law (mirror reflection; equal angles to the edge)."""
+@pytest.mark.parametrize("z_tx,z_rx", [(0.8, 2.0), (1.0, 2.2), (0.6, 1.8), (2.0, 0.8), (1.8, 0.6)])
+def test_reflection_and_diffraction_closed_form(z_tx, z_rx):
+    """Paths mixing both interaction kinds, in either order: the floor point and the
+    edge point are those of the floor image of the lower end joined to the other end
+    through its Keller point, each obeys its own law (mirror reflection; equal angles
+    to the edge), and the order whose Keller point would lie below the floor is absent."""
     sc = scenes.wedge_on_floor(z_tx=z_tx, z_rx=z_rx)
     p = config.params_for(sc, grad_stop=1e-10)
     _, _, e = oracle.run(sc, p)
     got = _exact_by_labels(e.paths())
-    F, D, L = _floor_then_edge(z_tx, z_rx)
-    pts, length, types = got[(0, 0, (3, 2))]
-    assert types == (0, 1)
-    np.testing.assert_allclose(pts[0], F, atol=1e-6)
-    np.testing.assert_allclose(pts[1], D, atol=1e-6)
-    assert length == pytest.approx(L, rel=1e-9)
     tx, rx = sc.tx[0], sc.rx[0]
-    d_in = (pts[0] - tx) / np.linalg.norm(pts[0] - tx)
-    d_out = (pts[1] - pts[0]) / np.linalg.norm(pts[1] - pts[0])
-    np.testing.assert_allclose(d_out, d_in - 2 * d_in[2] * np.array([0, 0, 1.0]), atol=1e-6)
-    e_in, e_out = d_out, (rx - pts[1]) / np.linalg.norm(rx - pts[1])
-    assert abs(e_in[2] - e_out[2]) < 1e-6
+    labels, types, want, L = corner_on_floor_mixed_path(tx, rx)
+    pts, length, got_types = got[(0, 0, labels)]
+    assert got_types == types
+    np.testing.assert_allclose(pts, want, atol=1e-6)
+    assert length == pytest.approx(L, rel=1e-9)
+    assert (0, 0, labels[::-1]) not in got
+    nodes = [tx, pts[0], pts[1], rx]
+    d = [(nodes[k + 1] - nodes[k]) / np.linalg.norm(nodes[k + 1] - nodes[k]) for k in range(3)]
+    kf = types.index(0)                   # floor: mirror law about z
+    np.testing.assert_allclose(d[kf + 1], d[kf] * np.array([1.0, 1.0, -1.0]), atol=1e-6)
+    kd = types.index(1)                   # edge (z axis): equal angles
+    assert abs(d[kd][2] - d[kd + 1][2]) < 1e-6
     # the pure diffraction is there too, at the Keller point of TX and RX themselves
     dpts, dlen, dtypes = got[(0, 0, (2,))]
     np.testing.assert_allclose(dpts[0], [0.0, 0.0, (z_tx + z_rx) / 2.0], atol=1e-6)

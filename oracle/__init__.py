@@ -16,7 +16,13 @@ Parity pins (tests/test_oracle_pins.py):
 - the exact-plane SDF and the continuity of a label's surface;
 - a Monte-Carlo cone-sphere test and the Fibonacci lattice properties;
 - integer re-derivation of the voxel keys, and the reflection law at refined points;
-- the first Fresnel zone radius of the duplicate removal, just inside and just outside.
+- the first Fresnel zone radius of the duplicate removal, just inside and just outside;
+- Eq. 1's Gaussian weights on two points (a tanh profile), the image-method paths with
+  faces turned away, the self-hit rule of the visibility test, the lattice's equal-area
+  zones and golden-angle turns, and delay = length / c.
+tests/test_oracle_mutants.py plants one mistake at a time in a copy of the source and
+checks that these pins catch it.  The secant placement after a sign change of f is
+reached by no pinned scene.
 
 The coarse-path set and the kappa choice on noisy scenes have no closed form: parity
 unpinned beyond those invariants.
@@ -76,12 +82,17 @@ def to_struct(p) -> OracleParams:
     return s
 
 
+def build_from(src: str, out: str) -> str:
+    """Compile an oracle source with g++ (no FP contraction: FP32 binning must be exact)."""
+    cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", src, "-o", out]
+    subprocess.run(cmd, check=True)
+    return out
+
+
 def build(force: bool = False) -> str:
-    """Compile the oracle with g++ (no FP contraction: FP32 binning must be exact)."""
+    """Compile the oracle into oracle/libnimbus_oracle.so when its source is newer."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-               _SRC, "-o", _LIB]
-        subprocess.run(cmd, check=True)
+        build_from(_SRC, _LIB)
     return _LIB
 
 
@@ -89,10 +100,13 @@ _lib = None
 
 
 def lib():
+    """The loaded oracle library.  NIMBUS_ORACLE_LIB names another build of this same
+    interface instead: the mutation tests plant one mistake in a copy of the source,
+    build it with build_from() and run the pins against it."""
     global _lib
     if _lib is None:
-        build()
-        L = C.CDLL(_LIB)
+        path = os.environ.get("NIMBUS_ORACLE_LIB") or build()
+        L = C.CDLL(path)
         vp, i64, i32, u32, d = C.c_void_p, C.c_int64, C.c_int32, C.c_uint32, C.c_double
         P = C.POINTER
         L.oracle_voxelize.restype = vp

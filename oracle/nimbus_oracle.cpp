@@ -16,7 +16,9 @@
 // Pins (tests/test_oracle_pins.py) fix voxelisation, the march field, Eq. 1,
 // visibility, the cone test and the refined exact paths (image method, Keller point,
 // a reflection and a diffraction in either order) against closed forms and brute
-// force.  The coarse-path set and the kappa choice on noisy clouds have no
+// force; tests/test_oracle_mutants.py checks that planted mistakes fail them (the
+// secant placement after a sign change of f is reached by no pinned scene).  The
+// coarse-path set and the kappa choice on noisy clouds have no
 // closed form: parity unpinned beyond their invariants (kappa, depth limits) and the
 // exact paths they refine to.
 // The only FP32 arithmetic is the subvoxel binning, which both sides perform with

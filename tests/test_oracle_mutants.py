@@ -1,0 +1,118 @@
+"""The oracle's pins catch plausible mistakes (CPU).
+
+Each case plants one mistake -- a dropped term, a wrong sign, a swapped operand or
+index -- in a temporary copy of oracle/nimbus_oracle.cpp, builds that copy, and runs
+the pins named for it (tests/test_oracle_pins.py) against the build through
+NIMBUS_ORACLE_LIB.  A case passes when at least one of those pins fails and none
+crashes.  The planted text must occur exactly once in the source, so a change to the
+oracle that removes it shows up here rather than silently weakening the check.
+Nothing here touches the CUDA library or the committed oracle build.
+"""
+import concurrent.futures as cf
+import os
+import re
+import subprocess
+import sys
+
+import pytest
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "nimbus_oracle.cpp")
+TINY = "test_image_method_room_tiny and not paper and not facing"
+
+# (name, text in the oracle, planted mistake, pins expected to catch it (pytest -k))
+MUTANTS = [
+    ("eq1_weight_square_dropped",      # Eq. 1: Gaussian of the distance, not its square
+     "double w = std::exp(-dot(d, d) * inv_s2);\n    sw += w;\n    sp = sp + w * P;",
+     "double w = std::exp(-std::sqrt(dot(d, d)) * inv_s2);\n    sw += w;\n    sp = sp + w * P;",
+     "two_points"),
+    ("newton_placement_dropped",       # Section 2.2.1: hit placed at the last march point
+     "double th = std::fabs(dn) > 1e-3 ? t - f / dn : t;", "double th = t;", "sdf_on_exact_plane"),
+    ("binning_by_voxel",               # Section 2.1: points binned by voxel, not subvoxel
+     "float t = diff / s.hs32;", "float t = diff / (2.0f * s.hs32);", "voxel_membership"),
+    ("march_field_six_neighbours",     # Section 2.2.4: L1 instead of L-infinity distance
+     "if (!in_grid(*s, vx + dx, vy + dy, vz + dz)) continue;",
+     "if (!in_grid(*s, vx + dx, vy + dy, vz + dz) || abs(dx) + abs(dy) + abs(dz) > 1) continue;",
+     "chessboard"),
+    ("cone_sphere_margin_sign",        # Section 2.2.4: sphere margin subtracted from the cone
+     "return t + r * sin_a >= cos_a * std::sqrt(d2 - r * r);",
+     "return t - r * sin_a >= cos_a * std::sqrt(d2 - r * r);", "cone_sphere"),
+    ("fibonacci_offset",               # launch lattice shifted off the zone centres
+     "double z = 1.0 - (2.0 * (double)i + 1.0) / (double)N;",
+     "double z = 1.0 - (2.0 * (double)i) / (double)N;", "fibonacci"),
+    ("onb_v_sign",                     # basis (u, v) of the refinement, one sign flipped
+     "*v = mk(b, sign + n.y * n.y * a, -n.y);", "*v = mk(b, sign + n.y * n.y * a, n.y);", "orthonormal_basis"),
+    ("self_hit_any_label",             # a reflection node ignores every surface near it
+     "if (e.mode == IGN_LABEL) return lbl == e.label;", "if (e.mode == IGN_LABEL) return true;", "self_hit"),
+    ("self_hit_radius_doubled",        # ignore radius 2 h_s sqrt 3
+     "if (dist >= r) return false;", "if (dist >= 2.0 * r) return false;", "self_hit"),
+    ("reflected_axis_sign",            # Section 2.2.4: reflected cone not mirrored
+     "c.axis = unit(e - 2.0 * dot(e, n) * n);", "c.axis = unit(e + 2.0 * dot(e, n) * n);", TINY),
+    ("normal_orientation_dropped",     # separation plane on the far side of a surface
+     "if (dot(n, e) > 0) n = -1.0 * n;", "", "facing_away"),
+    ("keller_fan_exterior_and",        # Keller fan kept only where both faces see it
+     "if (!(dot(d, E.n0) > 0.0 || dot(d, E.n1) > 0.0)) continue;",
+     "if (!(dot(d, E.n0) > 0.0 && dot(d, E.n1) > 0.0)) continue;", "keller_point"),
+    ("gradient_sign",                  # Eq. 2: e_in - e_out instead of e_in + e_out
+     "V3 e = unit(I[k] - I[k - 1]) + unit(I[k] - I[k + 1]);",
+     "V3 e = unit(I[k] - I[k - 1]) - unit(I[k] - I[k + 1]);", "keller_point"),
+    ("reprojection_target_v_sign",     # Section 2.3: R_k = c_k + r u_k - s v_k
+     "V3 R = c[k] + r * u[k] + sv * v[k];", "V3 R = c[k] + r * u[k] - sv * v[k];", TINY),
+    ("edge_parameter_sign",            # Section 2.3: D_k = c_k - t w_k
+     "In[k] = c[k] + tpar[k] * w[k];", "In[k] = c[k] - tpar[k] * w[k];", "keller_point"),
+    ("length_last_segment_dropped",    # path length without its last segment
+     "for (int k = 0; k <= n; ++k) L += norm(I[k + 1] - I[k]);",
+     "for (int k = 0; k < n; ++k) L += norm(I[k + 1] - I[k]);", "los_length"),
+    ("delay_scaled",                   # delay off length / c by one part in 1e9
+     "ex.delay = L / C_LIGHT;", "ex.delay = L / (C_LIGHT * (1.0 + 1e-9));", TINY),
+    ("kappa_farthest_first",           # Section 2.2.3: kappa keeps the farthest cone axes
+     "if (a.miss != b.miss) return a.miss < b.miss;", "if (a.miss != b.miss) return a.miss > b.miss;", "kappa"),
+    ("fresnel_radius_misplaced_root",  # Section 2.3: sqrt(lambda a b) / (a + b)
+     "double r = std::sqrt(lambda * ak * bk / (ak + bk));", "double r = std::sqrt(lambda * ak * bk) / (ak + bk);",
+     "fresnel_zone_radius"),
+]
+
+
+def _run_mutant(tmp, name, text, planted, pins):
+    src = open(SRC).read()
+    if src.count(text) != 1:
+        return name, None, f"the oracle holds {src.count(text)} copies of the planted text"
+    cpp = os.path.join(tmp, name + ".cpp")
+    with open(cpp, "w") as fh:
+        fh.write(src.replace(text, planted))
+    so = oracle.build_from(cpp, os.path.join(tmp, name + ".so"))
+    env = dict(os.environ, NIMBUS_ORACLE_LIB=so)
+    r = subprocess.run([sys.executable, "-m", "pytest", os.path.join("tests", "test_oracle_pins.py"), "-q",
+                        "-p", "no:cacheprovider", "-rf", "-m", "not gpu", "-k", pins],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    return name, r.returncode, r.stdout[-2000:] + r.stderr[-2000:]
+
+
+@pytest.fixture(scope="module")
+def outcomes(tmp_path_factory):
+    tmp = str(tmp_path_factory.mktemp("oracle_mutants"))
+    workers = max(1, min(8, os.cpu_count() or 1))
+    with cf.ThreadPoolExecutor(workers) as ex:
+        futs = [ex.submit(_run_mutant, tmp, *m) for m in MUTANTS]
+        return {name: (rc, log) for name, rc, log in (f.result() for f in futs)}
+
+
+def test_unmutated_source_passes_the_same_pins():
+    """The selections run clean on the oracle as it is (pytest exit 0)."""
+    ks = " or ".join(f"({m[3]})" for m in MUTANTS)
+    r = subprocess.run([sys.executable, "-m", "pytest", os.path.join("tests", "test_oracle_pins.py"), "-q",
+                        "-p", "no:cacheprovider", "-m", "not gpu", "-k", ks],
+                       cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stdout[-3000:]
+
+
+@pytest.mark.parametrize("name", [m[0] for m in MUTANTS])
+def test_pins_catch_planted_mistake(outcomes, name):
+    rc, log = outcomes[name]
+    assert rc is not None, log
+    # 1: some selected pin failed; 0 would mean the mistake went unnoticed, and
+    # anything else (a crash, no test selected) is not a pin catching it
+    assert rc == 1, f"{name}: pytest exit {rc}\n{log}"
+    assert re.search(r"FAILED ", log), log

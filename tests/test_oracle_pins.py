@@ -58,6 +58,28 @@ def test_image_method_room_tiny(tiny_run):
         rp, rl = ref[lab]
         np.testing.assert_allclose(pts, rp, atol=1e-6)
         assert abs(length - rl) <= 1e-9 * rl
+    # delay = length / c, with c = 299,792,458 m/s exactly (the SI definition of the metre)
+    P = e.paths()
+    for i in range(len(P["n"])):
+        assert P["delay"][i] * 299_792_458.0 == pytest.approx(P["length"][i], rel=1e-15)
+
+
+@pytest.mark.parametrize("flipped", [(0, 1, 2, 3, 4, 5), (0, 3, 4)])
+def test_image_method_with_surfaces_facing_away(room_tiny, flipped):
+    """The normals of a scan have no agreed side: a surface whose normals all face
+    away from the room reflects the same rays (mirroring about n or -n is the same
+    map), so turning whole faces around leaves the image method's 25 paths."""
+    sc = room_tiny
+    nrm = np.where(np.isin(sc.label, flipped)[:, None], -sc.nrm, sc.nrm).astype(np.float32)
+    turned = scenes.Scene("room_tiny_turned", sc.xyz, nrm, sc.label, sc.material, tx=sc.tx, rx=sc.rx,
+                          max_refl=2, max_diff=0)
+    _, _, e = oracle.run(turned, config.params_for(turned, grad_stop=1e-9))
+    ref = image_paths(box_room_planes(10.0, 10.0, 3.0), sc.tx[0], sc.rx[0], max_order=2)
+    got = _exact_by_labels(e.paths())
+    assert set(k[2] for k in got) == set(ref)
+    for (t, r, lab), (pts, length, types) in got.items():
+        np.testing.assert_allclose(pts, ref[lab][0], atol=1e-6)
+        assert abs(length - ref[lab][1]) <= 1e-9 * ref[lab][1]
 
 
 def test_image_method_room_tiny_paper_launch(room_tiny):
@@ -180,6 +202,41 @@ def test_visibility_closed_form_plane_patch():
             assert s.visible(c, d)
 
 
+def test_visibility_self_hit_rule():
+    """Hits near a path node (Sections 2.2.4, 2.3), with the rule read for them: a hit
+    closer than r = h_s sqrt(3) to a node is ignored when it lies on that node's own
+    label (a reflection) or on any label (a diffraction), and blocks otherwise.  A
+    floor (label 0) with a 0.3 m high wall (label 1) at x = 0.2: the ray from the floor
+    point F = 0 to (2, 0, 1) crosses the wall 0.22 m from F; the ray from (0, 0, 0.1)
+    to (0.2, 0, -0.5) crosses the floor 0.03 m from its start, the ray to
+    (-2.9, 0, -0.5) 0.49 m from it (beyond r)."""
+    X, Y, Z = np.eye(3)
+    parts = [scenes.plane_patch([-3, -2, 0], X, Y, 6.0, 4.0, 0.05, [0, 0, 1], 0),
+             scenes.plane_patch([0.2, -2, 0], Y, Z, 4.0, 0.3, 0.05, [-1, 0, 0], 1)]
+    xyz, nrm, lab, mat = scenes.merge_clouds(parts)
+    sc = scenes.Scene("floor_low_wall", xyz, nrm, lab, mat, region=np.array([[-3.0, -2, -1], [3.0, 2, 1.5]]))
+    p = config.Params()
+    assert 0.22 < p.ignore_dist < 0.49
+    s = oracle.Scene.from_scene(sc, p)
+    NONE, LABEL, ANY, NL = 0, 1, 2, oracle.NONE_LABEL
+
+    def vis(a, b, mode, label):   # the rule at either end of the ray
+        v = s.visible(a, b, mode, label)
+        assert s.visible(b, a, NONE, NL, mode, label) == v
+        return v
+
+    F, R = np.zeros(3), np.array([2.0, 0.0, 1.0])
+    assert not vis(F, R, LABEL, 0)        # another surface near a reflection blocks
+    assert vis(F, R, LABEL, 1)            # ... and is ignored on the node's own label
+    assert vis(F, R, ANY, 0)              # ... and near a diffraction on any label
+    A, near, far = np.array([0, 0, 0.1]), np.array([0.2, 0, -0.5]), np.array([-2.9, 0, -0.5])
+    assert not vis(A, near, NONE, NL)
+    assert vis(A, near, LABEL, 0) and vis(A, near, ANY, 0)
+    assert not vis(A, near, LABEL, 1)
+    for mode, label in ((NONE, NL), (LABEL, 0), (ANY, 0)):
+        assert not vis(A, far, mode, label)   # beyond r nothing is ignored
+
+
 def test_march_field_is_chessboard_distance(room_tiny):
     """March distance (Section 2.2.4) equals scipy's chessboard distance transform."""
     from scipy import ndimage
@@ -248,6 +305,30 @@ def test_sdf_on_exact_plane(room_tiny):
         assert t is not None and t == pytest.approx(t_ref, abs=1e-9)
 
 
+def test_sdf_weights_two_points_closed_form():
+    """Eq. 1's weighted average with the Gaussian weights exp(-|x - p_i|^2 / sigma^2)
+    (the Adamson-Alexa weights the paper cites) on two points p -/+ h z with a shared
+    normal z: the weight ratio is exp(4 z h / sigma^2) at height z above their
+    midpoint, whatever the lateral offset, so the weighted position sits at
+    h tanh(2 z h / sigma^2) and f = z - h tanh(2 z h / sigma^2).  Any other weight
+    profile (a dropped square, another width) moves f off this curve."""
+    p = config.Params()
+    c, h = np.array([1.125, 1.125, 1.125]), 0.0625      # exact in FP32, one subvoxel
+    xyz = np.array([c - [0, 0, h], c + [0, 0, h]], np.float32)
+    nrm = np.array([[0, 0, 1], [0, 0, 1]], np.float32)
+    sc = scenes.Scene("two_points", xyz, nrm, np.zeros(2, np.uint32), np.zeros(2, np.uint8))
+    s = oracle.Scene.from_scene(sc, p)
+    I = s.ies()
+    assert len(I["label"]) == 1 and I["prange"][0, 1] == 2
+    s2 = p.sdf_sigma ** 2
+    for z in (-0.1, -0.04, -0.01, 0.0, 0.02, 0.07, 0.1):
+        for lat in ((0.0, 0.0), (0.06, -0.03)):
+            x = c + np.array([lat[0], lat[1], z])
+            f, n = s.sdf(0, x)
+            assert f == pytest.approx(z - h * math.tanh(2 * z * h / s2), abs=1e-12)
+            np.testing.assert_allclose(n, [0, 0, 1], atol=1e-12)
+
+
 def test_cone_sphere_against_sampling():
     rng = np.random.default_rng(5)
     checked = 0
@@ -283,6 +364,16 @@ def test_fibonacci_lattice():
     # equal area: z is uniform on [-1, 1]
     hist, _ = np.histogram(d[:, 2], bins=20, range=(-1, 1))
     assert hist.min() >= n / 20 - 2 and hist.max() <= n / 20 + 2
+    # the lattice's construction: by Archimedes' hat-box theorem, zones of equal height
+    # on the unit sphere have equal area, and each point sits at the middle height of
+    # one of N such zones (so the set is symmetric about z = 0, nothing at the poles);
+    # successive points turn about z by the golden angle pi (3 - sqrt 5)
+    z = np.sort(d[:, 2])
+    np.testing.assert_allclose(np.diff(z), 2.0 / n, atol=1e-12)
+    assert z[-1] == pytest.approx(1.0 - 1.0 / n, abs=1e-15) and z[0] == pytest.approx(-1.0 + 1.0 / n, abs=1e-15)
+    np.testing.assert_allclose(d.mean(axis=0), 0.0, atol=1e-5)
+    turn = np.mod(np.diff(np.arctan2(d[:, 1], d[:, 0])), 2 * math.pi)
+    np.testing.assert_allclose(turn, math.pi * (3.0 - math.sqrt(5.0)), atol=1e-9)
     rng = np.random.default_rng(1)
     sample = rng.integers(0, n, 100)
     delta = math.radians(0.5)

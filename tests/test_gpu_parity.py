@@ -85,6 +85,26 @@ def test_room_tiny_exact_paths(ctx, room_tiny, launch_mode):
         assert abs(L - ref[k[3]][1]) <= 1e-6 * ref[k[3]][1]
 
 
+def test_room_tiny_faces_turned_away(ctx, room_tiny):
+    """The tiny room with three faces' normals turned away from the room (a scan's
+    normals have no agreed side): the oracle's paths and the 25 image-method paths."""
+    sc = room_tiny
+    nrm = np.where(np.isin(sc.label, (0, 3, 4))[:, None], -sc.nrm, sc.nrm).astype(np.float32)
+    turned = scenes.Scene("room_tiny_turned", sc.xyz, nrm, sc.label, sc.material, tx=sc.tx, rx=sc.rx,
+                          max_refl=2, max_diff=0)
+    p = config.params_for(turned)
+    G = ctx.run(turned, p)
+    _, _, e = oracle.run(turned, p)
+    cmp = compare(G, e.paths(), atol_pts=1e-3, rtol_len=1e-6)
+    assert cmp["only_gpu"] == [] and cmp["only_ref"] == [] and cmp["bad"] == [], cmp
+    ref = image_paths(box_room_planes(10.0, 10.0, 3.0), sc.tx[0], sc.rx[0], max_order=2)
+    got = keyed(G)
+    assert {k[3] for k in got} == set(ref)
+    for k, (pts, L) in got.items():
+        np.testing.assert_allclose(pts, ref[k[3]][0], atol=1e-3)
+        assert abs(L - ref[k[3]][1]) <= 1e-6 * ref[k[3]][1]
+
+
 def test_wedge_keller_point(ctx):
     sc = scenes.wedge(z_tx=0.5, z_rx=2.0)
     p = config.params_for(sc)

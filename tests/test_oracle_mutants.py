@@ -1,16 +1,20 @@
-"""The oracle's pins catch plausible mistakes (CPU).
+"""The oracles' pins catch plausible mistakes (CPU).
 
 Each case plants one mistake -- a dropped term, a wrong sign, a swapped operand or
-index -- in a temporary copy of oracle/nimbus_oracle.cpp, builds that copy, and runs
-the pins named for it (tests/test_oracle_pins.py) against the build through
-NIMBUS_ORACLE_LIB.  A case passes when at least one of those pins fails and none
-crashes.  The planted text must occur exactly once in the source, so a change to the
-oracle that removes it shows up here rather than silently weakening the check.
-Nothing here touches the CUDA library or the committed oracle build.
+index -- in a temporary copy of an oracle and runs the pins named for it against that
+copy.  For the C++ oracle (oracle/nimbus_oracle.cpp) the copy is built and loaded
+through NIMBUS_ORACLE_LIB by tests/test_oracle_pins.py; for the labelling oracle
+(oracle/segment.py) tests/test_segment_oracle.py runs in a temporary copy of the
+repository's Python sources with the planted module.  A case passes when at least one
+of those pins fails and none crashes.  The planted text must occur exactly once in
+the source, so a change to an oracle that removes it shows up here rather than
+silently weakening the check.  Nothing here touches the CUDA library or the committed
+oracle build.
 """
 import concurrent.futures as cf
 import os
 import re
+import shutil
 import subprocess
 import sys
 
@@ -114,5 +118,93 @@ def test_pins_catch_planted_mistake(outcomes, name):
     assert rc is not None, log
     # 1: some selected pin failed; 0 would mean the mistake went unnoticed, and
     # anything else (a crash, no test selected) is not a pin catching it
+    assert rc == 1, f"{name}: pytest exit {rc}\n{log}"
+    assert re.search(r"FAILED ", log), log
+
+
+# ---------------------------------------------------------------- labelling oracle
+SEG_SRC = os.path.join(ROOT, "oracle", "segment.py")
+
+# (name, text in oracle/segment.py, planted mistake, pins expected to catch it (pytest -k))
+SEGMENT_MUTANTS = [
+    ("largest_eigenvector",            # group normal from the largest, not smallest, eigenvalue
+     "    w, V = np.linalg.eigh(C)                      # ascending eigenvalues\n    n = V[:, 0].copy()",
+     "    w, V = np.linalg.eigh(C)                      # ascending eigenvalues\n    n = V[:, 2].copy()", "box_room"),
+    ("covariance_uncentred",           # covariance about the origin
+     "    d = p - c\n    C = d.T @ d / m", "    d = p\n    C = d.T @ d / m", "box_room"),
+    ("group_normal_unoriented",        # group normal not turned toward the input normals
+     "    n = V[:, 0].copy()\n    if n @ nr.sum(axis=0) < 0.0:\n        n = -n\n    tr", "    n = V[:, 0].copy()\n    tr",
+     "box_room"),
+    ("spread_test_dropped",            # a single row of points counted as a plane
+     "w[0] <= sp.flat_max * tr and w[1] >= sp.spread_min * tr", "w[0] <= sp.flat_max * tr", "convex_corner"),
+    ("binning_by_voxel",               # groups per voxel instead of per subvoxel
+     "t = (x32 - o32[None, :]) / hs32", "t = (x32 - o32[None, :]) / (2 * hs32)", "convex_corner"),
+    ("join_any_angle",                 # planar neighbours joined at any angle
+     "return (nor[a] @ nor[b] >= cos_join and", "return (nor[a] @ nor[b] >= -1.0 and", "folded_sheet"),
+    ("join_distance_dropped",          # planar neighbours joined at any offset
+     "abs(nor[a] @ (cen[b] - cen[a])) <= sp.join_dist\n                and abs(nor[b] @ (cen[a] - cen[b])) <= sp.join_dist)",
+     "True)", "offset_sheets"),
+    ("root_highest",                   # surfaces numbered by their last group
+     "parent[max(ra, rb)] = min(ra, rb)", "parent[min(ra, rb)] = max(ra, rb)", "numbered"),
+    ("relabel_dropped",                # points keep their own group's surface
+     "labels[i] = surf[best] if best >= 0 else surf[g]", "labels[i] = surf[g]", "box_room"),
+    ("concave_edges",                  # edges where the surfaces face each other
+     "nA @ (cB - cA) < 0.0 and nB @ (cA - cB) < 0.0", "nA @ (cB - cA) > 0.0 and nB @ (cA - cB) > 0.0", "box_room"),
+    ("edge_angle_reversed",            # edges only between nearly parallel surfaces
+     "if not (nA @ nB <= cos_edge and", "if not (nA @ nB >= cos_edge and", "convex_corner"),
+    ("edge_min_groups_ignored",        # edges between surfaces of a subvoxel or two
+     "if len(members[A]) < sp.edge_min_groups or len(members[B]) < sp.edge_min_groups:", "if False:",
+     "small_boxes"),
+    ("edge_span_halved",               # edge ends pulled halfway in
+     "edges.append(np.concatenate([x0 + min(t) * w, x0 + max(t) * w, nA, nB]))",
+     "edges.append(np.concatenate([x0 + 0.5 * min(t) * w, x0 + 0.5 * max(t) * w, nA, nB]))", "convex_corner"),
+    ("line_point_sign",                # point on the planes' line solved with one sign flipped
+     "r = np.array([nA @ cA - nA @ mid, nB @ cB - nB @ mid])", "r = np.array([nA @ cA - nA @ mid, nB @ mid - nB @ cB])",
+     "convex_corner"),
+]
+
+
+def _run_segment_mutant(tmp, name, text, planted, pins):
+    src = open(SEG_SRC).read()
+    if src.count(text) != 1:
+        return name, None, f"oracle/segment.py holds {src.count(text)} copies of the planted text"
+    d = os.path.join(tmp, name)
+    shutil.copytree(os.path.join(ROOT, "oracle"), os.path.join(d, "oracle"),
+                    ignore=shutil.ignore_patterns("__pycache__"))
+    os.makedirs(os.path.join(d, "paper_2402_13747_b300"))
+    for f in ("__init__.py", "config.py", "scenes.py"):
+        shutil.copy(os.path.join(ROOT, "paper_2402_13747_b300", f), os.path.join(d, "paper_2402_13747_b300", f))
+    os.makedirs(os.path.join(d, "tests"))
+    for f in ("conftest.py", "test_segment_oracle.py"):
+        shutil.copy(os.path.join(ROOT, "tests", f), os.path.join(d, "tests", f))
+    with open(os.path.join(d, "oracle", "segment.py"), "w") as fh:
+        fh.write(src.replace(text, planted))
+    r = subprocess.run([sys.executable, "-m", "pytest", os.path.join("tests", "test_segment_oracle.py"), "-q",
+                        "-p", "no:cacheprovider", "-rf", "-k", pins],
+                       cwd=d, capture_output=True, text=True, timeout=600)
+    return name, r.returncode, r.stdout[-2000:] + r.stderr[-2000:]
+
+
+@pytest.fixture(scope="module")
+def segment_outcomes(tmp_path_factory):
+    oracle.build()                        # the copies carry the built C++ oracle (grid of the cloud)
+    tmp = str(tmp_path_factory.mktemp("segment_mutants"))
+    workers = max(1, min(8, os.cpu_count() or 1))
+    with cf.ThreadPoolExecutor(workers) as ex:
+        futs = [ex.submit(_run_segment_mutant, tmp, *m) for m in SEGMENT_MUTANTS]
+        return {name: (rc, log) for name, rc, log in (f.result() for f in futs)}
+
+
+def test_unmutated_labelling_passes_the_same_pins():
+    ks = " or ".join(f"({m[3]})" for m in SEGMENT_MUTANTS)
+    r = subprocess.run([sys.executable, "-m", "pytest", os.path.join("tests", "test_segment_oracle.py"), "-q",
+                        "-p", "no:cacheprovider", "-k", ks], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stdout[-3000:]
+
+
+@pytest.mark.parametrize("name", [m[0] for m in SEGMENT_MUTANTS])
+def test_labelling_pins_catch_planted_mistake(segment_outcomes, name):
+    rc, log = segment_outcomes[name]
+    assert rc is not None, log
     assert rc == 1, f"{name}: pytest exit {rc}\n{log}"
     assert re.search(r"FAILED ", log), log

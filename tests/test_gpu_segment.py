@@ -8,6 +8,7 @@ import pytest
 import oracle
 import oracle.segment as seg
 from paper_2402_13747_b300 import config, scenes
+from tests import segclouds
 from tests.pathsets import compare
 
 pytestmark = pytest.mark.gpu
@@ -28,12 +29,28 @@ def _scene(name):
             "room_noisy": lambda: scenes.room_noisy(n_tx=1, n_rx=3)}[name]()
 
 
-@pytest.mark.parametrize("name", ["room_tiny", "wedge_on_floor", "room_noisy"])
+def _cloud(name):
+    """xyz, nrm of a named cloud: a scene, or one of the labelling pins' sheets and boxes."""
+    kind, _, arg = name.partition(":")
+    if kind == "fold":
+        return segclouds.folded_sheet(float(arg))[:2]
+    if kind == "offset":
+        return segclouds.offset_sheets(float(arg))[:2]
+    if kind == "box":
+        return segclouds.box_on_floor(float(arg))[:2]
+    if kind == "rows":
+        return segclouds.two_sheets_in_row_order()[:2]
+    sc = _scene(name)
+    return sc.xyz, sc.nrm
+
+
+@pytest.mark.parametrize("name", ["room_tiny", "wedge_on_floor", "room_noisy", "fold:5", "fold:11", "fold:20",
+                                  "fold:-40", "offset:0.01", "offset:0.1", "box:0.5", "box:1.0", "rows"])
 def test_labels_and_edges_match_oracle(ctx, name):
     """Integer labels bit for bit; edges to 1e-9 m (FP64 sums in another order)."""
-    sc = _scene(name)
-    G = ctx.segment(sc.xyz, sc.nrm, SP)
-    lab, E, EL, ns = seg.segment(sc.xyz, sc.nrm, SP)
+    xyz, nrm = _cloud(name)
+    G = ctx.segment(xyz, nrm, SP)
+    lab, E, EL, ns = seg.segment(xyz, nrm, SP)
     assert G["counts"]["n_surfaces"] == ns
     np.testing.assert_array_equal(G["labels"], lab)
     np.testing.assert_array_equal(G["edge_labels"], EL)

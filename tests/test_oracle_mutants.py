@@ -175,7 +175,7 @@ def _run_segment_mutant(tmp, name, text, planted, pins):
     for f in ("__init__.py", "config.py", "scenes.py"):
         shutil.copy(os.path.join(ROOT, "paper_2402_13747_b300", f), os.path.join(d, "paper_2402_13747_b300", f))
     os.makedirs(os.path.join(d, "tests"))
-    for f in ("conftest.py", "test_segment_oracle.py"):
+    for f in ("conftest.py", "test_segment_oracle.py", "segclouds.py"):
         shutil.copy(os.path.join(ROOT, "tests", f), os.path.join(d, "tests", f))
     with open(os.path.join(d, "oracle", "segment.py"), "w") as fh:
         fh.write(src.replace(text, planted))

@@ -7,6 +7,7 @@ import pytest
 
 import oracle.segment as seg
 from paper_2402_13747_b300 import config, scenes
+from tests import segclouds
 
 SP = config.SegmentParams()
 
@@ -91,29 +92,16 @@ def test_labels_do_not_depend_on_point_order():
     np.testing.assert_allclose(E2, E, atol=1e-12)
 
 
-def _folded_sheet(deg):
-    """A 2 x 2 m sheet at z = 0.6 (label 0) continued past x = 2 by a second 2 x 2 m
-    sheet (label 1) turned by deg about the fold line x = 2, z = 0.6 (up: concave,
-    down: convex)."""
-    a = np.radians(deg)
-    X, Y = np.eye(3)[0], np.eye(3)[1]
-    u = np.array([np.cos(a), 0.0, np.sin(a)])
-    n = np.array([-np.sin(a), 0.0, np.cos(a)])
-    parts = [scenes.plane_patch([0, 0, 0.6], X, Y, 2.0, 2.0, 0.05, [0, 0, 1], 0),
-             scenes.plane_patch([2.0, 0, 0.6], u, Y, 2.0, 2.0, 0.05, n, 1)]
-    xyz, nrm, lab, _ = scenes.merge_clouds(parts)
-    return xyz, nrm, lab, n
-
 
 @pytest.mark.parametrize("deg", [5, -5, 11, -11, 20, -20, 40, -40])
 def test_folded_sheet_joins_within_the_join_angle(deg):
     """Two planar sheets meeting along a line join into one surface when their normals
     agree within the join angle (10 degrees) and stay two otherwise (at 11 degrees the
     groups next to the fold still lie within the join distance of each other's plane,
-    so the angle alone keeps them apart); the fold is an
-    exterior edge only when it is convex and at least the edge angle (30 degrees), and
-    then it lies on the fold line with the two sheets' normals."""
-    xyz, nrm, lab, n = _folded_sheet(deg)
+    so the angle alone keeps them apart); the fold is an exterior edge only when it is
+    convex and at least the edge angle (30 degrees), and then it lies on the fold line
+    with the two sheets' normals."""
+    xyz, nrm, lab, n = segclouds.folded_sheet(deg)
     L, E, EL, ns = seg.segment(xyz, nrm, SP)
     if abs(deg) < SP.join_angle_deg:
         assert len(set(L.tolist())) == 1 and len(E) == 0
@@ -136,10 +124,7 @@ def test_folded_sheet_joins_within_the_join_angle(deg):
 def test_offset_sheets_join_within_the_join_distance(dz, surfaces):
     """Two parallel sheets side by side, one raised by dz: within the join distance
     (3 cm) their groups join across the seam, beyond it they are two surfaces."""
-    X, Y = np.eye(3)[0], np.eye(3)[1]
-    parts = [scenes.plane_patch([0, 0, 0.6], X, Y, 1.95, 2.0, 0.05, [0, 0, 1], 0),
-             scenes.plane_patch([2.0, 0, 0.6 + dz], X, Y, 2.0, 2.0, 0.05, [0, 0, 1], 1)]
-    xyz, nrm, lab, _ = scenes.merge_clouds(parts)
+    xyz, nrm, lab = segclouds.offset_sheets(dz)
     L, E, _, _ = seg.segment(xyz, nrm, SP)
     assert len(set(L.tolist())) == surfaces and len(E) == 0
     if surfaces == 2:
@@ -151,24 +136,16 @@ def test_small_boxes_have_no_edges(size, edges):
     """A box on a floor: a face needs edge_min_groups (4) planar subvoxel groups before
     its edges count, so boxes of a subvoxel or two across give none, and a 1 m box gives
     its eight exterior edges (four vertical, four on top; the floor's are concave)."""
-    X, Y = np.eye(3)[0], np.eye(3)[1]
-    lo = np.array([0.4, 0.4, 0.0])
-    parts = [scenes.plane_patch([-1, -1, 0], X, Y, 3.0, 3.0, 0.05, [0, 0, 1], 0)]
-    parts += scenes._box_parts(lo, lo + size, 0.05, 1, 0)
-    xyz, nrm, _, _ = scenes.merge_clouds(parts)
+    xyz, nrm, _ = segclouds.box_on_floor(size)
     _, E, _, _ = seg.segment(xyz, nrm, SP)
     assert len(E) == edges
 
 
 def test_surfaces_are_numbered_by_their_first_subvoxel():
     """Surface numbers follow each surface's first subvoxel group in (voxel, subvoxel)
-    order, whatever its other groups: sheet A (x in [0, 1], y in [0, 4]) starts in the
-    first grid row before sheet B (x in [3, 4], y in [0, 1]), so A's number is lower,
-    although B's last subvoxel comes long before A's."""
-    X, Y = np.eye(3)[0], np.eye(3)[1]
-    parts = [scenes.plane_patch([0, 0, 0.6], X, Y, 1.0, 4.0, 0.05, [0, 0, 1], 0),
-             scenes.plane_patch([3.0, 0, 0.6], X, Y, 1.0, 1.0, 0.05, [0, 0, 1], 1)]
-    xyz, nrm, lab, _ = scenes.merge_clouds(parts)
+    order, whatever its other groups: sheet A starts in the first grid row before
+    sheet B, so A's number is lower, although B's last subvoxel comes long before A's."""
+    xyz, nrm, lab = segclouds.two_sheets_in_row_order()
     L, _, _, _ = seg.segment(xyz, nrm, SP)
     assert _partition_matches(L, lab)
     assert L[lab == 0][0] < L[lab == 1][0]

@@ -19,7 +19,10 @@ Parity pins (tests/test_oracle_pins.py):
 - the first Fresnel zone radius of the duplicate removal, just inside and just outside;
 - Eq. 1's Gaussian weights on two points (a tanh profile), the image-method paths with
   faces turned away, the self-hit rule of the visibility test, the lattice's equal-area
-  zones and golden-angle turns, and delay = length / c.
+  zones and golden-angle turns, and delay = length / c;
+- the depth limits, the LOS miss against the brute-force nearest launch axis, the rho /
+  delta validity rule, diffractions refined off their edge, the shortest path per label
+  sequence, and the image method with an occluding panel.
 tests/test_oracle_mutants.py plants one mistake at a time in a copy of the source and
 checks that these pins catch it.  The secant placement after a sign change of f is
 reached by no pinned scene.

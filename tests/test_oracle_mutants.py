@@ -73,6 +73,29 @@ MUTANTS = [
      "ex.delay = L / C_LIGHT;", "ex.delay = L / (C_LIGHT * (1.0 + 1e-9));", TINY),
     ("kappa_farthest_first",           # Section 2.2.3: kappa keeps the farthest cone axes
      "if (a.miss != b.miss) return a.miss < b.miss;", "if (a.miss != b.miss) return a.miss > b.miss;", "kappa"),
+    ("separation_plane_behind",        # Section 2.2.4: children behind the surface
+     "if (c.kind == CONE_REFLECT) return dot(r, c.pn) > s.p.sep_eps;",
+     "if (c.kind == CONE_REFLECT) return dot(r, c.pn) < -s.p.sep_eps;", TINY),
+    ("separation_margin_dropped",      # children on the apex's own tangent plane accepted
+     "if (c.kind == CONE_REFLECT) return dot(r, c.pn) > s.p.sep_eps;",
+     "if (c.kind == CONE_REFLECT) return dot(r, c.pn) > -s.p.sep_eps;", TINY),
+    ("child_direction_from_tx",        # incoming direction of a child taken from the TX
+     "          ch.in_dir = unit(ie.rp - nd.apex);", "          ch.in_dir = unit(ie.rp - store[0].apex);", TINY),
+    ("reflection_limit_plus_one",      # one reflection more than allowed
+     "if (ch.nr > p.max_refl || ch.nd > p.max_diff) continue;",
+     "if (ch.nr > p.max_refl + 1 || ch.nd > p.max_diff) continue;", "reflection_limit"),
+    ("los_keeps_largest_miss",         # LOS miss from the farthest launch axis
+     "if (it == los.end() || h.second < it->second) los[h.first] = h.second;",
+     "if (it == los.end() || h.second > it->second) los[h.first] = h.second;", "los_miss"),
+    ("off_edge_check_dropped",         # Section 2.3: diffraction points beyond the edge kept
+     "        if (along < 0.0 || along > elen[k]) {", "        if (false) {", "leaving"),
+    ("delta_validity_dropped",         # Section 2.3: paths kept whatever their gradient
+     "  if (!(gn < p.delta)) { ex.status = ST_NOT_CONVERGED; return ex; }", "", "rho_iterations"),
+    ("label_dedup_keeps_longest",      # Section 2.3: the longest path per label sequence
+     "    if (a.length != b.length) return a.length < b.length;\n    return ie_less(a, b);",
+     "    if (a.length != b.length) return a.length > b.length;\n    return ie_less(a, b);", "label_dedup"),
+    ("fresnel_any_chain",              # Section 2.3: Fresnel zones across interaction chains
+     "      if (!same_chain) continue;", "", "fresnel_zone_radius"),
     ("fresnel_radius_misplaced_root",  # Section 2.3: sqrt(lambda a b) / (a + b)
      "double r = std::sqrt(lambda * ak * bk / (ak + bk));", "double r = std::sqrt(lambda * ak * bk) / (ak + bk);",
      "fresnel_zone_radius"),

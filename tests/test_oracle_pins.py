@@ -82,6 +82,134 @@ def test_image_method_with_surfaces_facing_away(room_tiny, flipped):
         assert abs(length - ref[lab][1]) <= 1e-9 * ref[lab][1]
 
 
+def test_reflection_limit_below_interaction_limit(room_tiny):
+    """The depth limits count reflections and diffractions apart: at most one
+    reflection and one diffraction (two interactions) on the box room, which has no
+    edges, leaves LOS and the six single reflections of the image method."""
+    p = config.params_for(room_tiny, max_refl=1, max_diff=1, grad_stop=1e-9)
+    assert p.max_interactions == 2
+    _, _, e = oracle.run(room_tiny, p)
+    ref = image_paths(box_room_planes(10.0, 10.0, 3.0), room_tiny.tx[0], room_tiny.rx[0], max_order=1)
+    got = _exact_by_labels(e.paths())
+    assert set(k[2] for k in got) == set(ref) and len(ref) == 7
+
+
+def test_rho_iterations_then_delta(room_tiny):
+    """Section 2.3: once rho iterations are reached a path is valid only if its
+    gradient norm is below delta.  Three iterations leave every reflection path of the
+    box room far from stationary (gradient norms up to 0.3), so only LOS remains and
+    every refined reflection path is reported not converged."""
+    p = config.params_for(room_tiny, rho=3)
+    _, _, e = oracle.run(room_tiny, p)
+    P, A = e.paths(), e.paths(all_refined=True)
+    assert [int(n) for n in P["n"]] == [0]
+    refl = A["n"] > 0
+    assert refl.sum() > 100
+    assert all(oracle.STATUS[int(st)] == "not_converged" for st in A["status"][refl])
+    assert np.all(A["grad"][refl] >= p.delta)
+
+
+def test_label_dedup_keeps_the_shortest(room_tiny):
+    """Label-based duplicate removal (Section 2.3) keeps, per TX/RX pair, only the
+    shortest path of each interaction and label combination: with the walls x = 0 and
+    y = 0 sharing label 0, each merged label sequence keeps its shortest image path
+    (20 of the 25)."""
+    lab = room_tiny.label.copy()
+    lab[lab == 2] = 0
+    sc = scenes.Scene("room_tiny_merged", room_tiny.xyz, room_tiny.nrm, lab, room_tiny.material,
+                      tx=room_tiny.tx, rx=room_tiny.rx, max_refl=2, max_diff=0)
+    _, _, e = oracle.run(sc, config.params_for(sc, grad_stop=1e-9))
+    best = {}
+    for seq, (pts, L) in image_paths(box_room_planes(10.0, 10.0, 3.0), sc.tx[0], sc.rx[0], max_order=2).items():
+        k = tuple(0 if l == 2 else l for l in seq)
+        if k not in best or L < best[k][1]:
+            best[k] = (pts, L)
+    got = _exact_by_labels(e.paths())
+    assert len(best) == 20 and set(k[2] for k in got) == set(best)
+    for (t, r, k), (pts, length, types) in got.items():
+        np.testing.assert_allclose(pts, best[k][0], atol=1e-6)
+        assert abs(length - best[k][1]) <= 1e-9 * best[k][1]
+
+
+def test_los_miss_is_the_nearest_launch_axis(tiny_run):
+    """The LOS coarse path keeps the smallest miss over the launch cones that see the
+    RX: by brute force over the whole lattice, the smallest distance of the RX from a
+    launch axis pointing its way."""
+    sc, p, s, c, e = tiny_run
+    C = c.paths()
+    los = [i for i in range(len(C["n"])) if C["n"][i] == 0]
+    assert len(los) == 1
+    d = oracle.fibonacci(p.launch_count)
+    r = sc.rx[0] - sc.tx[0]
+    along = d @ r
+    perp = np.linalg.norm(r[None, :] - along[:, None] * d, axis=1)
+    assert C["miss"][los[0]] == pytest.approx(perp[along > 0].min(), abs=1e-12)
+
+
+@pytest.mark.parametrize("z_tx,z_rx,on_edge", [(2.6, 3.36, True), (2.6, 3.44, False), (2.8, 3.36, False)])
+def test_diffraction_leaving_its_edge_is_dropped(z_tx, z_rx, on_edge):
+    """The wedge's edge ends at z = 3: a TX and an RX whose Keller point lies just
+    beyond it (z = 3.02, 3.08) get a coarse diffraction path whose refinement walks off
+    the edge, and no exact path; with the Keller point at z = 2.98 the path is there at
+    its closed form."""
+    import dataclasses
+    sc = dataclasses.replace(scenes.wedge(z_tx=z_tx, z_rx=z_rx), region=np.array([[-4.0, -4.0, 0.0], [1.5, 1.5, 4.0]]))
+    _, c, e = oracle.run(sc, config.params_for(sc, grad_stop=1e-10))
+    assert len(c.paths()["n"]) == 1
+    P, A = e.paths(), e.paths(all_refined=True)
+    if on_edge:
+        assert len(P["n"]) == 1
+        np.testing.assert_allclose(P["pts"][0][0], [0.0, 0.0, (z_tx + z_rx) / 2.0], atol=1e-6)
+    else:
+        assert len(P["n"]) == 0 and oracle.STATUS[int(A["status"][0])] == "off_edge"
+
+
+def test_image_method_with_an_occluding_panel(room_tiny):
+    """The box room with a free-standing 1.8 x 2 m panel (label 6) at x = 4 between TX
+    and RX: the image-method paths whose segments all pass the panel at least 0.3 m
+    outside its border are found at their image points, and none whose segment crosses
+    the panel is found (LOS among them).  Paths within 0.3 m of the panel's border are
+    not judged: the point set's implicit surface reaches a little past its last row."""
+    Y, Z = np.eye(3)[1], np.eye(3)[2]
+    x0, y0, y1, z0, z1 = 4.0, 3.6, 5.4, 0.5, 2.5
+    panel = scenes.plane_patch([x0, y0, z0], Y, Z, y1 - y0, z1 - z0, 0.1, [-1, 0, 0], 6)
+    rt = room_tiny
+    xyz, nrm, lab, mat = scenes.merge_clouds([(rt.xyz, rt.nrm, rt.label, rt.material), panel])
+    sc = scenes.Scene("room_panel", xyz, nrm, lab, mat, tx=rt.tx, rx=rt.rx, max_refl=2, max_diff=0)
+    _, _, e = oracle.run(sc, config.params_for(sc, grad_stop=1e-9))
+    planes = box_room_planes(10.0, 10.0, 3.0) + [(0, x0, 6, np.array([x0, y0, z0]), np.array([x0, y1, z1]))]
+    ref = image_paths(planes, sc.tx[0], sc.rx[0], max_order=2)
+
+    def inside(q):            # signed distance of a point of the plane x = x0 inside the panel
+        return min(q[1] - y0, y1 - q[1], q[2] - z0, z1 - q[2])
+
+    clear, blocked, near = {}, set(), set()
+    for seq, (pts, L) in ref.items():
+        nodes = [sc.tx[0]] + list(pts) + [sc.rx[0]]
+        cross = []
+        for a, b in zip(nodes[:-1], nodes[1:]):
+            if (a[0] - x0) * (b[0] - x0) < 0:
+                cross.append(inside(a + (x0 - a[0]) / (b[0] - a[0]) * (b - a)))
+        on_panel = [inside(pts[k]) for k in range(len(seq)) if seq[k] == 6]
+        if any(d > 0 for d in cross):
+            blocked.add(seq)
+        elif all(d < -0.3 for d in cross) and all(d > 0.3 for d in on_panel):
+            clear[seq] = (pts, L)
+        else:
+            near.add(seq)
+    assert () in blocked and len(clear) >= 8 and len(blocked) >= 4
+    got = {k[2]: v for k, v in _exact_by_labels(e.paths()).items()}
+    assert not blocked & set(got)
+    assert set(clear) <= set(got)
+    for k, (pts, length, types) in got.items():
+        if k in clear:
+            np.testing.assert_allclose(pts, clear[k][0], atol=1e-6)
+            assert abs(length - clear[k][1]) <= 1e-9 * clear[k][1]
+        elif k not in near:   # a panel reflection the image method bounds out: within the border's reach
+            kp = [q for q, l in zip(pts, k) if l == 6]
+            assert kp and all(abs(inside(q)) < 0.3 for q in kp), k
+
+
 def test_image_method_room_tiny_paper_launch(room_tiny):
     """The paper's own transmission phase (a ray toward every IE and RX, Section 2.2.2)
     finds the same 25 image-method paths in the sampled box room."""

@@ -4,6 +4,7 @@ import pytest
 
 import oracle
 from paper_2402_13747_b300 import config, scenes
+from tests import cases
 from tests.imagemethod import box_room_planes, corner_on_floor_mixed_path, image_paths
 from tests.pathsets import compare, keyed
 
@@ -132,6 +133,57 @@ def test_reflection_and_diffraction(ctx, z_tx, z_rx):
     assert tuple(G["type"][i][:2]) == types
     np.testing.assert_allclose(G["pts"][i][:2], want, atol=1e-3)
     assert abs(G["length"][i] - L) <= 1e-6 * L
+
+
+@pytest.mark.parametrize("case", ["panel", "merged_labels", "rho3", "refl1_diff1", "edge_end_inside",
+                                  "edge_end_beyond"])
+def test_pinned_cases_match_oracle(ctx, room_tiny, case):
+    """The scenes of the oracle's refinement and visibility pins, on the CUDA path: the
+    oracle's path set exactly (points 1e-3 m, lengths 1e-6 relative), and each case's
+    own expectation -- no path through the occluding panel (LOS among them), the
+    shortest path per merged label sequence, only LOS after three iterations, only
+    first-order paths under a one-reflection limit, a Keller point on the edge and none
+    beyond its end."""
+    if case == "panel":
+        sc, kw = cases.room_with_panel(room_tiny), {}
+    elif case == "merged_labels":
+        sc, kw = cases.room_with_merged_labels(room_tiny), {}
+    elif case == "rho3":
+        sc, kw = room_tiny, {"rho": 3}
+    elif case == "refl1_diff1":
+        sc, kw = room_tiny, {"max_refl": 1, "max_diff": 1}
+    else:
+        sc, kw = cases.tall_wedge(2.6, 3.36 if case == "edge_end_inside" else 3.44), {}
+    p = config.params_for(sc, **kw)
+    G = ctx.run(sc, p)
+    _, _, e = oracle.run(sc, p)
+    cmp = compare(G, e.paths(), atol_pts=1e-3, rtol_len=1e-6)
+    assert cmp["bad"] == [], cmp
+    labels = {tuple(int(l) for l in G["label"][i][:G["n"][i]]) for i in range(len(G["n"]))}
+    if case == "panel":
+        # FP32 against FP64 may decide the paths within the implicit surface's reach of
+        # the panel's border either way; every other path is the same on both sides,
+        # and none that crosses the panel is found
+        g, r = keyed(G), keyed(e.paths())
+        for k in cmp["only_gpu"] + cmp["only_ref"]:
+            pts = (g[k] if k in g else r[k])[0]
+            assert cases.panel_margin(sc.tx[0], sc.rx[0], k[3], pts)[1] < 0.3, (k, cmp)
+        for k, (pts, L) in g.items():   # through the panel, past its last rows' reach
+            assert cases.panel_margin(sc.tx[0], sc.rx[0], k[3], pts)[0] < 0.05, k
+        assert () not in labels and cmp["n_common"] >= 8
+        return
+    assert cmp["only_gpu"] == [] and cmp["only_ref"] == [], cmp
+    if case == "merged_labels":
+        assert len(labels) == 20
+    elif case == "rho3":
+        assert labels == {()}
+    elif case == "refl1_diff1":
+        assert len(labels) == 7 and all(len(k) <= 1 for k in labels)
+    elif case == "edge_end_inside":
+        assert len(G["n"]) == 1
+        np.testing.assert_allclose(G["pts"][0][0], [0.0, 0.0, 2.98], atol=1e-3)
+    else:
+        assert len(G["n"]) == 0
 
 
 def test_noisy_room_subset_matches_oracle(ctx):

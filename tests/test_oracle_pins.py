@@ -13,6 +13,7 @@ import pytest
 
 import oracle
 from paper_2402_13747_b300 import config, scenes
+from tests import cases
 from tests.imagemethod import box_room_planes, corner_on_floor_mixed_path, image_paths
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -114,10 +115,7 @@ def test_label_dedup_keeps_the_shortest(room_tiny):
     shortest path of each interaction and label combination: with the walls x = 0 and
     y = 0 sharing label 0, each merged label sequence keeps its shortest image path
     (20 of the 25)."""
-    lab = room_tiny.label.copy()
-    lab[lab == 2] = 0
-    sc = scenes.Scene("room_tiny_merged", room_tiny.xyz, room_tiny.nrm, lab, room_tiny.material,
-                      tx=room_tiny.tx, rx=room_tiny.rx, max_refl=2, max_diff=0)
+    sc = cases.room_with_merged_labels(room_tiny)
     _, _, e = oracle.run(sc, config.params_for(sc, grad_stop=1e-9))
     best = {}
     for seq, (pts, L) in image_paths(box_room_planes(10.0, 10.0, 3.0), sc.tx[0], sc.rx[0], max_order=2).items():
@@ -152,8 +150,7 @@ def test_diffraction_leaving_its_edge_is_dropped(z_tx, z_rx, on_edge):
     beyond it (z = 3.02, 3.08) get a coarse diffraction path whose refinement walks off
     the edge, and no exact path; with the Keller point at z = 2.98 the path is there at
     its closed form."""
-    import dataclasses
-    sc = dataclasses.replace(scenes.wedge(z_tx=z_tx, z_rx=z_rx), region=np.array([[-4.0, -4.0, 0.0], [1.5, 1.5, 4.0]]))
+    sc = cases.tall_wedge(z_tx, z_rx)
     _, c, e = oracle.run(sc, config.params_for(sc, grad_stop=1e-10))
     assert len(c.paths()["n"]) == 1
     P, A = e.paths(), e.paths(all_refined=True)
@@ -170,12 +167,8 @@ def test_image_method_with_an_occluding_panel(room_tiny):
     outside its border are found at their image points, and none whose segment crosses
     the panel is found (LOS among them).  Paths within 0.3 m of the panel's border are
     not judged: the point set's implicit surface reaches a little past its last row."""
-    Y, Z = np.eye(3)[1], np.eye(3)[2]
-    x0, y0, y1, z0, z1 = 4.0, 3.6, 5.4, 0.5, 2.5
-    panel = scenes.plane_patch([x0, y0, z0], Y, Z, y1 - y0, z1 - z0, 0.1, [-1, 0, 0], 6)
-    rt = room_tiny
-    xyz, nrm, lab, mat = scenes.merge_clouds([(rt.xyz, rt.nrm, rt.label, rt.material), panel])
-    sc = scenes.Scene("room_panel", xyz, nrm, lab, mat, tx=rt.tx, rx=rt.rx, max_refl=2, max_diff=0)
+    x0, (y0, y1), (z0, z1) = cases.PANEL_X, cases.PANEL_Y, cases.PANEL_Z
+    sc = cases.room_with_panel(room_tiny)
     _, _, e = oracle.run(sc, config.params_for(sc, grad_stop=1e-9))
     planes = box_room_planes(10.0, 10.0, 3.0) + [(0, x0, 6, np.array([x0, y0, z0]), np.array([x0, y1, z1]))]
     ref = image_paths(planes, sc.tx[0], sc.rx[0], max_order=2)

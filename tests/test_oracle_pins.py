@@ -166,7 +166,8 @@ def test_image_method_with_an_occluding_panel(room_tiny):
     and RX: the image-method paths whose segments all pass the panel at least 0.3 m
     outside its border are found at their image points, and none whose segment crosses
     the panel is found (LOS among them).  Paths within 0.3 m of the panel's border are
-    not judged: the point set's implicit surface reaches a little past its last row."""
+    left out of the comparison: the point set's implicit surface reaches a little past its
+    last row."""
     x0, (y0, y1), (z0, z1) = cases.PANEL_X, cases.PANEL_Y, cases.PANEL_Z
     sc = cases.room_with_panel(room_tiny)
     _, _, e = oracle.run(sc, config.params_for(sc, grad_stop=1e-9))

@@ -182,17 +182,18 @@ def rank_scene(rank: int):
     return sc
 
 
-def reduce_over_ranks(t_total: float, cones: float, paths: float, device):
+def reduce_over_ranks(t_total: float, cones: float, paths: float, device, *more: float):
     """Whole-job figures after the timed region: the slowest rank's time and the
-    units of all ranks (the only collectives; none on the data path)."""
+    units of all ranks -- cones, paths and any further counts -- (the only
+    collectives; none on the data path)."""
     import torch
     import torch.distributed as dist
-    t = torch.tensor([t_total, cones, paths], dtype=torch.float64, device=device)
+    t = torch.tensor([t_total, cones, paths, *more], dtype=torch.float64, device=device)
     tmax = t[:1].clone()
     dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
     units = t[1:].clone()
     dist.all_reduce(units, op=dist.ReduceOp.SUM)
-    return float(tmax[0]), float(units[0]), float(units[1])
+    return (float(tmax[0]),) + tuple(float(u) for u in units)
 
 
 def main():
@@ -279,8 +280,9 @@ def main():
     t_total = sum(ms) / 1e3
     cones = sum(c["n_cones"] for c in counts)
     paths = sum(c["n_paths"] for c in counts)
+    vis = sum(c["n_vis"] for c in counts)
     if world > 1:
-        t_total, cones, paths = reduce_over_ranks(t_total, cones, paths, dev)
+        t_total, cones, paths, vis = reduce_over_ranks(t_total, cones, paths, dev, vis)
     c0 = counts[-1]
     value = cones / t_total
     exact_ps = paths / t_total
@@ -409,6 +411,7 @@ def main():
                           "tuning": {k: v for k, v in tuning.items() if not k.endswith("_ms")},
                           "tuning_sample": "all TX x 4 RX of the workload"},
                "exact_paths_per_s": exact_ps, "exact_paths_per_step": paths / args.steps / world,
+               "visibility_rays_per_s": vis / t_total,
                "cones_per_step": cones / args.steps / world, "wall_s_timed_region": wall,
                "plain": plain, "latency": latency, "segment": segment, "roofline": roof, "cpu_baseline": cpu,
                "e2e": e2e,

@@ -27,8 +27,8 @@ def _rank_main(rank, world, port, out):
     try:
         sc = bench.rank_scene(rank)
         # per-rank figures as the timed loop would produce them
-        t_total, cones, paths = 1.0 + rank, 1000.0 * (rank + 1), 10.0 * (rank + 1)
-        res = bench.reduce_over_ranks(t_total, cones, paths, torch.device("cpu"))
+        t_total, cones, paths, vis = 1.0 + rank, 1000.0 * (rank + 1), 10.0 * (rank + 1), 5e4 * (rank + 1)
+        res = bench.reduce_over_ranks(t_total, cones, paths, torch.device("cpu"), vis)
         dist.barrier()
         out[rank] = (res, sc.tx.copy(), sc.rx.copy(), int(sc.xyz.shape[0]))
     finally:
@@ -45,7 +45,7 @@ def test_two_ranks_reduce_and_draw_their_own_pairs():
         res0, tx0, rx0, n0 = out[0]
         res1, tx1, rx1, n1 = out[1]
     # max over ranks for the time, sums for the units, identical on every rank
-    assert res0 == res1 == (2.0, 3000.0, 30.0)
+    assert res0 == res1 == (2.0, 3000.0, 30.0, 150000.0)
     # same geometry, different seeded pairs, same pair count (fixed work per rank)
     assert n0 == n1
     assert tx0.shape == tx1.shape == (4, 3) and rx0.shape == rx1.shape == (16, 3)

@@ -115,3 +115,26 @@ def test_param_blocks():
     assert v.has_region == 1 and list(v.region_max) == [1, 2, 3]
     r = _abi.refine_params(p)
     assert r.rho == 2000 and r.delta == 1e-4
+
+
+def test_error_codes_without_a_context(lib):
+    """The boundary's error behaviour, with no device work: a device index no machine
+    has is an argument error that leaves no context; every entry point refuses a null
+    context with NIMBUS_ERR_ARG (no crash, no exception); the null context has an error
+    text; the launch counter reads without a context."""
+    from paper_2402_13747_b300 import _abi
+    ctx = C.c_void_p(12345)
+    assert lib.nimbus_create(C.byref(ctx), 1 << 20, 0) == _abi.ERR_ARG
+    assert ctx.value is None
+    assert lib.nimbus_last_error(None) == b"null context"
+    pointer_types = (C.c_void_p, C.c_char_p)
+    for name in _abi.EXPORTS:
+        if name in ("nimbus_create", "nimbus_last_error", "nimbus_kernel_launches"):
+            continue
+        f = getattr(lib, name)
+        args = [None if (t in pointer_types or hasattr(t, "contents") or t.__name__.startswith("LP_")) else t(0)
+                for t in f.argtypes]
+        assert f(*args) == _abi.ERR_ARG, name
+    n = C.c_int64(-1)
+    assert lib.nimbus_kernel_launches(None) == _abi.ERR_ARG
+    assert lib.nimbus_kernel_launches(C.byref(n)) == _abi.OK and n.value >= 0

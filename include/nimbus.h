@@ -195,8 +195,15 @@ typedef struct {
   int32_t* march;           /* [n_cells] capped L-infinity distance to the nearest voxel with IEs */
 } nimbus_scene_view;
 
-/* Context on CUDA device `device` with a device-memory budget in bytes
- * (0 = 90% of the free memory).  out receives the context. */
+/* Contexts (operational; the paper has no counterpart).
+ * nimbus_create: a context on CUDA device `device` with a device-memory budget in
+ * bytes (0 = 90% of the free memory); *out receives it, owned by the caller until
+ * nimbus_destroy.  NIMBUS_ERR_ARG for a NULL out or a device index this machine does
+ * not have (then *out = NULL); NIMBUS_ERR_CUDA when the device cannot be queried.
+ * nimbus_destroy: releases every scene, coarse set and path set of the context,
+ * synchronises its device and frees the context; NIMBUS_ERR_ARG for NULL.
+ * nimbus_last_error: the text of the context's last error, valid until the next call
+ * on that context ("null context" for NULL). */
 NIMBUS_API int nimbus_create(nimbus_ctx** out, int device, size_t mem_budget_bytes);
 NIMBUS_API int nimbus_destroy(nimbus_ctx* ctx);
 NIMBUS_API const char* nimbus_last_error(nimbus_ctx* ctx);
@@ -210,10 +217,13 @@ NIMBUS_API const char* nimbus_last_error(nimbus_ctx* ctx);
 NIMBUS_API int nimbus_voxelize(nimbus_ctx* ctx, const nimbus_cloud* cloud, const nimbus_edges* edges,
                     const nimbus_vox_params* params, nimbus_handle* scene_out, void* stream);
 
-/* Dynamic scenes: drop the points of the scene whose position lies inside the
- * box [aabb_min, aabb_max] and add `replacement` (may be NULL or empty), then
- * rebuild the scene's tables in place on the same grid.  The result equals a
- * full nimbus_voxelize of the updated cloud on that grid. */
+/* Dynamic scenes (the paper treats static clouds; the tables rebuilt are those of
+ * Section 2.1): drop the points of the scene whose position lies inside the box
+ * [aabb_min, aabb_max] (metres, world frame) and add `replacement` (host or device
+ * arrays, copied; may be NULL or empty), then rebuild the scene's tables in place on
+ * the same grid.  The result equals a full nimbus_voxelize of the updated cloud on
+ * that grid.  NIMBUS_ERR_ARG for a NULL box, NIMBUS_ERR_STATE for a handle that is
+ * not a scene of ctx, NIMBUS_ERR_OOM past the budget. */
 NIMBUS_API int nimbus_update_region(nimbus_ctx* ctx, nimbus_handle scene, const double aabb_min[3],
                          const double aabb_max[3], const nimbus_cloud* replacement, void* stream);
 
@@ -238,32 +248,49 @@ NIMBUS_API int nimbus_trace_coarse(nimbus_ctx* ctx, nimbus_handle scene, const d
 NIMBUS_API int nimbus_refine(nimbus_ctx* ctx, nimbus_handle scene, nimbus_handle coarse,
                   const nimbus_refine_params* params, nimbus_handle* paths_out, void* stream);
 
-/* Exact paths: counts (required) and, when view != NULL, the paths.  which = 0:
- * paths after duplicate removal; 1: every refined coarse path with its status.
- * Synchronises the stream. */
+/* The exact paths of Section 2.3 (per path: TX and RX index, interaction types,
+ * labels, materials and entities, FP64 interaction points, length, delay = length /
+ * c, final gradient norm, iterations and status; layouts in nimbus_path_view):
+ * counts (required) and, when view != NULL, the paths copied into the caller's host
+ * arrays, sized from a call with view == NULL.  which = 0: paths after duplicate
+ * removal, in delay order; 1: every refined coarse path with its status.
+ * Synchronises the stream.  NIMBUS_ERR_ARG for a NULL counts, NIMBUS_ERR_STATE for
+ * a handle that is not a path set of ctx. */
 NIMBUS_API int nimbus_query(nimbus_ctx* ctx, nimbus_handle paths, int32_t which, nimbus_path_counts* counts,
                  const nimbus_path_view* view, void* stream);
 
-/* Coarse paths after the kappa limit: counts and, when view != NULL, the paths. */
+/* The coarse paths of Section 2.2.3 after the kappa limit (TX, RX, interaction
+ * entities, types and labels, miss distance of the last cone axis from the RX;
+ * layouts in nimbus_coarse_view): counts (required) and, when view != NULL, the paths
+ * copied into the caller's host arrays.  Synchronises the stream.  NIMBUS_ERR_ARG for
+ * a NULL counts, NIMBUS_ERR_STATE for a handle that is not a coarse set of ctx. */
 NIMBUS_API int nimbus_query_coarse(nimbus_ctx* ctx, nimbus_handle coarse, nimbus_path_counts* counts,
                         const nimbus_coarse_view* view, void* stream);
 
-/* Grid and table sizes of a scene: origin[3], dims[3], number of entities. */
+/* Grid and table sizes of a scene (Section 2.1): origin[3] in metres, dims[3] in
+ * voxels, the number of entities and of grouped points; any output may be NULL.
+ * NIMBUS_ERR_STATE for a handle that is not a scene of ctx. */
 NIMBUS_API int nimbus_scene_info(nimbus_ctx* ctx, nimbus_handle scene, double origin[3], int32_t dims[3],
                       int64_t* n_ie, int64_t* n_points);
 
-/* Copy a scene's entity and voxel tables into caller-owned host arrays. */
+/* Copy a scene's entity and voxel tables (Section 2.1; layouts in
+ * nimbus_scene_view, sized by nimbus_scene_info) into caller-owned host arrays.
+ * Synchronises the stream.  NIMBUS_ERR_ARG for a NULL view, NIMBUS_ERR_STATE for a
+ * handle that is not a scene of ctx. */
 NIMBUS_API int nimbus_scene_tables(nimbus_ctx* ctx, nimbus_handle scene, const nimbus_scene_view* view,
                         void* stream);
 
-/* Free a scene, coarse set or path set. */
+/* Free a scene, coarse set or path set (operational; the paper has no counterpart).
+ * NIMBUS_ERR_STATE for a handle ctx does not hold. */
 NIMBUS_API int nimbus_release(nimbus_ctx* ctx, nimbus_handle h);
 
-/* Bytes of device memory the context currently holds. */
+/* Bytes of device memory the context currently holds (operational; the paper has no
+ * counterpart).  NIMBUS_ERR_ARG for a NULL argument. */
 NIMBUS_API int nimbus_memory_used(nimbus_ctx* ctx, size_t* bytes);
 
 /* Number of CUDA kernels this library has launched in this process so far (all
- * contexts); differences around a region count the kernels launched in it. */
+ * contexts); differences around a region count the kernels launched in it
+ * (operational; the paper has no counterpart).  NIMBUS_ERR_ARG for NULL. */
 NIMBUS_API int nimbus_kernel_launches(int64_t* count);
 
 /* ---------------------------------------------------------------------------

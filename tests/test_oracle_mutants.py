@@ -34,6 +34,26 @@ MUTANTS = [
      "two_points"),
     ("newton_placement_dropped",       # Section 2.2.1: hit placed at the last march point
      "double th = std::fabs(dn) > 1e-3 ? t - f / dn : t;", "double th = t;", "sdf_on_exact_plane"),
+    ("sdf_segment_halved",             # Section 2.2.1: march over half a subvoxel diameter
+     "  const double L = s.hs * std::sqrt(3.0);\n  double tc = dot(ie.bbc - P, d);",
+     "  const double L = 0.5 * s.hs * std::sqrt(3.0);\n  double tc = dot(ie.bbc - P, d);", "subvoxel_diameter"),
+    ("voxel_sphere_halved",            # Section 2.2.4: voxel spheres of half their radius
+     "voxel_center(s, u[0], u[1], u[2]), s.r_vox))", "voxel_center(s, u[0], u[1], u[2]), 0.5 * s.r_vox))",
+     "reflection_and_diffraction"),
+    ("ie_sphere_halved",               # Section 2.2.4: entity spheres of half their radius
+     "if (!cone_sphere(cone.apex, cone.axis, cone.sin_a, cone.cos_a, ie.sc, s.r_sub)) continue;",
+     "if (!cone_sphere(cone.apex, cone.axis, cone.sin_a, cone.cos_a, ie.sc, 0.5 * s.r_sub)) continue;",
+     "reflection_and_diffraction"),
+    ("march_skip_adjacent",            # Section 2.2.4: no evaluation next to occupied voxels
+     "if (ctx.march[cell_of(s, v[0], v[1], v[2])] > 1) return true;",
+     "if (ctx.march[cell_of(s, v[0], v[1], v[2])] > 0) return true;", TINY),
+    ("neighbourhood_reevaluated",      # a cone evaluating one neighbourhood twice
+     "          if (have_last && std::abs(u[0] - last[0]) <= 1", "          if (false && have_last && std::abs(u[0] - last[0]) <= 1",
+     "leaving"),
+    ("keller_fan_half_count",          # Section 2.2.4: half the fan's cones
+     "int M = (int)std::ceil(PI / alpha);", "int M = (int)std::ceil(PI / (2.0 * alpha));", "leaving"),
+    ("keller_cone_flipped",            # Section 2.2.4: fan on the incoming side of the Keller cone
+     "V3 d = cb * w + sb * r;", "V3 d = -cb * w + sb * r;", "leaving"),
     ("binning_by_voxel",               # Section 2.1: points binned by voxel, not subvoxel
      "float t = diff / s.hs32;", "float t = diff / (2.0f * s.hs32);", "voxel_membership"),
     ("march_field_six_neighbours",     # Section 2.2.4: L1 instead of L-infinity distance

@@ -451,6 +451,28 @@ def test_sdf_weights_two_points_closed_form():
             np.testing.assert_allclose(n, [0, 0, 1], atol=1e-12)
 
 
+def test_sdf_hit_marches_one_subvoxel_diameter(room_tiny):
+    """Section 2.2.1: the march covers a segment one subvoxel diameter long (h_s sqrt 3)
+    centred on the projection of the point set's bounding-box centre onto the ray.
+    Rays 10 degrees above a floor entity's plane meet it 0.049 to 0.197 m along the ray
+    from that projection -- found, at the exact plane crossing -- or 0.246 and 0.295 m
+    from it, beyond the half length of 0.2165 m -- no intersection."""
+    p = config.Params()
+    s = oracle.Scene.from_scene(room_tiny, p)
+    I = s.ies()
+    k = np.where((I["label"] == 4) & (I["prange"][:, 1] >= 9))[0][0]
+    th = math.radians(10.0)
+    d = np.array([math.cos(th), 0.0, -math.sin(th)])
+    for delta, found in ((0.05, True), (0.15, True), (0.2, True), (0.25, False), (0.3, False)):
+        assert (delta * math.cos(th) < 0.5 * p.voxel_size / p.dv * math.sqrt(3.0)) == found
+        P = I["bbc"][k] + np.array([delta, 0.0, 0.0]) - 2.0 * d     # 2 m back from the plane crossing
+        t = s.sdf_hit(k, P, d)
+        if found:
+            assert t == pytest.approx(2.0, abs=1e-9)
+        else:
+            assert t is None
+
+
 def test_cone_sphere_against_sampling():
     rng = np.random.default_rng(5)
     checked = 0

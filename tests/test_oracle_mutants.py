@@ -116,6 +116,15 @@ MUTANTS = [
      "    if (a.length != b.length) return a.length > b.length;\n    return ie_less(a, b);", "label_dedup"),
     ("fresnel_any_chain",              # Section 2.3: Fresnel zones across interaction chains
      "      if (!same_chain) continue;", "", "fresnel_zone_radius"),
+    ("kappa_plus_one",                 # Section 2.2.3: kappa + 1 coarse paths kept
+     "for (size_t q = g; q < h && (int)(q - g) < p.kappa; ++q)",
+     "for (size_t q = g; q < h && (int)(q - g) <= p.kappa; ++q)", "kappa"),
+    ("fresnel_longest_first",          # Section 2.3: Fresnel pass in decreasing delay
+     "    if (qa != qb) return qa < qb;", "    if (qa != qb) return qa > qb;", "fresnel_zone_radius"),
+    ("fresnel_bins_coarse",            # delay ties in 10 cm bins instead of 1 um
+     "long long qa = (long long)std::floor(a.length * 1e6), qb = (long long)std::floor(b.length * 1e6);",
+     "long long qa = (long long)std::floor(a.length * 1e1), qb = (long long)std::floor(b.length * 1e1);",
+     "fresnel_zone_radius"),
     ("fresnel_radius_misplaced_root",  # Section 2.3: sqrt(lambda a b) / (a + b)
      "double r = std::sqrt(lambda * ak * bk / (ak + bk));", "double r = std::sqrt(lambda * ak * bk) / (ak + bk);",
      "fresnel_zone_radius"),

@@ -116,6 +116,9 @@ MUTANTS = [
      "    if (a.length != b.length) return a.length > b.length;\n    return ie_less(a, b);", "label_dedup"),
     ("fresnel_any_chain",              # Section 2.3: Fresnel zones across interaction chains
      "      if (!same_chain) continue;", "", "fresnel_zone_radius"),
+    ("paper_launch_skips_edges",       # Section 2.2.2: the launch toward every IE misses the edges
+     "        const IE& ie = s.ies[id];\n        if (ie.kind == IE_EDGE && !test_edges) continue;",
+     "        const IE& ie = s.ies[id];\n        if (ie.kind == IE_EDGE) continue;", "keller_point"),
     ("kappa_plus_one",                 # Section 2.2.3: kappa + 1 coarse paths kept
      "for (size_t q = g; q < h && (int)(q - g) < p.kappa; ++q)",
      "for (size_t q = g; q < h && (int)(q - g) <= p.kappa; ++q)", "kappa"),

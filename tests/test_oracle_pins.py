@@ -225,15 +225,16 @@ def test_los_length(tiny_run):
     assert got[(0, 0, ())][1] == pytest.approx(math.sqrt(25 + 9), rel=1e-15)
 
 
+@pytest.mark.parametrize("launch_mode", [0, 1])
 @pytest.mark.parametrize("z_tx,z_rx", [(0.5, 2.5), (0.5, 2.0), (2.2, 0.7)])
-def test_keller_point_on_sampled_wedge(z_tx, z_rx):
+def test_keller_point_on_sampled_wedge(z_tx, z_rx, launch_mode):
     """Diffraction at an exterior edge: the refined point is the closed-form Keller point.
 
     TX and RX are both sqrt(10) m from the edge line, so the point divides the
     height difference in the ratio r1/(r1+r2) = 1/2; the path obeys the equal-angle law.
     """
     sc = scenes.wedge(z_tx=z_tx, z_rx=z_rx)
-    p = config.params_for(sc, grad_stop=1e-10)
+    p = config.params_for(sc, grad_stop=1e-10, launch_mode=launch_mode)
     s, c, e = oracle.run(sc, p)
     P = e.paths()
     assert len(P["n"]) == 1

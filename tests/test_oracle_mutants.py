@@ -54,6 +54,18 @@ MUTANTS = [
      "int M = (int)std::ceil(PI / alpha);", "int M = (int)std::ceil(PI / (2.0 * alpha));", "leaving"),
     ("keller_cone_flipped",            # Section 2.2.4: fan on the incoming side of the Keller cone
      "V3 d = cb * w + sb * r;", "V3 d = -cb * w + sb * r;", "leaving"),
+    ("grid_without_pad",               # grid origin without its one-voxel pad
+     "    org[a] = (std::floor(lo[a] / s->h) - 1.0) * s->h;", "    org[a] = (std::floor(lo[a] / s->h) - 0.0) * s->h;",
+     "voxel_membership"),
+    ("reception_point_first_point",    # Section 2.1: reception point = a point, not the centroid
+     "      ie.rp = (1.0 / (double)(j - i)) * sum;  // reception point: centroid",
+     "      ie.rp = s->pts[i];  // reception point: centroid", "rho_iterations"),
+    ("edge_reception_point_at_start",  # an edge entity received at its piece's start, not middle
+     "      ie.rp = E.p0 + tm * (E.p1 - E.p0);", "      ie.rp = E.p0;", "leaving"),
+    ("diffraction_planes_swapped",     # Section 2.2.4: the fan ray's sector outside its planes
+     "if (c.kind == CONE_DIFFRACT) return dot(r, c.tlo) >= 0.0 && dot(r, c.thi) < 0.0 && dot(r, c.rmid) > 0.0;",
+     "if (c.kind == CONE_DIFFRACT) return dot(r, c.tlo) < 0.0 && dot(r, c.thi) >= 0.0 && dot(r, c.rmid) > 0.0;",
+     "leaving"),
     ("binning_by_voxel",               # Section 2.1: points binned by voxel, not subvoxel
      "float t = diff / s.hs32;", "float t = diff / (2.0f * s.hs32);", "voxel_membership"),
     ("march_field_six_neighbours",     # Section 2.2.4: L1 instead of L-infinity distance

@@ -204,6 +204,22 @@ def test_image_method_with_an_occluding_panel(room_tiny):
             assert kp and all(abs(inside(q)) < 0.3 for q in kp), k
 
 
+def test_paths_move_with_the_scene(tiny_run):
+    """Nothing depends on where the scene sits: the box room, its TX and its RX shifted
+    by whole voxels (1, -2, 0.5) m give the same paths, each point shifted by the same
+    amount and each length unchanged."""
+    rt, p, s, c, e = tiny_run
+    shift = np.array([1.0, -2.0, 0.5])
+    moved = scenes.Scene("room_tiny_moved", (rt.xyz.astype(np.float64) + shift).astype(np.float32), rt.nrm,
+                         rt.label, rt.material, tx=rt.tx + shift, rx=rt.rx + shift, max_refl=2, max_diff=0)
+    _, _, e2 = oracle.run(moved, config.params_for(moved, grad_stop=1e-9))
+    a, b = _exact_by_labels(e.paths()), _exact_by_labels(e2.paths())
+    assert a.keys() == b.keys() and len(a) == 25
+    for k in a:
+        np.testing.assert_allclose(b[k][0], a[k][0] + shift, atol=1e-7)
+        assert b[k][1] == pytest.approx(a[k][1], rel=1e-12)
+
+
 def test_image_method_room_tiny_paper_launch(room_tiny):
     """The paper's own transmission phase (a ray toward every IE and RX, Section 2.2.2)
     finds the same 25 image-method paths in the sampled box room."""

@@ -22,8 +22,8 @@ Parity pins (tests/test_oracle_pins.py):
   zones and golden-angle turns, and delay = length / c;
 - the depth limits, the LOS miss against the brute-force nearest launch axis, the rho /
   delta validity rule, diffractions refined off their edge, the shortest path per label
-  sequence, the image method with an occluding panel, and the march's segment of one
-  subvoxel diameter.
+  sequence, the image method with an occluding panel, the march's segment of one
+  subvoxel diameter, and paths that move with the scene.
 tests/test_oracle_mutants.py plants one mistake at a time in a copy of the source and
 checks that these pins catch it.  The secant placement after a sign change of f is
 reached by no pinned scene.

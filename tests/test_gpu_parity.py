@@ -186,6 +186,26 @@ def test_pinned_cases_match_oracle(ctx, room_tiny, case):
         assert len(G["n"]) == 0
 
 
+def test_memory_returns_after_release(ctx, room_tiny):
+    """The context's device-memory accounting: a scene, a coarse set and a path set
+    each hold memory while alive, the scratch of a call is freed by the call itself,
+    and releasing the three returns the context to where it started."""
+    p = config.params_for(room_tiny)
+    ctx.run(room_tiny, p)                      # whatever a first call leaves in place exists from here on
+    before = ctx.memory_used()
+    s = ctx.voxelize_scene(room_tiny, p)
+    held_s = ctx.memory_used()
+    c = ctx.trace(s, room_tiny.tx, room_tiny.rx, p)
+    held_c = ctx.memory_used()
+    P = ctx.refine(s, c, p)
+    held_p = ctx.memory_used()
+    assert before < held_s < held_c < held_p
+    for h in (P, c, s):
+        ctx.release(h)
+    assert ctx.memory_used() == before
+    assert set(ctx.get_tuning()) >= {"level_block", "refine_blocks", "refine_order", "graph"}
+
+
 def test_noisy_room_subset_matches_oracle(ctx):
     """Noisy room with the box: 1 TX x 3 RX, <= 2 reflections + 1 diffraction."""
     full = scenes.room_noisy()

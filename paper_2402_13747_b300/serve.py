@@ -251,10 +251,11 @@ class Server:
                     r.future.set_result(res)
                     with self.lock:
                         self.completed.append(r)
-            except Exception as e:  # report the failure on every request of the batch
+            except Exception as e:  # report the failure on every request of the batch not yet answered
                 for r in batch:
-                    r.t_done = time.perf_counter()
-                    r.future.set_exception(e)
+                    if not r.future.done():
+                        r.t_done = time.perf_counter()
+                        r.future.set_exception(e)
             finally:
                 self.sched.done(est)
 

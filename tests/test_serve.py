@@ -44,6 +44,36 @@ def _server(n_workers=1, delay=0.05, mem=1 << 40, max_pairs=256):
     return srv, log
 
 
+class FailingExecutor(FakeExecutor):
+    """A device call that fails for requests on scene "bad" (an error from the library)."""
+
+    def run(self, batch):
+        if batch[0].scene == "bad":
+            raise RuntimeError("NIMBUS_ERR_OOM: device memory budget exhausted")
+        return super().run(batch)
+
+
+def test_a_failed_batch_reports_its_error_and_the_worker_keeps_serving():
+    """A batch whose device call fails: each of its requests gets the error, the memory
+    it held is returned to the scheduler, and the same worker serves the next batches."""
+    srv = Server({"a": None, "bad": None}, config.Params(), n_workers=1, mem_budget=1 << 40,
+                 executor_factory=lambda: FailingExecutor(0.01))
+    bad = [srv.submit("bad", [0, 0, 0], np.zeros((1, 3)), 2) for _ in range(3)]
+    good = [srv.submit("a", [0, 0, 0], np.zeros((2, 3)), 2) for _ in range(3)]
+    for r in bad:
+        with pytest.raises(RuntimeError, match="NIMBUS_ERR_OOM"):
+            r.future.result(timeout=30)
+    for r in good:
+        assert r.future.result(timeout=30)["id"] == r.id
+    later = srv.submit("a", [0, 0, 0], np.zeros((1, 3)), 2)
+    assert later.future.result(timeout=30)["id"] == later.id
+    end = time.perf_counter() + 5.0          # a batch returns its memory just after its results
+    while srv.sched.in_flight and time.perf_counter() < end:
+        time.sleep(0.01)
+    assert srv.sched.in_flight == 0
+    srv.close()
+
+
 def test_batches_hold_one_scene_and_route_results():
     srv, log = _server(delay=0.1)
     reqs = [srv.submit("a" if i % 2 else "b", [1, 1, 1], np.zeros((2, 3)), 2) for i in range(9)]

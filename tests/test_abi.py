@@ -138,3 +138,30 @@ def test_error_codes_without_a_context(lib):
     n = C.c_int64(-1)
     assert lib.nimbus_kernel_launches(None) == _abi.ERR_ARG
     assert lib.nimbus_kernel_launches(C.byref(n)) == _abi.OK and n.value >= 0
+
+
+def test_a_c_program_links_and_calls_the_library(lib, tmp_path):
+    """A plain C caller: the header compiles as C, the program links against
+    libnimbus.so, and the calls that need no device answer as declared (an absent
+    device is NIMBUS_ERR_ARG and leaves no context; the launch counter reads)."""
+    from paper_2402_13747_b300 import _abi
+    src = tmp_path / "caller.c"
+    src.write_text(textwrap.dedent("""\
+        #include <stdio.h>
+        #include "nimbus.h"
+        int main(void) {
+          nimbus_ctx* ctx = (nimbus_ctx*)1;
+          int rc = nimbus_create(&ctx, 1 << 20, 0);
+          int64_t n = -1;
+          int rl = nimbus_kernel_launches(&n);
+          printf("%d %d %d %lld %s\\n", rc, ctx == NULL, rl, (long long)n, nimbus_last_error(NULL));
+          return 0;
+        }
+        """))
+    exe = tmp_path / "caller"
+    libdir = os.path.dirname(_abi.LIB_PATH)
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src),
+                    os.path.join(libdir, "libnimbus.so"), "-Wl,-rpath," + libdir, "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split(maxsplit=4)
+    assert out[:4] == [str(_abi.ERR_ARG), "1", str(_abi.OK), "0"]
+    assert out[4].strip() == "null context"

@@ -1,24 +1,32 @@
 """Benchmark: the point-cloud ray launcher's whole hot path on synthetic scenes.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload indoor|room_noisy|street]
 
 A step is one pass of the whole path -- voxelisation of the cloud, coarse path
-tracing for every TX/RX pair and refinement with duplicate removal -- over the
-noisy box room: 10x10x3 m at 5 cm (~133k points, 5 mm position noise, 2 degree
-normal tilt), a 1x1x2 m box with 8 exterior edges, 4 TX x 16 RX, up to 3
-reflections and 1 diffraction.  Inputs are resident on the device when the timed
-region starts; L2 is flushed between timed steps (the scene fits in L2).
+tracing for every TX/RX pair (transmission phase, every propagation level, kappa)
+and refinement with duplicate removal -- over one synthetic scene.  The default
+workload is the indoor scan: a 3x2 grid of 8x7x3 m rooms with doorways and 40
+seeded floor boxes, 1.92M points at 3 cm spacing with 1 cm jitter, 8 materials,
+1 TX x 256 RX, up to 3 reflections and 1 diffraction, kappa 100, rho 2000.  Inputs
+are resident on the device when the timed region starts; L2 is flushed between
+timed steps.
 
 Metric: rays/s = cones traced (uniform TX launch + every propagation level +
-Keller fans) per second of step time, with exact paths/s beside it, the batched
-form (all pairs in one trace + refine) against the plain form (one trace +
-refine per TX/RX pair), and p50/p99 request latency of the serving loop.
+Keller fans) per second of step time (``value``), and per second of the coarse
+stage alone (``coarse_rays_per_s``: visibility tables + launch + levels + kappa),
+with exact paths/s beside them; the batched form (all pairs in one trace + refine)
+against the plain form (one trace + refine per TX/RX pair, on a sample of pairs);
+p50/p99 request latency of the serving loop; and secondary lines for the noisy
+room (4 TX x 16 RX) and the street canyon (20M points, 16 TX x 1024 RX).
 
-N > 1 (torchrun): each rank runs the same workload with its own seeded TX/RX
-draw (weak scaling, no collective on the data path; a barrier brackets timing).
+N > 1 (torchrun): one workload of N TXs is split by TX (paper_2402_13747_b300.shard):
+rank r traces TX r of a seeded draw (rank 0 the scene's own TX) against all RXs on
+a full replica of the scene -- weak scaling, no collective on the data path; a
+barrier brackets timing and the exact paths are gathered to rank 0 afterwards.
 
---impl reference times the FP64 CPU oracle on a bounded sample of the same
-workload (1 TX x 16 RX, <= 1 reflection + 1 diffraction) on the host cores.
+--impl reference times the FP64 CPU oracle on a bounded sample of the workload
+(1 TX x 256 RX at <= 1 reflection) on the host cores.
 """
 from __future__ import annotations
 
@@ -37,20 +45,46 @@ if ROOT not in sys.path:
 import numpy as np  # noqa: E402
 
 METRIC = "rays/s and exact paths/s on 1 B300, batched vs plain; p50/p99 request latency"
-WORKLOAD = ("room_noisy: 10x10x3 m box room at 5 cm (~133k pts, sigma 5 mm / 2 deg noise), 1x1x2 m box "
-            "with 8 exterior edges, 4 TX x 16 RX, <=3 reflections + <=1 diffraction, kappa 100, rho 2000")
-CPU_SAMPLE = "room_noisy geometry, 1 TX x 16 RX, <=1 reflection + <=1 diffraction, full 0.5 deg launch"
+
+# Workloads: scene generator, method overrides, description.  Every one is seeded and
+# synthetic (the paper's corridor scan is not available); the indoor scan is the
+# configuration the metric is quoted on.
+WORKLOADS = {
+    "indoor": dict(
+        desc=("indoor: 3x2 grid of 8x7x3 m rooms with 1.0x2.1 m doorways and 40 seeded floor boxes, 1.92M points "
+              "at 3 cm (1 cm jitter), 8 materials, 1 TX x 256 RX, <=3 reflections + <=1 diffraction, kappa 100, "
+              "rho 2000"),
+        overrides={}),
+    "room_noisy": dict(
+        desc=("room_noisy: 10x10x3 m box room at 5 cm (133k pts, sigma 5 mm / 2 deg noise), 1x1x2 m box with 8 "
+              "exterior edges, 4 TX x 16 RX, <=3 reflections + <=1 diffraction, kappa 100, rho 2000"),
+        overrides={}),
+    "street": dict(
+        desc=("street: 200x50 m canyon, 20.0M points at 3 cm on facades, roofs and ground, 4 materials, 16 TX x "
+              "1024 RX at 1.5 m, <=1 reflection + <=1 diffraction (the deepest tree whose levels fit one B300's "
+              "node buffers in a bounded step), kappa 100, rho 2000"),
+        overrides=dict(max_refl=1, max_diff=1)),
+}
+CPU_SAMPLE = {
+    "indoor": ("indoor geometry (1.92M points), 1 TX x 256 RX, <=1 reflection, full 0.5 deg launch",
+               dict(max_refl=1, max_diff=0), 1, 256),
+    "room_noisy": ("room_noisy geometry, 1 TX x 16 RX, <=1 reflection + <=1 diffraction, full 0.5 deg launch",
+                   dict(max_refl=1, max_diff=1), 1, 16),
+    "street": ("street geometry (20.0M points), 1 TX x 16 RX, <=1 reflection, full 0.5 deg launch",
+               dict(max_refl=1, max_diff=0), 1, 16),
+}
+PLAIN_PAIRS = 16   # the plain per-pair form is timed on this many pairs of the workload
 
 
 def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
-# DRAM traffic of one full-size refine launch (dram__bytes_read.sum + dram__bytes_write.sum,
-# one-pass ncu capture of a k_refine launch of this workload), valid only for the device
-# code it was taken on: the hash below covers that code -- refine.cu up to its host
-# launcher, and the two headers whole -- and a changed kernel reports null.
-REFINE_TRAFFIC = {"bytes": 52.97e6 + 99.52e6, "sources_sha256": "2309aa0d002312697627dcaa165922f93141daba6e930a7497bd3c373c7e0daf"}
+# DRAM traffic of one full-size refine launch of the indoor workload
+# (dram__bytes_read.sum + dram__bytes_write.sum, one-pass ncu capture), valid only for
+# the device code it was taken on: the hash covers that code -- refine.cu up to its
+# host launcher, and the two headers whole -- and a changed kernel reports null.
+REFINE_TRAFFIC = {"bytes": None, "sources_sha256": None}
 KERNEL_SOURCES = (("paper_2402_13747_b300/csrc/refine.cu", b"\nint refine_paths("),
                   ("paper_2402_13747_b300/csrc/warp_geom.cuh", None),
                   ("paper_2402_13747_b300/csrc/nimbus_internal.cuh", None))
@@ -127,59 +161,67 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def make_scene(name: str):
+    from paper_2402_13747_b300 import scenes
+    return {"indoor": scenes.indoor, "room_noisy": scenes.room_noisy, "street": scenes.street}[name]()
+
+
+def oracle_sample(name: str, sc=None):
+    """One run of the oracle on the bounded CPU sample of a workload: (seconds,
+    cones, exact paths, description)."""
+    import oracle
+    from paper_2402_13747_b300 import config
+    desc, over, nt, nr = CPU_SAMPLE[name]
+    full = make_scene(name) if sc is None else sc
+    s_ = full.with_pairs(full.tx[:nt], full.rx[:nr])
+    p = config.params_for(s_, **over)
+    t0 = time.perf_counter()
+    _, c, e = oracle.run(s_, p)
+    return time.perf_counter() - t0, c.stats["n_cones"], len(e.paths()["n"]), desc
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    import oracle
-    from paper_2402_13747_b300 import config, scenes
-    full = scenes.room_noisy()
-    sc = full.with_pairs(full.tx[:1], full.rx[:16])
-    p = config.params_for(sc, max_refl=1, max_diff=1)
-    times, cones, paths = [], 0, 0
+    sc = make_scene(args.workload)
+    times, cones, paths, desc = [], 0, 0, ""
     for i in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        s, c, e = oracle.run(sc, p)
-        dt = time.perf_counter() - t0
+        dt, c, n, desc = oracle_sample(args.workload, sc)
         if i >= args.warmup:
             times.append(dt)
-            cones += c.stats["n_cones"]
-            paths += len(e.paths()["n"])
+            cones += c
+            paths += n
     T = sum(times)
     v = cones / T
     line = {"metric": METRIC, "value": v, "unit": "rays/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": CPU_SAMPLE}, "impl": "reference",
+            "config": {"workload": WORKLOADS[args.workload]["desc"], "sample": desc}, "impl": "reference",
             "exact_paths_per_s": paths / T,
-            "cpu_baseline": {"value": v, "unit": "rays/s", "cores": 1, "kind": "oracle", "sample": CPU_SAMPLE},
+            "cpu_baseline": {"value": v, "unit": "rays/s", "cores": 1, "kind": "oracle", "sample": desc},
             "e2e": {"value": v, "unit": "rays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline():
+def cpu_baseline(name: str, sc):
     """The oracle as it stands, single-threaded, on a bounded sample of the workload."""
-    import oracle
-    from paper_2402_13747_b300 import config, scenes
-    full = scenes.room_noisy()
-    sc = full.with_pairs(full.tx[:1], full.rx[:16])
-    p = config.params_for(sc, max_refl=1, max_diff=1)
-    t0 = time.perf_counter()
-    s, c, e = oracle.run(sc, p)
-    T = time.perf_counter() - t0
-    return {"value": c.stats["n_cones"] / T, "unit": "rays/s", "cores": 1, "kind": "oracle",
-            "sample": CPU_SAMPLE + f" ({T:.1f} s, {c.stats['n_cones']} cones, {len(e.paths()['n'])} exact paths)",
-            "exact_paths_per_s": len(e.paths()["n"]) / T}
+    T, cones, paths, desc = oracle_sample(name, sc)
+    return {"value": cones / T, "unit": "rays/s", "cores": 1, "kind": "oracle",
+            "sample": desc + f" ({T:.1f} s, {cones} cones, {paths} exact paths)", "exact_paths_per_s": paths / T}
 
 
-def rank_scene(rank: int):
-    """The workload of one rank: the same noisy room on every rank; rank 0 uses the
-    scene's own 4 TX x 16 RX, rank r > 0 its own seeded draw (weak scaling)."""
-    from paper_2402_13747_b300 import scenes
-    sc = scenes.room_noisy()
-    if rank:
-        sc = sc.with_pairs(*scenes.room_noisy_pairs(1000 + rank, sc.tx.shape[0], sc.rx.shape[0]))
-    return sc
+def rank_pairs(sc, rank: int, world: int):
+    """TX list of the N-rank workload (the scene's own TXs, then a seeded draw from the
+    scene's RX pool up to N) and this rank's TX shard; every rank takes every RX."""
+    from paper_2402_13747_b300 import shard
+    tx = sc.tx
+    if world > tx.shape[0]:
+        rng = np.random.default_rng(1000)
+        extra = sc.rx[rng.choice(sc.rx.shape[0], size=world - tx.shape[0], replace=False)]
+        tx = np.vstack([tx, extra])
+    txi = shard.tx_shard(tx.shape[0], rank, world)
+    return tx, txi
 
 
 def reduce_over_ranks(t_total: float, cones: float, paths: float, device, *more: float):
@@ -196,17 +238,107 @@ def reduce_over_ranks(t_total: float, cones: float, paths: float, device, *more:
     return (float(tmax[0]),) + tuple(float(u) for u in units)
 
 
+def trace_sized(ctx, s, tx, rx, p, sizes: dict, **kw):
+    """trace_coarse with node and coarse bounds taken from earlier calls of the same
+    workload; a first overflowing call reports the sizes it needed and is retried."""
+    c = ctx.trace(s, tx, rx, p, max_nodes=sizes.get("nodes", 0), max_coarse=sizes.get("coarse", 0),
+                  allow_overflow=True, **kw)
+    cc = ctx.coarse_counts(c)
+    if cc["overflow"]:
+        ctx.release(c)
+        sizes["nodes"] = max(8 << 20, int(cc["needed_nodes"] * 1.1))
+        sizes["coarse"] = max(8 << 20, int(cc["needed_coarse"] * 1.1))
+        c = ctx.trace(s, tx, rx, p, max_nodes=sizes["nodes"], max_coarse=sizes["coarse"], **kw)
+    return c
+
+
+def secondary_line(ctx, name: str, steps: int, warmup: int, flush, stream):
+    """A shorter measurement of another workload: step time, rays/s, exact paths/s."""
+    import torch
+    from paper_2402_13747_b300 import config
+    sc = make_scene(name)
+    p = config.params_for(sc, **WORKLOADS[name]["overrides"])
+    dev = torch.device("cuda", torch.cuda.current_device())
+    T = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)  # noqa: E731
+    args = (T(sc.xyz, torch.float32), T(sc.nrm, torch.float32),
+            T(sc.label.astype(np.int64), torch.int64).to(torch.int32), T(sc.material, torch.uint8),
+            T(sc.edges, torch.float64), T(sc.edge_label.astype(np.int64), torch.int64).to(torch.int32))
+    d_tx, d_rx = T(sc.tx, torch.float64), T(sc.rx, torch.float64)
+    sizes = {}
+    ms, counts = [], []
+    for i in range(warmup + steps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s = ctx.voxelize(*args, params=p)
+        c = trace_sized(ctx, s, d_tx, d_rx, p, sizes)
+        P = ctx.refine(s, c, p)
+        cnt = ctx.counts(P)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        for h in (P, c, s):
+            ctx.release(h)
+        if i >= warmup:
+            ms.append(e0.elapsed_time(e1))
+            counts.append(cnt)
+    t = sum(ms) / 1e3
+    c0 = counts[-1]
+    coarse_ms = c0["ms_vis"] + c0["ms_primary"] + c0["ms_levels"] + c0["ms_kappa"]
+    return {"workload": WORKLOADS[name]["desc"], "points": int(sc.xyz.shape[0]),
+            "pairs": int(sc.tx.shape[0] * sc.rx.shape[0]), "steps": steps, "ms_per_step": 1e3 * t / steps,
+            "rays_per_s": sum(c["n_cones"] for c in counts) / t,
+            "coarse_rays_per_s": c0["n_cones"] / (coarse_ms / 1e3) if coarse_ms > 0 else None,
+            "exact_paths_per_s": sum(c["n_paths"] for c in counts) / t,
+            "exact_paths_per_step": c0["n_paths"], "cones_per_step": c0["n_cones"],
+            "stage_ms": {k: c0[k] for k in ("ms_vis", "ms_primary", "ms_levels", "ms_kappa", "ms_refine",
+                                            "ms_dedup")},
+            "node_bounds": sizes or "default"}
+
+
+def roofline_of(c0, pk):
+    """Dominant stage and its roofline: algorithmic bytes / CUDA-event time against the
+    measured HBM copy peak.  Eq. 1 reads each point's position and normal (6 FP32 =
+    24 B); the same fraction at 16 B per point is printed beside it."""
+    stages = {"trace_levels": (c0["ms_levels"], c0["bytes_levels"]),
+              "trace_primary": (c0["ms_primary"], c0["bytes_primary"]),
+              "refine": (c0["ms_refine"], c0["bytes_refine"])}
+    dom = max(stages, key=lambda k: stages[k][0])
+    dms, dbytes = stages[dom]
+    peak = pk["hbm_gbs"] if pk else 6400.0
+    achieved = dbytes / (dms * 1e-3) / 1e9 if dms > 0 else 0.0
+    traffic = None
+    if dom == "refine" and REFINE_TRAFFIC["bytes"] and REFINE_TRAFFIC["sources_sha256"] == kernel_sources_sha256():
+        traffic = REFINE_TRAFFIC["bytes"]
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic, "kernel": dom, "kernel_ms": dms, "algorithmic_bytes": dbytes,
+            "bytes_per_point": 24, "peak_source": "measured" if pk else "fallback",
+            "stage_ms": {k: v[0] for k, v in stages.items()} | {"vis_tables": c0["ms_vis"], "kappa": c0["ms_kappa"],
+                                                                 "dedup": c0["ms_dedup"]}}
+    if dom == "refine":
+        roof["frac_at_16B_per_point"] = achieved * 16.0 / 24.0 / peak
+    lv_ms = c0["ms_levels"]
+    if lv_ms > 0:
+        lv = c0["bytes_levels"] / (lv_ms * 1e-3) / 1e9
+        roof["traversal"] = {"kernel": "trace_levels", "achieved": lv, "frac": lv / peak, "kernel_ms": lv_ms}
+    return roof
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--plain-steps", type=int, default=1)
+    ap.add_argument("--workload", default="indoor", choices=sorted(WORKLOADS))
+    ap.add_argument("--plain-pairs", type=int, default=PLAIN_PAIRS)
+    ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-segment", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true")
+    ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--pairs", default="", help="TxR: only the first T TX and R RX (small profiling cases)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -214,7 +346,7 @@ def main():
         return
 
     import torch
-    from paper_2402_13747_b300 import _abi, config, scenes
+    from paper_2402_13747_b300 import _abi, config, shard
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     if world > 1:
@@ -226,37 +358,42 @@ def main():
             import torch.distributed as dist
             dist.barrier()
 
-    sc = rank_scene(rank)
-    workload = WORKLOAD
+    sc = make_scene(args.workload)
+    workload = WORKLOADS[args.workload]["desc"]
     if args.pairs:
         nt, nr = (int(v) for v in args.pairs.lower().split("x"))
         sc = sc.with_pairs(sc.tx[:nt], sc.rx[:nr])
-        workload = WORKLOAD.replace("4 TX x 16 RX", f"{nt} TX x {nr} RX (subset)")
-    p = config.params_for(sc)
+        workload += f" [subset: first {nt} TX x {nr} RX]"
+    tx_all, txi = rank_pairs(sc, rank, world)
+    my = sc.with_pairs(tx_all[txi], sc.rx)
+    p = config.params_for(sc, **WORKLOADS[args.workload]["overrides"])
     dev = torch.device("cuda", local)
     T = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)  # noqa: E731
     d_xyz, d_nrm = T(sc.xyz, torch.float32), T(sc.nrm, torch.float32)
     d_lab = T(sc.label.astype(np.int64), torch.int64).to(torch.int32)
     d_mat = T(sc.material, torch.uint8)
     d_edges, d_elab = T(sc.edges, torch.float64), T(sc.edge_label.astype(np.int64), torch.int64).to(torch.int32)
-    d_tx, d_rx = T(sc.tx, torch.float64), T(sc.rx, torch.float64)
+    d_tx, d_rx = T(my.tx, torch.float64), T(my.rx, torch.float64)
     ctx = _abi.Context(local)
     stream = torch.cuda.current_stream()
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)   # larger than the 126 MB L2
+    sizes = {}
 
     def step():
         s = ctx.voxelize(d_xyz, d_nrm, d_lab, d_mat, d_edges, d_elab, params=p)
-        c = ctx.trace(s, d_tx, d_rx, p)
+        c = trace_sized(ctx, s, d_tx, d_rx, p, sizes)
         P = ctx.refine(s, c, p)
         cnt = ctx.counts(P)
         for h in (P, c, s):
             ctx.release(h)
         return cnt
 
-    # launch layouts (result-neutral) tuned on a small sample of the workload, untimed
-    s0 = ctx.voxelize(d_xyz, d_nrm, d_lab, d_mat, d_edges, d_elab, params=p)
-    tuning = ctx.autotune(s0, sc.tx, sc.rx[:4], p)   # every TX: the level work grows with the TX trees
-    ctx.release(s0)
+    # launch layouts (result-neutral) tuned on a sample of the workload, untimed
+    tuning = ctx.get_tuning()
+    if not args.no_tune:
+        s0 = ctx.voxelize(d_xyz, d_nrm, d_lab, d_mat, d_edges, d_elab, params=p)
+        tuning = ctx.autotune(s0, my.tx, my.rx[:8], p)
+        ctx.release(s0)
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -281,96 +418,105 @@ def main():
     cones = sum(c["n_cones"] for c in counts)
     paths = sum(c["n_paths"] for c in counts)
     vis = sum(c["n_vis"] for c in counts)
+    coarse_t = sum(c["ms_vis"] + c["ms_primary"] + c["ms_levels"] + c["ms_kappa"] for c in counts) / 1e3
     if world > 1:
-        t_total, cones, paths, vis = reduce_over_ranks(t_total, cones, paths, dev, vis)
+        t_total, cones, paths, vis, coarse_t = reduce_over_ranks(t_total, cones, paths, dev, vis, coarse_t)
+        coarse_t /= world   # mean coarse-stage time per rank (the ranks run concurrently)
     c0 = counts[-1]
     value = cones / t_total
     exact_ps = paths / t_total
 
     # end to end through the public API from pinned host buffers, results read back;
-    # every rank runs it on its own draw (whole-job figure like the value)
+    # every rank runs it on its own shard (whole-job figure like the value)
     h = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in
          dict(xyz=sc.xyz, nrm=sc.nrm, lab=sc.label, mat=sc.material, edges=sc.edges, elab=sc.edge_label,
-              tx=sc.tx, rx=sc.rx).items()}
+              tx=my.tx, rx=my.rx).items()}
     h2d = sum(int(t.numel() * t.element_size()) for t in h.values())
     e2e_t, e2e_cones, e2e_paths, d2h = [], 0, 0, 0
+    last = None
     barrier()
-    for i in range(0 if args.no_e2e else args.warmup + args.steps):
+    n_e2e = 0 if args.no_e2e else 1 + max(1, args.e2e_steps)
+    for i in range(n_e2e):
         flush.fill_(1)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         s = ctx.voxelize(h["xyz"], h["nrm"], h["lab"], h["mat"], h["edges"], h["elab"], params=p)
-        c = ctx.trace(s, h["tx"], h["rx"], p)
+        c = trace_sized(ctx, s, h["tx"], h["rx"], p, sizes)
         P = ctx.refine(s, c, p)
         res = ctx.query(P)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         for hh in (P, c, s):
             ctx.release(hh)
-        if i >= args.warmup:
+        if i >= 1:
             e2e_t.append(dt)
             e2e_cones += res["counts"]["n_cones"]
             e2e_paths += res["counts"]["n_paths"]
             d2h = int(len(res["n"]) * 320 + 8 * 24)
+        last = res
     e2e = None
-    if not args.no_e2e:
+    if n_e2e:
         t_e2e = sum(e2e_t)
         if world > 1:
             t_e2e, e2e_cones, e2e_paths = reduce_over_ranks(t_e2e, e2e_cones, e2e_paths, dev)
         e2e = {"value": e2e_cones / t_e2e, "unit": "rays/s", "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h, "exact_paths_per_s": e2e_paths / t_e2e}
+               "d2h_bytes_per_step": d2h, "exact_paths_per_s": e2e_paths / t_e2e, "steps": len(e2e_t)}
+    # TX-sharded result: every rank's exact paths gathered to rank 0 (host gather, after timing)
+    gathered = None
+    if last is not None:
+        gathered = shard.gather_paths(txi, last, rank, world)
 
     out = None
     if rank == 0:
-        # dominant kernel and its roofline (algorithmic bytes / CUDA-event time)
-        stages = {"trace_levels": (c0["ms_levels"], c0["bytes_levels"]),
-                  "trace_primary": (c0["ms_primary"], c0["bytes_primary"]),
-                  "refine": (c0["ms_refine"], c0["bytes_refine"])}
-        dom = max(stages, key=lambda k: stages[k][0])
-        dms, dbytes = stages[dom]
         pk = peaks()
-        peak = pk["hbm_gbs"] if pk else 6400.0
-        achieved = dbytes / (dms * 1e-3) / 1e9 if dms > 0 else 0.0
-        traffic = None
-        if dom == "refine" and REFINE_TRAFFIC["sources_sha256"] == kernel_sources_sha256():
-            traffic = REFINE_TRAFFIC["bytes"]
-        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": dom, "kernel_ms": dms, "algorithmic_bytes": dbytes,
-                "peak_source": "measured" if pk else "fallback",
-                "stage_ms": {k: v[0] for k, v in stages.items()} | {"vis_tables": c0["ms_vis"],
-                                                                     "kappa": c0["ms_kappa"],
-                                                                     "dedup": c0["ms_dedup"]}}
+        roof = roofline_of(c0, pk)
 
-        # plain form: one trace + refine per TX/RX pair on the resident scene
+        # plain form: one trace + refine per TX/RX pair on the resident scene, timed on
+        # the first pairs of the workload (rates; the batched form runs all pairs)
         plain = None
-        if args.plain_steps > 0:
-            pl_ms, pl_cones, pl_paths, lat = [], 0, 0, []
-            for _ in range(args.plain_steps):
-                torch.cuda.synchronize()
-                t0 = time.perf_counter()
-                s = ctx.voxelize(d_xyz, d_nrm, d_lab, d_mat, d_edges, d_elab, params=p)
-                for ti in range(sc.tx.shape[0]):
-                    for ri in range(sc.rx.shape[0]):
-                        q0 = time.perf_counter()
-                        c = ctx.trace(s, d_tx[ti:ti + 1], d_rx[ri:ri + 1], p)
-                        P = ctx.refine(s, c, p)
-                        cc = ctx.counts(P)
-                        lat.append(time.perf_counter() - q0)
-                        pl_cones += cc["n_cones"]
-                        pl_paths += cc["n_paths"]
-                        ctx.release(P)
-                        ctx.release(c)
-                ctx.release(s)
-                torch.cuda.synchronize()
-                pl_ms.append(1e3 * (time.perf_counter() - t0))
-            tpl = sum(pl_ms) / 1e3
-            # rays_per_s counts the cones the plain form traced (each pair re-traces its TX's
-            # launch); workload_rays_per_s is the batched workload's cones over the plain time
-            plain = {"rays_per_s": pl_cones / tpl, "workload_rays_per_s": cones / len(counts) / world * args.plain_steps / tpl,
-                     "exact_paths_per_s": pl_paths / tpl,
-                     "ms_per_step": statistics.mean(pl_ms), "calls_per_step": int(sc.tx.shape[0] * sc.rx.shape[0]),
+        if args.plain_pairs > 0:
+            pairs = [(ti, ri) for ti in range(my.tx.shape[0]) for ri in range(my.rx.shape[0])][:args.plain_pairs]
+            s = ctx.voxelize(d_xyz, d_nrm, d_lab, d_mat, d_edges, d_elab, params=p)
+            psz = {}
+            ti, ri = pairs[0]
+            ctx.release(trace_sized(ctx, s, d_tx[ti:ti + 1], d_rx[ri:ri + 1], p, psz))   # warm-up call
+            torch.cuda.synchronize()
+            pl_cones, pl_paths, lat = 0, 0, []
+            t0 = time.perf_counter()
+            for ti, ri in pairs:
+                q0 = time.perf_counter()
+                c = trace_sized(ctx, s, d_tx[ti:ti + 1], d_rx[ri:ri + 1], p, psz)
+                P = ctx.refine(s, c, p)
+                cc = ctx.counts(P)
+                lat.append(time.perf_counter() - q0)
+                pl_cones += cc["n_cones"]
+                pl_paths += cc["n_paths"]
+                ctx.release(P)
+                ctx.release(c)
+            torch.cuda.synchronize()
+            tpl = time.perf_counter() - t0
+            ctx.release(s)
+            n_all = my.tx.shape[0] * my.rx.shape[0]
+            # rays_per_s counts the cones the plain form traced (each pair re-traces its
+            # TX's launch); workload_rays_per_s is the batched workload's cones over the
+            # plain time scaled to all pairs
+            plain = {"rays_per_s": pl_cones / tpl,
+                     "workload_rays_per_s": (cones / len(counts) / world) / (tpl * n_all / len(pairs)),
+                     "exact_paths_per_s": pl_paths / tpl, "pairs_timed": len(pairs), "pairs_in_workload": n_all,
+                     "ms_per_pair": 1e3 * tpl / len(pairs),
                      "pair_latency_ms_p50": 1e3 * float(np.percentile(lat, 50)),
                      "pair_latency_ms_p99": 1e3 * float(np.percentile(lat, 99))}
+
+        secondary = None
+        if not args.no_secondary and world == 1 and not args.pairs:
+            secondary = {}
+            for name in ("room_noisy", "street"):
+                if name == args.workload:
+                    continue
+                try:
+                    secondary[name] = secondary_line(ctx, name, 2, 1, flush, stream)
+                except Exception as ex:  # must not hide the main line
+                    secondary[name] = {"error": repr(ex)}
 
         latency = None
         if not args.no_serving:
@@ -398,23 +544,27 @@ def main():
 
         cpu = None
         if not args.no_cpu_baseline and world == 1:
-            cpu = cpu_baseline()
+            cpu = cpu_baseline(args.workload, sc)
 
         clocks = clk.summary()
         out = {"metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": float(statistics.mean(ms)), "higher_is_better": True,
-               "scaling": "weak", "vs_baseline": None, "dtype": "f32 traversal / f64 refinement",
+               "scaling": "weak", "vs_baseline": None,
+               "dtype": "f32 traversal and Eq. 1; refinement: f64 iterate, points, length and delay, f32 step",
                "data": "synthetic",
                "config": {"workload": workload, "l2": "flushed between timed steps (512 MB write)",
-                          "points": int(sc.xyz.shape[0]), "pairs": int(sc.tx.shape[0] * sc.rx.shape[0]),
+                          "points": int(sc.xyz.shape[0]), "pairs": int(tx_all.shape[0] * sc.rx.shape[0]),
                           "form": "batched: all pairs in one trace_coarse + refine",
                           "tuning": {k: v for k, v in tuning.items() if not k.endswith("_ms")},
-                          "tuning_sample": "all TX x 4 RX of the workload"},
-               "exact_paths_per_s": exact_ps, "exact_paths_per_step": paths / args.steps / world,
+                          "tuning_sample": "the rank's TXs x 8 RX of the workload",
+                          "parallelism": f"tx-sharded x{world}" if world > 1 else "1 GPU"},
+               "coarse_rays_per_s": cones / coarse_t if coarse_t > 0 else None,
+               "exact_paths_per_s": exact_ps, "exact_paths_per_step": paths / args.steps,
                "visibility_rays_per_s": vis / t_total,
-               "cones_per_step": cones / args.steps / world, "wall_s_timed_region": wall,
+               "cones_per_step": cones / args.steps, "wall_s_timed_region": wall,
                "plain": plain, "latency": latency, "segment": segment, "roofline": roof, "cpu_baseline": cpu,
-               "e2e": e2e,
+               "e2e": e2e, "secondary": secondary,
+               "gathered_paths": None if gathered is None else int(len(gathered["n"])),
                "gpu_launches": launches, "clocks": clocks,
                "counts_last_step": {k: c0[k] for k in ("n_paths", "n_coarse", "n_coarse_raw", "n_nodes", "n_vis",
                                                        "n_cones", "launches")}}

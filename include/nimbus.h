@@ -293,6 +293,11 @@ NIMBUS_API int nimbus_memory_used(nimbus_ctx* ctx, size_t* bytes);
  * (operational; the paper has no counterpart).  NIMBUS_ERR_ARG for NULL. */
 NIMBUS_API int nimbus_kernel_launches(int64_t* count);
 
+/* Number of device allocations (cudaMallocAsync calls) this library has made in this
+ * process so far (all contexts); differences around a call count the allocations it
+ * made (operational; the paper has no counterpart).  NIMBUS_ERR_ARG for NULL. */
+NIMBUS_API int nimbus_device_allocations(int64_t* count);
+
 /* ---------------------------------------------------------------------------
  * Scene checkpoint.
  *
@@ -416,9 +421,8 @@ NIMBUS_API int nimbus_autotune(nimbus_ctx* ctx, nimbus_handle scene, const doubl
  *
  * Not part of the paper's method (the paper has no counterpart): an operational
  * variant for callers that cannot allocate device memory while they run -- for
- * example code inside a host callback of a CUDA graph, a process whose device
- * memory is carved up in advance by another allocator, or a real-time loop that
- * must not block on the allocator.  It computes the same tables as
+ * example a process whose device memory is carved up in advance by another
+ * allocator, or a real-time loop that must not block on the allocator.  It computes the same tables as
  * nimbus_voxelize + nimbus_scene_tables for a cloud without edges, but writes them
  * into caller-owned device buffers and keeps every intermediate in one fixed
  * device array inside this library (NIMBUS_STATIC_MAX_POINTS points and
@@ -427,13 +431,19 @@ NIMBUS_API int nimbus_autotune(nimbus_ctx* ctx, nimbus_handle scene, const doubl
  *
  * - Inputs (cloud->xyz, nrm, label, material) must be device pointers.
  * - Larger clouds or grids: NIMBUS_ERR_ARG with a message; output capacities
- *   too small: NIMBUS_ERR_OVERFLOW with the needed sizes in *info.
+ *   too small: NIMBUS_ERR_OVERFLOW with the needed sizes in *info, and the
+ *   outputs untouched.  A voxel capacity below the grid's size is found before
+ *   the entities are counted: info->n_cells is set and info->n_ie is -1.
  * - The first call on a device resolves the fixed array's device address
  *   (cudaGetSymbolAddress) with that device current; make that first call before
  *   any stream capture on that device.
  * - Every call shares the one array: calls that overlap on the GPU (other
  *   streams, other host threads) race and must be serialised by the caller.  The
- *   call reads two counters back and so returns after its work has finished.
+ *   call reads two counters back and so returns after its work has finished; it
+ *   synchronises its stream, so it cannot run inside a CUDA host function (one
+ *   that cudaLaunchHostFunc or a graph host node runs) or under stream capture.
+ * - Null or non-device output pointers for a non-zero capacity: NIMBUS_ERR_ARG,
+ *   before any device work.
  * - Calls no cudaMalloc, cudaFree or other allocating routine. */
 #define NIMBUS_STATIC_MAX_POINTS (1 << 17)
 #define NIMBUS_STATIC_MAX_CELLS (1 << 20)

@@ -26,7 +26,7 @@ ERR_NAMES = {1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_OVERFLOW", 5: "E
 EXPORTS = ("nimbus_create", "nimbus_destroy", "nimbus_last_error", "nimbus_voxelize", "nimbus_update_region",
            "nimbus_trace_coarse", "nimbus_refine", "nimbus_query", "nimbus_query_coarse", "nimbus_scene_info",
            "nimbus_scene_tables", "nimbus_release", "nimbus_memory_used", "nimbus_kernel_launches",
-           "nimbus_voxelize_static", "nimbus_get_tuning", "nimbus_set_tuning", "nimbus_autotune",
+           "nimbus_device_allocations", "nimbus_voxelize_static", "nimbus_get_tuning", "nimbus_set_tuning", "nimbus_autotune",
            "nimbus_scene_save", "nimbus_scene_load", "nimbus_segment")
 
 _vp = C.c_void_p
@@ -146,6 +146,13 @@ def kernel_launches() -> int:
     return int(v.value)
 
 
+def device_allocations() -> int:
+    """Device allocations the library has made in this process so far."""
+    v = C.c_int64(0)
+    load().nimbus_device_allocations(C.byref(v))
+    return int(v.value)
+
+
 def load():
     """Load libnimbus.so (raises if it has not been built)."""
     global _lib
@@ -172,6 +179,7 @@ def load():
     L.nimbus_release.argtypes = [ctxp, C.c_uint64]
     L.nimbus_memory_used.argtypes = [ctxp, P(C.c_size_t)]
     L.nimbus_kernel_launches.argtypes = [P(C.c_int64)]
+    L.nimbus_device_allocations.argtypes = [P(C.c_int64)]
     L.nimbus_voxelize_static.argtypes = [ctxp, P(Cloud), P(VoxParams), P(StaticTables), P(StaticInfo), _vp]
     L.nimbus_scene_save.argtypes = [ctxp, C.c_uint64, C.c_char_p, _vp]
     L.nimbus_scene_load.argtypes = [ctxp, C.c_char_p, P(C.c_uint64), _vp]
@@ -476,14 +484,17 @@ class Context:
         return out
 
     def voxelize_static(self, xyz, nrm, label, out: dict, material=None, params: Params = None, region=None,
-                        stream=None) -> dict:
+                        stream=None, allow_overflow=False) -> dict:
         """Voxelise into caller-owned device buffers without any device allocation.
 
-        For callers that cannot allocate while they run (graph host callbacks,
-        pre-carved memory pools, real-time loops): the inputs must be device tensors
+        For callers that cannot allocate while they run (device memory carved up in
+        advance by another allocator, real-time loops that must not wait on the
+        allocator): the inputs must be device tensors
         and ``out`` holds device tensors named as in nimbus_static_tables, sized by
         the capacities ``out['ie_capacity']`` and ``out['cell_capacity']``.
-        Calls that overlap on the GPU share one fixed scratch array and race.
+        Calls that overlap on the GPU share one fixed scratch array and race.  The
+        call synchronises its stream (it reads counters back), so it cannot run
+        inside a CUDA host function or under stream capture.
         """
         params = params or Params()
         cl = Cloud(_ptr(xyz), _ptr(nrm), _ptr(label), _ptr(material), int(xyz.shape[0]))
@@ -496,7 +507,9 @@ class Context:
         rc = self.L.nimbus_voxelize_static(self.h, C.byref(cl), C.byref(vp), C.byref(t), C.byref(info),
                                            _stream(stream))
         res = dict(origin=np.array(info.origin[:]), dims=np.array(info.dims[:], np.int32), n_ie=info.n_ie,
-                   n_cells=info.n_cells)
+                   n_cells=info.n_cells, overflow=rc == ERR_OVERFLOW)
+        if rc == ERR_OVERFLOW and allow_overflow:
+            return res   # the needed sizes; the outputs are untouched
         self._check(rc, "voxelize_static")
         return res
 

@@ -24,6 +24,7 @@ struct nimbus_ctx {
 namespace nb {
 
 std::atomic<long long> g_launches{0};
+std::atomic<long long> g_allocs{0};
 
 int cuda_fail(std::string* err, cudaError_t e, const char* what) {
   char buf[512];
@@ -52,6 +53,7 @@ int Mem::alloc(void** p, size_t bytes, cudaStream_t st) {
     *p = nullptr;
     return cuda_fail(err, e, "cudaMallocAsync");
   }
+  g_allocs.fetch_add(1);
   sizes[*p] = bytes;
   used += bytes;
   peak = std::max(peak, used);
@@ -630,6 +632,12 @@ int nimbus_autotune(nimbus_ctx* ctx, nimbus_handle scene, const double* tx, int3
 int nimbus_kernel_launches(int64_t* count) {
   if (!count) return NIMBUS_ERR_ARG;
   *count = (int64_t)nb::g_launches.load();
+  return NIMBUS_OK;
+}
+
+int nimbus_device_allocations(int64_t* count) {
+  if (!count) return NIMBUS_ERR_ARG;
+  *count = (int64_t)nb::g_allocs.load();
   return NIMBUS_OK;
 }
 

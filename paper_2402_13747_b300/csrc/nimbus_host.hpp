@@ -68,6 +68,8 @@ int cuda_fail(std::string* err, cudaError_t e, const char* what);
   } while (0)
 // Kernel launches made by the library (process-wide), for launch accounting.
 extern std::atomic<long long> g_launches;
+// Device allocations made by the library (process-wide), for allocation accounting.
+extern std::atomic<long long> g_allocs;
 #define NB_LAUNCHED(err)                 \
   do {                                   \
     ::nb::g_launches.fetch_add(1);       \

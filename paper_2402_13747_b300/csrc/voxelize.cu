@@ -967,6 +967,29 @@ int voxelize_static(std::string* err, const nimbus_cloud* cloud, const nimbus_vo
     *err = "voxelize_static: inputs must be device pointers";
     return NIMBUS_ERR_ARG;
   }
+  // every output a non-zero capacity promises must be a device buffer: a null or
+  // host pointer is refused here, before any device work writes through it
+  if (out->ie_capacity < 0 || out->cell_capacity < 0) {
+    *err = "voxelize_static: negative output capacity";
+    return NIMBUS_ERR_ARG;
+  }
+  if (out->ie_capacity > 0) {
+    const void* ie_out[8] = {out->kind, out->label, out->gs, out->pcount, out->rp, out->normal, out->bbc,
+                             out->material};
+    for (const void* q : ie_out)
+      if (!q || !is_device_ptr(q)) {
+        *err = "voxelize_static: entity outputs must be device pointers";
+        return NIMBUS_ERR_ARG;
+      }
+  }
+  if (out->cell_capacity > 0) {
+    const void* cell_out[3] = {out->cell_begin, out->cell_count, out->march};
+    for (const void* q : cell_out)
+      if (!q || !is_device_ptr(q)) {
+        *err = "voxelize_static: voxel outputs must be device pointers";
+        return NIMBUS_ERR_ARG;
+      }
+  }
   void* base = nullptr;
   NB_TRY(static_scratch(err, &base));
   Mem m;  // error sink only: the arena below serves every buffer
@@ -1023,6 +1046,11 @@ int voxelize_static(std::string* err, const nimbus_cloud* cloud, const nimbus_vo
   if (n_cells > (int64_t)kStaticCells) {
     *err = "voxelize_static: the voxel grid has more than NIMBUS_STATIC_MAX_CELLS voxels";
     return NIMBUS_ERR_ARG;
+  }
+  if (n_cells > out->cell_capacity) {   // known before the sort: no work spent on it
+    info->n_ie = -1;                     // not counted yet
+    *err = "voxelize_static: output capacity too small (needed sizes in info)";
+    return NIMBUS_ERR_OVERFLOW;
   }
   GridK g;
   for (int a = 0; a < 3; ++a) {

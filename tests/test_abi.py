@@ -129,7 +129,7 @@ def test_error_codes_without_a_context(lib):
     assert lib.nimbus_last_error(None) == b"null context"
     pointer_types = (C.c_void_p, C.c_char_p)
     for name in _abi.EXPORTS:
-        if name in ("nimbus_create", "nimbus_last_error", "nimbus_kernel_launches"):
+        if name in ("nimbus_create", "nimbus_last_error", "nimbus_kernel_launches", "nimbus_device_allocations"):
             continue
         f = getattr(lib, name)
         args = [None if (t in pointer_types or hasattr(t, "contents") or t.__name__.startswith("LP_")) else t(0)
@@ -138,6 +138,8 @@ def test_error_codes_without_a_context(lib):
     n = C.c_int64(-1)
     assert lib.nimbus_kernel_launches(None) == _abi.ERR_ARG
     assert lib.nimbus_kernel_launches(C.byref(n)) == _abi.OK and n.value >= 0
+    assert lib.nimbus_device_allocations(None) == _abi.ERR_ARG
+    assert lib.nimbus_device_allocations(C.byref(n)) == _abi.OK and n.value >= 0
 
 
 def test_a_c_program_links_and_calls_the_library(lib, tmp_path):

@@ -1,8 +1,9 @@
 """The N > 1 path of bench.py on CPU: two gloo ranks, no GPU.
 
-Each rank runs its own TX/RX draw on a replica of the same scene (weak scaling, no
-collective on the data path); after the timed region the slowest rank's time and
-the units of all ranks are reduced.
+One workload of N TXs is split by TX: each rank takes its own TX against every RX
+on a replica of the same scene (weak scaling, no collective on the data path);
+after the timed region the slowest rank's time and the units of all ranks are
+reduced.
 """
 import os
 import socket
@@ -22,36 +23,38 @@ def _free_port():
 def _rank_main(rank, world, port, out):
     import torch
     import torch.distributed as dist
+    from paper_2402_13747_b300 import scenes
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
-        sc = bench.rank_scene(rank)
+        sc = scenes.room_noisy(n_tx=1, n_rx=16)
+        tx_all, txi = bench.rank_pairs(sc, rank, world)
         # per-rank figures as the timed loop would produce them
         t_total, cones, paths, vis = 1.0 + rank, 1000.0 * (rank + 1), 10.0 * (rank + 1), 5e4 * (rank + 1)
         res = bench.reduce_over_ranks(t_total, cones, paths, torch.device("cpu"), vis)
         dist.barrier()
-        out[rank] = (res, sc.tx.copy(), sc.rx.copy(), int(sc.xyz.shape[0]))
+        out[rank] = (res, tx_all.copy(), txi.copy(), sc.rx.copy())
     finally:
         dist.destroy_process_group()
 
 
-def test_two_ranks_reduce_and_draw_their_own_pairs():
+def test_two_ranks_reduce_and_split_the_tx_list():
     world = 2
     ctx = mp.get_context("spawn")
     with ctx.Manager() as m:
         out = m.dict()
         mp.start_processes(_rank_main, args=(world, _free_port(), out), nprocs=world, join=True,
                            start_method="spawn")
-        res0, tx0, rx0, n0 = out[0]
-        res1, tx1, rx1, n1 = out[1]
+        res0, tx0, txi0, rx0 = out[0]
+        res1, tx1, txi1, rx1 = out[1]
     # max over ranks for the time, sums for the units, identical on every rank
     assert res0 == res1 == (2.0, 3000.0, 30.0, 150000.0)
-    # same geometry, different seeded pairs, same pair count (fixed work per rank)
-    assert n0 == n1
-    assert tx0.shape == tx1.shape == (4, 3) and rx0.shape == rx1.shape == (16, 3)
-    assert not np.allclose(tx0, tx1)
-    for p in np.vstack([tx0, tx1, rx0, rx1]):
-        assert 0.3 <= p[0] <= 9.7 and 0.3 <= p[1] <= 9.7 and 0.3 <= p[2] <= 2.7
+    # one workload: the same TX list and RXs on every rank, the scene's own TX first,
+    # each rank one TX of it (fixed work per rank)
+    np.testing.assert_array_equal(tx0, tx1)
+    np.testing.assert_array_equal(rx0, rx1)
+    assert tx0.shape == (2, 3) and not np.allclose(tx0[0], tx0[1])
+    assert list(txi0) == [0] and list(txi1) == [1]
 
 
 def test_traffic_gate_hashes_device_code_only():

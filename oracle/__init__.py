@@ -24,9 +24,12 @@ Parity pins (tests/test_oracle_pins.py):
   delta validity rule, diffractions refined off their edge, the shortest path per label
   sequence, the image method with an occluding panel, the march's segment of one
   subvoxel diameter, and paths that move with the scene.
+- the secant placement after a sign change of f, in an entity's march and in the
+  re-projection, on two sheets whose Eq. 1 surface is f = u - h tanh(2uh/sigma^2);
+  the final visibility check, which alone removes a path passing 0.0545 m outside a
+  panel's border; the RX reception sphere centred on the RX, on one launch cone.
 tests/test_oracle_mutants.py plants one mistake at a time in a copy of the source and
-checks that these pins catch it.  The secant placement after a sign change of f is
-reached by no pinned scene.
+checks that these pins catch it.
 
 The coarse-path set and the kappa choice on noisy scenes have no closed form: parity
 unpinned beyond those invariants.
@@ -138,6 +141,8 @@ def lib():
         L.oracle_sdf_label.argtypes = [vp, u32, vp, vp, vp]
         L.oracle_sdf_hit.restype = i32
         L.oracle_sdf_hit.argtypes = [vp, i64, vp, vp, vp]
+        L.oracle_reproject.restype = i32
+        L.oracle_reproject.argtypes = [vp, vp, vp, u32, vp, vp]
         L.oracle_visible.restype = i32
         L.oracle_visible.argtypes = [vp, vp, vp, i32, u32, i32, u32, i32]
         L.oracle_cone_sphere.restype = i32
@@ -250,6 +255,14 @@ class Scene:
         t = np.zeros(1)
         ok = lib().oracle_sdf_hit(self.h, int(ie), _p(_c(P, np.float64)), _p(_c(d, np.float64)), _p(t))
         return float(t[0]) if ok else None
+
+    def reproject(self, P, R, label):
+        """Section 2.3's re-projection alone: the ray from P toward R on the surface of
+        `label`; (new point, normal), or (None, None) on a miss."""
+        c = np.zeros(3)
+        n = np.zeros(3)
+        ok = lib().oracle_reproject(self.h, _p(_c(P, np.float64)), _p(_c(R, np.float64)), int(label), _p(c), _p(n))
+        return (c, n) if ok else (None, None)
 
     def visible(self, a, b, mode_a=0, label_a=NONE_LABEL, mode_b=0, label_b=NONE_LABEL, brute=False):
         return bool(lib().oracle_visible(self.h, _p(_c(a, np.float64)), _p(_c(b, np.float64)), mode_a,

@@ -16,9 +16,11 @@
 // Pins (tests/test_oracle_pins.py) fix voxelisation, the march field, Eq. 1,
 // visibility, the cone test and the refined exact paths (image method, Keller point,
 // a reflection and a diffraction in either order) against closed forms and brute
-// force; tests/test_oracle_mutants.py checks that planted mistakes fail them (the
-// secant placement after a sign change of f is reached by no pinned scene).  The
-// coarse-path set and the kappa choice on noisy clouds have no
+// force; tests/test_oracle_mutants.py checks that planted mistakes fail them.  The
+// secant placement after a sign change of f is pinned on two sheets whose Eq. 1
+// surface has a closed form (both marches), the final visibility check on a path
+// that passes just outside a panel, and the RX reception sphere on a single launch
+// cone.  The coarse-path set and the kappa choice on noisy clouds have no
 // closed form: parity unpinned beyond their invariants (kappa, depth limits) and the
 // exact paths they refine to.
 // The only FP32 arithmetic is the subvoxel binning, which both sides perform with
@@ -1489,6 +1491,16 @@ int32_t oracle_sdf_label(void* sp, uint32_t label, const double* x, double* f, d
 int32_t oracle_sdf_hit(void* sp, int64_t ie, const double* P, const double* d, double* t) {
   Scene* s = (Scene*)sp;
   return sdf_hit(*s, s->ies[ie], mk(P[0], P[1], P[2]), unit(mk(d[0], d[1], d[2])), t) ? 1 : 0;
+}
+
+// Re-projection of Section 2.3 alone: the ray from P toward R met by the surface of
+// label `label`; writes the new interaction point and its normal.  0 on a miss.
+int32_t oracle_reproject(void* sp, const double* P, const double* R, uint32_t label, double* c, double* n) {
+  V3 cn, nn;
+  if (!reproject(*(Scene*)sp, mk(P[0], P[1], P[2]), mk(R[0], R[1], R[2]), label, &cn, &nn)) return 0;
+  c[0] = cn.x; c[1] = cn.y; c[2] = cn.z;
+  n[0] = nn.x; n[1] = nn.y; n[2] = nn.z;
+  return 1;
 }
 
 // mode: 0 none, 1 same label, 2 any label near that endpoint; brute: 1 = all-voxel slab test.

@@ -186,6 +186,49 @@ def test_pinned_cases_match_oracle(ctx, room_tiny, case):
         assert len(G["n"]) == 0
 
 
+def test_final_visibility_removes_the_path_past_the_panel_border(ctx, room_tiny):
+    """Section 2.3's last step on the CUDA path: the panel scene's ceiling-then-far-wall
+    path crosses the panel's plane 0.0545 m outside its border.  Its coarse paths
+    refine to the image points and the final visibility check marks every one
+    occluded, as in the oracle, so no exact path has its label sequence.  A refinement
+    that skipped the check would report it."""
+    sc = cases.room_with_panel(room_tiny)
+    p = config.params_for(sc)
+    s = ctx.voxelize_scene(sc, p)
+    c = ctx.trace(s, sc.tx, sc.rx, p)
+    P = ctx.refine(s, c, p)
+    A, F = ctx.query(P, 1), ctx.query(P, 0)
+    for h in (P, c, s):
+        ctx.release(h)
+    seq = (5, 1)
+    pts, _ = image_paths(box_room_planes(10.0, 10.0, 3.0), sc.tx[0], sc.rx[0], max_order=2)[seq]
+    rows = [i for i in range(len(A["n"])) if tuple(int(l) for l in A["label"][i][:A["n"][i]]) == seq]
+    assert rows
+    for i in rows:
+        assert int(A["status"][i]) == 3, (i, A["status"][i])     # occluded
+        np.testing.assert_allclose(A["pts"][i][:2], pts, atol=1e-3)
+    assert seq not in {tuple(int(l) for l in F["label"][i][:n]) for i, n in enumerate(F["n"])}
+
+
+def test_rx_sphere_is_centred_on_the_rx(ctx, room_tiny):
+    """One launch cone along +x (n_launch = 1) of half-angle 4 degrees from (2, 5, 1.5)
+    reaches the reception sphere around the RX at (7, 5.52, 1.5) but not one around
+    its subvoxel's centre: the LOS coarse path exists with the RX's own miss distance
+    0.52 m, and refines to the length |TX - RX|, as in the oracle."""
+    p = config.Params(max_refl=0, max_diff=0, n_launch=1)
+    tx, rx = np.array([[2.0, 5.0, 1.5]]), np.array([[7.0, 5.52, 1.5]])
+    sc = room_tiny.with_pairs(tx, rx)
+    s = ctx.voxelize_scene(sc, p)
+    c = ctx.trace(s, sc.tx, sc.rx, p)
+    C = ctx.query_coarse(c)
+    P = ctx.refine(s, c, p)
+    F = ctx.query(P, 0)
+    for h in (P, c, s):
+        ctx.release(h)
+    assert list(C["n"]) == [0] and C["miss"][0] == pytest.approx(0.52, abs=1e-5)
+    assert len(F["n"]) == 1 and F["length"][0] == pytest.approx(np.linalg.norm(rx - tx), rel=1e-9)
+
+
 def test_memory_returns_after_release(ctx, room_tiny):
     """The context's device-memory accounting: a scene, a coarse set and a path set
     each hold memory while alive, the scratch of a call is freed by the call itself,

@@ -140,6 +140,18 @@ MUTANTS = [
      "long long qa = (long long)std::floor(a.length * 1e6), qb = (long long)std::floor(b.length * 1e6);",
      "long long qa = (long long)std::floor(a.length * 1e1), qb = (long long)std::floor(b.length * 1e1);",
      "fresnel_zone_radius"),
+    ("sdf_hit_secant_dropped",         # Section 2.2.1: hit at the march point past the sign change
+     "      *t_hit = t - f * (t_next - t) / (f_next - f);", "      *t_hit = t_next;", "secant_after"),
+    ("reprojection_secant_sign",       # Section 2.3: secant through the wrong pair of values
+     "      th = t - f * (t_next - t) / (f_next - f);", "      th = t - f * (t_next - t) / (f_next + f);",
+     "middle_plane"),
+    ("final_visibility_dropped",       # Section 2.3: refined segments not validated by RT
+     "    if (!visible(s, I[k], I[k + 1], ea, eb)) { ex.status = ST_OCCLUDED; return ex; }", "",
+     "past_the_panel"),
+    ("rx_sphere_at_subvoxel_centre",   # RX reception sphere centred on its subvoxel
+     "    ctx.rx_sc.push_back(r);",
+     "    ctx.rx_sc.push_back(mk(s.origin.x + (gs[0] + 0.5) * s.hs, s.origin.y + (gs[1] + 0.5) * s.hs,\n"
+     "                           s.origin.z + (gs[2] + 0.5) * s.hs));", "rx_sphere"),
     ("fresnel_radius_misplaced_root",  # Section 2.3: sqrt(lambda a b) / (a + b)
      "double r = std::sqrt(lambda * ak * bk / (ak + bk));", "double r = std::sqrt(lambda * ak * bk) / (ak + bk);",
      "fresnel_zone_radius"),

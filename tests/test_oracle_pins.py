@@ -711,3 +711,155 @@ def test_rx_on_the_tx_gives_normal_incidence_images(room_tiny):
     a = np.sort(P["length"][P["rx"] == 1])
     b = np.sort(P["length"][P["rx"] == 2])
     np.testing.assert_array_equal(a, b)
+
+
+# ------------------------------------------------- the march's secant placement
+def _sheet_pair(zs, lo, hi, spacing):
+    """Horizontal sheets of one label with normals +z at heights zs, on one lattice
+    (all coordinates exact in FP32)."""
+    g = np.arange(lo, hi + 1e-12, spacing)
+    X, Y = np.meshgrid(g, g, indexing="ij")
+    xyz = np.vstack([np.stack([X.ravel(), Y.ravel(), np.full(X.size, z)], 1) for z in zs]).astype(np.float32)
+    nrm = np.tile(np.array([0, 0, 1], np.float32), (xyz.shape[0], 1))
+    return scenes.Scene("sheet_pair", xyz, nrm, np.zeros(xyz.shape[0], np.uint32), np.zeros(xyz.shape[0], np.uint8))
+
+
+def _march_closed_form(f, u0, cos_t, length, eps):
+    """The |f| march of Section 2.2.1 on a closed-form f(u), u = u0 - t cos_t: step
+    t += |f| until |f| < eps or the sign of f changes, then place the hit by the
+    secant through the last two march points.  Returns (branch, t)."""
+    t, fv = 0.0, f(u0)
+    for _ in range(64):
+        if abs(fv) < eps:
+            return "near_zero", t
+        tn = t + abs(fv)
+        if tn > length:
+            return "miss", None
+        fn = f(u0 - tn * cos_t)
+        if (fn < 0) != (fv < 0):
+            return "secant", t - fv * (tn - t) / (fn - fv)
+        t, fv = tn, fn
+    return "budget", None
+
+
+def test_sdf_hit_secant_after_a_sign_change():
+    """Two sheets 2h apart inside one subvoxel with shared normals: Eq. 1 gives
+    f = u - h tanh(2uh/sigma^2) at height u above their middle plane, whatever the
+    lateral position (both sheets share one lattice, so the lateral weight sums
+    cancel).  With h > sigma the slope of f exceeds 1 along a ray 70 degrees off the
+    normal, so the |f| march steps over the middle zero and the hit is the secant
+    through the two march points around it.  The closed-form f, marched by the same
+    rule, fixes that point."""
+    p = config.Params(sdf_sigma=0.05)
+    c, h = 0.375, 0.09375
+    s = oracle.Scene.from_scene(_sheet_pair([c - h, c + h], 0.25, 0.4375, 0.0625), p)
+    I = s.ies()
+    assert len(I["label"]) == 1 and I["prange"][0, 1] == 32
+    f = lambda u: u - h * math.tanh(2.0 * u * h / p.sdf_sigma ** 2)  # noqa: E731
+    th = math.radians(70.0)
+    d = np.array([math.sin(th), 0.0, -math.cos(th)])
+    half = 0.5 * p.voxel_size / p.dv * math.sqrt(3.0)
+    assert (2 * h * h / p.sdf_sigma ** 2 - 1.0) * math.cos(th) > 1.0 and half * math.cos(th) < h
+    branch, t_ref = _march_closed_form(f, half * math.cos(th), math.cos(th), 2 * half, p.sdf_eps)
+    assert branch == "secant"
+    bbc = I["bbc"][0]
+    np.testing.assert_allclose(bbc, [0.34375, 0.34375, c], atol=1e-7)
+    for lat in (0.0, 0.05):
+        P = bbc + np.array([0.0, lat, 0.0]) - 2.0 * d
+        t = s.sdf_hit(0, P, d)
+        assert t == pytest.approx(2.0 - half + t_ref, abs=1e-9)
+
+
+def test_reprojection_secant_lands_on_the_middle_plane():
+    """The re-projection of Section 2.3 on the same sheet pair, 2h = 0.375 m apart
+    across three subvoxel layers (one label, default sigma): the 3x3x3 block of every
+    march point holds both sheets, so f = u - h tanh(2uh/sigma^2) exactly, odd in u.
+    A ray 60 degrees off the normal toward a target on the middle plane oversteps the
+    middle zero; the secant places the hit at the closed-form march's point, 0.28 mm
+    from the plane (the zero of f by symmetry; the secant's error on the curved f),
+    with normal +z."""
+    p = config.Params()
+    c, h = 0.375, 0.1875
+    s = oracle.Scene.from_scene(_sheet_pair([c - h, c + h], 0.0, 2.0, 0.0625), p)
+    f = lambda u: u - h * math.tanh(2.0 * u * h / p.sdf_sigma ** 2)  # noqa: E731
+    th = math.radians(60.0)
+    d = np.array([math.sin(th), 0.0, -math.cos(th)])
+    half = 0.5 * p.voxel_size / p.dv * math.sqrt(3.0)
+    assert (2 * h * h / p.sdf_sigma ** 2 - 1.0) * math.cos(th) > 1.0
+    branch, t_ref = _march_closed_form(f, half * math.cos(th), math.cos(th), 2 * half, p.sdf_eps)
+    assert branch == "secant"
+    u_ref = half * math.cos(th) - t_ref * math.cos(th)
+    assert abs(u_ref) < 1e-3
+    for R in ([1.03125, 1.0625, c], [0.96875, 1.125, c]):
+        R = np.array(R)
+        cn, nn = s.reproject(R - 3.0 * d, R, 0)
+        assert cn is not None
+        np.testing.assert_allclose(cn, R + (u_ref / -math.cos(th)) * d, atol=1e-9)
+        np.testing.assert_allclose(nn, [0, 0, 1], atol=1e-12)
+
+
+# ------------------------------------------------- final visibility (Section 2.3)
+def test_final_visibility_removes_a_path_past_the_panel_border(room_tiny):
+    """Section 2.3 ends with a visibility check of every refined segment.  On the box
+    room with the panel, the ceiling-then-far-wall image path crosses the panel's
+    plane 0.0545 m outside its border: the image method lets it through, but an exact
+    plane's Eq. 1 surface is the whole plane (f = distance to it), and the crossing
+    lies within half a subvoxel diameter of the border entities' marched segments, so
+    the segment is blocked.  The coarse path refines to its image points, is marked
+    occluded, and no exact path has its label sequence -- the final check alone
+    decides it."""
+    x0, (y0, y1), (z0, z1) = cases.PANEL_X, cases.PANEL_Y, cases.PANEL_Z
+    sc = cases.room_with_panel(room_tiny)
+    p = config.params_for(sc, grad_stop=1e-9)
+    s, _, e = oracle.run(sc, p)
+    planes = box_room_planes(10.0, 10.0, 3.0)
+    ref = image_paths(planes, sc.tx[0], sc.rx[0], max_order=2)
+    seq = (5, 1)
+    pts, L = ref[seq]
+    deepest, margin = cases.panel_margin(sc.tx[0], sc.rx[0], seq, pts)
+    assert deepest < 0 and margin == pytest.approx(0.0545, abs=5e-4)          # clear of the panel
+    assert margin < 0.5 * p.voxel_size / p.dv * math.sqrt(3.0)                 # within a border entity's reach
+    A = e.paths(all_refined=True)
+    rows = [i for i in range(len(A["n"])) if tuple(int(l) for l in A["label"][i][:A["n"][i]]) == seq]
+    assert rows
+    for i in rows:
+        assert oracle.STATUS[int(A["status"][i])] == "occluded"
+        np.testing.assert_allclose(A["pts"][i][:2], pts, atol=1e-6)
+    nodes = [sc.tx[0]] + list(pts) + [sc.rx[0]]
+    ends = [(0, oracle.NONE_LABEL), (1, 5), (1, 1), (0, oracle.NONE_LABEL)]
+    blocked = [k for k in range(3) if not s.visible(nodes[k], nodes[k + 1], *ends[k], *ends[k + 1], brute=True)]
+    assert blocked == [0]                       # brute force over every entity: TX to the ceiling
+    assert seq not in {tuple(int(l) for l in e.paths()["label"][i][:n]) for i, n in enumerate(e.paths()["n"])}
+
+
+# ------------------------------------------------- RX reception sphere (reading C10b)
+def test_rx_sphere_is_centred_on_the_rx(room_tiny):
+    """One launch cone (n_launch = 1: the Fibonacci lattice's single direction is +x)
+    of half-angle 4 degrees from (2, 5, 1.5).  An RX at (7, 5.52, 1.5) lies 5.94
+    degrees off the axis; a sphere of the subvoxel radius h_s sqrt(3)/2 around it
+    reaches the cone (limit 4 + asin(r/|v|) = 6.47 degrees), one around its subvoxel's
+    centre (7.125, 5.625, 1.625) does not (7.09 against 6.40 degrees).  The oracle
+    finds the LOS path with the miss distance of the RX itself, 0.52 m, and its
+    exact length |TX - RX|."""
+    p = config.Params(max_refl=0, max_diff=0, n_launch=1)
+    tx, rx = np.array([2.0, 5.0, 1.5]), np.array([7.0, 5.52, 1.5])
+    sc = room_tiny.with_pairs(tx[None], rx[None])
+    np.testing.assert_allclose(oracle.fibonacci(1)[0], [1, 0, 0], atol=1e-15)
+    r = p.voxel_size / p.dv * math.sqrt(3.0) / 2.0
+    alpha = math.radians(max(p.cone_half_angle_deg, p.launch_spacing_deg / math.sqrt(2.0)))
+
+    def reaches(cen):
+        v = np.asarray(cen) - tx
+        ang = math.acos(v[0] / np.linalg.norm(v))
+        return ang <= alpha + math.asin(r / np.linalg.norm(v))
+
+    s = oracle.Scene.from_scene(sc, p)
+    centre = s.origin + (np.floor((rx - s.origin) / (p.voxel_size / p.dv)) + 0.5) * (p.voxel_size / p.dv)
+    np.testing.assert_allclose(centre, [7.125, 5.625, 1.625])
+    assert reaches(rx) and not reaches(centre)
+    c = s.trace(sc.tx, sc.rx)
+    C = c.paths()
+    assert list(C["n"]) == [0]
+    assert C["miss"][0] == pytest.approx(0.52, abs=1e-9)
+    P = s.refine(c).paths()
+    assert len(P["n"]) == 1 and P["length"][0] == pytest.approx(np.linalg.norm(rx - tx), rel=1e-12)

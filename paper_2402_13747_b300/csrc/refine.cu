@@ -137,66 +137,79 @@ __device__ void fill_cache(const DScene& s, LabelCache& lc, const int gR[3], uin
   __syncwarp();
 }
 
+// The cached entities selected for one Eq. 1 evaluation, in cache order, as a flat
+// list of points: entity j holds points [beg[j], end[j]) of the list, its first one
+// at pb[j] in the scene.  Per warp, in shared memory.
+struct SelList {
+  uint32_t end[32];
+  uint32_t beg[32];
+  uint32_t pb[32];
+};
+
 // Eq. 1 over the nearby points of one label -- the points of the cached IEs whose
 // subvoxel lies in the 3x3x3 block around the subvoxel of x -- in FP32 in a frame
 // centred on c0 (the target); xl = x - c0, dg = subvoxel of x minus gR.  The block's
-// IEs are found with one ballot per 32 cache entries and taken IE_BATCH at a time:
-// lane k reads point k of each IE of the batch before any of them is summed, so
-// IE_BATCH loads are in flight per lane (the kernel is bound by latency).
-// Each lane adds its points in IE order; every lane returns the same f and normal.
-constexpr int IE_BATCH = 2;
-__device__ bool sdf_label_warp(const DScene& s, const LabelCache& lc, float3 xl, const int dg[3], float3 c0,
-                               float* f, float3* n_out, int lane, unsigned long long& bytes) {
+// entities (at most one per subvoxel and label, so at most 27) are found with one
+// ballot per 32 cache entries and laid out as one flat list of their points; lane l
+// takes points l and l + 32 of every 64 of it, so every lane has two points' loads
+// in flight and no lane idles at an entity's end.  Every lane returns the same f
+// and normal.  REFINE_PTS is the number of points (loads in flight) per lane and pass.
+#ifndef REFINE_PTS
+#define REFINE_PTS 2
+#endif
+__device__ bool sdf_label_warp(const DScene& s, const LabelCache& lc, SelList& sl, float3 xl, const int dg[3],
+                               float3 c0, float* f, float3* n_out, int lane, unsigned long long& bytes) {
   if (abs(dg[0]) > 1 || abs(dg[1]) > 1 || abs(dg[2]) > 1) return false;
   const int di = (dg[2] + 1) * 9 + (dg[1] + 1) * 3 + dg[0] + 1;
   const int nc = lc.n;
   static_assert(RCAP <= 96, "three ballots cover the cache");
-  const unsigned sel0 = __ballot_sync(FULL, lane < nc && ((lc.nbr[lane] >> di) & 1u));
-  const unsigned sel1 = __ballot_sync(FULL, 32 + lane < nc && ((lc.nbr[32 + lane] >> di) & 1u));
-  const unsigned sel2 = __ballot_sync(FULL, 64 + lane < nc && ((lc.nbr[64 + lane] >> di) & 1u));
-  float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  int r = 0;
-  unsigned m = sel0;
-  uint32_t total = 0;
-  for (;;) {
-    uint32_t pb[IE_BATCH], pc[IE_BATCH];
-    int got = 0;
+  const bool b0 = lane < nc && ((lc.nbr[lane] >> di) & 1u);
+  const bool b1 = 32 + lane < nc && ((lc.nbr[32 + lane] >> di) & 1u);
+  const bool b2 = 64 + lane < nc && ((lc.nbr[64 + lane] >> di) & 1u);
+  const unsigned sel0 = __ballot_sync(FULL, b0), sel1 = __ballot_sync(FULL, b1), sel2 = __ballot_sync(FULL, b2);
+  const unsigned lt = (1u << lane) - 1u;
+  const int n0 = __popc(sel0), n01 = n0 + __popc(sel1), ns = n01 + __popc(sel2);
+  // entity j of the list: its first point and count, written by the lane that holds it
+  if (b0) { sl.pb[__popc(sel0 & lt)] = lc.pb[lane]; sl.beg[__popc(sel0 & lt)] = lc.pc[lane]; }
+  if (b1) { sl.pb[n0 + __popc(sel1 & lt)] = lc.pb[32 + lane]; sl.beg[n0 + __popc(sel1 & lt)] = lc.pc[32 + lane]; }
+  if (b2) { sl.pb[n01 + __popc(sel2 & lt)] = lc.pb[64 + lane]; sl.beg[n01 + __popc(sel2 & lt)] = lc.pc[64 + lane]; }
+  __syncwarp();
+  const uint32_t pc = lane < ns ? sl.beg[lane] : 0u;
+  uint32_t e = pc;   // inclusive scan of the counts: the list end of entity `lane`
 #pragma unroll
-    for (int u = 0; u < IE_BATCH; ++u) {
-      while (!m && r < 2) {
-        ++r;
-        m = r == 1 ? sel1 : sel2;
-      }
-      pb[u] = 0;
-      pc[u] = 0;
-      if (m) {
-        const int q = 32 * r + __ffs(m) - 1;
-        m &= m - 1;
-        pb[u] = lc.pb[q];
-        pc[u] = lc.pc[q];
-        ++got;
-      }
-    }
-    if (!got) break;
-    uint32_t most = 0;
-#pragma unroll
-    for (int u = 0; u < IE_BATCH; ++u) {
-      most = max(most, pc[u]);
-      total += pc[u];
-    }
-    for (uint32_t k = lane; k < most; k += 32) {
-      float4 P[IE_BATCH], N[IE_BATCH];
-#pragma unroll
-      for (int u = 0; u < IE_BATCH; ++u) {   // past an IE's end: re-read its first point, unused
-        const uint32_t kk = k < pc[u] ? k : 0u;
-        P[u] = __ldg(&s.pts[pb[u] + kk]);
-        N[u] = __ldg(&s.pnrm[pb[u] + kk]);
-      }
-#pragma unroll
-      for (int u = 0; u < IE_BATCH; ++u)
-        if (k < pc[u]) eq1_term(v, xl, P[u], N[u], c0, s.sdf_inv_s2);
-    }
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(FULL, e, o);
+    if (lane >= o) e += t;
   }
+  const uint32_t total = __shfl_sync(FULL, e, 31);
+  __syncwarp();
+  sl.end[lane] = e;
+  sl.beg[lane] = e - pc;
+  __syncwarp();
+  float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  int j[REFINE_PTS];
+#pragma unroll
+  for (int u = 0; u < REFINE_PTS; ++u) j[u] = 0;
+  for (uint32_t base = 0; base < total; base += 32 * REFINE_PTS) {
+    float4 P[REFINE_PTS], N[REFINE_PTS];
+    bool in[REFINE_PTS];
+#pragma unroll
+    for (int u = 0; u < REFINE_PTS; ++u) {
+      const uint32_t q = base + 32 * u + lane;
+      in[u] = q < total;
+      if (u > 0) j[u] = max(j[u], j[u - 1]);
+      if (in[u])
+        while (q >= sl.end[j[u]]) ++j[u];
+      // past the list's end: re-read a point of the list, unused
+      const uint32_t a = in[u] ? sl.pb[j[u]] + (q - sl.beg[j[u]]) : sl.pb[0];
+      P[u] = __ldg(&s.pts[a]);
+      N[u] = __ldg(&s.pnrm[a]);
+    }
+#pragma unroll
+    for (int u = 0; u < REFINE_PTS; ++u)
+      if (in[u]) eq1_term(v, xl, P[u], N[u], c0, s.sdf_inv_s2);
+  }
+  __syncwarp();
   if (lane == 0) bytes += 24ull * total;
   wsum8(v, lane);
   return eq1_finish(v, xl, f, n_out);
@@ -217,7 +230,7 @@ __device__ __forceinline__ void rel_subvoxel(const DScene& s, float3 c0, float3 
 // centred on R.  The march runs in FP32 relative to R; the new point is R plus the
 // FP32 offset along the ray, in FP64.
 __device__ bool reproject_warp(const DScene& s, const d3* Pp, const d3* Rp, uint32_t label, d3* c_out, float3* n_out,
-                               int lane, unsigned long long& bytes, LabelCache& lc) {
+                               int lane, unsigned long long& bytes, LabelCache& lc, SelList& sl) {
   const d3 P = *Pp, R = *Rp;
   const float3 dvf = tof(R - P);
   const float tR = len(dvf);                // FP32: only compared with offsets of the segment
@@ -239,14 +252,14 @@ __device__ bool reproject_warp(const DScene& s, const d3* Pp, const d3* Rp, uint
     float3 x = r0 + t * d;
     int g[3];
     rel_subvoxel(s, c0, x, gR, g);
-    return sdf_label_warp(s, lc, x, g, c0, fo, no, lane, bytes);
+    return sdf_label_warp(s, lc, sl, x, g, c0, fo, no, lane, bytes);
   };
   if (!march_abs_f<false>(eval, d, -half, half, s.sdf_eps, s.sdf_max_steps, &th)) return false;
   // the placed hit must stay on the marched segment (and in front of P)
   if (!(tR + th > 0.f) || fabsf(th) > half) return false;
   float3 xl = r0 + th * d;
   rel_subvoxel(s, c0, xl, gR, dg);
-  if (!sdf_label_warp(s, lc, xl, dg, c0, &f, &n, lane, bytes)) return false;
+  if (!sdf_label_warp(s, lc, sl, xl, dg, c0, &f, &n, lane, bytes)) return false;
   *c_out = *Rp + (double)th * tod(d);
   *n_out = n;
   return true;
@@ -262,13 +275,14 @@ __device__ bool reproject_warp(const DScene& s, const d3* Pp, const d3* Rp, uint
 // points and the path length are FP64; directions, gradient, local Hessian and step
 // are FP32 evaluations from FP64 differences, except that once ||grad|| < delta the
 // gradient that decides the stop and drives the last steps is FP64.
-// Occupancy: six 4-warp blocks per SM (80 registers a thread; 7 KB of static and
+// Occupancy: six 4-warp blocks per SM (80 registers a thread; 8.3 KB of static and
 // 14 KB of dynamic shared memory a block for three reflections).  The kernel is bound
-// by latency: resident warps pay most (measured on the noisy-room workload: 4 blocks
-// with four IEs' loads in flight per lane 4.41 s, 5 blocks with three 3.85 s, 6
-// blocks with two 3.72 s), and any sizeable register spill in the point loop costs
-// more than any of it.  So each path's FP64 state lives in shared memory (WarpPath),
-// indexed by node (0 = TX, n+1 = RX), and is read where it is used.
+// by latency: resident warps pay most (measured with the flat point list on the
+// indoor and noisy-room workloads: 2 points per lane and 6 blocks 5.08 / 2.71 s, 3
+// and 6 4.80 / 2.79 s, 4 and 5 5.14 / 2.96 s, 3 and 5 5.31 / 2.93 s), and any
+// sizeable register spill in the point loop costs more than any of it.  So each
+// path's FP64 state lives in shared memory (WarpPath), indexed by node (0 = TX,
+// n+1 = RX), and is read where it is used.
 struct WarpPath {
   d3 I[NB_MAXI + 2], c[NB_MAXI + 2], R[NB_MAXI + 2], In[NB_MAXI + 2], p0[NB_MAXI + 2];
   double tpar[NB_MAXI + 2];
@@ -276,13 +290,17 @@ struct WarpPath {
   float elen[NB_MAXI + 2];
 };
 
-__global__ void __launch_bounds__(128, 6) k_refine(DScene s, DRefine rp, CoarseView C, const double* txd,
+#ifndef REFINE_BLOCKS_PER_SM
+#define REFINE_BLOCKS_PER_SM 6
+#endif
+__global__ void __launch_bounds__(128, REFINE_BLOCKS_PER_SM) k_refine(DScene s, DRefine rp, CoarseView C, const double* txd,
                                                    const double* rxd, ExactRec* out, unsigned long long* bytes_out,
                                                    unsigned long long* next_path, const uint32_t* order, int n_cache) {
   // label caches: n_cache per warp (the trace's reflection limit), in dynamic shared
   // memory, so that the rest of the SM's 256 KB stays L1 for the point loads
   extern __shared__ LabelCache s_dyn[];
   __shared__ WarpPath s_path[4];
+  __shared__ SelList s_sel[4];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   LabelCache* cache = s_dyn + wib * n_cache;
   WarpPath& W = s_path[wib];
@@ -433,7 +451,7 @@ __global__ void __launch_bounds__(128, 6) k_refine(DScene s, DRefine rp, CoarseV
           status = ST_MISS;
           break;
         }
-        if (!reproject_warp(s, &W.I[k - 1], &W.R[k], lk, &cn, &nn, lane, bytes, cache[r])) {
+        if (!reproject_warp(s, &W.I[k - 1], &W.R[k], lk, &cn, &nn, lane, bytes, cache[r], s_sel[wib])) {
           status = ST_MISS;
           break;
         }

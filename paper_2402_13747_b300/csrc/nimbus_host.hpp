@@ -289,6 +289,8 @@ struct SceneObj : Obj {
   uint32_t max_label = 0;
   // derived tables (owned; freed and rebuilt by region updates)
   std::vector<void*> table_bufs;
+  uint32_t* ie_start = nullptr;   // [n_ie + 1] first entry of each IE in the grouped point table
+  uint32_t* ie_cell = nullptr;    // [n_ie] voxel of each IE
 };
 
 // Coarse paths after the kappa limit (Section 2.2.3), structure of arrays.

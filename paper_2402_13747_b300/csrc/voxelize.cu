@@ -302,6 +302,52 @@ __global__ void k_march_axis(const uint8_t* __restrict__ din, uint8_t* __restric
   dout[i] = (uint8_t)best;
 }
 
+// Edge pieces per edge (the same FP64 steps as the device kernel): nf[e] pieces of
+// length <= h_s / 4, slots off[e]..off[e+1] of the sort.
+int edge_layout(std::string* err, const SceneObj* S, std::vector<int64_t>& off, std::vector<int32_t>& nf) {
+  const int64_t n_edges = (int64_t)S->edge_label_h.size();
+  const double hs = S->params.voxel_size / S->params.dv;
+  off.assign(n_edges + 1, 0);
+  nf.assign(n_edges, 1);
+  for (int64_t e = 0; e < n_edges; ++e) {
+    const double* E = &S->edges_h[12 * e];
+    double dx = E[3] - E[0], dy = E[4] - E[1], dz = E[5] - E[2];
+    double L = std::sqrt(dx * dx + dy * dy + dz * dz);
+    double q = std::ceil(L / (hs / 4.0));
+    if (q > 1e8) {
+      *err = "edge too long";
+      return NIMBUS_ERR_ARG;
+    }
+    nf[e] = std::max(1, (int)q);
+    off[e + 1] = off[e] + nf[e];
+  }
+  return NIMBUS_OK;
+}
+
+// Grid constants of the sort key and its width for the scene's grid, labels and edges.
+int grid_keys(std::string* err, const SceneObj* S, GridK* g, int* key_bits) {
+  const int dv = S->params.dv;
+  const int64_t n_edges = (int64_t)S->edge_label_h.size();
+  const int64_t n_cells = (int64_t)S->dims[0] * S->dims[1] * S->dims[2];
+  for (int a = 0; a < 3; ++a) {
+    g->o[a] = (float)S->origin[a];
+    g->gmax[a] = S->dims[a] * dv - 1;
+  }
+  g->hs = (float)(S->params.voxel_size / dv);
+  g->dv = dv;
+  g->nx = S->dims[0];
+  g->ny = S->dims[1];
+  g->sub_bits = std::max(1, bits_for((uint64_t)dv * dv * dv - 1));
+  uint64_t max_id = std::max<uint64_t>(S->max_label, n_edges > 0 ? (uint64_t)(n_edges - 1) : 0);
+  g->id_bits = std::max(1, bits_for(max_id));
+  *key_bits = bits_for((uint64_t)n_cells) + g->sub_bits + 1 + g->id_bits;
+  if (*key_bits > 64) {
+    *err = "sort key exceeds 64 bits (labels or grid too large)";
+    return NIMBUS_ERR_ARG;
+  }
+  return NIMBUS_OK;
+}
+
 // Build every derived table of a scene from its device cloud on a fixed grid.
 int build_tables(Mem& mem, SceneObj* S, cudaStream_t st) {
   std::string* err = mem.err;
@@ -315,21 +361,9 @@ int build_tables(Mem& mem, SceneObj* S, cudaStream_t st) {
     return NIMBUS_ERR_ARG;
   }
   const double h = S->params.voxel_size, hs = h / dv;
-  // edge pieces per edge (same FP64 steps as the device kernel)
-  std::vector<int64_t> off(n_edges + 1, 0);
-  std::vector<int32_t> nf(n_edges, 1);
-  for (int64_t e = 0; e < n_edges; ++e) {
-    const double* E = &S->edges_h[12 * e];
-    double dx = E[3] - E[0], dy = E[4] - E[1], dz = E[5] - E[2];
-    double L = std::sqrt(dx * dx + dy * dy + dz * dz);
-    double q = std::ceil(L / (hs / 4.0));
-    if (q > 1e8) {
-      *err = "edge too long";
-      return NIMBUS_ERR_ARG;
-    }
-    nf[e] = std::max(1, (int)q);
-    off[e + 1] = off[e] + nf[e];
-  }
+  std::vector<int64_t> off;
+  std::vector<int32_t> nf;
+  NB_TRY(edge_layout(err, S, off, nf));
   const int64_t n_piece_slots = off[n_edges];
   const int64_t n_total = n + n_piece_slots;
   if (n_total >= (1ll << 32) - 2) {
@@ -337,23 +371,8 @@ int build_tables(Mem& mem, SceneObj* S, cudaStream_t st) {
     return NIMBUS_ERR_ARG;
   }
   GridK g;
-  for (int a = 0; a < 3; ++a) {
-    g.o[a] = (float)S->origin[a];
-    g.gmax[a] = S->dims[a] * dv - 1;
-  }
-  g.hs = (float)hs;
-  g.dv = dv;
-  g.nx = S->dims[0];
-  g.ny = S->dims[1];
-  g.sub_bits = std::max(1, bits_for((uint64_t)dv * dv * dv - 1));
-  uint64_t max_id = std::max<uint64_t>(S->max_label, n_edges > 0 ? (uint64_t)(n_edges - 1) : 0);
-  g.id_bits = std::max(1, bits_for(max_id));
-  int cell_bits = bits_for((uint64_t)n_cells);
-  int key_bits = cell_bits + g.sub_bits + 1 + g.id_bits;
-  if (key_bits > 64) {
-    *err = "sort key exceeds 64 bits (labels or grid too large)";
-    return NIMBUS_ERR_ARG;
-  }
+  int key_bits = 0;
+  NB_TRY(grid_keys(err, S, &g, &key_bits));
   uint64_t *keys, *keys_alt;
   uint32_t *vals, *vals_alt, *flags, *ids, *counter;
   int4* pieces;
@@ -399,13 +418,6 @@ int build_tables(Mem& mem, SceneObj* S, cudaStream_t st) {
   NB_CUDA(err, cudaStreamSynchronize(st));
   const int64_t n_valid = n + hc[0];
   const int64_t n_ie = hc[1];
-  uint32_t* starts;
-  uint32_t* ie_cell;
-  NB_TRY(sc.get(&starts, n_ie + 1));
-  NB_TRY(sc.get(&ie_cell, std::max<int64_t>(1, n_ie)));
-  k_run_starts<<<G, B, 0, st>>>(flags, ids, n_total, starts, (uint32_t)n_ie, (uint32_t)n_valid);
-  NB_LAUNCHED(err);
-
   // owned tables: freed first if this is a rebuild
   for (void* p : S->table_bufs) mem.release(p, st);
   S->table_bufs.clear();
@@ -414,6 +426,13 @@ int build_tables(Mem& mem, SceneObj* S, cudaStream_t st) {
     if (rc == NIMBUS_OK) S->table_bufs.push_back(*p);
     return rc;
   };
+  // each IE's first entry and its voxel are kept for region updates
+  uint32_t* starts;
+  uint32_t* ie_cell;
+  NB_TRY(own(&starts, n_ie + 1));
+  NB_TRY(own(&ie_cell, std::max<int64_t>(1, n_ie)));
+  k_run_starts<<<G, B, 0, st>>>(flags, ids, n_total, starts, (uint32_t)n_ie, (uint32_t)n_valid);
+  NB_LAUNCHED(err);
   float4 *pts, *pnrm;
   IERec* ies;
   uint2* cells;
@@ -460,6 +479,8 @@ int build_tables(Mem& mem, SceneObj* S, cudaStream_t st) {
   // the scratch buffers are released when sc leaves scope (stream-ordered)
   S->n_ie = n_ie;
   S->n_slots = n_valid;
+  S->ie_start = starts;
+  S->ie_cell = ie_cell;
   DScene& d = S->d;
   d.cells = cells;
   d.march = march;
@@ -644,6 +665,396 @@ __global__ void k_compact_points(const float* __restrict__ xyz, const float* __r
 }
 }  // namespace
 
+// ----------------------------------------------------------- region-local rebuild
+// A region update re-bins only the voxels whose points change: those that lose a
+// point to the region or gain one from the replacement ("affected").  Their points
+// and edge pieces are sorted on their own and reduced to IEs exactly as the full
+// build does; the IEs and point entries of every other voxel are copied, in voxel
+// order, to the positions a full build of the new cloud gives them.  The full
+// build's order is a stable sort by (voxel, subvoxel, kind, label), so the result
+// equals it entry for entry.
+namespace {
+
+__device__ __forceinline__ uint32_t cell_of_point(const GridK& g, const float* xyz) {
+  int gs[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) gs[a] = subvoxel_axis(xyz[a], g.o[a], g.hs, g.gmax[a]);
+  return (uint32_t)(((uint64_t)(gs[2] / g.dv) * g.ny + (gs[1] / g.dv)) * g.nx + (gs[0] / g.dv));
+}
+
+// Voxels of the points in [i0, i1) with want(i): marked affected.
+__global__ void k_mark_cells(GridK g, const float* __restrict__ xyz, int64_t i0, int64_t i1,
+                             const uint32_t* __restrict__ keep, uint32_t* __restrict__ aff) {
+  for (int64_t i = i0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < i1; i += (int64_t)gridDim.x * blockDim.x)
+    if (!keep || !keep[i]) aff[cell_of_point(g, xyz + 3 * i)] = 1u;
+}
+
+__global__ void k_points_in_cells(GridK g, const float* __restrict__ xyz, int64_t n, const uint32_t* __restrict__ aff,
+                                  uint32_t* __restrict__ flag) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    flag[i] = aff[cell_of_point(g, xyz + 3 * i)];
+}
+
+__global__ void k_edges_in_cells(const uint64_t* __restrict__ keys, int64_t n, int cell_shift,
+                                 const uint32_t* __restrict__ aff, uint32_t* __restrict__ flag) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    flag[i] = keys[i] != INVALID_KEY && aff[keys[i] >> cell_shift] ? 1u : 0u;
+}
+
+// Local sort entries: the flagged points (new-cloud index as value), then the flagged
+// edge-piece runs (value n_points + slot), each list in index order -- the order of
+// equal keys in the full build's stable sort.
+__global__ void k_local_entries(GridK g, const float* __restrict__ xyz, const uint32_t* __restrict__ label,
+                                int64_t n_points, const uint32_t* __restrict__ pflag, const uint32_t* __restrict__ ppos,
+                                const uint64_t* __restrict__ ekeys, int64_t n_slots, const uint32_t* __restrict__ eflag,
+                                const uint32_t* __restrict__ epos, const uint32_t* __restrict__ m_pts,
+                                uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+  const int64_t total = n_points + n_slots;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    if (i < n_points) {
+      if (!pflag[i]) continue;
+      int gs[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) gs[a] = subvoxel_axis(xyz[3 * i + a], g.o[a], g.hs, g.gmax[a]);
+      keys[ppos[i]] = pack_key(g, gs, IE_POINT, label[i]);
+      vals[ppos[i]] = (uint32_t)i;
+    } else {
+      const int64_t e = i - n_points;
+      if (!eflag[e]) continue;
+      const uint32_t j = *m_pts + epos[e];
+      keys[j] = ekeys[e];
+      vals[j] = (uint32_t)(n_points + e);
+    }
+  }
+}
+
+// Per voxel: the local IE count, entry count and first local IE / entry.
+__global__ void k_local_tally(const uint32_t* __restrict__ l_cell, const uint32_t* __restrict__ l_start, int64_t n_l,
+                              uint32_t* __restrict__ cnt, uint32_t* __restrict__ ent, uint32_t* __restrict__ first_ie,
+                              uint32_t* __restrict__ first_ent) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n_l; j += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t c = l_cell[j];
+    atomicAdd(&cnt[c], 1u);
+    atomicAdd(&ent[c], l_start[j + 1] - l_start[j]);
+    if (j == 0 || l_cell[j - 1] != c) {
+      first_ie[c] = (uint32_t)j;
+      first_ent[c] = l_start[j];
+    }
+  }
+}
+
+// New IE and entry counts of every voxel: the local ones where affected, else the old.
+__global__ void k_new_counts(const uint32_t* __restrict__ aff, const uint2* __restrict__ old_cells,
+                             const uint32_t* __restrict__ old_start, const uint32_t* __restrict__ l_cnt,
+                             const uint32_t* __restrict__ l_ent, int64_t n_cells, uint32_t* __restrict__ ie_cnt,
+                             uint32_t* __restrict__ ent_cnt) {
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n_cells; c += (int64_t)gridDim.x * blockDim.x) {
+    if (aff[c]) {
+      ie_cnt[c] = l_cnt[c];
+      ent_cnt[c] = l_ent[c];
+    } else {
+      const uint2 oc = old_cells[c];
+      ie_cnt[c] = oc.y;
+      ent_cnt[c] = oc.y ? old_start[oc.x + oc.y] - old_start[oc.x] : 0u;
+    }
+  }
+}
+
+__device__ __forceinline__ bool point_ie(const IERec& r) { return (__float_as_uint(r.nrm_meta.w) & 1u) == IE_POINT; }
+
+// The IEs of unaffected voxels, moved to their new positions.
+__global__ void k_splice_old_ies(const IERec* __restrict__ old_ies, const uint32_t* __restrict__ old_start,
+                                 const uint32_t* __restrict__ old_cell, int64_t n_old, const uint2* __restrict__ old_cells,
+                                 const uint32_t* __restrict__ aff, const uint32_t* __restrict__ ie_first,
+                                 const uint32_t* __restrict__ ent_first, IERec* __restrict__ ies,
+                                 uint32_t* __restrict__ starts, uint32_t* __restrict__ cellv) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_old; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t c = old_cell[i];
+    if (aff[c]) continue;
+    const uint32_t c0 = old_cells[c].x;
+    const uint32_t ni = ie_first[c] + ((uint32_t)i - c0), ne = ent_first[c] + (old_start[i] - old_start[c0]);
+    IERec r = old_ies[i];
+    if (point_ie(r)) r.bbc_pb.w = __uint_as_float(ne);
+    ies[ni] = r;
+    starts[ni] = ne;
+    cellv[ni] = c;
+  }
+}
+
+// Their point entries: moved, with each point's index in the cloud renumbered after
+// the removal (new index = pos[old index]).
+__global__ void k_splice_old_pts(const float4* __restrict__ old_pts, const float4* __restrict__ old_nrm, int64_t n_ent,
+                                 const uint32_t* __restrict__ old_start, int64_t n_old, const uint32_t* __restrict__ old_cell,
+                                 const IERec* __restrict__ old_ies, const uint2* __restrict__ old_cells,
+                                 const uint32_t* __restrict__ aff, const uint32_t* __restrict__ ent_first,
+                                 const uint32_t* __restrict__ pos, float4* __restrict__ pts, float4* __restrict__ nrm) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n_ent; k += (int64_t)gridDim.x * blockDim.x) {
+    int64_t lo = 0, hi = n_old;   // the IE of entry k: last i with old_start[i] <= k
+    while (hi - lo > 1) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (old_start[mid] <= (uint32_t)k) lo = mid;
+      else hi = mid;
+    }
+    const uint32_t c = old_cell[lo];
+    if (aff[c]) continue;
+    const uint32_t ne = ent_first[c] + ((uint32_t)k - old_start[old_cells[c].x]);
+    float4 P = old_pts[k];
+    if (point_ie(old_ies[lo])) P.w = __uint_as_float(pos[__float_as_uint(P.w)]);
+    pts[ne] = P;
+    nrm[ne] = old_nrm[k];
+  }
+}
+
+// The rebuilt IEs of affected voxels and their entries, at their new positions.
+__global__ void k_splice_new_ies(const IERec* __restrict__ l_ies, const uint32_t* __restrict__ l_start,
+                                 const uint32_t* __restrict__ l_cell, int64_t n_l, const uint32_t* __restrict__ first_ie,
+                                 const uint32_t* __restrict__ first_ent, const uint32_t* __restrict__ ie_first,
+                                 const uint32_t* __restrict__ ent_first, IERec* __restrict__ ies,
+                                 uint32_t* __restrict__ starts, uint32_t* __restrict__ cellv) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n_l; j += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t c = l_cell[j];
+    const uint32_t ni = ie_first[c] + ((uint32_t)j - first_ie[c]), ne = ent_first[c] + (l_start[j] - first_ent[c]);
+    IERec r = l_ies[j];
+    if (point_ie(r)) r.bbc_pb.w = __uint_as_float(ne);
+    ies[ni] = r;
+    starts[ni] = ne;
+    cellv[ni] = c;
+  }
+}
+
+__global__ void k_splice_new_pts(const float4* __restrict__ l_pts, const float4* __restrict__ l_nrm, int64_t m,
+                                 const uint32_t* __restrict__ l_flags, const uint32_t* __restrict__ l_ids,
+                                 const uint32_t* __restrict__ l_cell, const uint32_t* __restrict__ first_ent,
+                                 const uint32_t* __restrict__ ent_first, float4* __restrict__ pts,
+                                 float4* __restrict__ nrm) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m; k += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t j = l_ids[k] + l_flags[k] - 1u;   // local IE of entry k
+    const uint32_t c = l_cell[j];
+    const uint32_t ne = ent_first[c] + ((uint32_t)k - first_ent[c]);
+    pts[ne] = l_pts[k];
+    nrm[ne] = l_nrm[k];
+  }
+}
+
+__global__ void k_new_cells(const uint32_t* __restrict__ ie_cnt, const uint32_t* __restrict__ ie_first, int64_t n_cells,
+                            uint2* __restrict__ cells) {
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n_cells; c += (int64_t)gridDim.x * blockDim.x)
+    cells[c] = make_uint2(ie_cnt[c] ? ie_first[c] : 0u, ie_cnt[c]);
+}
+
+__global__ void k_set_last(uint32_t* __restrict__ starts, int64_t n_ie, const uint32_t* __restrict__ total) {
+  starts[n_ie] = *total;
+}
+
+}  // namespace
+
+// The tables of the scene's new cloud (already in S) from its old tables, given the
+// affected voxels and the renumbering pos[] of the old cloud's kept points.
+int splice_region(Mem& mem, SceneObj* S, const uint32_t* aff, const uint32_t* pos, cudaStream_t st) {
+  std::string* err = mem.err;
+  Scratch sc(&mem, st);
+  const int64_t n = S->n_points, n_cells = (int64_t)S->dims[0] * S->dims[1] * S->dims[2];
+  const int64_t n_edges = (int64_t)S->edge_label_h.size();
+  const int64_t n_old = S->n_ie, n_old_ent = S->n_slots;
+  std::vector<int64_t> off;
+  std::vector<int32_t> nf;
+  NB_TRY(edge_layout(err, S, off, nf));
+  const int64_t n_slots = off[n_edges];
+  GridK g;
+  int key_bits = 0;
+  NB_TRY(grid_keys(err, S, &g, &key_bits));
+  const int cell_shift = g.sub_bits + 1 + g.id_bits;
+  const int B = 256;
+  auto grid = [&](int64_t m) { return std::min<unsigned>(grid_for(std::max<int64_t>(m, 1), B), 148u * 16u); };
+  // entries of the affected voxels: points, then edge-piece runs
+  uint32_t *pflag, *ppos, *cnt2;
+  NB_TRY(sc.get(&pflag, std::max<int64_t>(1, n)));
+  NB_TRY(sc.get(&ppos, std::max<int64_t>(1, n)));
+  NB_TRY(sc.get(&cnt2, 4));
+  NB_CUDA(err, cudaMemsetAsync(cnt2, 0, 4 * sizeof(uint32_t), st));
+  if (n > 0) {
+    k_points_in_cells<<<grid(n), B, 0, st>>>(g, S->xyz, n, aff, pflag);
+    NB_LAUNCHED(err);
+  }
+  NB_TRY(exclusive_scan(sc, pflag, ppos, n, cnt2));
+  uint64_t *ekeys = nullptr;
+  uint32_t *evals = nullptr, *eflag = nullptr, *epos = nullptr, *d_elabel = nullptr;
+  int4* pieces = nullptr;
+  int64_t* d_off = nullptr;
+  int32_t* d_nf = nullptr;
+  NB_TRY(sc.get(&pieces, std::max<int64_t>(1, n_slots)));
+  if (n_edges > 0) {
+    NB_TRY(sc.get(&ekeys, n_slots));
+    NB_TRY(sc.get(&evals, n_slots));
+    NB_TRY(sc.get(&eflag, n_slots));
+    NB_TRY(sc.get(&epos, n_slots));
+    NB_TRY(sc.get(&d_off, n_edges + 1));
+    NB_TRY(sc.get(&d_nf, n_edges));
+    NB_TRY(sc.get(&d_elabel, n_edges));
+    NB_CUDA(err, cudaMemcpyAsync(d_off, off.data(), (n_edges + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    NB_CUDA(err, cudaMemcpyAsync(d_nf, nf.data(), n_edges * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    NB_CUDA(err, cudaMemcpyAsync(d_elabel, S->edge_label_h.data(), n_edges * sizeof(uint32_t),
+                                 cudaMemcpyHostToDevice, st));
+    k_edge_pieces<<<grid_for(n_edges, 64), 64, 0, st>>>(g, S->d.edges, (int)n_edges, d_off, d_nf, 0, ekeys, evals,
+                                                         pieces, cnt2 + 2);
+    NB_LAUNCHED(err);
+    k_edges_in_cells<<<grid(n_slots), B, 0, st>>>(ekeys, n_slots, cell_shift, aff, eflag);
+    NB_LAUNCHED(err);
+    NB_TRY(exclusive_scan(sc, eflag, epos, n_slots, cnt2 + 1));
+  }
+  uint32_t hm[2] = {0, 0};
+  NB_CUDA(err, cudaMemcpyAsync(hm, cnt2, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+  NB_CUDA(err, cudaStreamSynchronize(st));
+  const int64_t m = (int64_t)hm[0] + hm[1];
+  // local sort and IE build (as in build_tables, on the affected voxels only)
+  uint64_t *keys, *keys_alt;
+  uint32_t *vals, *vals_alt, *flags, *ids, *l_n;
+  NB_TRY(sc.get(&keys, std::max<int64_t>(1, m)));
+  NB_TRY(sc.get(&keys_alt, std::max<int64_t>(1, m)));
+  NB_TRY(sc.get(&vals, std::max<int64_t>(1, m)));
+  NB_TRY(sc.get(&vals_alt, std::max<int64_t>(1, m)));
+  NB_TRY(sc.get(&flags, std::max<int64_t>(1, m)));
+  NB_TRY(sc.get(&ids, std::max<int64_t>(1, m)));
+  NB_TRY(sc.get(&l_n, 1));
+  if (m > 0) {
+    k_local_entries<<<grid(n + n_slots), B, 0, st>>>(g, S->xyz, S->label, n, pflag, ppos, ekeys, n_edges > 0 ? n_slots : 0,
+                                                    eflag, epos, cnt2, keys, vals);
+    NB_LAUNCHED(err);
+    NB_TRY(radix_sort(sc, keys, vals, keys_alt, vals_alt, m, key_bits));
+    k_run_flags<<<grid(m), B, 0, st>>>(keys, m, flags);
+    NB_LAUNCHED(err);
+  }
+  NB_TRY(exclusive_scan(sc, flags, ids, m, l_n));
+  uint32_t hl = 0;
+  NB_CUDA(err, cudaMemcpyAsync(&hl, l_n, sizeof hl, cudaMemcpyDeviceToHost, st));
+  NB_CUDA(err, cudaStreamSynchronize(st));
+  const int64_t n_l = hl;
+  uint32_t *l_start, *l_cell;
+  float4 *l_pts, *l_nrm;
+  IERec* l_ies;
+  NB_TRY(sc.get(&l_start, n_l + 1));
+  NB_TRY(sc.get(&l_cell, std::max<int64_t>(1, n_l)));
+  NB_TRY(sc.get(&l_pts, std::max<int64_t>(1, m)));
+  NB_TRY(sc.get(&l_nrm, std::max<int64_t>(1, m)));
+  NB_TRY(sc.get(&l_ies, std::max<int64_t>(1, n_l)));
+  k_run_starts<<<grid(m), B, 0, st>>>(flags, ids, m, l_start, (uint32_t)n_l, (uint32_t)m);
+  NB_LAUNCHED(err);
+  if (m > 0) {
+    k_gather<<<grid(m), B, 0, st>>>(vals, m, n, S->xyz, S->nrm, l_pts, l_nrm);
+    NB_LAUNCHED(err);
+  }
+  if (n_l > 0) {
+    BuildK bk;
+    bk.g = g;
+    for (int a = 0; a < 3; ++a) bk.o[a] = S->origin[a];
+    bk.hs = S->params.voxel_size / S->params.dv;
+    bk.n_points = n;
+    bk.n_ie = (int)n_l;
+    k_ie_build<<<grid_for(n_l, 128), 128, 0, st>>>(bk, keys, vals, l_start, l_pts, l_nrm, S->material, pieces,
+                                                   S->d.edges, l_ies, l_cell);
+    NB_LAUNCHED(err);
+    if (n_edges > 0) {
+      k_edge_labels<<<grid_for(n_l, 256), 256, 0, st>>>(l_ies, (int)n_l, d_elabel);
+      NB_LAUNCHED(err);
+    }
+  }
+  // new counts per voxel, and where each voxel's IEs and entries start
+  uint32_t *l_cnt, *l_ent, *first_ie, *first_ent, *ie_cnt, *ent_cnt, *ie_first, *ent_first, *tot;
+  NB_TRY(sc.get(&l_cnt, n_cells));
+  NB_TRY(sc.get(&l_ent, n_cells));
+  NB_TRY(sc.get(&first_ie, n_cells));
+  NB_TRY(sc.get(&first_ent, n_cells));
+  NB_TRY(sc.get(&ie_cnt, n_cells));
+  NB_TRY(sc.get(&ent_cnt, n_cells));
+  NB_TRY(sc.get(&ie_first, n_cells));
+  NB_TRY(sc.get(&ent_first, n_cells));
+  NB_TRY(sc.get(&tot, 2));
+  NB_CUDA(err, cudaMemsetAsync(l_cnt, 0, n_cells * sizeof(uint32_t), st));
+  NB_CUDA(err, cudaMemsetAsync(l_ent, 0, n_cells * sizeof(uint32_t), st));
+  if (n_l > 0) {
+    k_local_tally<<<grid(n_l), B, 0, st>>>(l_cell, l_start, n_l, l_cnt, l_ent, first_ie, first_ent);
+    NB_LAUNCHED(err);
+  }
+  k_new_counts<<<grid(n_cells), B, 0, st>>>(aff, S->d.cells, S->ie_start, l_cnt, l_ent, n_cells, ie_cnt, ent_cnt);
+  NB_LAUNCHED(err);
+  NB_TRY(exclusive_scan(sc, ie_cnt, ie_first, n_cells, tot));
+  NB_TRY(exclusive_scan(sc, ent_cnt, ent_first, n_cells, tot + 1));
+  uint32_t ht[2] = {0, 0};
+  NB_CUDA(err, cudaMemcpyAsync(ht, tot, sizeof ht, cudaMemcpyDeviceToHost, st));
+  NB_CUDA(err, cudaStreamSynchronize(st));
+  const int64_t n_ie = ht[0], n_valid = ht[1];
+  // the new tables
+  std::vector<void*> old_bufs = S->table_bufs;
+  std::vector<void*> bufs;
+  auto own = [&](auto** p, size_t c) {
+    int rc = mem.alloc_n(p, c, st);
+    if (rc == NIMBUS_OK) bufs.push_back(*p);
+    return rc;
+  };
+  auto drop_new = [&]() {
+    for (void* p : bufs) mem.release(p, st);
+  };
+  uint32_t *starts, *cellv;
+  float4 *pts, *pnrm;
+  IERec* ies;
+  uint2* cells;
+  uint8_t *march, *d1, *d2;
+  int rc = NIMBUS_OK;
+  if ((rc = own(&starts, n_ie + 1)) != NIMBUS_OK || (rc = own(&cellv, std::max<int64_t>(1, n_ie))) != NIMBUS_OK ||
+      (rc = own(&pts, std::max<int64_t>(1, n_valid))) != NIMBUS_OK ||
+      (rc = own(&pnrm, std::max<int64_t>(1, n_valid))) != NIMBUS_OK ||
+      (rc = own(&ies, std::max<int64_t>(1, n_ie))) != NIMBUS_OK || (rc = own(&cells, n_cells)) != NIMBUS_OK ||
+      (rc = own(&march, n_cells)) != NIMBUS_OK) {
+    drop_new();
+    return rc;
+  }
+  NB_TRY(sc.get(&d1, n_cells));
+  NB_TRY(sc.get(&d2, n_cells));
+  if (n_old > 0) {
+    k_splice_old_ies<<<grid(n_old), B, 0, st>>>(S->d.ies, S->ie_start, S->ie_cell, n_old, S->d.cells, aff, ie_first,
+                                               ent_first, ies, starts, cellv);
+    NB_LAUNCHED(err);
+  }
+  if (n_old_ent > 0) {
+    k_splice_old_pts<<<grid(n_old_ent), B, 0, st>>>(S->d.pts, S->d.pnrm, n_old_ent, S->ie_start, n_old, S->ie_cell,
+                                                   S->d.ies, S->d.cells, aff, ent_first, pos, pts, pnrm);
+    NB_LAUNCHED(err);
+  }
+  if (n_l > 0) {
+    k_splice_new_ies<<<grid(n_l), B, 0, st>>>(l_ies, l_start, l_cell, n_l, first_ie, first_ent, ie_first, ent_first, ies,
+                                             starts, cellv);
+    NB_LAUNCHED(err);
+    k_splice_new_pts<<<grid(m), B, 0, st>>>(l_pts, l_nrm, m, flags, ids, l_cell, first_ent, ent_first, pts, pnrm);
+    NB_LAUNCHED(err);
+  }
+  k_set_last<<<1, 1, 0, st>>>(starts, n_ie, tot + 1);
+  NB_LAUNCHED(err);
+  k_new_cells<<<grid(n_cells), B, 0, st>>>(ie_cnt, ie_first, n_cells, cells);
+  NB_LAUNCHED(err);
+  const int nx = S->dims[0], ny = S->dims[1], nz = S->dims[2];
+  k_march_x<<<grid_for((int64_t)ny * nz, 128), 128, 0, st>>>(cells, nx, ny, nz, d1);
+  NB_LAUNCHED(err);
+  k_march_axis<<<grid_for(n_cells, 256), 256, 0, st>>>(d1, d2, nx, ny, nz, 1);
+  NB_LAUNCHED(err);
+  k_march_axis<<<grid_for(n_cells, 256), 256, 0, st>>>(d2, march, nx, ny, nz, 2);
+  NB_LAUNCHED(err);
+  // swap the tables (the old ones are released stream-ordered after the copies)
+  for (void* p : old_bufs) mem.release(p, st);
+  S->table_bufs = bufs;
+  S->n_ie = n_ie;
+  S->n_slots = n_valid;
+  S->ie_start = starts;
+  S->ie_cell = cellv;
+  DScene& d = S->d;
+  d.cells = cells;
+  d.march = march;
+  d.ies = ies;
+  d.pts = pts;
+  d.pnrm = pnrm;
+  d.n_ie = (int)n_ie;
+  return NIMBUS_OK;
+}
+
 int update_scene_region(Mem& mem, SceneObj* S, const double lo[3], const double hi[3], const nimbus_cloud* repl,
                         cudaStream_t st) {
   std::string* err = mem.err;
@@ -664,6 +1075,22 @@ int update_scene_region(Mem& mem, SceneObj* S, const double lo[3], const double 
     NB_LAUNCHED(err);
   }
   NB_TRY(exclusive_scan(sc, keep, pos, n, cnt));
+  // voxels that lose points (marked now, on the old cloud) or gain replacement
+  // points (marked below) are the only ones re-binned
+  const int64_t n_cells = (int64_t)S->dims[0] * S->dims[1] * S->dims[2];
+  const bool local = S->ie_start != nullptr && S->ie_cell != nullptr;
+  uint32_t* aff = nullptr;
+  GridK gm;
+  int kb_unused = 0;
+  if (local) {
+    NB_TRY(grid_keys(err, S, &gm, &kb_unused));
+    NB_TRY(sc.get(&aff, n_cells));
+    NB_CUDA(err, cudaMemsetAsync(aff, 0, n_cells * sizeof(uint32_t), st));
+    if (n > 0) {
+      k_mark_cells<<<std::min<unsigned>(grid_for(n, 256), 148u * 8u), 256, 0, st>>>(gm, S->xyz, 0, n, keep, aff);
+      NB_LAUNCHED(err);
+    }
+  }
   uint32_t n_keep = 0;
   NB_CUDA(err, cudaMemcpyAsync(&n_keep, cnt, sizeof n_keep, cudaMemcpyDeviceToHost, st));
   NB_CUDA(err, cudaStreamSynchronize(st));
@@ -710,7 +1137,13 @@ int update_scene_region(Mem& mem, SceneObj* S, const double lo[3], const double 
   S->label = nlab;
   S->material = nmat;
   S->n_points = n_new;
-  return build_tables(mem, S, st);
+  if (!local) return build_tables(mem, S, st);
+  if (nr > 0) {
+    k_mark_cells<<<std::min<unsigned>(grid_for(nr, 256), 148u * 8u), 256, 0, st>>>(gm, nxyz, n_keep, n_new, nullptr,
+                                                                                   aff);
+    NB_LAUNCHED(err);
+  }
+  return splice_region(mem, S, aff, pos, st);
 }
 
 // ----------------------------------------------------------- scene checkpoint

@@ -73,15 +73,17 @@ class Scheduler:
             self.cv.notify_all()
 
     def _form(self):
-        """Oldest request plus followers on the same scene with the same depth (so a
-        batch ends together), within the pair, TX and memory limits."""
+        """Oldest request plus followers on the same scene, of any depth (each RX keeps
+        its request's depth limit and each TX's tree grows only as deep as its own
+        RXs need, so a request's paths do not depend on its batch), within the pair,
+        TX and memory limits."""
         if not self.queue:
             return None
         head = self.queue[0]
         free = self.mem_budget - self.in_flight
         batch, pairs, depth = [], 0, 0
         for r in list(self.queue):
-            if r.scene != head.scene or r.depth != head.depth:
+            if r.scene != head.scene:
                 continue
             d = max(depth, r.depth)
             est = request_bytes(pairs + r.pairs, d) * (len(batch) + 1)
@@ -132,14 +134,21 @@ class GpuExecutor:
         self.handles = {}
         self.applied = {}
         self.need = {}   # (scene, depth) -> largest node / coarse counts per TX seen so far
+        self.resident = {}   # device bytes of each resident scene in this worker's context
+        self.update_ms = []  # wall time of each region update applied
         for sid, sc in scenes.items():
+            before = self.ctx.memory_used()
             self.handles[sid] = self.ctx.voxelize_scene(sc, params, stream=self.stream)
+            self.resident[sid] = self.ctx.memory_used() - before
             self.applied[sid] = 0
 
     def apply_updates(self, sid: str, updates: list):
         for k in range(self.applied.get(sid, 0), len(updates)):
             lo, hi, cloud = updates[k]
+            t0 = time.perf_counter()
             self.ctx.update_region(self.handles[sid], lo, hi, *cloud, stream=self.stream)
+            self.stream.synchronize()
+            self.update_ms.append(1e3 * (time.perf_counter() - t0))
         self.applied[sid] = len(updates)
 
     def run(self, batch: list[Request]) -> list[dict]:
@@ -267,24 +276,32 @@ class Server:
             if hasattr(e, "close"):
                 e.close()
 
-    def stats(self) -> dict:
-        lat = np.array([r.t_done - r.t_arrival for r in self.completed])
-        svc = np.array([r.t_done - r.t_start for r in self.completed])
-        paths = sum(len(r.future.result()["n"]) for r in self.completed if r.future.done()
-                    and r.future.exception() is None)
-        return {"requests": len(self.completed), "batches": self.batches,
-                "p50_ms": float(np.percentile(lat, 50) * 1e3) if len(lat) else None,
-                "p99_ms": float(np.percentile(lat, 99) * 1e3) if len(lat) else None,
-                "service_p50_ms": float(np.percentile(svc, 50) * 1e3) if len(svc) else None,
-                "service_p99_ms": float(np.percentile(svc, 99) * 1e3) if len(svc) else None, "exact_paths": paths,
-                "cones": self.cones}
+    def stats(self, since: int = 0) -> dict:
+        """Latency (arrival to result), service time (batch start to result) and
+        counts over the requests completed after the first `since`; per class
+        (scene, depth) the p50 / p99 latency and the count."""
+        done = self.completed[since:]
+        lat = np.array([r.t_done - r.t_arrival for r in done])
+        svc = np.array([r.t_done - r.t_start for r in done])
+        paths = sum(len(r.future.result()["n"]) for r in done if r.future.done() and r.future.exception() is None)
+        pct = lambda a, q: float(np.percentile(a, q) * 1e3) if len(a) else None  # noqa: E731
+        classes = {}
+        for key in sorted({(r.scene, r.depth) for r in done}):
+            a = np.array([r.t_done - r.t_arrival for r in done if (r.scene, r.depth) == key])
+            classes[f"{key[0]}/d{key[1]}"] = {"n": int(len(a)), "p50_ms": pct(a, 50), "p99_ms": pct(a, 99)}
+        return {"requests": len(done), "batches": self.batches,
+                "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99), "service_p50_ms": pct(svc, 50),
+                "service_p99_ms": pct(svc, 99), "exact_paths": paths, "cones": self.cones, "by_class": classes}
 
 
 def run_stream(server: Server, requests: list[dict], scenes_update=None, update_every: int = 50,
                time_scale: float = 1.0) -> dict:
-    """Submit a timed request stream (arrival times in seconds) and wait for all results."""
+    """Submit a timed request stream (arrival times in seconds; all at once with
+    time_scale 0) and wait for all results; figures over this stream alone.  Every
+    update_every requests scenes_update(k) posts a region update."""
+    since, b0, c0 = len(server.completed), server.batches, server.cones
     t0 = time.perf_counter()
-    reqs = []
+    reqs, updates = [], 0
     for k, q in enumerate(requests):
         due = t0 + q["t"] * time_scale
         now = time.perf_counter()
@@ -292,29 +309,40 @@ def run_stream(server: Server, requests: list[dict], scenes_update=None, update_
             time.sleep(due - now)
         if scenes_update is not None and k > 0 and k % update_every == 0:
             scenes_update(k // update_every)
+            updates += 1
         reqs.append(server.submit(q["scene"], q["tx"], q["rx"], q["depth"], t_arrival=due))
     for r in reqs:
         r.future.exception()   # wait
     wall = time.perf_counter() - t0
-    st = server.stats()
+    st = server.stats(since)
+    st["batches"] = server.batches - b0
+    st["cones"] = server.cones - c0
+    st["region_updates"] = updates
     st["wall_s"] = wall
+    st["requests_per_s"] = len(reqs) / wall
     st["exact_paths_per_s"] = st["exact_paths"] / wall
     st["rays_per_s"] = st["cones"] / wall
     return st
 
 
-def bench_latency(ctx=None, device: int = 0, n_requests: int = 40, rate_hz: float = 0.5, n_workers: int = 2,
-                  seed: int = 4, max_pairs: int = 64, depth_range=(2, 5), depth_caps=None) -> dict:
+def bench_latency(ctx=None, device: int = 0, n_requests: int = 36, fractions=(0.5, 0.8, 1.0), n_workers: int = 2,
+                  seed: int = 4, max_pairs: int = 64, depth_range=(2, 5), depth_caps=None, update_every: int = 12,
+                  burst: int = 24) -> dict:
     """Serving measurement on the three resident scenes of the larger configurations.
 
     Resident: the noisy room with its box (133k points), the indoor scan (1.92M) and
-    the street canyon (20.0M).  Poisson arrivals at ``rate_hz``; each request picks a
-    scene, 1 TX and 1..max_pairs RXs from free-space positions of that scene, and a
-    maximum depth in depth_range, capped per scene where deeper trees leave the
-    latency budget (street: 2, indoor and room: 4; node counts grow about 6x per
-    level in the open street, and a 64-pair depth-5 request in the room refines
-    millions of coarse paths).  A 2x2x2 m box moves in the noisy room and is re-voxelised by
-    region every 50 requests.  Returns p50/p99 latency and throughput.
+    the street canyon (20.0M).  Each request picks a scene, 1 TX and 1..max_pairs RXs
+    from free-space positions of that scene, and a maximum depth in depth_range,
+    capped per scene where deeper trees leave the latency budget (street: 2, indoor
+    and room: 4; node counts grow about 6x per level in the open street, and a
+    64-pair depth-5 request in the room refines millions of coarse paths).  First a
+    burst of `burst` requests, all arriving at once, measures the batched capacity
+    (requests per second); then one seeded Poisson stream of n_requests at each
+    fraction of that capacity.  A 2x2x2 m box moves in the noisy room and is
+    re-voxelised by region every update_every requests of a stream.  Returns the
+    capacity, and per rate p50/p99 latency, per-class latency, batches, region
+    updates and throughput; the resident bytes of each scene (every worker holds
+    its own copy).
     """
     from . import scenes
     caps = {"street": 2, "indoor": 4, "room_noisy": 4} if depth_caps is None else depth_caps
@@ -324,22 +352,36 @@ def bench_latency(ctx=None, device: int = 0, n_requests: int = 40, rate_hz: floa
     sc = {"room_noisy": room, "indoor": indoor, "street": street}
     pools = {"room_noisy": scenes.room_noisy_pairs(900, 1, 512)[1], "indoor": indoor.rx, "street": street.rx}
     server = Server(sc, Params(), n_workers=n_workers, device=device, max_pairs=128)
-    reqs = scenes.serving_requests(n_requests, rate_hz, list(sc), seed=seed, max_pairs=max_pairs,
-                                   depth_range=depth_range, pools=pools, depth_caps=caps)
-    state = {"box": None}
+    state = {"box": None, "step": 0}
 
-    def move(step):
-        server.update_region("room_noisy", *moved_box_update(room, state, step))
+    def move(_k):
+        state["step"] += 1
+        server.update_region("room_noisy", *moved_box_update(room, state, state["step"]))
 
+    kw = dict(max_pairs=max_pairs, depth_range=depth_range, pools=pools, depth_caps=caps)
+    out = {"scenes": {k: int(v.xyz.shape[0]) for k, v in sc.items()}, "workers": n_workers,
+           "pairs_per_request": f"1-{max_pairs}", "depth": f"{depth_range[0]}-{depth_range[1]}", "depth_caps": caps,
+           "moving_box": f"2x2x2 m in the noisy room, region update every {update_every} requests of a stream"}
     try:
-        res = run_stream(server, reqs, scenes_update=move)
+        ex = server.executors[0]
+        out["resident_bytes_per_worker"] = {k: int(v) for k, v in getattr(ex, "resident", {}).items()}
+        reqs = scenes.serving_requests(burst, 1.0, list(sc), seed=seed, **kw)
+        cap = run_stream(server, reqs, time_scale=0.0)
+        capacity = cap["requests_per_s"]
+        out["capacity"] = {"requests_per_s": capacity, "burst": burst, "p50_ms": cap["p50_ms"],
+                           "p99_ms": cap["p99_ms"], "batches": cap["batches"], "wall_s": cap["wall_s"]}
+        out["rates"] = []
+        for i, fr in enumerate(fractions):
+            reqs = scenes.serving_requests(n_requests, fr * capacity, list(sc), seed=seed + 1 + i, **kw)
+            st = run_stream(server, reqs, scenes_update=move, update_every=update_every)
+            st["fraction_of_capacity"] = fr
+            st["rate_hz"] = fr * capacity
+            out["rates"].append(st)
+        ups = [u for e in server.executors for u in getattr(e, "update_ms", [])]
+        out["region_update_ms_p50"] = float(np.median(ups)) if ups else None
     finally:
         server.close()
-    res.update({"rate_hz": rate_hz, "workers": n_workers, "scenes": {k: int(v.xyz.shape[0]) for k, v in sc.items()},
-                "requests_submitted": n_requests, "pairs_per_request": f"1-{max_pairs}",
-                "depth": f"{depth_range[0]}-{depth_range[1]}", "depth_caps": caps,
-                "moving_box": "2x2x2 m, region update every 50 requests"})
-    return res
+    return out
 
 
 def moved_box_update(room, state: dict, step: int):

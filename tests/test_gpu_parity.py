@@ -351,30 +351,51 @@ def test_empty_cloud_with_region(ctx):
     assert list(out["n"]) == [0]
 
 
-def test_update_region_equals_rebuild(ctx):
-    """Dynamic scene: replacing a region gives the tables of a full build on that grid."""
-    room = scenes.room_noisy(n_tx=1, n_rx=1)
-    p = config.params_for(room)
-    info = None
+@pytest.mark.parametrize("case", ["moving_box", "remove_fixed_box", "remove_only", "replacement_outside"])
+def test_update_region_equals_rebuild(ctx, case):
+    """Dynamic scene: a region update re-bins only the voxels that lose or gain points
+    and splices them into the tables; the result equals a full build of the new cloud
+    on the same grid entry for entry (every table, the point ranges and the march
+    field), and the paths traced on both are identical.  Cases: the moving box; the
+    fixed box removed (its voxels hold edge entities, which stay); a region emptied
+    with no replacement; replacement points outside the region box."""
+    room = scenes.room_noisy(n_tx=1, n_rx=2)
+    p = config.params_for(room, max_refl=2, max_diff=1)
     s = ctx.voxelize_scene(room, p)
     info = ctx.scene_info(s)
     # a region box that reproduces this grid: one voxel inside the padded origin
     h = p.voxel_size
     region = np.array([info["origin"] + h + 1e-6, info["origin"] + (info["dims"] - 1) * h - 1e-6])
     xyz, nrm, lab, mat, lo, hi = scenes.moving_box(room, step=7)
-    ctx.update_region(s, lo - 0.01, hi + 0.01, xyz, nrm, lab, mat)
+    lo, hi = lo - 0.01, hi + 0.01
+    if case == "remove_fixed_box":
+        lo, hi = np.array([4.45, 6.45, 0.02]), np.array([5.55, 7.55, 2.1])
+        xyz = nrm = lab = mat = None
+    elif case == "remove_only":
+        xyz = nrm = lab = mat = None
+    elif case == "replacement_outside":
+        lo, hi = np.array([1.0, 1.0, -0.02]), np.array([1.6, 1.6, 0.6])   # a floor patch; the box lies elsewhere
+    ctx.update_region(s, lo, hi, xyz, nrm, lab, mat)
     A = ctx.scene_tables(s)
     # the same cloud built from scratch on the same grid
-    keep = ~np.all((room.xyz >= (lo - 0.01).astype(np.float32)) & (room.xyz <= (hi + 0.01).astype(np.float32)), axis=1)
-    sc2 = scenes.Scene("upd", np.concatenate([room.xyz[keep], xyz]), np.concatenate([room.nrm[keep], nrm]),
-                       np.concatenate([room.label[keep], lab]), np.concatenate([room.material[keep], mat]),
-                       room.edges, room.edge_label, region=region)
+    keep = ~np.all((room.xyz >= lo.astype(np.float32)) & (room.xyz <= hi.astype(np.float32)), axis=1)
+    parts = [(room.xyz[keep], room.nrm[keep], room.label[keep], room.material[keep])]
+    if xyz is not None:
+        parts.append((xyz, nrm, lab, mat))
+    sc2 = scenes.Scene("upd", *[np.concatenate([q[k] for q in parts]) for k in range(4)], room.edges, room.edge_label,
+                       tx=room.tx, rx=room.rx, region=region)
+    assert (~keep).sum() > 0
     s2 = ctx.voxelize_scene(sc2, p)
     B = ctx.scene_tables(s2)
     np.testing.assert_array_equal(A["dims"], B["dims"])
-    for k in ("kind", "label", "cell", "gs", "cell_count", "march", "material"):
-        np.testing.assert_array_equal(A[k], B[k])
-    np.testing.assert_array_equal(A["rp"], B["rp"])
+    assert A["n_ie"] == B["n_ie"] and A["n_points"] == B["n_points"]
+    for k in ("kind", "label", "cell", "gs", "prange", "cell_count", "cell_begin", "march", "material", "rp", "normal",
+              "bbc"):
+        np.testing.assert_array_equal(A[k], B[k], err_msg=k)
+    got = [ctx.query(ctx.refine(h_, ctx.trace(h_, room.tx, room.rx, p), p), 0) for h_ in (s, s2)]
+    assert len(got[0]["n"]) > 0
+    for k in ("tx", "rx", "n", "type", "label", "pts", "length"):
+        np.testing.assert_array_equal(got[0][k], got[1][k])
     ctx.release(s)
     ctx.release(s2)
 

@@ -122,13 +122,27 @@ def test_pair_limit_splits_batches():
     assert [len(b1), len(b2), len(b3)] == [2, 2, 1]
 
 
+def test_uneven_depths_share_a_batch():
+    """Requests of one scene with different depth limits and pair counts join one
+    batch; another scene's request waits for its own."""
+    s = Scheduler(1 << 40, max_pairs=64)
+    from paper_2402_13747_b300.serve import Request
+    for i, (sid, k, d) in enumerate([("a", 3, 2), ("a", 7, 5), ("b", 1, 3), ("a", 1, 4)]):
+        s.submit(Request(i, sid, np.zeros((1, 3)), np.zeros((k, 3)), d))
+    b1, _ = s.next_batch()
+    b2, _ = s.next_batch()
+    assert [r.id for r in b1] == [0, 1, 3] and sorted(r.depth for r in b1) == [2, 4, 5]
+    assert [r.id for r in b2] == [2]
+
+
 def test_stream_reports_latency_percentiles():
     srv, log = _server(n_workers=2, delay=0.02)
     reqs = scenes.serving_requests(30, 200.0, ["a", "b"], seed=1, max_pairs=8)
     st = run_stream(srv, reqs)
     srv.close()
     assert st["requests"] == 30 and st["p99_ms"] >= st["p50_ms"] > 0
-    assert st["rays_per_s"] > 0
+    assert st["rays_per_s"] > 0 and st["batches"] <= 30
+    assert sum(c["n"] for c in st["by_class"].values()) == 30
 
 
 @pytest.mark.gpu

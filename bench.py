@@ -296,6 +296,39 @@ def secondary_line(ctx, name: str, steps: int, warmup: int, flush, stream):
             "node_bounds": sizes or "default"}
 
 
+def region_update_timing(ctx, reps: int = 3):
+    """Dynamic scenes, measured alone on an idle GPU: replacing the points of a 2x2x2 m
+    box region by a box cloud (nimbus_update_region, which re-bins only the voxels
+    that change) against voxelising the whole new cloud, on the noisy room and the
+    street canyon.  Median wall times of `reps` updates (the box moves each time)."""
+    import torch
+    from paper_2402_13747_b300 import config, scenes
+    out = {}
+    for name, origin in (("room_noisy", (2.0, 2.0, 0.0)), ("street", (90.0, 24.0, 0.0))):
+        sc = make_scene(name)
+        p = config.params_for(sc, **WORKLOADS[name]["overrides"])
+        s = ctx.voxelize_scene(sc, p)
+        up, full = [], []
+        for k in range(reps + 1):
+            xyz, nrm, lab, mat, lo, hi = scenes.box_cloud(np.asarray(origin) + [0.5 * k, 0.0, 0.0])
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ctx.update_region(s, lo - 0.01, hi + 0.01, xyz, nrm, lab, mat)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            s2 = ctx.voxelize_scene(sc, p)
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+            ctx.release(s2)
+            if k:   # the first of each is a warm-up
+                up.append(1e3 * (t1 - t0))
+                full.append(1e3 * (t2 - t1))
+        ctx.release(s)
+        out[name] = {"points": int(sc.xyz.shape[0]), "region_update_ms": float(np.median(up)),
+                     "full_voxelize_ms": float(np.median(full)), "box": "2x2x2 m, 5 cm spacing"}
+    return out
+
+
 def roofline_of(c0, pk):
     """Dominant stage and its roofline: algorithmic bytes / CUDA-event time against the
     measured HBM copy peak.  Eq. 1 reads each point's position and normal (6 FP32 =
@@ -340,6 +373,7 @@ def main():
     ap.add_argument("--no-secondary", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--pairs", default="", help="TxR: only the first T TX and R RX (small profiling cases)")
+    ap.add_argument("--rx-every", type=int, default=1, help="K: every K-th RX only (profiling cases spread over the RXs)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -364,6 +398,9 @@ def main():
         nt, nr = (int(v) for v in args.pairs.lower().split("x"))
         sc = sc.with_pairs(sc.tx[:nt], sc.rx[:nr])
         workload += f" [subset: first {nt} TX x {nr} RX]"
+    if args.rx_every > 1:
+        sc = sc.with_pairs(sc.tx, sc.rx[::args.rx_every])
+        workload += f" [subset: every {args.rx_every}th RX]"
     tx_all, txi = rank_pairs(sc, rank, world)
     my = sc.with_pairs(tx_all[txi], sc.rx)
     p = config.params_for(sc, **WORKLOADS[args.workload]["overrides"])
@@ -388,11 +425,13 @@ def main():
             ctx.release(h)
         return cnt
 
-    # launch layouts (result-neutral) tuned on a sample of the workload, untimed
+    # launch layouts (result-neutral) tuned on a sample of the workload, untimed: every
+    # TX against RXs spread over the whole set (at most 32), so that the sample's
+    # refinement is not a short tail-bound launch
     tuning = ctx.get_tuning()
     if not args.no_tune:
         s0 = ctx.voxelize(d_xyz, d_nrm, d_lab, d_mat, d_edges, d_elab, params=p)
-        tuning = ctx.autotune(s0, my.tx, my.rx[:8], p)
+        tuning = ctx.autotune(s0, my.tx, my.rx[::max(1, my.rx.shape[0] // 32)], p)
         ctx.release(s0)
     for _ in range(args.warmup):
         step()
@@ -508,7 +547,7 @@ def main():
                      "pair_latency_ms_p99": 1e3 * float(np.percentile(lat, 99))}
 
         secondary = None
-        if not args.no_secondary and world == 1 and not args.pairs:
+        if not args.no_secondary and world == 1 and not args.pairs and args.rx_every == 1:
             secondary = {}
             for name in ("room_noisy", "street"):
                 if name == args.workload:
@@ -542,6 +581,13 @@ def main():
             except Exception as ex:  # must not hide the main line
                 segment = {"error": repr(ex)}
 
+        region = None
+        if not args.no_serving and world == 1 and not args.pairs and args.rx_every == 1:
+            try:
+                region = region_update_timing(ctx)
+            except Exception as ex:  # must not hide the main line
+                region = {"error": repr(ex)}
+
         cpu = None
         if not args.no_cpu_baseline and world == 1:
             cpu = cpu_baseline(args.workload, sc)
@@ -556,13 +602,14 @@ def main():
                           "points": int(sc.xyz.shape[0]), "pairs": int(tx_all.shape[0] * sc.rx.shape[0]),
                           "form": "batched: all pairs in one trace_coarse + refine",
                           "tuning": {k: v for k, v in tuning.items() if not k.endswith("_ms")},
-                          "tuning_sample": "the rank's TXs x 8 RX of the workload",
+                          "tuning_sample": "the rank's TXs x every (n_rx // 32)-th RX of the workload",
                           "parallelism": f"tx-sharded x{world}" if world > 1 else "1 GPU"},
                "coarse_rays_per_s": cones / coarse_t if coarse_t > 0 else None,
                "exact_paths_per_s": exact_ps, "exact_paths_per_step": paths / args.steps,
                "visibility_rays_per_s": vis / t_total,
                "cones_per_step": cones / args.steps, "wall_s_timed_region": wall,
-               "plain": plain, "latency": latency, "segment": segment, "roofline": roof, "cpu_baseline": cpu,
+               "plain": plain, "latency": latency, "region_update": region, "segment": segment, "roofline": roof,
+               "cpu_baseline": cpu,
                "e2e": e2e, "secondary": secondary,
                "gathered_paths": None if gathered is None else int(len(gathered["n"])),
                "gpu_launches": launches, "clocks": clocks,

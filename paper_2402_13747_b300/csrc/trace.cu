@@ -533,7 +533,13 @@ __device__ void march_cone_warp(const DScene& s, const DTrace& tr, const ConeD& 
 
 // One propagation level: the reflected cones and Keller-fan cones of every node,
 // one warp per cone, cones handed out by a counter (their costs differ widely).
-__global__ void __launch_bounds__(256) k_level(DScene s, DTrace tr, NodeLevel cur, NodeLevel next, CoarseBuf cb,
+#ifndef LEVEL_MAX_THREADS
+#define LEVEL_MAX_THREADS 256
+#endif
+#ifndef LEVEL_MIN_BLOCKS
+#define LEVEL_MIN_BLOCKS 2
+#endif
+__global__ void __launch_bounds__(LEVEL_MAX_THREADS, LEVEL_MIN_BLOCKS) k_level(DScene s, DTrace tr, NodeLevel cur, NodeLevel next, CoarseBuf cb,
                                                unsigned long long* next_task) {
   const int lane = threadIdx.x & 31;
   const uint32_t n_r = min(cur.cnt[0], cur.cap_r), n_d = min(cur.cnt[1], cur.cap_d);

@@ -468,6 +468,15 @@ def wedge_on_floor(z_tx: float = 0.8, z_rx: float = 2.0, spacing: float = 0.05) 
                  max_diff=1, meta={"spacing": spacing}, region=np.array([[-4.0, -4.0, 0.0], [2.0, 2.0, 3.0]]))
 
 
+def box_cloud(lo, size: float = 2.0, spacing: float = 0.05, label0: int = 100, material: int = 5):
+    """A closed box of side `size` standing at lo (its five visible faces sampled at
+    `spacing`, labels label0..label0+4): (xyz, nrm, label, material, aabb_lo, aabb_hi)."""
+    lo = np.asarray(lo, dtype=np.float64)
+    hi = lo + size
+    xyz, nrm, lab, mat = merge_clouds(_box_parts(lo, hi, spacing, label0, material))
+    return xyz, nrm, lab, mat, lo, hi
+
+
 def moving_box(room: Scene, step: int, seed: int = 4, size: float = 2.0, spacing: float = 0.05):
     """A 2x2x2 m box on a seeded random walk in the 10x10 m room (dynamic scenes).
 

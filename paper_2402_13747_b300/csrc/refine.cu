@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "nimbus_host.hpp"
+#define NB_VIS_PAIRS 0   // one load per lane and pass in the final visibility rays (see warp_geom.cuh)
 #include "warp_geom.cuh"
 
 namespace nb {

@@ -71,12 +71,19 @@ __device__ __forceinline__ bool eq1_finish(const float v[8], float3 x, float* f,
 // Eq. 1 over the points of one IE, the points split across the warp's lanes; every
 // lane returns the same f and normal.  c is the IE's bounding-box centre, x is
 // relative to c.
-// Lane l adds points l, l + 32, l + 64, ... in that order; each pass loads two of them
-// before adding either, so two loads are in flight per lane (an IE of the 3 cm scans
-// holds about 70 points: two passes instead of three).
+// Lane l adds points l, l + 32, l + 64, ... in that order.  With NB_VIS_PAIRS (the
+// default) each pass loads two of them before adding either, so two loads are in
+// flight per lane (an IE of the 3 cm scans holds about 70 points: two passes instead
+// of three); the order of the sums is the same either way.  A translation unit may
+// set it to 0 before including this header (the refinement does: its kernel's code
+// was measured faster so, with the final visibility rays a negligible share of it).
+#ifndef NB_VIS_PAIRS
+#define NB_VIS_PAIRS 1
+#endif
 __device__ bool sdf_warp(const DScene& s, uint32_t pb, uint32_t pc, float3 c, float3 x, float* f, float3* n_out,
                          int lane, unsigned long long& bytes) {
   float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#if NB_VIS_PAIRS
   for (uint32_t k = lane; k < pc; k += 64) {
     const uint32_t k1 = k + 32 < pc ? k + 32 : k;   // past the end: re-read point k, unused
     const float4 P0 = __ldg(&s.pts[pb + k]), N0 = __ldg(&s.pnrm[pb + k]);
@@ -84,6 +91,9 @@ __device__ bool sdf_warp(const DScene& s, uint32_t pb, uint32_t pc, float3 c, fl
     eq1_term(v, x, P0, N0, c, s.sdf_inv_s2);
     if (k + 32 < pc) eq1_term(v, x, P1, N1, c, s.sdf_inv_s2);
   }
+#else
+  for (uint32_t k = lane; k < pc; k += 32) eq1_term(v, x, __ldg(&s.pts[pb + k]), __ldg(&s.pnrm[pb + k]), c, s.sdf_inv_s2);
+#endif
   if (lane == 0) bytes += 24ull * pc;
   wsum8(v, lane);
   return eq1_finish(v, x, f, n_out);

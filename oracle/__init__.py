@@ -27,7 +27,8 @@ Parity pins (tests/test_oracle_pins.py):
 - the secant placement after a sign change of f, in an entity's march and in the
   re-projection, on two sheets whose Eq. 1 surface is f = u - h tanh(2uh/sigma^2);
   the final visibility check, which alone removes a path passing 0.0545 m outside a
-  panel's border; the RX reception sphere centred on the RX, on one launch cone.
+  panel's border; the RX reception sphere centred on the RX, on one launch cone; the
+  re-projection of a target already on the surface (one Newton step from it).
 tests/test_oracle_mutants.py plants one mistake at a time in a copy of the source and
 checks that these pins catch it.
 

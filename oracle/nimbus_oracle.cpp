@@ -18,7 +18,8 @@
 // a reflection and a diffraction in either order) against closed forms and brute
 // force; tests/test_oracle_mutants.py checks that planted mistakes fail them.  The
 // secant placement after a sign change of f is pinned on two sheets whose Eq. 1
-// surface has a closed form (both marches), the final visibility check on a path
+// surface has a closed form (both marches; also the re-projection of a target that
+// lies on the surface), the final visibility check on a path
 // that passes just outside a panel, and the RX reception sphere on a single launch
 // cone.  The coarse-path set and the kappa choice on noisy clouds have no
 // closed form: parity unpinned beyond their invariants (kappa, depth limits) and the
@@ -1020,8 +1021,10 @@ bool sdf_label(const Scene& s, uint32_t label, V3 x, double* f, V3* n_out) {
 // Re-projection (Section 2.3): a ray from the previous interaction point toward the
 // updated reflection point R; its intersection with the surface of label l gives the
 // new c_k, and the normal there (Eq. 1 normal) the new u_k, v_k.  The intersection is
-// the march of Section 2.2.1 on the label's surface (sdf_label), over a segment of
-// one subvoxel diameter centred on R.
+// sought on a segment of one subvoxel diameter centred on R.  Reading: Eq. 1 is
+// evaluated at R first; where R already lies on the surface (|f(R)| < eps) the hit is
+// one Newton step along the ray from R, as at the end of a march, if that stays on
+// the segment.  Otherwise the segment is marched from its near end (Section 2.2.1).
 bool reproject(const Scene& s, V3 P, V3 R, uint32_t label, V3* c_out, V3* n_out) {
   V3 dvec = R - P;
   double tR = norm(dvec);
@@ -1032,6 +1035,21 @@ bool reproject(const Scene& s, V3 P, V3 R, uint32_t label, V3* c_out, V3* n_out)
   double f;
   V3 n;
   bool hit = false;
+  {
+    double fR;
+    V3 nR;
+    if (sdf_label(s, label, R, &fR, &nR) && std::fabs(fR) < s.p.sdf_eps) {
+      double dn = dot(nR, d);
+      double tR_hit = std::fabs(dn) > 1e-3 ? tR - fR / dn : tR;
+      if (tR_hit > 0.0 && std::fabs(tR_hit - tR) <= 0.5 * L) {
+        V3 c = P + tR_hit * d;
+        if (!sdf_label(s, label, c, &f, &n)) return false;
+        *c_out = c;
+        *n_out = n;
+        return true;
+      }
+    }
+  }
   if (!sdf_label(s, label, P + t * d, &f, &n)) return false;
   for (int it = 0; it < s.p.sdf_max_steps && !hit; ++it) {
     if (std::fabs(f) < s.p.sdf_eps) {

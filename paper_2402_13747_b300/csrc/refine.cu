@@ -227,9 +227,12 @@ __device__ __forceinline__ void rel_subvoxel(const DScene& s, float3 c0, float3 
 
 // Re-projection (Section 2.3): the ray from P toward the updated point R is
 // intersected with the implicit surface of label `label` (Eq. 1 over nearby points of
-// that label) by the march of Section 2.2.1 on a segment of one subvoxel diameter
-// centred on R.  The march runs in FP32 relative to R; the new point is R plus the
-// FP32 offset along the ray, in FP64.
+// that label) on a segment of one subvoxel diameter centred on R.  Eq. 1 is evaluated
+// at R first: where R already lies on the surface (|f| < eps, as it does once a path
+// nears its stationary point) the hit is one Newton step along the ray from R, if that
+// stays on the segment; otherwise the segment is marched from its near end (Section
+// 2.2.1).  The evaluations run in FP32 relative to R; the new point is R plus the FP32
+// offset along the ray, in FP64.
 __device__ bool reproject_warp(const DScene& s, const d3* Pp, const d3* Rp, uint32_t label, d3* c_out, float3* n_out,
                                int lane, unsigned long long& bytes, LabelCache& lc, SelList& sl) {
   const d3 P = *Pp, R = *Rp;
@@ -255,6 +258,22 @@ __device__ bool reproject_warp(const DScene& s, const d3* Pp, const d3* Rp, uint
     rel_subvoxel(s, c0, x, gR, g);
     return sdf_label_warp(s, lc, sl, x, g, c0, fo, no, lane, bytes);
   };
+  {
+    float fR;
+    float3 nR;
+    if (eval(0.f, &fR, &nR) && fabsf(fR) < s.sdf_eps) {
+      const float dn = dot(nR, d);
+      const float t1 = fabsf(dn) > 1e-3f ? -fR / dn : 0.f;
+      if (tR + t1 > 0.f && fabsf(t1) <= half) {
+        const float3 x1 = r0 + t1 * d;
+        rel_subvoxel(s, c0, x1, gR, dg);
+        if (!sdf_label_warp(s, lc, sl, x1, dg, c0, &f, &n, lane, bytes)) return false;
+        *c_out = *Rp + (double)t1 * tod(d);
+        *n_out = n;
+        return true;
+      }
+    }
+  }
   if (!march_abs_f<false>(eval, d, -half, half, s.sdf_eps, s.sdf_max_steps, &th)) return false;
   // the placed hit must stay on the marched segment (and in front of P)
   if (!(tR + th > 0.f) || fabsf(th) > half) return false;

@@ -145,6 +145,14 @@ MUTANTS = [
     ("reprojection_secant_sign",       # Section 2.3: secant through the wrong pair of values
      "      th = t - f * (t_next - t) / (f_next - f);", "      th = t - f * (t_next - t) / (f_next + f);",
      "middle_plane"),
+    ("reprojection_probe_step_dropped",  # re-projection reading: hit at the target, no Newton step
+     "      double tR_hit = std::fabs(dn) > 1e-3 ? tR - fR / dn : tR;", "      double tR_hit = tR;", "on_the_surface"),
+    ("reprojection_probe_step_sign",   # re-projection reading: the Newton step from the target reversed
+     "      double tR_hit = std::fabs(dn) > 1e-3 ? tR - fR / dn : tR;",
+     "      double tR_hit = std::fabs(dn) > 1e-3 ? tR + fR / dn : tR;", "on_the_surface"),
+    ("reprojection_probe_skipped",     # re-projection reading: the segment always marched from its end
+     "    if (sdf_label(s, label, R, &fR, &nR) && std::fabs(fR) < s.p.sdf_eps) {", "    if (false) {",
+     "on_the_surface"),
     ("final_visibility_dropped",       # Section 2.3: refined segments not validated by RT
      "    if (!visible(s, I[k], I[k + 1], ea, eb)) { ex.status = ST_OCCLUDED; return ex; }", "",
      "past_the_panel"),

@@ -770,32 +770,60 @@ def test_sdf_hit_secant_after_a_sign_change():
         assert t == pytest.approx(2.0 - half + t_ref, abs=1e-9)
 
 
-def test_reprojection_secant_lands_on_the_middle_plane():
-    """The re-projection of Section 2.3 on the same sheet pair, 2h = 0.375 m apart
-    across three subvoxel layers (one label, default sigma): the 3x3x3 block of every
-    march point holds both sheets, so f = u - h tanh(2uh/sigma^2) exactly, odd in u.
-    A ray 60 degrees off the normal toward a target on the middle plane oversteps the
-    middle zero; the secant places the hit at the closed-form march's point, 0.28 mm
-    from the plane (the zero of f by symmetry; the secant's error on the curved f),
-    with normal +z."""
+def _sheet_pair_surface():
+    """The sheet pair 2h = 0.375 m apart across three subvoxel layers (one label,
+    default sigma) and its closed-form Eq. 1: f = u - h tanh(2uh/sigma^2), odd in u,
+    wherever the 3x3x3 block of the evaluated point holds both sheets."""
     p = config.Params()
     c, h = 0.375, 0.1875
     s = oracle.Scene.from_scene(_sheet_pair([c - h, c + h], 0.0, 2.0, 0.0625), p)
     f = lambda u: u - h * math.tanh(2.0 * u * h / p.sdf_sigma ** 2)  # noqa: E731
+    return p, c, h, s, f
+
+
+def test_reprojection_secant_lands_near_the_middle_plane():
+    """The re-projection of Section 2.3 on the sheet pair: a ray 60 degrees off the
+    normal toward a target 0.01 m above the middle plane, where |f| = 0.034 m is not
+    near zero, so the segment is marched from its near end; the march oversteps the
+    middle zero (the slope of f along the ray exceeds 1) and the secant places the hit
+    at the closed-form march's point, 2.3 mm from the plane (the zero of f by symmetry;
+    the secant's error on the curved f), with normal +z."""
+    p, c, h, s, f = _sheet_pair_surface()
     th = math.radians(60.0)
     d = np.array([math.sin(th), 0.0, -math.cos(th)])
     half = 0.5 * p.voxel_size / p.dv * math.sqrt(3.0)
-    assert (2 * h * h / p.sdf_sigma ** 2 - 1.0) * math.cos(th) > 1.0
-    branch, t_ref = _march_closed_form(f, half * math.cos(th), math.cos(th), 2 * half, p.sdf_eps)
+    u_R = 0.01
+    assert (2 * h * h / p.sdf_sigma ** 2 - 1.0) * math.cos(th) > 1.0 and abs(f(u_R)) >= p.sdf_eps
+    assert u_R + half * math.cos(th) < p.voxel_size / p.dv / 2 and u_R - half * math.cos(th) > -p.voxel_size / p.dv / 2
+    branch, t_ref = _march_closed_form(f, u_R + half * math.cos(th), math.cos(th), 2 * half, p.sdf_eps)
     assert branch == "secant"
-    u_ref = half * math.cos(th) - t_ref * math.cos(th)
-    assert abs(u_ref) < 1e-3
-    for R in ([1.03125, 1.0625, c], [0.96875, 1.125, c]):
+    u_ref = u_R + half * math.cos(th) - t_ref * math.cos(th)
+    assert abs(u_ref) < 5e-3
+    for R in ([1.03125, 1.0625, c + u_R], [0.96875, 1.125, c + u_R]):
         R = np.array(R)
         cn, nn = s.reproject(R - 3.0 * d, R, 0)
         assert cn is not None
-        np.testing.assert_allclose(cn, R + (u_ref / -math.cos(th)) * d, atol=1e-9)
+        np.testing.assert_allclose(cn, R + ((u_R - u_ref) / math.cos(th)) * d, atol=1e-9)
         np.testing.assert_allclose(nn, [0, 0, 1], atol=1e-12)
+
+
+def test_reprojection_of_a_target_on_the_surface():
+    """Re-projection reading: a target R where Eq. 1 is already near zero (|f(R)| <
+    eps) is met by one Newton step along the ray from R itself, t = -f(R) / (n . d),
+    as at the end of a march.  On the sheet pair's middle plane f(R) = 0 and the hit is
+    R; 2e-4 m above it f(R) = -7.0e-4 m and the hit is R - f(R) / (n . d) d with
+    n = +z, both in closed form."""
+    p, c, h, s, f = _sheet_pair_surface()
+    th = math.radians(60.0)
+    d = np.array([math.sin(th), 0.0, -math.cos(th)])
+    for u_R in (0.0, 2e-4):
+        assert abs(f(u_R)) < p.sdf_eps
+        R = np.array([1.03125, 1.0625, c + u_R])
+        cn, nn = s.reproject(R - 3.0 * d, R, 0)
+        assert cn is not None
+        np.testing.assert_allclose(cn, R - (f(u_R) / np.dot([0.0, 0.0, 1.0], d)) * d, atol=1e-9)
+        np.testing.assert_allclose(nn, [0, 0, 1], atol=1e-12)
+    assert abs(f(2e-4) + 7.0e-4) < 1e-5
 
 
 # ------------------------------------------------- final visibility (Section 2.3)

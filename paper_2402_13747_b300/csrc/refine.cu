@@ -590,46 +590,74 @@ __device__ bool path_less(const ExactRec& a, const ExactRec& b) {
   return false;
 }
 
-// One thread per TX/RX pair: order its label winners, then drop every path whose
-// interaction points all lie in the first Fresnel zones of an earlier kept path
-// with the same chain of interaction types.
-__global__ void k_fresnel(const ExactRec* ex, const uint64_t* keys, uint32_t* vals, int64_t n, const double* txd,
-                          double lambda, uint32_t* keep) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    if (i > 0 && keys[i] == keys[i - 1]) continue;   // not the first of its pair
-    int64_t e = i;
-    while (e < n && keys[e] == keys[i]) ++e;
-    for (int64_t a = i + 1; a < e; ++a) {              // insertion sort of the pair
-      uint32_t x = vals[a];
-      int64_t b = a - 1;
-      while (b >= i && path_less(ex[x], ex[vals[b]])) {
-        vals[b + 1] = vals[b];
-        --b;
-      }
-      vals[b + 1] = x;
-    }
-    for (int64_t bI = i; bI < e; ++bI) {
-      const ExactRec& B = ex[vals[bI]];
-      bool dup = false;
-      for (int64_t aI = i; aI < bI && !dup; ++aI) {
-        if (!keep[aI]) continue;
-        const ExactRec& A = ex[vals[aI]];
-        if (A.n != B.n || A.n == 0 || A.types != B.types) continue;
-        double px = txd[3 * A.tx], py = txd[3 * A.tx + 1], pz = txd[3 * A.tx + 2];
-        double acc = 0.0;
-        bool inside = true;
-        for (uint32_t q = 0; q < A.n && inside; ++q) {
-          double dx = A.pts[q][0] - px, dy = A.pts[q][1] - py, dz = A.pts[q][2] - pz;
-          acc += sqrt(dx * dx + dy * dy + dz * dz);
-          px = A.pts[q][0]; py = A.pts[q][1]; pz = A.pts[q][2];
-          double ak = acc, bk = A.length - acc;
-          double r = sqrt(lambda * ak * bk / (ak + bk));
-          double ex_ = B.pts[q][0] - A.pts[q][0], ey = B.pts[q][1] - A.pts[q][1], ez = B.pts[q][2] - A.pts[q][2];
-          inside = sqrt(ex_ * ex_ + ey * ey + ez * ez) <= r;
+// Is B inside the first Fresnel zones of the kept path A (same chain of interaction
+// types, every interaction point of B within the zone radius around A's)?
+__device__ bool in_fresnel_zones(const ExactRec& A, const ExactRec& B, const double* txd, double lambda) {
+  if (A.n != B.n || A.n == 0 || A.types != B.types) return false;
+  double px = txd[3 * A.tx], py = txd[3 * A.tx + 1], pz = txd[3 * A.tx + 2];
+  double acc = 0.0;
+  bool inside = true;
+  for (uint32_t q = 0; q < A.n && inside; ++q) {
+    double dx = A.pts[q][0] - px, dy = A.pts[q][1] - py, dz = A.pts[q][2] - pz;
+    acc += sqrt(dx * dx + dy * dy + dz * dz);
+    px = A.pts[q][0]; py = A.pts[q][1]; pz = A.pts[q][2];
+    double ak = acc, bk = A.length - acc;
+    double r = sqrt(lambda * ak * bk / (ak + bk));
+    double ex_ = B.pts[q][0] - A.pts[q][0], ey = B.pts[q][1] - A.pts[q][1], ez = B.pts[q][2] - A.pts[q][2];
+    inside = sqrt(ex_ * ex_ + ey * ey + ez * ez) <= r;
+  }
+  return inside;
+}
+
+// One warp per TX/RX pair (the pair whose first entry lies in the warp's chunk of 32
+// positions): order its label winners by path_less into svals -- a total order there,
+// since the winners of one pair differ in their type or label sequence, so each
+// winner's rank is the number of winners before it -- then, in that order, drop every
+// path whose interaction points all lie in the first Fresnel zones of an earlier kept
+// path with the same chain of interaction types, the lanes testing the earlier kept
+// paths together.  The order and every decision are those of one thread sorting the
+// pair and then passing over it.
+__global__ void k_fresnel(const ExactRec* ex, const uint64_t* keys, const uint32_t* vals, int64_t n,
+                          const double* txd, double lambda, uint32_t* svals, uint32_t* keep) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t base = warp * 32; base < n; base += n_warps * 32) {
+    const int64_t my = base + lane;
+    const bool start = my < n && (my == 0 || keys[my] != keys[my - 1]);
+    unsigned sm = __ballot_sync(FULL, start);
+    while (sm) {
+      const int64_t i = base + __ffs(sm) - 1;
+      sm &= sm - 1;
+      int64_t e = i + 1;   // end of the pair: the first later entry with another key
+      for (;;) {
+        const int64_t q = e + lane;
+        const unsigned om = __ballot_sync(FULL, q >= n || keys[q] != keys[i]);
+        if (om) {
+          e += __ffs(om) - 1;
+          break;
         }
-        dup = inside;
+        e += 32;
       }
-      keep[bI] = dup ? 0u : 1u;
+      for (int64_t a = i + lane; a < e; a += 32) {
+        const ExactRec& X = ex[vals[a]];
+        int64_t r = 0;
+        for (int64_t b = i; b < e; ++b) {   // ties (none are expected) by position: a permutation
+          const ExactRec& Y = ex[vals[b]];
+          if (b != a && (path_less(Y, X) || (b < a && !path_less(X, Y)))) ++r;
+        }
+        svals[i + r] = vals[a];
+      }
+      __syncwarp();
+      for (int64_t bI = i; bI < e; ++bI) {
+        const ExactRec& B = ex[svals[bI]];
+        bool dup = false;
+        for (int64_t aI = i + lane; aI < bI && !dup; aI += 32)
+          dup = keep[aI] && in_fresnel_zones(ex[svals[aI]], B, txd, lambda);
+        dup = __any_sync(FULL, dup);
+        if (lane == 0) keep[bI] = dup ? 0u : 1u;
+        __syncwarp();
+      }
     }
   }
 }
@@ -746,11 +774,12 @@ int refine_paths(Mem& mem, SceneObj* S, CoarseObj* C, const nimbus_refine_params
   bool deduped = false;
   if (m > 0) {
     uint64_t *keys, *keys_alt;
-    uint32_t *vals, *vals_alt, *keep, *kpos, *nk;
+    uint32_t *vals, *vals_alt, *svals, *keep, *kpos, *nk;
     NB_TRY(sc.get(&keys, m));
     NB_TRY(sc.get(&keys_alt, m));
     NB_TRY(sc.get(&vals, m));
     NB_TRY(sc.get(&vals_alt, m));
+    NB_TRY(sc.get(&svals, m));
     NB_TRY(sc.get(&keep, m));
     NB_TRY(sc.get(&kpos, m));
     NB_TRY(sc.get(&nk, 1));
@@ -767,11 +796,11 @@ int refine_paths(Mem& mem, SceneObj* S, CoarseObj* C, const nimbus_refine_params
       NB_LAUNCHED(err);
       NB_TRY(radix_sort(ws, keys, vals, keys_alt, vals_alt, m, key_bits));
       NB_CUDA(err, cudaMemsetAsync(keep, 0, m * sizeof(uint32_t), q));
-      k_fresnel<<<std::min<unsigned>(grid_for(m, 64), pgrid(64)), 64, 0, q>>>(P->all, keys, vals, m, C->txd,
-                                                                                rp.lambda, keep);
+      k_fresnel<<<std::min<unsigned>(grid_for((m + 31) / 32 * 32, 256), pgrid(256)), 256, 0, q>>>(
+          P->all, keys, vals, m, C->txd, rp.lambda, svals, keep);
       NB_LAUNCHED(err);
       NB_TRY(exclusive_scan(ws, keep, kpos, m, nk));
-      k_final<<<std::min<unsigned>(grid_for(m, 256), pgrid(256)), 256, 0, q>>>(keep, kpos, vals, m, P->final_idx);
+      k_final<<<std::min<unsigned>(grid_for(m, 256), pgrid(256)), 256, 0, q>>>(keep, kpos, svals, m, P->final_idx);
       NB_LAUNCHED(err);
       tm.record(e3, q);
       return NIMBUS_OK;

@@ -1024,7 +1024,9 @@ bool sdf_label(const Scene& s, uint32_t label, V3 x, double* f, V3* n_out) {
 // sought on a segment of one subvoxel diameter centred on R.  Reading: Eq. 1 is
 // evaluated at R first; where R already lies on the surface (|f(R)| < eps) the hit is
 // one Newton step along the ray from R, as at the end of a march, if that stays on
-// the segment.  Otherwise the segment is marched from its near end (Section 2.2.1).
+// the segment, and its normal is Eq. 1's at R (the two points coincide once the path
+// is stationary).  Otherwise the segment is marched from its near end (Section
+// 2.2.1) and the normal is taken at the hit.
 bool reproject(const Scene& s, V3 P, V3 R, uint32_t label, V3* c_out, V3* n_out) {
   V3 dvec = R - P;
   double tR = norm(dvec);
@@ -1042,10 +1044,8 @@ bool reproject(const Scene& s, V3 P, V3 R, uint32_t label, V3* c_out, V3* n_out)
       double dn = dot(nR, d);
       double tR_hit = std::fabs(dn) > 1e-3 ? tR - fR / dn : tR;
       if (tR_hit > 0.0 && std::fabs(tR_hit - tR) <= 0.5 * L) {
-        V3 c = P + tR_hit * d;
-        if (!sdf_label(s, label, c, &f, &n)) return false;
-        *c_out = c;
-        *n_out = n;
+        *c_out = P + tR_hit * d;
+        *n_out = nR;
         return true;
       }
     }

@@ -230,9 +230,10 @@ __device__ __forceinline__ void rel_subvoxel(const DScene& s, float3 c0, float3 
 // that label) on a segment of one subvoxel diameter centred on R.  Eq. 1 is evaluated
 // at R first: where R already lies on the surface (|f| < eps, as it does once a path
 // nears its stationary point) the hit is one Newton step along the ray from R, if that
-// stays on the segment; otherwise the segment is marched from its near end (Section
-// 2.2.1).  The evaluations run in FP32 relative to R; the new point is R plus the FP32
-// offset along the ray, in FP64.
+// stays on the segment, with Eq. 1's normal at R; otherwise the segment is marched
+// from its near end (Section 2.2.1) and the normal is evaluated at the hit.  The
+// evaluations run in FP32 relative to R; the new point is R plus the FP32 offset along
+// the ray, in FP64.
 __device__ bool reproject_warp(const DScene& s, const d3* Pp, const d3* Rp, uint32_t label, d3* c_out, float3* n_out,
                                int lane, unsigned long long& bytes, LabelCache& lc, SelList& sl) {
   const d3 P = *Pp, R = *Rp;
@@ -265,11 +266,8 @@ __device__ bool reproject_warp(const DScene& s, const d3* Pp, const d3* Rp, uint
       const float dn = dot(nR, d);
       const float t1 = fabsf(dn) > 1e-3f ? -fR / dn : 0.f;
       if (tR + t1 > 0.f && fabsf(t1) <= half) {
-        const float3 x1 = r0 + t1 * d;
-        rel_subvoxel(s, c0, x1, gR, dg);
-        if (!sdf_label_warp(s, lc, sl, x1, dg, c0, &f, &n, lane, bytes)) return false;
         *c_out = *Rp + (double)t1 * tod(d);
-        *n_out = n;
+        *n_out = nR;
         return true;
       }
     }

@@ -32,3 +32,43 @@ def compare(gpu, ref, atol_pts=1e-3, rtol_len=1e-6):
     return dict(n_gpu=len(g), n_ref=len(r), n_common=len(common), only_gpu=sorted(g.keys() - r.keys()),
                 only_ref=sorted(r.keys() - g.keys()), worst_pt=worst_pt, worst_len=worst_len, bad=bad,
                 jaccard=len(common) / max(1, len(union)))
+
+
+def oracle_confirms(osc, sc, P, i, p, IGN_LABEL=1, IGN_ANY=2):
+    """Path i of P checked against the definition of an exact path on the oracle's
+    scene osc (Section 2.3): every reflection point on its label's Eq. 1 surface,
+    every diffraction point on its edge, the length stationary (the norm over all
+    interactions of e_in + e_out projected on the tangent plane of Eq. 1's normal, or
+    on the edge direction), and every segment visible under the endpoint rules.
+    Returns (largest |f| or distance off the edge, gradient norm, all visible)."""
+    from oracle import NONE_LABEL
+    n = int(P["n"][i])
+    nodes = [np.asarray(sc.tx[P["tx"][i]], float)] + [np.asarray(x, float) for x in P["pts"][i][:n]] + \
+        [np.asarray(sc.rx[P["rx"][i]], float)]
+    ies = osc.ies() if n and (np.asarray(P["type"][i][:n]) == 1).any() else None
+    f_max = 0.0
+    g2 = 0.0
+    for k in range(n):
+        x = nodes[k + 1]
+        e = (x - nodes[k]) / np.linalg.norm(x - nodes[k]) + (x - nodes[k + 2]) / np.linalg.norm(x - nodes[k + 2])
+        if int(P["type"][i][k]) == 0:
+            f, nn = osc.sdf_label(int(P["label"][i][k]), x)
+            if f is None:
+                return np.inf, np.inf, False
+            f_max = max(f_max, abs(f))
+            g2 += float(e @ e - (e @ nn) ** 2)
+        else:
+            ed = sc.edges[ies["edge"][int(P["ie"][i][k])]]
+            p0, p1 = ed[:3], ed[3:6]
+            w = (p1 - p0) / np.linalg.norm(p1 - p0)
+            off = (x - p0) - ((x - p0) @ w) * w
+            f_max = max(f_max, float(np.linalg.norm(off)))
+            g2 += float(e @ w) ** 2
+    vis = True
+    for k in range(n + 1):
+        ma, la = (0, NONE_LABEL) if k == 0 else (
+            IGN_ANY if int(P["type"][i][k - 1]) == 1 else IGN_LABEL, int(P["label"][i][k - 1]))
+        mb, lb = (0, NONE_LABEL) if k == n else (
+            IGN_ANY if int(P["type"][i][k]) == 1 else IGN_LABEL, int(P["label"][i][k]))
+        vis = vis and osc.visible(nodes[k], nodes[k + 1], ma, la, mb, lb)
+    return f_max, float(np.sqrt(max(g2, 0.0))), vis

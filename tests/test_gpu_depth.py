@@ -11,7 +11,19 @@ import numpy as np
 import pytest
 
 from tests.golden.make_room_noisy_1x16 import MAX_INT, OUT, workload
-from tests.pathsets import compare
+from tests.pathsets import compare, oracle_confirms
+
+# On the noisy cloud the gradient descent of one coarse path can settle on one of
+# several stationary points a few centimetres to decimetres apart, or cycle around
+# one until rho (Section 2.3 fixes neither the start nor the step).  Which candidate
+# of a label sequence wins the shortest-path dedup can then depend on rounding: in
+# the oracle, 64 of the 100 coarse paths of one (ceiling, wall, wall) sequence of
+# this workload cycle between two points 1.8 cm apart that straddle a stationary
+# point the CUDA path converges to from another candidate.  Such an alternate winner
+# is accepted when the oracle confirms it is an exact path (on its surfaces,
+# stationary, visible) and its length is within 1e-4 relative, for at most one path
+# in 500 of the set.
+ALT_PER = 500
 
 
 def _golden():
@@ -45,11 +57,49 @@ def test_stored_oracle_paths_are_consistent():
         assert ref["length"][i] == pytest.approx(math.dist(sc.tx[ref["tx"][i]], sc.rx[ref["rx"][i]]), rel=1e-12)
 
 
+def test_exact_path_check_on_the_stored_paths():
+    """The exact-path check that admits alternate winners, on the oracle's own stored
+    reflection paths (the file keeps no entity indices, which the check needs for an
+    edge): each passes; a reflection point moved 1 cm along its surface fails the
+    stationarity bound, one lifted 1 mm off it fails the surface bound."""
+    import oracle
+    ref, _ = _golden()
+    sc, p = workload()
+    osc = oracle.Scene.from_scene(sc, p)
+    rng = np.random.default_rng(7)
+    refl_only = (ref["n"] >= 1) & ~((ref["type"] == 1) & (np.arange(8)[None, :] < ref["n"][:, None])).any(1)
+    picks = rng.choice(np.nonzero(refl_only)[0], size=40, replace=False)
+    moved = lifted = 0
+    for i in picks:
+        f_max, grad, vis = oracle_confirms(osc, sc, ref, i, p)
+        assert f_max < 1e-4 and grad < p.delta and vis, (i, f_max, grad, vis)
+        refl = [k for k in range(int(ref["n"][i])) if ref["type"][i][k] == 0]
+        if not refl:
+            continue
+        k = refl[0]
+        x = ref["pts"][i][k]
+        _, nn = osc.sdf_label(int(ref["label"][i][k]), x)
+        t = np.cross(nn, [1.0, 0.0, 0.0] if abs(nn[0]) < 0.9 else [0.0, 1.0, 0.0])
+        t /= np.linalg.norm(t)
+        for shift, which in ((0.01 * t, "moved"), (1e-3 * nn, "lifted")):
+            Q = {kk: np.array(v[i:i + 1]) for kk, v in ref.items()}
+            Q["pts"] = Q["pts"].copy()
+            Q["pts"][0][k] = x + shift
+            f2, g2, _ = oracle_confirms(osc, sc, Q, 0, p)
+            if which == "moved":
+                assert g2 > p.delta, (i, g2)
+                moved += 1
+            else:
+                assert f2 > 5e-4, (i, f2)
+                lifted += 1
+    assert moved >= 20 and lifted >= 20
+
+
 @pytest.mark.gpu
 def test_noisy_room_1x16_full_depth_matches_oracle():
     """The CUDA path's exact paths equal the oracle's: the same (TX, RX, type sequence,
     label sequence) set, every point within 1e-3 m and every length within 1e-6
-    relative.  The coarse sets may differ by a few paths whose FP32 cone or
+    relative, up to the oracle-confirmed alternate winners above.  The coarse sets may differ by a few paths whose FP32 cone or
     visibility decisions sit at a margin (2 of 86,633 when this was written); none
     of them reaches the exact set."""
     from paper_2402_13747_b300 import _abi
@@ -65,5 +115,22 @@ def test_noisy_room_1x16_full_depth_matches_oracle():
     assert abs(C["n_coarse"] - n_coarse) <= 1e-3 * n_coarse, (C["n_coarse"], n_coarse)
     cmp = compare(G, ref, atol_pts=1e-3, rtol_len=1e-6)
     assert cmp["only_gpu"] == [] and cmp["only_ref"] == [], cmp
-    assert cmp["bad"] == [], cmp["bad"][:5]
     assert cmp["n_common"] == len(ref["n"])
+    assert len(cmp["bad"]) <= len(ref["n"]) // ALT_PER, cmp["bad"][:5]
+    _confirm_alternates(G, cmp["bad"], sc, p)
+
+
+def _confirm_alternates(G, bad, sc, p):
+    if not bad:
+        return
+    import oracle
+    osc = oracle.Scene.from_scene(sc, p)
+    where = {}
+    for i in range(len(G["n"])):
+        n = int(G["n"][i])
+        where[(int(G["tx"][i]), int(G["rx"][i]), tuple(int(t) for t in G["type"][i][:n]),
+               tuple(int(l) for l in G["label"][i][:n]))] = i
+    for key, dp, dl in bad:
+        f_max, grad, vis = oracle_confirms(osc, sc, G, where[key], p)
+        assert f_max < 1e-4 and grad < p.delta and vis, (key, dp, dl, f_max, grad, vis)
+        assert dl < 1e-4, (key, dp, dl)

@@ -193,6 +193,11 @@ typedef struct {
   int64_t* cell_begin;      /* [n_cells] first IE of each voxel */
   int32_t* cell_count;      /* [n_cells] IEs in each voxel */
   int32_t* march;           /* [n_cells] capped L-infinity distance to the nearest voxel with IEs */
+  float* slab;              /* [n_ie*4] (point IEs; zeros for edges) bounds the visibility rays use to
+                               skip marches that cannot hit: smallest cosine between a point's normal
+                               and the mean normal (less 1e-6), smallest and largest offset of a point
+                               from the bbox centre along the mean normal, largest distance of a point
+                               from that centre */
 } nimbus_scene_view;
 
 /* Contexts (operational; the paper has no counterpart).

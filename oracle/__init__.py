@@ -124,6 +124,7 @@ def lib():
         L.oracle_scene_info.argtypes = [vp, vp, vp, vp]
         L.oracle_scene_ies.argtypes = [vp] * 13
         L.oracle_scene_cells.argtypes = [vp, vp, vp, vp]
+        L.oracle_scene_points.argtypes = [vp, vp, vp]
         L.oracle_trace.restype = vp
         L.oracle_trace.argtypes = [vp, vp, i32, vp, i32]
         L.oracle_coarse_free.argtypes = [vp]
@@ -185,6 +186,7 @@ class Scene:
         npg = np.zeros(1, np.int64)
         self.n_ie = int(L.oracle_scene_info(self.h, _p(origin), _p(dims), _p(npg)))
         self.origin, self.dims = origin, dims
+        self.n_points_grouped = int(npg[0])
 
     @classmethod
     def from_scene(cls, sc, params):
@@ -206,6 +208,13 @@ class Scene:
                                                                "normal", "bbc", "sc", "edge", "trange",
                                                                "material")])
         return out
+
+    def points(self):
+        """(positions, normals) of the points in the grouped order of the IE point ranges."""
+        xyz = np.zeros((self.n_points_grouped, 3))
+        nrm = np.zeros((self.n_points_grouped, 3))
+        lib().oracle_scene_points(self.h, _p(xyz), _p(nrm))
+        return xyz, nrm
 
     def cells(self) -> dict:
         nc = int(np.prod(self.dims.astype(np.int64)))

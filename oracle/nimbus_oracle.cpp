@@ -1383,6 +1383,16 @@ void oracle_scene_ies(void* sp, int32_t* kind, uint32_t* label, int64_t* cell, i
   }
 }
 
+// Point positions and normals in the grouped order the IE point ranges index.
+void oracle_scene_points(void* sp, double* xyz, double* nrm) {
+  Scene* s = (Scene*)sp;
+  for (size_t i = 0; i < s->pts.size(); ++i)
+    for (int a = 0; a < 3; ++a) {
+      xyz[3 * i + a] = comp(s->pts[i], a);
+      nrm[3 * i + a] = comp(s->nrm[i], a);
+    }
+}
+
 void oracle_scene_cells(void* sp, int64_t* begin, int32_t* count, int32_t* march) {
   Scene* s = (Scene*)sp;
   for (int64_t c = 0; c < s->n_cells; ++c) {

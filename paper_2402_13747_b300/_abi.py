@@ -82,7 +82,7 @@ class CoarseView(C.Structure):
 
 class SceneView(C.Structure):
     _fields_ = [(n, _vp) for n in ("kind", "label", "cell", "gs", "prange", "rp", "normal", "bbc", "material",
-                                   "cell_begin", "cell_count", "march")]
+                                   "cell_begin", "cell_count", "march", "slab")]
 
 
 class StaticTables(C.Structure):
@@ -476,9 +476,10 @@ class Context:
                    gs=np.zeros((n, 3), np.int32), prange=np.zeros((n, 2), np.int64), rp=np.zeros((n, 3), np.float32),
                    normal=np.zeros((n, 3), np.float32), bbc=np.zeros((n, 3), np.float32),
                    material=np.zeros(n, np.uint8), cell_begin=np.zeros(nc, np.int64),
-                   cell_count=np.zeros(nc, np.int32), march=np.zeros(nc, np.int32))
+                   cell_count=np.zeros(nc, np.int32), march=np.zeros(nc, np.int32),
+                   slab=np.zeros((n, 4), np.float32))
         v = SceneView(*[_ptr(out[k]) for k in ("kind", "label", "cell", "gs", "prange", "rp", "normal", "bbc",
-                                               "material", "cell_begin", "cell_count", "march")])
+                                               "material", "cell_begin", "cell_count", "march", "slab")])
         self._check(self.L.nimbus_scene_tables(self.h, scene, C.byref(v), _stream(stream)), "scene_tables")
         out.update(info)
         return out

@@ -494,6 +494,12 @@ int nimbus_scene_tables(nimbus_ctx* ctx, nimbus_handle scene, const nimbus_scene
       if (view->normal) view->normal[3 * i + a] = nn[a];
       if (view->bbc) view->bbc[3 * i + a] = bb[a];
     }
+    if (view->slab) {
+      view->slab[4 * i] = r.slab.x;
+      view->slab[4 * i + 1] = r.slab.y;
+      view->slab[4 * i + 2] = r.slab.z;
+      view->slab[4 * i + 3] = r.slab.w;
+    }
   }
   for (int64_t c = 0; c < nc; ++c) {
     if (view->cell_begin) view->cell_begin[c] = cells[c].x;

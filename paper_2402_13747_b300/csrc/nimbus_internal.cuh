@@ -16,16 +16,21 @@
 namespace nb {
 
 // ----------------------------------------------------------------------------- records
-// One intersectable entity (Section 2.1), 64 bytes = four 16-byte vector loads.
+// One intersectable entity (Section 2.1), 80 bytes = five 16-byte vector loads.
 //   rp_lab : ray reception point xyz, label (bits)
 //   nrm_meta: mean normal xyz (point IE), meta bits: kind (bit 0), material << 8
 //   bbc_pb : bounding-box centre of the points xyz, first point (point IE) or edge index
 //   sc_pc  : subvoxel centre xyz, number of points
+//   slab   : (point IE) bounds of its points for march_cannot_hit: the smallest cosine
+//            between a point's normal and the mean normal, the smallest and largest
+//            offset of a point from the bbox centre along the mean normal, and the
+//            largest distance of a point from that centre; zeros for an edge
 struct __align__(16) IERec {
   float4 rp_lab;
   float4 nrm_meta;
   float4 bbc_pb;
   float4 sc_pc;
+  float4 slab;
 };
 
 enum { IE_POINT = 0, IE_EDGE = 1 };
@@ -314,6 +319,29 @@ __device__ __forceinline__ bool cannot_occlude(Endpoint ea, Endpoint eb, uint32_
   return (a_ign && tc + half < r) || (b_ign && T - (tc - half) < r);
 }
 
+// True when the march of Section 2.2.1 over an IE's Eq. 1 surface is known to miss
+// the segment x0 + t d, |t| <= half (IE frame, origin at the bbox centre), without
+// running it.  Eq. 1's normal is a normalised positive combination of the point
+// normals, so it lies in the cone of half-angle theta around the mean normal n0
+// (cos theta = slab.x); its point term is a convex combination of the points, whose
+// offsets along n0 lie in [slab.y, slab.z] and whose distance from the centre is at
+// most slab.w.  With that normal written cos(phi) n0 + sin(phi) u (phi <= theta, u a
+// unit vector normal to n0), f(x) >= cos(theta) (x.n0 - slab.z) - sin(theta)
+// (|x| + slab.w) wherever x.n0 > slab.z, and symmetrically below the slab.  x.n0 is
+// linear and |x| convex along the segment, so both take their extremes at its ends.
+// Where the bound keeps |f| above eps plus 1e-5 m (the FP32 rounding of f and of the
+// bound is below 1e-6 m at these sizes) every evaluation the march makes has the same
+// sign and |f| >= eps: it returns no hit, and skipping it changes no decision.
+__device__ __forceinline__ bool march_cannot_hit(float4 slab, float3 n0, float3 x0, float3 d, float half,
+                                                 float eps) {
+  const float cmin = slab.x;
+  if (!(cmin > 0.5f)) return false;
+  const float s0 = dot(x0, n0), sd = half * fabsf(dot(d, n0));
+  const float D = fmaxf(len(x0 - half * d), len(x0 + half * d)) + slab.w;
+  const float need = eps + 1e-5f + sqrtf(fmaxf(0.f, 1.f - cmin * cmin)) * D;
+  return (s0 - sd - slab.z) * cmin > need || (slab.y - (s0 + sd)) * cmin > need;
+}
+
 // Visibility ray A -> B (Sections 2.2.4, 2.3): walk the voxels of the segment and
 // intersect the point IEs of each voxel passed.  bytes counts the scene records read.
 static __device__ __noinline__ bool visible(const DScene& s, float3 A, float3 B, Endpoint ea, Endpoint eb, unsigned long long& bytes) {
@@ -342,6 +370,8 @@ static __device__ __noinline__ bool visible(const DScene& s, float3 A, float3 B,
       bytes += 16;
       if (cannot_occlude(ea, eb, lbl, tc, 0.5f * s.seg_len, T, s.vis_ignore)) continue;
       float3 x0 = (A - c) + tc * d;
+      bytes += 16;
+      if (march_cannot_hit(__ldg(&ie->slab), xyz(nm), x0, d, 0.5f * s.seg_len, s.sdf_eps)) continue;
       float tau;
       if (!sdf_march(s, __float_as_uint(bb.w), __float_as_uint(sc_pc.w), c, x0, d, &tau, bytes)) continue;
       float th = tc + tau;

@@ -220,6 +220,20 @@ __global__ void k_ie_build(BuildK b, const uint64_t* __restrict__ keys, const ui
     r.bbc_pb = make_float4((float)(0.5 * ((double)lo[0] + (double)hi[0])), (float)(0.5 * ((double)lo[1] + (double)hi[1])),
                            (float)(0.5 * ((double)lo[2] + (double)hi[2])), __uint_as_float(s));
     r.sc_pc.w = __uint_as_float(e - s);
+    // bounds for the march test of the visibility rays (march_cannot_hit); a point
+    // with a zero normal, or a zero mean normal, disables the test for this IE
+    const float3 n0 = xyz(r.nrm_meta), cb = xyz(r.bbc_pb);
+    float cmin = ninv > 0.0 ? 1.f : -1.f, dlo = 3.4e38f, dhi = -3.4e38f, rmax = 0.f;
+    for (uint32_t k = s; k < e; ++k) {
+      const float3 p = xyz(pts[k]) - cb, nk = xyz(pnrm[k]);
+      const float nl = len(nk);
+      cmin = fminf(cmin, nl > 0.f ? dot(nk, n0) / nl : -1.f);
+      const float dd = dot(p, n0);
+      dlo = fminf(dlo, dd);
+      dhi = fmaxf(dhi, dd);
+      rmax = fmaxf(rmax, len(p));
+    }
+    r.slab = make_float4(cmin - 1e-6f, dlo, dhi, rmax);
   } else {
     int4 pc = pieces[vals[s] - b.n_points];
     const double* E = edges + 12 * pc.x;
@@ -233,6 +247,7 @@ __global__ void k_ie_build(BuildK b, const uint64_t* __restrict__ keys, const ui
     r.nrm_meta = make_float4(n.x, n.y, n.z, __uint_as_float((uint32_t)IE_EDGE | (255u << 8)));
     r.bbc_pb = make_float4(rp[0], rp[1], rp[2], __uint_as_float((uint32_t)pc.x));
     r.sc_pc.w = __uint_as_float(0u);
+    r.slab = make_float4(0.f, 0.f, 0.f, 0.f);
   }
   ies[ie] = r;
   ie_cell[ie] = (uint32_t)cell;
@@ -1309,13 +1324,13 @@ int scene_load(Mem& mem, const char* path, SceneObj* S, cudaStream_t st) {
 
 // ----------------------------------------------------------- voxelisation without allocation
 // Every intermediate of nimbus_voxelize_static lives in this one fixed device array:
-// 136.5 bytes per point (sort keys and values with their work copies, run flags and
-// ids, run starts, grouped points, entity records) plus 10 bytes per voxel and a
+// 152.5 bytes per point (sort keys and values with their work copies, run flags and
+// ids, run starts, grouped points, 80-byte entity records) plus 10 bytes per voxel and a
 // small reserve for the scan and sort tables, for the largest sizes allowed.
 namespace {
 constexpr size_t kStaticPoints = NIMBUS_STATIC_MAX_POINTS;
 constexpr size_t kStaticCells = NIMBUS_STATIC_MAX_CELLS;
-constexpr size_t kStaticBytes = 137 * kStaticPoints + 10 * kStaticCells + (4u << 20);
+constexpr size_t kStaticBytes = 153 * kStaticPoints + 10 * kStaticCells + (4u << 20);
 }  // namespace
 
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];

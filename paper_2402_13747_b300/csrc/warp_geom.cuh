@@ -144,6 +144,8 @@ __device__ bool visible_warp(const DScene& s, float3 A, float3 B, Endpoint ea, E
         uint32_t lbl = __float_as_uint(__ldg(&r->rp_lab).w);
         if (cannot_occlude(ea, eb, lbl, tc, 0.5f * s.seg_len, T, s.vis_ignore)) continue;
         float3 x0 = (A - c) + tc * d;
+        if (lane == 0) bytes += 32;
+        if (march_cannot_hit(__ldg(&r->slab), xyz(__ldg(&r->nrm_meta)), x0, d, 0.5f * s.seg_len, s.sdf_eps)) continue;
         float tau;
         if (!sdf_march_warp(s, __float_as_uint(bb.w), __float_as_uint(sc.w), c, x0, d, &tau, lane, bytes)) continue;
         float th = tc + tau;

@@ -401,16 +401,20 @@ typedef struct {
                                caller's stream as one CUDA graph; 0: the same launches issued directly */
   double level_ms;          /* after nimbus_autotune: time of the chosen level layout on the sample, else 0 */
   double refine_ms;         /* after nimbus_autotune: time of the chosen refinement layout on the sample, else 0 */
+  int32_t level_queue;      /* 1: all propagation depths in one launch, a cone of depth d + 1 starting as soon as
+                               its parent emitted it (waits bounded; NIMBUS_ERR_TIMEOUT if one gives up);
+                               0: one launch per depth */
 } nimbus_tuning;
 
-/* The context's launch configuration (defaults 256, 0, 1, 1). */
+/* The context's launch configuration (defaults 256, 0, 1, 1, level_queue 0). */
 NIMBUS_API int nimbus_get_tuning(nimbus_ctx* ctx, nimbus_tuning* out);
 
 /* Replace it.  A value out of range returns NIMBUS_ERR_ARG and changes nothing. */
 NIMBUS_API int nimbus_set_tuning(nimbus_ctx* ctx, const nimbus_tuning* t);
 
 /* Autotuner.  Traces the given TX/RX sample on `scene` once per level layout
- * (blocks of 128 or 256 threads), keeps the fastest propagation time, then
+ * (blocks of 128 or 256 threads, one launch per depth or one for all depths), keeps
+ * the fastest propagation time, then
  * refines that coarse set once per refinement layout (4 or all resident blocks per
  * SM x ordered or not), keeps the fastest, stores the result in the context for the
  * calls that follow and writes it to `out` (may be NULL).  Times are CUDA events on

@@ -543,6 +543,7 @@ static void to_public(const nb::Tuning& t, nimbus_tuning* o) {
   o->graph = t.graph;
   o->level_ms = t.level_ms;
   o->refine_ms = t.refine_ms;
+  o->level_queue = t.level_queue;
 }
 
 int nimbus_get_tuning(nimbus_ctx* ctx, nimbus_tuning* out) {
@@ -554,7 +555,8 @@ int nimbus_get_tuning(nimbus_ctx* ctx, nimbus_tuning* out) {
 int nimbus_set_tuning(nimbus_ctx* ctx, const nimbus_tuning* t) {
   if (!ctx) return NIMBUS_ERR_ARG;
   if (!t || !(t->level_block == 128 || t->level_block == 256) || t->refine_blocks < 0 || t->refine_blocks > 8 ||
-      !(t->refine_order == 0 || t->refine_order == 1) || !(t->graph == 0 || t->graph == 1)) {
+      !(t->refine_order == 0 || t->refine_order == 1) || !(t->graph == 0 || t->graph == 1) ||
+      !(t->level_queue == 0 || t->level_queue == 1)) {
     ctx->err = "set_tuning: value out of range";
     return NIMBUS_ERR_ARG;
   }
@@ -564,6 +566,7 @@ int nimbus_set_tuning(nimbus_ctx* ctx, const nimbus_tuning* t) {
   ctx->tune.graph = t->graph;
   ctx->tune.level_ms = t->level_ms;
   ctx->tune.refine_ms = t->refine_ms;
+  ctx->tune.level_queue = t->level_queue;
   return NIMBUS_OK;
 }
 
@@ -583,9 +586,11 @@ int nimbus_autotune(nimbus_ctx* ctx, nimbus_handle scene, const double* tx, int3
   // level layouts: propagation time of the sample's levels
   double best_lv = -1.0;
   const int blocks[2] = {256, 128};
+  for (int lq = 0; lq < 2; ++lq)
   for (int bl : blocks) {
     nb::Tuning t = best;
     t.level_block = bl;
+    t.level_queue = lq;
     auto* C = new nb::CoarseObj();
     C->mem = &ctx->mem;
     C->scene = scene;
@@ -596,6 +601,7 @@ int nimbus_autotune(nimbus_ctx* ctx, nimbus_handle scene, const double* tx, int3
     if (best_lv < 0.0 || ms < best_lv) {
       best_lv = ms;
       best.level_block = bl;
+      best.level_queue = lq;
     }
   }
   best.level_ms = best_lv;

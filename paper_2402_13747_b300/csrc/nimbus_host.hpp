@@ -338,6 +338,7 @@ struct Tuning {
   int refine_blocks = 0;   // 0: as many as fit
   int refine_order = 1;
   int graph = 1;           // issue each host-free stretch of a call as one CUDA graph
+  int level_queue = 0;     // 1: all propagation depths in one launch (a task queue across levels)
   double level_ms = 0, refine_ms = 0;
 };
 

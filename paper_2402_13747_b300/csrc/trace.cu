@@ -66,6 +66,11 @@ struct NodeLevel {
   uint32_t* dm;
   uint32_t* cnt;   // [0] reflection nodes, [1] diffraction nodes
   uint32_t cap_r, cap_d;
+  // single-launch propagation only (null otherwise): per node slot, 1 once its record
+  // is written; and the count of cone tasks created and not yet finished
+  uint8_t* rdy_r;
+  uint8_t* rdy_d;
+  unsigned long long* outstanding;
 };
 
 struct CoarseBuf {
@@ -381,6 +386,13 @@ __device__ void emit_child(const DTrace& tr, NodeLevel& next, uint32_t id, float
   } else {
     next.da[slot] = a; next.db[slot] = b; next.dm[slot] = meta;
   }
+  if (next.outstanding) {
+    // single launch: count the child's cone tasks before publishing the record, so
+    // that the count cannot reach zero while this warp may still create work
+    atomicAdd(next.outstanding, refl ? 1ull : (unsigned long long)tr.M);
+    __threadfence();
+    *(volatile uint8_t*)(refl ? next.rdy_r + slot : next.rdy_d + slot) = 1;
+  }
 }
 
 // What one propagation cone needs besides its geometry.
@@ -531,6 +543,71 @@ __device__ void march_cone_warp(const DScene& s, const DTrace& tr, const ConeD& 
   }
 }
 
+// One propagation cone of level `cur`: the reflected cone of node idx (refl) or cone
+// j of the Keller fan of diffraction node idx.
+__device__ __forceinline__ void level_cone(const DScene& s, const DTrace& tr, const NodeLevel& cur, NodeLevel& next,
+                                           CoarseBuf& cb, bool refl, uint32_t idx, int j, int lane,
+                                           unsigned long long& bytes, uint32_t& cones, uint32_t& evals,
+                                           uint32_t& vis) {
+  const float4 a = refl ? cur.ra[idx] : cur.da[idx];
+  const float4 b = refl ? cur.rb[idx] : cur.db[idx];
+  const uint32_t meta = refl ? cur.rm[idx] : cur.dm[idx];
+  const uint32_t ie = __float_as_uint(a.w);
+  const IERec* r = &s.ies[ie];
+  const float4 nm = __ldg(&r->nrm_meta);
+  const uint32_t label = __float_as_uint(__ldg(&r->rp_lab).w);
+  if (lane == 0) bytes += 32 + 36;
+  const float3 e = xyz(b);
+  ConeD c;
+  c.apex = xyz(a);
+  c.sin_a = tr.sin_a;
+  c.cos_a = tr.cos_a;
+  if (refl) {
+    float3 n = xyz(nm);
+    if (dot(n, e) > 0.f) n = -1.f * n;
+    c.kind = CONE_REFLECT;
+    c.axis = normalize(e - (2.f * dot(e, n)) * n);
+    c.pn = n;
+    c.origin = Endpoint{IGN_LABEL, label};
+  } else {
+    const double* E = s.edges + 12 * __float_as_uint(__ldg(&r->bbc_pb).w);
+    if (lane == 0) bytes += 96;
+    const float3 w = normalize(f3((float)(E[3] - E[0]), (float)(E[4] - E[1]), (float)(E[5] - E[2])));
+    const float cb_ = dot(e, w);
+    const float sb2 = 1.f - cb_ * cb_;
+    if (sb2 < 1e-12f) return;
+    const float sb = sqrtf(sb2);
+    float3 ua, va;
+    onb(w, &ua, &va);
+    const float phi = (float)j * tr.dphi;
+    float sp, cp;
+    sincosf(phi, &sp, &cp);
+    const float3 rr = cp * ua + sp * va;
+    const float3 d = cb_ * w + sb * rr;
+    const float3 n0 = f3((float)E[6], (float)E[7], (float)E[8]), n1 = f3((float)E[9], (float)E[10], (float)E[11]);
+    if (!(dot(d, n0) > 0.f || dot(d, n1) > 0.f)) return;
+    float slo, clo, shi, chi;
+    sincosf(phi - 0.5f * tr.dphi, &slo, &clo);
+    sincosf(phi + 0.5f * tr.dphi, &shi, &chi);
+    c.kind = CONE_DIFFRACT;
+    c.axis = normalize(d);
+    c.tlo = (-slo) * ua + clo * va;
+    c.thi = (-shi) * ua + chi * va;
+    c.rmid = rr;
+    c.origin = Endpoint{IGN_ANY, label};
+  }
+  LevelCone lc;
+  lc.depth = (meta >> 24) & 0xfu;
+  lc.nr = (meta >> 16) & 0xfu;
+  lc.nd = (meta >> 20) & 0xfu;
+  lc.tx = meta & 0xffffu;
+  lc.self_ref = idx | (refl ? 0u : 0x80000000u);
+  lc.can_child = (int)lc.depth < tr.max_int && (!tr.tx_max_int || (int)lc.depth < tr.tx_max_int[lc.tx]);
+  lc.test_edges = lc.can_child && (int)lc.nd < tr.max_diff;
+  if (lane == 0) ++cones;
+  march_cone_warp(s, tr, c, lc, next, cb, lane, bytes, evals, vis);
+}
+
 // One propagation level: the reflected cones and Keller-fan cones of every node,
 // one warp per cone, cones handed out by a counter (their costs differ widely).
 #ifndef LEVEL_MAX_THREADS
@@ -554,65 +631,163 @@ __global__ void __launch_bounds__(LEVEL_MAX_THREADS, LEVEL_MIN_BLOCKS) k_level(D
     const bool refl = task < n_r;
     const uint32_t idx = refl ? (uint32_t)task : (uint32_t)((task - n_r) / tr.M);
     const int j = refl ? 0 : (int)((task - n_r) % tr.M);
-    const float4 a = refl ? cur.ra[idx] : cur.da[idx];
-    const float4 b = refl ? cur.rb[idx] : cur.db[idx];
-    const uint32_t meta = refl ? cur.rm[idx] : cur.dm[idx];
-    const uint32_t ie = __float_as_uint(a.w);
-    const IERec* r = &s.ies[ie];
-    const float4 nm = __ldg(&r->nrm_meta);
-    const uint32_t label = __float_as_uint(__ldg(&r->rp_lab).w);
-    if (lane == 0) bytes += 32 + 36;
-    const float3 e = xyz(b);
-    ConeD c;
-    c.apex = xyz(a);
-    c.sin_a = tr.sin_a;
-    c.cos_a = tr.cos_a;
-    if (refl) {
-      float3 n = xyz(nm);
-      if (dot(n, e) > 0.f) n = -1.f * n;
-      c.kind = CONE_REFLECT;
-      c.axis = normalize(e - (2.f * dot(e, n)) * n);
-      c.pn = n;
-      c.origin = Endpoint{IGN_LABEL, label};
-    } else {
-      const double* E = s.edges + 12 * __float_as_uint(__ldg(&r->bbc_pb).w);
-      if (lane == 0) bytes += 96;
-      const float3 w = normalize(f3((float)(E[3] - E[0]), (float)(E[4] - E[1]), (float)(E[5] - E[2])));
-      const float cb_ = dot(e, w);
-      const float sb2 = 1.f - cb_ * cb_;
-      if (sb2 < 1e-12f) continue;
-      const float sb = sqrtf(sb2);
-      float3 ua, va;
-      onb(w, &ua, &va);
-      const float phi = (float)j * tr.dphi;
-      float sp, cp;
-      sincosf(phi, &sp, &cp);
-      const float3 rr = cp * ua + sp * va;
-      const float3 d = cb_ * w + sb * rr;
-      const float3 n0 = f3((float)E[6], (float)E[7], (float)E[8]), n1 = f3((float)E[9], (float)E[10], (float)E[11]);
-      if (!(dot(d, n0) > 0.f || dot(d, n1) > 0.f)) continue;
-      float slo, clo, shi, chi;
-      sincosf(phi - 0.5f * tr.dphi, &slo, &clo);
-      sincosf(phi + 0.5f * tr.dphi, &shi, &chi);
-      c.kind = CONE_DIFFRACT;
-      c.axis = normalize(d);
-      c.tlo = (-slo) * ua + clo * va;
-      c.thi = (-shi) * ua + chi * va;
-      c.rmid = rr;
-      c.origin = Endpoint{IGN_ANY, label};
-    }
-    LevelCone lc;
-    lc.depth = (meta >> 24) & 0xfu;
-    lc.nr = (meta >> 16) & 0xfu;
-    lc.nd = (meta >> 20) & 0xfu;
-    lc.tx = meta & 0xffffu;
-    lc.self_ref = idx | (refl ? 0u : 0x80000000u);
-    lc.can_child = (int)lc.depth < tr.max_int && (!tr.tx_max_int || (int)lc.depth < tr.tx_max_int[lc.tx]);
-    lc.test_edges = lc.can_child && (int)lc.nd < tr.max_diff;
-    if (lane == 0) ++cones;
-    march_cone_warp(s, tr, c, lc, next, cb, lane, bytes, evals, vis);
+    level_cone(s, tr, cur, next, cb, refl, idx, j, lane, bytes, cones, evals, vis);
   }
   add_stats(tr, cones, vis, bytes, evals);
+}
+
+// All propagation levels in one launch.  A cone of depth d + 1 becomes a task as
+// soon as its parent has emitted it, so no level waits for the slowest cone of the
+// level before it (each level's last cones otherwise leave most SMs idle).
+//   - Per level two ticket counters hand out reflected-cone tasks and Keller-fan
+//     tasks (M per diffraction node) in slot order.  A warp takes a ticket with one
+//     atomicAdd once the level shows more tasks than tickets; a ticket past the
+//     level's current end is held until a parent emits that task, or dropped once
+//     the level can grow no more.  (A compare-and-swap claim let only one of the
+//     waiting warps succeed per round of the counter's atomic unit: 8-18x slower.)
+//   - Per level a count of tasks created and not finished.  Level e can grow no more
+//     once the counts of levels 1..e-1, read in that order, are zero: a level-k task
+//     is created only by a running level-(k-1) task, and level 1 is complete from
+//     the start.  The tree is done when every count reads zero that way.
+//   - Per node slot a flag set once its record is written.
+// A warp takes the shallowest task available, skipping the levels it has seen final
+// with every task ticketed; it leaves once that holds for every level.  Every wait is bounded (ten seconds
+// for work, a second and a half for a record): a warp that gives up sets err and
+// leaves, and the call reports NIMBUS_ERR_TIMEOUT.  The grid is at most what is
+// resident.
+struct LevelSet {
+  NodeLevel lv[MAX_LEVELS + 1];   // lv[d] for d = 1..max_int; lv[max_int + 1] is the sink
+  unsigned long long* take;       // [2 * (MAX_LEVELS + 1)]: tickets handed out per level (reflected, fan)
+  uint32_t* err;
+  unsigned long long* dbg;        // [20]: where a wait gave up
+  int max_int;
+};
+
+__device__ __forceinline__ unsigned long long ldv64(const unsigned long long* p) {
+  return *(const volatile unsigned long long*)p;
+}
+
+// Tasks level e holds now: reflected cones (kind 0) or fan cones (kind 1).
+__device__ __forceinline__ unsigned long long level_total(const LevelSet& L, int e, int kind, int M) {
+  const NodeLevel& c = L.lv[e];
+  if (kind == 0) return min(*(const volatile uint32_t*)&c.cnt[0], c.cap_r);
+  return (unsigned long long)min(*(const volatile uint32_t*)&c.cnt[1], c.cap_d) * (unsigned)M;
+}
+
+// Levels 1..e-1 have no task left (read in increasing order), so level e is final.
+__device__ __forceinline__ bool levels_done(const LevelSet& L, int e) {
+  for (int k = 1; k < e; ++k)
+    if (ldv64(L.lv[k].outstanding) != 0ull) return false;
+  return true;
+}
+
+__global__ void __launch_bounds__(LEVEL_MAX_THREADS, LEVEL_MIN_BLOCKS) k_levels(DScene s, DTrace tr, LevelSet L,
+                                                                                 CoarseBuf cb) {
+  const int lane = threadIdx.x & 31;
+  unsigned long long bytes = 0;
+  uint32_t cones = 0, vis = 0, evals = 0;
+  const int M = tr.M;
+  int lo = 1;   // lane 0: levels below lo are final and every task of theirs is ticketed
+  for (;;) {
+    // lane 0 finds a task (level d, kind, ticket t) or learns that the tree is done
+    int d = 0, kind = 0;
+    unsigned long long t = 0;
+    if (lane == 0) {
+      const long long t0 = clock64();
+      unsigned nap = 128;
+      for (;;) {
+        int e = lo, k = 0;
+        bool held = false;
+        for (; e <= L.max_int && !held; ++e)
+          for (k = 0; k < 2; ++k)
+            if (ldv64(&L.take[2 * e + k]) < level_total(L, e, k, M)) {
+              t = atomicAdd(&L.take[2 * e + k], 1ull);
+              held = true;
+              break;
+            }
+        if (held) {
+          --e;   // the loop's increment ran once more
+          // wait for the ticket's task, or drop it once level e is final
+          for (;;) {
+            if (t < level_total(L, e, k, M)) {
+              d = e;
+              kind = k;
+              break;
+            }
+            if (levels_done(L, e)) {
+              if (t < level_total(L, e, k, M)) {
+                d = e;
+                kind = k;
+              }
+              break;
+            }
+            if (clock64() - t0 > 20000000000ll) break;
+            __nanosleep(nap);
+            nap = min(nap * 2, 16384u);
+          }
+          if (d != 0) break;
+          continue;   // dropped: look again
+        }
+        while (lo <= L.max_int && ldv64(&L.take[2 * lo]) >= level_total(L, lo, 0, M) &&
+               ldv64(&L.take[2 * lo + 1]) >= level_total(L, lo, 1, M) && levels_done(L, lo))
+          ++lo;
+        if (lo > L.max_int) break;   // no level can grow and every task is ticketed: done
+        if (clock64() - t0 > 20000000000ll) {
+          if (atomicExch(L.err, 1u) == 0u) {
+            L.dbg[0] = 1;
+            for (int q = 1; q <= L.max_int && q < 8; ++q) {
+              L.dbg[2 * q] = ldv64(&L.take[2 * q]);
+              L.dbg[2 * q + 1] = ldv64(L.lv[q].outstanding);
+            }
+          }
+          break;
+        }
+        // back off while there is nothing to take: the waiting warps' loads of the
+        // counters otherwise compete with the working warps' memory traffic
+        __nanosleep(nap);
+        nap = min(nap * 2, 16384u);
+      }
+      if (d != 0) {
+        // the record of a node made in this launch: wait until it is written
+        const uint32_t node = kind == 0 ? (uint32_t)t : (uint32_t)(t / (unsigned)M);
+        const uint8_t* rdy = kind == 0 ? L.lv[d].rdy_r : L.lv[d].rdy_d;
+        if (rdy) {
+          const long long t1 = clock64();
+          while (*(const volatile uint8_t*)(rdy + node) == 0) {
+            if (clock64() - t1 > 3000000000ll) {
+              if (atomicExch(L.err, 2u) == 0u) {
+                L.dbg[0] = 2;
+                L.dbg[1] = (unsigned long long)d | ((unsigned long long)kind << 8);
+                L.dbg[2] = node;
+              }
+              d = -1;
+              break;
+            }
+            __nanosleep(32);
+          }
+          __threadfence();
+        }
+      }
+    }
+    d = __shfl_sync(FULL, d, 0);
+    if (d <= 0) break;
+    kind = __shfl_sync(FULL, kind, 0);
+    t = __shfl_sync(FULL, t, 0);
+    const uint32_t idx = kind == 0 ? (uint32_t)t : (uint32_t)(t / (unsigned)M);
+    const int j = kind == 0 ? 0 : (int)(t % (unsigned)M);
+    level_cone(s, tr, L.lv[d], L.lv[d + 1], cb, kind == 0, idx, j, lane, bytes, cones, evals, vis);
+    __syncwarp();
+    if (lane == 0) {
+      __threadfence();
+      atomicAdd(L.lv[d].outstanding, ~0ull);   // this task is finished
+    }
+  }
+  add_stats(tr, cones, vis, bytes, evals);
+}
+
+// Tasks of the first level (written before the launch) for the single launch.
+__global__ void k_levels_init(NodeLevel L1, int M) {
+  *L1.outstanding = (unsigned long long)min(L1.cnt[0], L1.cap_r) + (unsigned long long)min(L1.cnt[1], L1.cap_d) * M;
 }
 
 // March field of one trace call: the scene's field capped at R+1, lowered to the
@@ -971,6 +1146,40 @@ int trace_coarse(Mem& mem, SceneObj* S, const double* txh, int n_tx, const doubl
   }
   unsigned long long* task_ctr;   // cones handed out so far, one counter per level
   NB_TRY(sc.get(&task_ctr, MAX_LEVELS));
+  // single-launch propagation: task counters, created-not-finished count, error flag
+  // and per-slot ready flags of the levels made inside the launch
+  const bool queue = tn.level_queue != 0 && max_int >= 1;
+  LevelSet LS;
+  std::memset(&LS, 0, sizeof LS);
+  unsigned long long* q_ctr = nullptr;
+  uint32_t* q_err = nullptr;
+  size_t rdy_bytes = 0;
+  uint8_t* rdy = nullptr;
+  if (queue) {
+    NB_TRY(sc.get(&q_ctr, 2 * (MAX_LEVELS + 1) + 1 + 20 + MAX_LEVELS + 1));
+    NB_TRY(sc.get(&q_err, 1));
+    for (int d = 2; d <= max_int; ++d) rdy_bytes += (size_t)lv[d].cap_r + lv[d].cap_d;
+    NB_TRY(sc.get(&rdy, std::max<size_t>(1, rdy_bytes)));
+    size_t off = 0;
+    for (int d = 1; d <= max_int; ++d) {
+      lv[d].outstanding = q_ctr + 2 * (MAX_LEVELS + 1) + 1 + 20 + d;
+      if (d >= 2) {
+        lv[d].rdy_r = rdy + off;
+        off += lv[d].cap_r;
+        lv[d].rdy_d = rdy + off;
+        off += lv[d].cap_d;
+      }
+      LS.lv[d] = lv[d];
+    }
+    NodeLevel sink;
+    std::memset(&sink, 0, sizeof sink);
+    sink.cnt = cnts + 2 * MAX_LEVELS - 2;
+    LS.lv[max_int + 1] = sink;
+    LS.take = q_ctr;
+    LS.dbg = q_ctr + 2 * (MAX_LEVELS + 1) + 1;
+    LS.err = q_err;
+    LS.max_int = max_int;
+  }
   // the sorts and scans of the stretch below draw from this arena
   const size_t arena_bytes =
       radix_arena_bytes(n_rx, 64) + (max_int >= 1 ? 2 * scan_arena_bytes(nflag, true) : 0);
@@ -978,6 +1187,10 @@ int trace_coarse(Mem& mem, SceneObj* S, const double* txh, int n_tx, const doubl
   NB_TRY(sc.get(&arena, std::max<size_t>(1, arena_bytes)));
   const unsigned PG = persistent_grid(256);
   const unsigned LG = persistent_grid(tn.level_block);
+  // the single launch's warps wait for one another's work: no more blocks than are resident
+  int q_blocks = 0;
+  if (queue) NB_CUDA(err, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q_blocks, k_levels, tn.level_block, 0));
+  const unsigned QG = (unsigned)(num_sms() * std::max(1, q_blocks));
   StageTimer tm(st);
   const int e0 = stretch_event(tm, mem, GRAPH_TRACE, 0), e1 = stretch_event(tm, mem, GRAPH_TRACE, 1),
             e2 = stretch_event(tm, mem, GRAPH_TRACE, 2), e3 = stretch_event(tm, mem, GRAPH_TRACE, 3),
@@ -1053,17 +1266,29 @@ int trace_coarse(Mem& mem, SceneObj* S, const double* txh, int n_tx, const doubl
       k_first_counts<<<1, 1, 0, q>>>(tot, tot + 1, lv[1]);
       NB_LAUNCHED(err);
     }
-    // propagation phase, one launch per depth
-    tm.record(e3, q);
-    for (int d = 1; d <= max_int; ++d) {
-      NodeLevel next = d < max_int ? lv[d + 1] : lv[0];
-      if (d == max_int) {
-        next.cap_r = 0;
-        next.cap_d = 0;
-        next.cnt = cnts + 2 * MAX_LEVELS - 2;  // unused sink
-      }
-      k_level<<<LG, tn.level_block, 0, q>>>(s, tr_lev, lv[d], next, cb, task_ctr + d);
+    // propagation phase: one launch per depth, or one launch for all depths
+    if (queue) {
+      NB_CUDA(err, cudaMemsetAsync(q_ctr, 0, (2 * (MAX_LEVELS + 1) + 1 + 20 + MAX_LEVELS + 1) * sizeof(unsigned long long), q));
+      NB_CUDA(err, cudaMemsetAsync(q_err, 0, sizeof(uint32_t), q));
+      if (rdy_bytes) NB_CUDA(err, cudaMemsetAsync(rdy, 0, rdy_bytes, q));
+      k_levels_init<<<1, 1, 0, q>>>(lv[1], tr.M);
       NB_LAUNCHED(err);
+    }
+    tm.record(e3, q);
+    if (queue) {
+      k_levels<<<QG, tn.level_block, 0, q>>>(s, tr_lev, LS, cb);
+      NB_LAUNCHED(err);
+    } else {
+      for (int d = 1; d <= max_int; ++d) {
+        NodeLevel next = d < max_int ? lv[d + 1] : lv[0];
+        if (d == max_int) {
+          next.cap_r = 0;
+          next.cap_d = 0;
+          next.cnt = cnts + 2 * MAX_LEVELS - 2;  // unused sink
+        }
+        k_level<<<LG, tn.level_block, 0, q>>>(s, tr_lev, lv[d], next, cb, task_ctr + d);
+        NB_LAUNCHED(err);
+      }
     }
     tm.record(e4, q);
     return NIMBUS_OK;
@@ -1074,7 +1299,21 @@ int trace_coarse(Mem& mem, SceneObj* S, const double* txh, int n_tx, const doubl
   NB_CUDA(err, cudaMemcpyAsync(hc, cnts, sizeof hc, cudaMemcpyDeviceToHost, st));
   NB_CUDA(err, cudaMemcpyAsync(hov, overflow, sizeof hov, cudaMemcpyDeviceToHost, st));
   NB_CUDA(err, cudaMemcpyAsync(hs, stats, sizeof hs, cudaMemcpyDeviceToHost, st));
+  uint32_t hqerr = 0;
+  if (queue) NB_CUDA(err, cudaMemcpyAsync(&hqerr, q_err, sizeof hqerr, cudaMemcpyDeviceToHost, st));
   NB_CUDA(err, cudaStreamSynchronize(st));
+  if (hqerr) {
+    unsigned long long hd[20];
+    cudaMemcpy(hd, LS.dbg, sizeof hd, cudaMemcpyDeviceToHost);
+    char buf[512];
+    int o = std::snprintf(buf, sizeof buf, "trace: a wait of the single-launch propagation gave up (%llu: %llu %llu |",
+                          hd[0], hd[1], hd[2]);
+    for (int d = 1; d <= max_int && d < 8 && o < 400; ++d)
+      o += std::snprintf(buf + o, sizeof buf - o, " L%d tickets %llu open %llu nodes %u/%u", d, hd[2 * d],
+                         hd[2 * d + 1], hc[2 * d], hc[2 * d + 1]);
+    *err = std::string(buf) + ")";
+    return NIMBUS_ERR_TIMEOUT;
+  }
   nimbus_path_counts& cnt = C->counts;
   std::memset(&cnt, 0, sizeof cnt);
   const int64_t n_raw = std::min<int64_t>(hc[0], cb.cap);

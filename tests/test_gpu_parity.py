@@ -412,13 +412,14 @@ def test_autotune_keeps_results(ctx):
     ctx.release(s)
     assert t["level_block"] in (128, 256)
     assert t["refine_blocks"] in (0, 4) and t["refine_order"] in (0, 1) and t["refine_ms"] > 0
-    for layout in (dict(level_block=128, refine_blocks=3, refine_order=0), t):
-        ctx.set_tuning(**{k: layout[k] for k in ("level_block", "refine_blocks", "refine_order")})
+    assert t["level_queue"] in (0, 1)
+    for layout in (dict(level_block=128, refine_blocks=3, refine_order=0, level_queue=1), t):
+        ctx.set_tuning(**{k: layout[k] for k in ("level_block", "refine_blocks", "refine_order", "level_queue")})
         G = ctx.run(sc, p)
         assert len(G["n"]) == len(base["n"])
         for k in ("tx", "rx", "n", "type", "label", "pts", "length"):
             np.testing.assert_array_equal(G[k], base[k])
-    ctx.set_tuning(level_block=256, refine_blocks=0, refine_order=1)
+    ctx.set_tuning(level_block=256, refine_blocks=0, refine_order=1, level_queue=0)
     with pytest.raises(Exception):
         ctx.set_tuning(level_block=96)
 
@@ -479,6 +480,50 @@ def test_graph_launch_keeps_results(ctx):
             ctx.release(s)
     with pytest.raises(Exception):
         ctx.set_tuning(graph=2)
+
+
+@pytest.mark.parametrize("case", ["room_2x3_d3", "wedge_d2", "batched", "rx_only_depth1"])
+def test_single_launch_propagation_keeps_results(ctx, case):
+    """All depths in one launch (a cone task queue across levels, level_queue=1)
+    against one launch per depth: the same coarse rows, exact paths and counters, at
+    128- and 256-thread blocks, with request batching (per-RX owner and depth), and
+    at depth 1 where the queue holds only the first level."""
+    full = scenes.room_noisy()
+    kw = {}
+    if case == "wedge_d2":
+        sc = scenes.wedge_on_floor(z_tx=0.8, z_rx=2.0)
+        p = config.params_for(sc, max_refl=1, max_diff=1)
+    else:
+        sc = full.with_pairs(full.tx[:2], full.rx[:3])
+        p = config.params_for(sc, max_refl=2 if case != "rx_only_depth1" else 1,
+                              max_diff=1 if case != "rx_only_depth1" else 0)
+        if case == "batched":
+            kw = dict(rx_owner=np.array([0, 1, -1], np.int32), rx_max_int=np.array([1, 3, 2], np.int32))
+    s = ctx.voxelize_scene(sc, p)
+    res = {}
+    try:
+        for lq in (0, 1):
+            for block in (128, 256):
+                ctx.set_tuning(level_queue=lq, level_block=block)
+                co = ctx.trace(s, sc.tx, sc.rx, p, **kw)
+                cq, cc = ctx.query_coarse(co), ctx.coarse_counts(co)
+                P = ctx.refine(s, co, p)
+                res[lq, block] = (cq, ctx.query(P, 0), cc)
+                ctx.release(P)
+                ctx.release(co)
+    finally:
+        ctx.set_tuning(level_queue=0, level_block=256)
+        ctx.release(s)
+    cq0, o0, cc0 = res[0, 256]
+    assert cc0["n_coarse"] > 0
+    for key, (cq, o, cc) in res.items():
+        assert _coarse_rows(cq) == _coarse_rows(cq0), key
+        for k in ("tx", "rx", "n", "type", "label", "pts", "length"):
+            np.testing.assert_array_equal(o[k], o0[k], err_msg=f"{key} {k}")
+        for k in ("n_cones", "n_vis", "n_nodes", "n_coarse", "n_coarse_raw"):
+            assert cc[k] == cc0[k], (key, k)
+    with pytest.raises(Exception):
+        ctx.set_tuning(level_queue=2)
 
 
 def test_scene_checkpoint_round_trip(ctx, tmp_path):

@@ -435,7 +435,7 @@ NIMBUS_API int nimbus_autotune(nimbus_ctx* ctx, nimbus_handle scene, const doubl
  * nimbus_voxelize + nimbus_scene_tables for a cloud without edges, but writes them
  * into caller-owned device buffers and keeps every intermediate in one fixed
  * device array inside this library (NIMBUS_STATIC_MAX_POINTS points and
- * NIMBUS_STATIC_MAX_CELLS voxels at most; about 33 MB that every GPU which loads
+ * NIMBUS_STATIC_MAX_CELLS voxels at most; about 35 MB that every GPU which loads
  * the library holds until the process exits).
  *
  * - Inputs (cloud->xyz, nrm, label, material) must be device pointers.

@@ -394,7 +394,9 @@ NIMBUS_API int nimbus_segment(nimbus_ctx* ctx, const nimbus_cloud* cloud, const 
 typedef struct {
   int32_t level_block;      /* threads per block of the propagation levels: 128 or 256 */
   int32_t refine_blocks;    /* 4-warp refinement blocks per SM: 1..8 (at most as many as fit), 0 = as many as fit */
-  int32_t refine_order;     /* 1: refine the paths with the most interactions first; 0: in coarse order */
+  int32_t refine_order;     /* 1: refine the paths with the most interactions first; 2: first the paths whose
+                               re-projection rays graze their surfaces at the start (smallest |n . d|), then by
+                               interactions; 0: in coarse order */
   int32_t graph;            /* 1: each stretch of a call with no host round trip (trace: RX table, march field,
                                transmission phase and all depths; refine: refinement, final visibility and
                                winners; then dedup) is captured on a private stream and launched on the
@@ -404,9 +406,12 @@ typedef struct {
   int32_t level_queue;      /* 1: all propagation depths in one launch, a cone of depth d + 1 starting as soon as
                                its parent emitted it (waits bounded; NIMBUS_ERR_TIMEOUT if one gives up);
                                0: one launch per depth */
+  int32_t refine_split;     /* > 0: refine in two launches, the first stopping every path after this many
+                               iterations and the second resuming the unfinished ones, costliest per
+                               iteration first (0..65535; 0 or >= rho: one launch) */
 } nimbus_tuning;
 
-/* The context's launch configuration (defaults 256, 0, 1, 1, level_queue 0). */
+/* The context's launch configuration (defaults 256, 0, 1, 1, level_queue 0, refine_split 0). */
 NIMBUS_API int nimbus_get_tuning(nimbus_ctx* ctx, nimbus_tuning* out);
 
 /* Replace it.  A value out of range returns NIMBUS_ERR_ARG and changes nothing. */
@@ -416,8 +421,8 @@ NIMBUS_API int nimbus_set_tuning(nimbus_ctx* ctx, const nimbus_tuning* t);
  * (blocks of 128 or 256 threads, one launch per depth or one for all depths), keeps
  * the fastest propagation time, then
  * refines that coarse set once per refinement layout (4 or all resident blocks per
- * SM x ordered or not), keeps the fastest, stores the result in the context for the
- * calls that follow and writes it to `out` (may be NULL).  Times are CUDA events on
+ * SM x coarse order, most interactions first or grazing rays first x one launch or
+ * two, the first stopping at 128 iterations), keeps the fastest, stores the result in the context for the calls that follow and writes it to `out` (may be NULL).  Times are CUDA events on
  * `stream`; the call synchronises.  Errors of the trace or refinement (including
  * NIMBUS_ERR_OVERFLOW: the sample needs larger bounds) are returned unchanged and
  * leave the configuration as it was. */

@@ -308,12 +308,37 @@ struct WarpPath {
   float elen[NB_MAXI + 2];
 };
 
+// Two-phase refinement (a launch layout; results are the same bit for bit).  Phase 1
+// runs every path for at most `cap` iterations; a path still running then saves its
+// iterate and leaves.  Phase 2 resumes those paths, the costliest per iteration
+// first, so the long ones start at the beginning of a launch instead of wherever the
+// hand-out order put them.  A resumed path continues the same iteration sequence from
+// the same FP64 state; its label caches are refilled, and a cache's content is a
+// function of its key only.
+struct PathState {
+  d3 I[NB_MAXI + 2];      // iterate (nodes 0..n+1)
+  d3 c[NB_MAXI + 2];      // re-projected points / edge base points
+  double tpar[NB_MAXI + 2];
+  float3 u[NB_MAXI + 2], v[NB_MAXI + 2];
+  int it;
+};
+
+struct RefineSplit {
+  int phase;              // 0: one pass; 1: stop at cap; 2: resume the saved paths
+  int cap;
+  PathState* st;          // [n] by coarse index
+  uint32_t* cont;         // phase 1: coarse indices of the saved paths; phase 2: in resume order
+  uint64_t* cont_key;     // phase 1: 0xffff minus the cost per iteration (ascending sort = costliest first)
+  unsigned* cont_n;
+};
+
 #ifndef REFINE_BLOCKS_PER_SM
 #define REFINE_BLOCKS_PER_SM 6
 #endif
 __global__ void __launch_bounds__(128, REFINE_BLOCKS_PER_SM) k_refine(DScene s, DRefine rp, CoarseView C, const double* txd,
                                                    const double* rxd, ExactRec* out, unsigned long long* bytes_out,
-                                                   unsigned long long* next_path, const uint32_t* order, int n_cache) {
+                                                   unsigned long long* next_path, const uint32_t* order, int n_cache,
+                                                   RefineSplit sp) {
   // label caches: n_cache per warp (the trace's reflection limit), in dynamic shared
   // memory, so that the rest of the SM's 256 KB stays L1 for the point loads
   extern __shared__ LabelCache s_dyn[];
@@ -327,8 +352,9 @@ __global__ void __launch_bounds__(128, REFINE_BLOCKS_PER_SM) k_refine(DScene s, 
     unsigned long long grab = 0;
     if (lane == 0) grab = atomicAdd(next_path, 1ull);
     const int64_t gi = (int64_t)__shfl_sync(FULL, grab, 0);
-    if (gi >= C.n) break;
-    const int64_t i = order ? order[gi] : gi;
+    const int64_t n_work = sp.phase == 2 ? (int64_t)*(volatile unsigned*)sp.cont_n : C.n;
+    if (gi >= n_work) break;
+    const int64_t i = sp.phase == 2 ? (int64_t)sp.cont[gi] : (order ? order[gi] : gi);
     const int n = (int)C.nint[i];
     const uint32_t types = C.types[i];
     const uint32_t tx = C.tx[i], rx = C.rx[i];
@@ -366,8 +392,42 @@ __global__ void __launch_bounds__(128, REFINE_BLOCKS_PER_SM) k_refine(DScene s, 
     __syncwarp();
     int status = ST_VALID, it = 0;
     bool converged = false;
+    if (sp.phase == 2) {
+      const PathState& ps = sp.st[i];
+      if (node) W.I[lane] = ps.I[lane];
+      if (mine) {
+        W.c[lane] = ps.c[lane];
+        W.tpar[lane] = ps.tpar[lane];
+        W.u[lane] = ps.u[lane];
+        W.v[lane] = ps.v[lane];
+      }
+      it = ps.it;
+      __syncwarp();
+    }
+    const long long t_path = clock64();
+    bool saved = false;
     float gn = 0.f;
     for (; it <= rp.rho; ++it) {
+      if (sp.phase == 1 && it == sp.cap) {
+        // phase 1 ends here for this path: save the iterate for phase 2
+        PathState& ps = sp.st[i];
+        if (node) ps.I[lane] = W.I[lane];
+        if (mine) {
+          ps.c[lane] = W.c[lane];
+          ps.tpar[lane] = W.tpar[lane];
+          ps.u[lane] = W.u[lane];
+          ps.v[lane] = W.v[lane];
+        }
+        if (lane == 0) {
+          ps.it = it;
+          const unsigned slot = atomicAdd(sp.cont_n, 1u);
+          const long long per_it = (clock64() - t_path) / max(1, sp.cap) / 64;
+          sp.cont[slot] = (uint32_t)i;
+          sp.cont_key[slot] = 0xffffull - (uint64_t)min(per_it, 0xffffll);
+        }
+        saved = true;
+        break;
+      }
       // gradient of Eq. 2: (e_in + e_out) . (u, v) for reflections, . w for diffractions
       float g0 = 0.f, g1 = 0.f, a = 1.f, b = 1.f;
       float3 ea = f3(0, 0, 0), eb = f3(0, 0, 0);
@@ -488,6 +548,7 @@ __global__ void __launch_bounds__(128, REFINE_BLOCKS_PER_SM) k_refine(DScene s, 
       __syncwarp();
     }
     __syncwarp();
+    if (saved) continue;
     if (status == ST_VALID && !converged && !(gn < (float)rp.delta)) status = ST_NOT_CONVERGED;
     if (status == ST_VALID) {
       // visibility between consecutive path nodes
@@ -537,9 +598,37 @@ __global__ void __launch_bounds__(128, REFINE_BLOCKS_PER_SM) k_refine(DScene s, 
   if (lane == 0 && bytes) atomicAdd(bytes_out, bytes);
 }
 
-__global__ void k_order_keys(const uint32_t* nint, int64_t n, uint64_t* keys, uint32_t* vals) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    keys[i] = (uint64_t)(NB_MAXI - nint[i]);
+// Hand-out order of the paths (it changes no result, only which paths run last).
+// Mode 1: the paths with the most interactions first.  Mode 2: first the paths whose
+// re-projection rays graze their surfaces at the starting iterate (the smallest
+// |n . d| over the reflections, in 16 buckets of 0.05), then by interactions.  A
+// re-projection ray nearly tangent to its surface marches in small |f| steps, and the
+// paths that keep such a ray while they run all rho iterations take hundreds of
+// milliseconds each; started last, they decide when the launch ends.  On the noisy
+// room the paths starting below 0.2 are a fifth of the paths and hold a third of the
+// oracle's Eq. 1 evaluations and most of the heaviest paths.
+__global__ void k_order_keys(DScene s, CoarseView C, const double* txd, const double* rxd, int mode, uint64_t* keys,
+                             uint32_t* vals) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < C.n; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t n = C.nint[i];
+    uint64_t key = (uint64_t)(NB_MAXI - n);
+    if (mode == 2) {
+      const uint32_t t = C.tx[i];
+      float3 prev = f3((float)txd[3 * t], (float)txd[3 * t + 1], (float)txd[3 * t + 2]);
+      float gmin = 1.f;
+      for (uint32_t q = 0; q < n && q < NB_MAXI; ++q) {
+        const IERec* r = &s.ies[C.ie[i * NB_MAXI + q]];
+        const float3 rp = xyz(__ldg(&r->rp_lab));
+        if (!((C.types[i] >> q) & 1u)) {
+          const float3 d = rp - prev;
+          const float dl = len(d);
+          if (dl > 0.f) gmin = fminf(gmin, fabsf(dot(d, xyz(__ldg(&r->nrm_meta)))) / dl);
+        }
+        prev = rp;
+      }
+      key += (uint64_t)min(15, (int)(gmin * 20.f)) << 4;
+    }
+    keys[i] = key;
     vals[i] = (uint32_t)i;
   }
 }
@@ -660,6 +749,15 @@ __global__ void k_fresnel(const ExactRec* ex, const uint64_t* keys, const uint32
   }
 }
 
+// Entries of the continuation list past its count sort after every saved path.
+__global__ void k_cont_fill(uint64_t* keys, uint32_t* vals, const unsigned* cnt, int64_t n) {
+  const int64_t m = *cnt;
+  for (int64_t i = m + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    keys[i] = 0x10000ull;
+    vals[i] = 0u;
+  }
+}
+
 __global__ void k_final(const uint32_t* keep, const uint32_t* pos, const uint32_t* vals, int64_t n, uint32_t* out) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     if (keep[i]) out[pos[i]] = vals[i];
@@ -704,6 +802,25 @@ int refine_paths(Mem& mem, SceneObj* S, CoarseObj* C, const nimbus_refine_params
   Scratch sc(&mem, st);
   unsigned long long* rbytes;   // [0] bytes read, [1] next path to hand out
   NB_TRY(sc.get(&rbytes, 2));
+  // two-phase layout: state, continuation list and its sort buffers
+  const bool split = tn.refine_split > 0 && tn.refine_split < p->rho;
+  RefineSplit sp1{}, sp2{}, sp0{};
+  uint64_t* ck_alt = nullptr;
+  uint32_t* cv_alt = nullptr;
+  if (split) {
+    PathState* st_buf;
+    uint32_t* cont;
+    uint64_t* ckey;
+    unsigned* cnt;
+    NB_TRY(sc.get(&st_buf, n));
+    NB_TRY(sc.get(&cont, n));
+    NB_TRY(sc.get(&ckey, n));
+    NB_TRY(sc.get(&cnt, 1));
+    NB_TRY(sc.get(&ck_alt, n));
+    NB_TRY(sc.get(&cv_alt, n));
+    sp1 = RefineSplit{1, tn.refine_split, st_buf, cont, ckey, cnt};
+    sp2 = RefineSplit{2, tn.refine_split, st_buf, cont, ckey, cnt};
+  }
   const int n_cache = std::max(1, std::min(C->max_refl, NB_MAXI));
   const size_t dyn = sizeof(LabelCache) * 4 * n_cache;
   int refine_blocks = 0;   // resident blocks per SM (a persistent grid)
@@ -728,7 +845,8 @@ int refine_paths(Mem& mem, SceneObj* S, CoarseObj* C, const nimbus_refine_params
   NB_TRY(sc.get(&flag, n));
   NB_TRY(sc.get(&pos, n));
   NB_TRY(sc.get(&nw, 1));
-  const size_t arena_bytes = (tn.refine_order ? radix_arena_bytes(n, 8) : 0) + scan_arena_bytes(n, true);
+  const size_t arena_bytes = (tn.refine_order ? radix_arena_bytes(n, 8) : 0) + scan_arena_bytes(n, true) +
+                             (split ? radix_arena_bytes(n, 17) : 0);
   char* arena;
   NB_TRY(sc.get(&arena, std::max<size_t>(1, arena_bytes)));
   const unsigned G2 = std::min<unsigned>(grid_for(n, 256), pgrid(256));
@@ -744,12 +862,24 @@ int refine_paths(Mem& mem, SceneObj* S, CoarseObj* C, const nimbus_refine_params
     NB_CUDA(err, cudaMemsetAsync(rbytes, 0, 2 * sizeof(unsigned long long), q));
     tm.record(e0, q);
     if (tn.refine_order) {
-      k_order_keys<<<grid_for(n, 256), 256, 0, q>>>(C->nint, n, okeys, ovals);
+      k_order_keys<<<grid_for(n, 256), 256, 0, q>>>(S->d, cv, C->txd, C->rxd, tn.refine_order, okeys, ovals);
       NB_LAUNCHED(err);
       NB_TRY(radix_sort(ws, okeys, ovals, okeys_alt, ovals_alt, n, 8));
     }
-    k_refine<<<G, 128, dyn, q>>>(S->d, rp, cv, C->txd, C->rxd, P->all, rbytes, rbytes + 1, ovals, n_cache);
-    NB_LAUNCHED(err);
+    if (!split) {
+      k_refine<<<G, 128, dyn, q>>>(S->d, rp, cv, C->txd, C->rxd, P->all, rbytes, rbytes + 1, ovals, n_cache, sp0);
+      NB_LAUNCHED(err);
+    } else {
+      NB_CUDA(err, cudaMemsetAsync(sp1.cont_n, 0, sizeof(unsigned), q));
+      k_refine<<<G, 128, dyn, q>>>(S->d, rp, cv, C->txd, C->rxd, P->all, rbytes, rbytes + 1, ovals, n_cache, sp1);
+      NB_LAUNCHED(err);
+      k_cont_fill<<<grid_for(n, 256), 256, 0, q>>>(sp1.cont_key, sp1.cont, sp1.cont_n, n);
+      NB_LAUNCHED(err);
+      NB_TRY(radix_sort(ws, sp1.cont_key, sp1.cont, ck_alt, cv_alt, n, 17));
+      NB_CUDA(err, cudaMemsetAsync(rbytes + 1, 0, sizeof(unsigned long long), q));
+      k_refine<<<G, 128, dyn, q>>>(S->d, rp, cv, C->txd, C->rxd, P->all, rbytes, rbytes + 1, ovals, n_cache, sp2);
+      NB_LAUNCHED(err);
+    }
     tm.record(e1, q);
     NB_CUDA(err, cudaMemsetAsync(best, 0xff, ng * sizeof(unsigned long long), q));
     NB_CUDA(err, cudaMemsetAsync(widx, 0xff, ng * sizeof(uint32_t), q));

@@ -84,7 +84,7 @@ def dist_env():
 # (dram__bytes_read.sum + dram__bytes_write.sum, one-pass ncu capture), valid only for
 # the device code it was taken on: the hash covers that code -- refine.cu up to its
 # host launcher, and the two headers whole -- and a changed kernel reports null.
-REFINE_TRAFFIC = {"bytes": 98812672 + 146604544, "sources_sha256": "8a05e1995beee2335ea0b0dcdcd83981b910c7aee058c4513d5166d7d59bf7c8"}
+REFINE_TRAFFIC = {"bytes": 98074112 + 148485376, "sources_sha256": "9fdbc6fafc6faa9944be0cf08634b696355ebb0167325114cf3d16ae05914037"}
 KERNEL_SOURCES = (("paper_2402_13747_b300/csrc/refine.cu", b"\nint refine_paths("),
                   ("paper_2402_13747_b300/csrc/warp_geom.cuh", None),
                   ("paper_2402_13747_b300/csrc/nimbus_internal.cuh", None))
@@ -252,8 +252,10 @@ def trace_sized(ctx, s, tx, rx, p, sizes: dict, **kw):
     return c
 
 
-def secondary_line(ctx, name: str, steps: int, warmup: int, flush, stream):
-    """A shorter measurement of another workload: step time, rays/s, exact paths/s."""
+def secondary_line(ctx, name: str, steps: int, warmup: int, flush, stream, tune: bool = True):
+    """A shorter measurement of another workload: step time, rays/s, exact paths/s, under
+    launch layouts tuned on that workload (untimed; the context's layouts are restored
+    afterwards)."""
     import torch
     from paper_2402_13747_b300 import config
     sc = make_scene(name)
@@ -265,6 +267,15 @@ def secondary_line(ctx, name: str, steps: int, warmup: int, flush, stream):
             T(sc.edges, torch.float64), T(sc.edge_label.astype(np.int64), torch.int64).to(torch.int32))
     d_tx, d_rx = T(sc.tx, torch.float64), T(sc.rx, torch.float64)
     sizes = {}
+    before = ctx.get_tuning()
+    tuning = before
+    if tune:
+        s0 = ctx.voxelize(*args, params=p)
+        try:
+            tuning = ctx.autotune(s0, sc.tx, sc.rx, p)
+        except Exception as e:   # e.g. the workload needs larger node bounds: keep the layouts
+            tuning = dict(before, autotune_error=str(e)[:120])
+        ctx.release(s0)
     ms, counts = [], []
     for i in range(warmup + steps):
         flush.fill_(1)
@@ -282,6 +293,7 @@ def secondary_line(ctx, name: str, steps: int, warmup: int, flush, stream):
         if i >= warmup:
             ms.append(e0.elapsed_time(e1))
             counts.append(cnt)
+    ctx.set_tuning(**{k: v for k, v in before.items() if not k.endswith("_ms")})
     t = sum(ms) / 1e3
     c0 = counts[-1]
     coarse_ms = c0["ms_vis"] + c0["ms_primary"] + c0["ms_levels"] + c0["ms_kappa"]
@@ -293,7 +305,8 @@ def secondary_line(ctx, name: str, steps: int, warmup: int, flush, stream):
             "exact_paths_per_step": c0["n_paths"], "cones_per_step": c0["n_cones"],
             "stage_ms": {k: c0[k] for k in ("ms_vis", "ms_primary", "ms_levels", "ms_kappa", "ms_refine",
                                             "ms_dedup")},
-            "node_bounds": sizes or "default"}
+            "node_bounds": sizes or "default",
+            "tuning": {k: v for k, v in tuning.items() if not k.endswith("_ms")}}
 
 
 def region_update_timing(ctx, reps: int = 3):
@@ -425,13 +438,14 @@ def main():
             ctx.release(h)
         return cnt
 
-    # launch layouts (result-neutral) tuned on a sample of the workload, untimed: every
-    # TX against RXs spread over the whole set (at most 32), so that the sample's
-    # refinement is not a short tail-bound launch
+    # launch layouts (result-neutral) tuned on this rank's whole workload, untimed: on a
+    # sample the refinement is one long tail whatever the layout, so a sample picks
+    # layouts by noise (every 32nd RX of the indoor scan chose one launch, 1.60 s on the
+    # full workload, where two phases take 1.34 s)
     tuning = ctx.get_tuning()
     if not args.no_tune:
         s0 = ctx.voxelize(d_xyz, d_nrm, d_lab, d_mat, d_edges, d_elab, params=p)
-        tuning = ctx.autotune(s0, my.tx, my.rx[::max(1, my.rx.shape[0] // 32)], p)
+        tuning = ctx.autotune(s0, my.tx, my.rx, p)
         ctx.release(s0)
     for _ in range(args.warmup):
         step()
@@ -553,7 +567,7 @@ def main():
                 if name == args.workload:
                     continue
                 try:
-                    secondary[name] = secondary_line(ctx, name, 2, 1, flush, stream)
+                    secondary[name] = secondary_line(ctx, name, 2, 1, flush, stream, tune=not args.no_tune)
                 except Exception as ex:  # must not hide the main line
                     secondary[name] = {"error": repr(ex)}
 
@@ -602,7 +616,7 @@ def main():
                           "points": int(sc.xyz.shape[0]), "pairs": int(tx_all.shape[0] * sc.rx.shape[0]),
                           "form": "batched: all pairs in one trace_coarse + refine",
                           "tuning": {k: v for k, v in tuning.items() if not k.endswith("_ms")},
-                          "tuning_sample": "the rank's TXs x every (n_rx // 32)-th RX of the workload",
+                          "tuning_sample": "the rank's whole workload (its TXs x every RX), untimed",
                           "parallelism": f"tx-sharded x{world}" if world > 1 else "1 GPU"},
                "coarse_rays_per_s": cones / coarse_t if coarse_t > 0 else None,
                "exact_paths_per_s": exact_ps, "exact_paths_per_step": paths / args.steps,

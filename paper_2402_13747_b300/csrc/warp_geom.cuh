@@ -121,36 +121,45 @@ __device__ bool visible_warp(const DScene& s, float3 A, float3 B, Endpoint ea, E
   for (int step = 0; step < max_steps; ++step) {
     uint2 cell = __ldg(&s.cells[cell_index(s, w.v[0], w.v[1], w.v[2])]);
     for (uint32_t base = 0; base < cell.y; base += 32) {
-      uint32_t k = base + lane;
-      uint32_t id = cell.x + k;
+      // each lane screens one IE of the voxel: its sphere against the segment, then
+      // the two exact march skips (cannot occlude, cannot hit), so that the warp walks
+      // the IEs one by one only for the marches that must run
+      const uint32_t k = base + lane;
+      const uint32_t id = cell.x + k;
       bool ok = false;
       if (k < cell.y) {
         const IERec* r = &s.ies[id];
-        float4 sc = __ldg(&r->sc_pc);
-        float4 nm = __ldg(&r->nrm_meta);
+        const float4 sc = __ldg(&r->sc_pc);
+        const float4 nm = __ldg(&r->nrm_meta);
         bytes += 32;
         ok = (__float_as_uint(nm.w) & 1u) == IE_POINT && segment_sphere(A, d, T, xyz(sc), s.r_sub);
+        if (ok) {
+          const float3 c = xyz(__ldg(&r->bbc_pb));
+          const float tc = dot(c - A, d);
+          const uint32_t lbl = __float_as_uint(__ldg(&r->rp_lab).w);
+          ok = !cannot_occlude(ea, eb, lbl, tc, 0.5f * s.seg_len, T, s.vis_ignore);
+          if (ok) {
+            bytes += 32;
+            ok = !march_cannot_hit(__ldg(&r->slab), xyz(nm), (A - c) + tc * d, d, 0.5f * s.seg_len, s.sdf_eps);
+          }
+        }
       }
       unsigned mask = __ballot_sync(FULL, ok);
       while (mask) {
-        int j = __ffs(mask) - 1;
+        const int j = __ffs(mask) - 1;
         mask &= mask - 1;
-        uint32_t cid = __shfl_sync(FULL, id, j);
-        const IERec* r = &s.ies[cid];
-        float4 bb = __ldg(&r->bbc_pb);
-        float4 sc = __ldg(&r->sc_pc);
-        float3 c = xyz(bb);
-        float tc = dot(c - A, d);
-        uint32_t lbl = __float_as_uint(__ldg(&r->rp_lab).w);
-        if (cannot_occlude(ea, eb, lbl, tc, 0.5f * s.seg_len, T, s.vis_ignore)) continue;
-        float3 x0 = (A - c) + tc * d;
-        if (lane == 0) bytes += 32;
-        if (march_cannot_hit(__ldg(&r->slab), xyz(__ldg(&r->nrm_meta)), x0, d, 0.5f * s.seg_len, s.sdf_eps)) continue;
+        const IERec* r = &s.ies[__shfl_sync(FULL, id, j)];
+        const float4 bb = __ldg(&r->bbc_pb);
+        const float4 sc = __ldg(&r->sc_pc);
+        const float3 c = xyz(bb);
+        const float tc = dot(c - A, d);
+        const uint32_t lj = __float_as_uint(__ldg(&r->rp_lab).w);
+        const float3 xj = (A - c) + tc * d;
         float tau;
-        if (!sdf_march_warp(s, __float_as_uint(bb.w), __float_as_uint(sc.w), c, x0, d, &tau, lane, bytes)) continue;
-        float th = tc + tau;
+        if (!sdf_march_warp(s, __float_as_uint(bb.w), __float_as_uint(sc.w), c, xj, d, &tau, lane, bytes)) continue;
+        const float th = tc + tau;
         if (!(th > 0.f && th < T)) continue;
-        if (ignored(ea, lbl, th, s.vis_ignore) || ignored(eb, lbl, T - th, s.vis_ignore)) continue;
+        if (ignored(ea, lj, th, s.vis_ignore) || ignored(eb, lj, T - th, s.vis_ignore)) continue;
         return false;
       }
     }

@@ -417,15 +417,18 @@ NIMBUS_API int nimbus_get_tuning(nimbus_ctx* ctx, nimbus_tuning* out);
 /* Replace it.  A value out of range returns NIMBUS_ERR_ARG and changes nothing. */
 NIMBUS_API int nimbus_set_tuning(nimbus_ctx* ctx, const nimbus_tuning* t);
 
-/* Autotuner.  Traces the given TX/RX sample on `scene` once per level layout
- * (blocks of 128 or 256 threads, one launch per depth or one for all depths), keeps
- * the fastest propagation time, then
- * refines that coarse set once per refinement layout (4 or all resident blocks per
- * SM x coarse order, most interactions first or grazing rays first x one launch or
- * two, the first stopping at 128 iterations), keeps the fastest, stores the result in the context for the calls that follow and writes it to `out` (may be NULL).  Times are CUDA events on
- * `stream`; the call synchronises.  Errors of the trace or refinement (including
- * NIMBUS_ERR_OVERFLOW: the sample needs larger bounds) are returned unchanged and
- * leave the configuration as it was. */
+/* Autotuner.  Traces the given TX/RX set on `scene` once per level layout (blocks
+ * of 128 or 256 threads x one launch per depth or one for all depths) and keeps the
+ * fastest propagation time.  Then it refines that coarse set once per refinement
+ * layout (4 or all resident blocks per SM x coarse order, most interactions first
+ * or grazing rays first x one launch or two, the first stopping at 128 or 512
+ * iterations) and keeps the fastest.  The result is stored in the context for the
+ * calls that follow and written to `out` (may be NULL).  Every layout gives the same
+ * results; tune on the workload itself where its refinement ends on long paths (a
+ * small sample is one tail whatever the layout).  Times are CUDA events on `stream`;
+ * the call synchronises.  Errors of the trace or refinement (including
+ * NIMBUS_ERR_OVERFLOW: the set needs larger bounds) are returned unchanged and leave
+ * the configuration as it was. */
 NIMBUS_API int nimbus_autotune(nimbus_ctx* ctx, nimbus_handle scene, const double* tx, int32_t n_tx,
                                const double* rx, int32_t n_rx, const nimbus_trace_params* trace_params,
                                const nimbus_refine_params* refine_params, nimbus_tuning* out, void* stream);

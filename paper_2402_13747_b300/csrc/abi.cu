@@ -617,7 +617,7 @@ int nimbus_autotune(nimbus_ctx* ctx, nimbus_handle scene, const double* tx, int3
     return rc;
   }
   double best_rf = -1.0;
-  const int rblocks[2] = {4, 0}, orders[3] = {0, 1, 2}, splits[2] = {0, 128};
+  const int rblocks[2] = {4, 0}, orders[3] = {0, 1, 2}, splits[3] = {0, 128, 512};
   for (int sl : splits)
   for (int rb : rblocks)
     for (int od : orders) {

@@ -413,7 +413,7 @@ def test_autotune_keeps_results(ctx):
     assert t["level_block"] in (128, 256)
     assert t["refine_blocks"] in (0, 4) and t["refine_order"] in (0, 1, 2) and t["refine_ms"] > 0
     assert t["level_queue"] in (0, 1)
-    assert t["refine_split"] in (0, 128)
+    assert t["refine_split"] in (0, 128, 512)
     for layout in (dict(level_block=128, refine_blocks=3, refine_order=0, level_queue=1, refine_split=0),
                    dict(level_block=256, refine_blocks=0, refine_order=2, level_queue=0, refine_split=0),
                    dict(level_block=256, refine_blocks=0, refine_order=1, level_queue=0, refine_split=5),

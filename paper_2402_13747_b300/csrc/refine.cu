@@ -76,58 +76,110 @@ __device__ __forceinline__ uint32_t block_mask(int gx, int gy, int gz) {
 
 __device__ __forceinline__ int floor_div(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
 
+// The cached entities selected for one Eq. 1 evaluation, in cache order, as a flat
+// list of points: entity j holds points [beg[j], end[j]) of the list, its first one
+// at pb[j] in the scene.  Per warp, in shared memory (also the scratch of fill_cache).
+struct SelList {
+  uint32_t end[32];
+  uint32_t beg[32];
+  uint32_t pb[32];
+};
+
 // (Re)build the cache for target subvoxel gR and label: the label's point IEs whose
 // subvoxel lies within two subvoxels of gR -- all that Eq. 1 at any point of a
-// re-projection segment around the target can draw on.
-__device__ void fill_cache(const DScene& s, LabelCache& lc, const int gR[3], uint32_t label, int lane,
+// re-projection segment around the target can draw on.  The region's voxels (z, y, x
+// order; 27 for two subvoxels a voxel) are taken 32 at a time: each lane loads one
+// voxel's entity range, a warp scan lays the ranges out as one flat list, and each
+// lane screens two entities of every 64, so the loads of the whole region are in
+// flight together instead of one voxel after another.  Entries keep the order of a
+// voxel-by-voxel scan.
+__device__ void fill_cache(const DScene& s, LabelCache& lc, SelList& sl, const int gR[3], uint32_t label, int lane,
                            unsigned long long& bytes) {
-  int v0[3], v1[3];
+  int v0[3], nv[3];
   for (int a = 0; a < 3; ++a) {
     v0[a] = floor_div(gR[a] - 2, s.dv);
-    v1[a] = floor_div(gR[a] + 2, s.dv);
+    nv[a] = floor_div(gR[a] + 2, s.dv) - v0[a] + 1;
   }
+  const int n_vox = nv[0] * nv[1] * nv[2];
   const float ofs[3] = {s.ox, s.oy, s.oz};
   const unsigned lt = (1u << lane) - 1u;
   int nc = 0;
-  for (int vz = v0[2]; vz <= v1[2]; ++vz)
-    for (int vy = v0[1]; vy <= v1[1]; ++vy)
-      for (int vx = v0[0]; vx <= v1[0]; ++vx) {
-        if (!in_grid(s, vx, vy, vz)) continue;
-        uint2 cell = __ldg(&s.cells[cell_index(s, vx, vy, vz)]);
-        for (uint32_t base = 0; base < cell.y; base += 32) {
-          uint32_t k = base + lane;
-          bool ok = false;
-          uint32_t pb = 0, pc = 0, nbr = 0;
-          if (k < cell.y) {
-            const IERec* r = &s.ies[cell.x + k];
-            float4 nm = __ldg(&r->nrm_meta);
-            float4 rp = __ldg(&r->rp_lab);
-            bytes += 32;
-            if ((__float_as_uint(nm.w) & 1u) == IE_POINT && __float_as_uint(rp.w) == label) {
-              float4 sc = __ldg(&r->sc_pc);
-              const float scv[3] = {sc.x, sc.y, sc.z};
-              int dg[3];
-              ok = true;
-              for (int a = 0; a < 3; ++a) {
-                dg[a] = (int)floorf((scv[a] - ofs[a]) * s.inv_hs) - gR[a];
-                ok = ok && abs(dg[a]) <= 2;
-              }
-              pc = __float_as_uint(sc.w);
-              nbr = block_mask(dg[0], dg[1], dg[2]);
-              pb = __float_as_uint(__ldg(&r->bbc_pb).w);
-              bytes += 32;
-            }
-          }
-          unsigned mask = __ballot_sync(FULL, ok);
-          int slot = nc + __popc(mask & lt);
-          if (ok && slot < RCAP) {
-            lc.pb[slot] = pb;
-            lc.pc[slot] = pc;
-            lc.nbr[slot] = nbr;
-          }
-          nc += __popc(mask);
+  for (int vb = 0; vb < n_vox; vb += 32) {
+    uint32_t first = 0, cnt = 0;
+    const int q = vb + lane;
+    if (q < n_vox) {
+      const int vx = v0[0] + q % nv[0], vy = v0[1] + (q / nv[0]) % nv[1], vz = v0[2] + q / (nv[0] * nv[1]);
+      if (in_grid(s, vx, vy, vz)) {
+        const uint2 cell = __ldg(&s.cells[cell_index(s, vx, vy, vz)]);
+        first = cell.x;
+        cnt = cell.y;
+      }
+    }
+    uint32_t e = cnt;   // inclusive scan: the flat list's end of voxel `lane`
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(FULL, e, o);
+      if (lane >= o) e += t;
+    }
+    const uint32_t total = __shfl_sync(FULL, e, 31);
+    __syncwarp();
+    sl.end[lane] = e;
+    sl.beg[lane] = e - cnt;   // the voxel's start in the flat list
+    sl.pb[lane] = first;      // its first entity in the scene
+    __syncwarp();
+    int jv0 = 0, jv1 = 0;
+    for (uint32_t base = 0; base < total; base += 64) {
+      bool ok[2] = {false, false};
+      uint32_t pb[2] = {0, 0}, pc[2] = {0, 0}, nbr[2] = {0, 0};
+      const IERec* r[2];
+      float4 nm[2], rp[2];
+      bool in[2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const uint32_t t = base + 32 * u + lane;
+        in[u] = t < total;
+        int& jv = u == 0 ? jv0 : jv1;
+        if (u == 1) jv1 = max(jv1, jv0);
+        if (in[u])
+          while (t >= sl.end[jv]) ++jv;
+        r[u] = &s.ies[in[u] ? sl.pb[jv] + (t - sl.beg[jv]) : sl.pb[0]];
+        if (in[u]) {
+          nm[u] = __ldg(&r[u]->nrm_meta);
+          rp[u] = __ldg(&r[u]->rp_lab);
+          bytes += 32;
         }
       }
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        if (in[u] && (__float_as_uint(nm[u].w) & 1u) == IE_POINT && __float_as_uint(rp[u].w) == label) {
+          const float4 sc = __ldg(&r[u]->sc_pc);
+          const float scv[3] = {sc.x, sc.y, sc.z};
+          int dg[3];
+          ok[u] = true;
+          for (int a = 0; a < 3; ++a) {
+            dg[a] = (int)floorf((scv[a] - ofs[a]) * s.inv_hs) - gR[a];
+            ok[u] = ok[u] && abs(dg[a]) <= 2;
+          }
+          pc[u] = __float_as_uint(sc.w);
+          nbr[u] = block_mask(dg[0], dg[1], dg[2]);
+          pb[u] = __float_as_uint(__ldg(&r[u]->bbc_pb).w);
+          bytes += 32;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const unsigned mask = __ballot_sync(FULL, ok[u]);
+        const int slot = nc + __popc(mask & lt);
+        if (ok[u] && slot < RCAP) {
+          lc.pb[slot] = pb[u];
+          lc.pc[slot] = pc[u];
+          lc.nbr[slot] = nbr[u];
+        }
+        nc += __popc(mask);
+      }
+    }
+    __syncwarp();
+  }
   if (lane == 0) {
     lc.gR[0] = gR[0];
     lc.gR[1] = gR[1];
@@ -137,15 +189,6 @@ __device__ void fill_cache(const DScene& s, LabelCache& lc, const int gR[3], uin
   }
   __syncwarp();
 }
-
-// The cached entities selected for one Eq. 1 evaluation, in cache order, as a flat
-// list of points: entity j holds points [beg[j], end[j]) of the list, its first one
-// at pb[j] in the scene.  Per warp, in shared memory.
-struct SelList {
-  uint32_t end[32];
-  uint32_t beg[32];
-  uint32_t pb[32];
-};
 
 // Eq. 1 over the nearby points of one label -- the points of the cached IEs whose
 // subvoxel lies in the 3x3x3 block around the subvoxel of x -- in FP32 in a frame
@@ -247,7 +290,7 @@ __device__ bool reproject_warp(const DScene& s, const d3* Pp, const d3* Rp, uint
   int gR[3];
   rel_subvoxel(s, c0, r0, zero, gR);
   if (lc.n < 0 || lc.label != label || lc.gR[0] != gR[0] || lc.gR[1] != gR[1] || lc.gR[2] != gR[2])
-    fill_cache(s, lc, gR, label, lane, bytes);
+    fill_cache(s, lc, sl, gR, label, lane, bytes);
   if (lc.n > RCAP || lc.n == 0) return false;
   const float half = 0.5f * s.seg_len;
   float th = 0.f, f;

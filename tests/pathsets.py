@@ -72,3 +72,27 @@ def oracle_confirms(osc, sc, P, i, p, IGN_LABEL=1, IGN_ANY=2):
             IGN_ANY if int(P["type"][i][k]) == 1 else IGN_LABEL, int(P["label"][i][k]))
         vis = vis and osc.visible(nodes[k], nodes[k + 1], ma, la, mb, lb)
     return f_max, float(np.sqrt(max(g2, 0.0))), vis
+
+
+def confirm_alternates(G, bad, sc, p, max_bad):
+    """The paths of G that differ from the oracle's winner of their label sequence
+    (compare's `bad`) are alternate stationary points: at most max_bad of them, each
+    confirmed by the oracle as an exact path (oracle_confirms) and within 1e-4
+    relative length of the oracle's winner.  On the noisy cloud one coarse path's
+    gradient descent can settle on one of several stationary points, or cycle around
+    one until rho, and which candidate wins the shortest-path dedup can depend on
+    rounding."""
+    assert len(bad) <= max_bad, bad[:5]
+    if not bad:
+        return
+    import oracle
+    osc = oracle.Scene.from_scene(sc, p)
+    where = {}
+    for i in range(len(G["n"])):
+        n = int(G["n"][i])
+        where[(int(G["tx"][i]), int(G["rx"][i]), tuple(int(t) for t in G["type"][i][:n]),
+               tuple(int(l) for l in G["label"][i][:n]))] = i
+    for key, dp, dl in bad:
+        f_max, grad, vis = oracle_confirms(osc, sc, G, where[key], p)
+        assert f_max < 1e-4 and grad < p.delta and vis, (key, dp, dl, f_max, grad, vis)
+        assert dl < 1e-4, (key, dp, dl)

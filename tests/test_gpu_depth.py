@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 from tests.golden.make_room_noisy_1x16 import MAX_INT, OUT, workload
-from tests.pathsets import compare, oracle_confirms
+from tests.pathsets import compare, confirm_alternates, oracle_confirms
 
 # On the noisy cloud the gradient descent of one coarse path can settle on one of
 # several stationary points a few centimetres to decimetres apart, or cycle around
@@ -116,21 +116,4 @@ def test_noisy_room_1x16_full_depth_matches_oracle():
     cmp = compare(G, ref, atol_pts=1e-3, rtol_len=1e-6)
     assert cmp["only_gpu"] == [] and cmp["only_ref"] == [], cmp
     assert cmp["n_common"] == len(ref["n"])
-    assert len(cmp["bad"]) <= len(ref["n"]) // ALT_PER, cmp["bad"][:5]
-    _confirm_alternates(G, cmp["bad"], sc, p)
-
-
-def _confirm_alternates(G, bad, sc, p):
-    if not bad:
-        return
-    import oracle
-    osc = oracle.Scene.from_scene(sc, p)
-    where = {}
-    for i in range(len(G["n"])):
-        n = int(G["n"][i])
-        where[(int(G["tx"][i]), int(G["rx"][i]), tuple(int(t) for t in G["type"][i][:n]),
-               tuple(int(l) for l in G["label"][i][:n]))] = i
-    for key, dp, dl in bad:
-        f_max, grad, vis = oracle_confirms(osc, sc, G, where[key], p)
-        assert f_max < 1e-4 and grad < p.delta and vis, (key, dp, dl, f_max, grad, vis)
-        assert dl < 1e-4, (key, dp, dl)
+    confirm_alternates(G, cmp["bad"], sc, p, len(ref["n"]) // ALT_PER)

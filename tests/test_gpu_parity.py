@@ -6,7 +6,7 @@ import oracle
 from paper_2402_13747_b300 import config, scenes
 from tests import cases
 from tests.imagemethod import box_room_planes, corner_on_floor_mixed_path, image_paths
-from tests.pathsets import compare, keyed
+from tests.pathsets import compare, confirm_alternates, keyed
 
 pytestmark = pytest.mark.gpu
 
@@ -250,7 +250,9 @@ def test_memory_returns_after_release(ctx, room_tiny):
 
 
 def test_noisy_room_subset_matches_oracle(ctx):
-    """Noisy room with the box: 1 TX x 3 RX, <= 2 reflections + 1 diffraction."""
+    """Noisy room with the box: 1 TX x 3 RX, <= 2 reflections + 1 diffraction.  The same
+    (TX, RX, types, labels) set; every path within 1e-3 m and 1e-6 relative length but
+    for oracle-confirmed alternate stationary points (at most 1 %)."""
     full = scenes.room_noisy()
     sc = full.with_pairs(full.tx[:1], full.rx[:3])
     p = config.params_for(sc, max_refl=2, max_diff=1)
@@ -258,8 +260,8 @@ def test_noisy_room_subset_matches_oracle(ctx):
     _, _, e = oracle.run(sc, p)
     cmp = compare(G, e.paths(), atol_pts=1e-3, rtol_len=1e-6)
     assert cmp["n_ref"] > 20
-    assert cmp["jaccard"] >= 0.9, cmp
-    assert len(cmp["bad"]) <= 0.05 * cmp["n_common"], cmp
+    assert cmp["only_gpu"] == [] and cmp["only_ref"] == [], cmp
+    confirm_alternates(G, cmp["bad"], sc, p, max(1, cmp["n_common"] // 100))
 
 
 def test_noisy_room_subset_paper_launch(ctx):
@@ -272,8 +274,8 @@ def test_noisy_room_subset_paper_launch(ctx):
     _, c, e = oracle.run(sc, p)
     cmp = compare(G, e.paths(), atol_pts=1e-3, rtol_len=1e-6)
     assert cmp["n_ref"] > 20
-    assert cmp["jaccard"] >= 0.9, cmp
-    assert len(cmp["bad"]) <= 0.05 * cmp["n_common"], cmp
+    assert cmp["only_gpu"] == [] and cmp["only_ref"] == [], cmp
+    confirm_alternates(G, cmp["bad"], sc, p, max(1, cmp["n_common"] // 100))
     # initial interactions: every IE visible from the TX, on both sides
     assert abs(G["counts"]["n_coarse_raw"] - c.stats["n_before_kappa"]) <= 0.02 * c.stats["n_before_kappa"]
 

@@ -409,9 +409,13 @@ typedef struct {
   int32_t refine_split;     /* > 0: refine in two launches, the first stopping every path after this many
                                iterations and the second resuming the unfinished ones, costliest per
                                iteration first (0..65535; 0 or >= rho: one launch) */
+  int32_t refine_split_key; /* the second launch's order: 0 the cost per iteration so far; 1 the predicted
+                               remaining time (that cost x the iterations still needed at the gradient's
+                               rate of decrease over the second half of the first launch) */
 } nimbus_tuning;
 
-/* The context's launch configuration (defaults 256, 0, 1, 1, level_queue 0, refine_split 0). */
+/* The context's launch configuration (defaults 256, 0, 1, 1, level_queue 0, refine_split 0,
+ * refine_split_key 0). */
 NIMBUS_API int nimbus_get_tuning(nimbus_ctx* ctx, nimbus_tuning* out);
 
 /* Replace it.  A value out of range returns NIMBUS_ERR_ARG and changes nothing. */
@@ -420,9 +424,10 @@ NIMBUS_API int nimbus_set_tuning(nimbus_ctx* ctx, const nimbus_tuning* t);
 /* Autotuner.  Traces the given TX/RX set on `scene` once per level layout (blocks
  * of 128 or 256 threads x one launch per depth or one for all depths) and keeps the
  * fastest propagation time.  Then it refines that coarse set once per refinement
- * layout (4 or all resident blocks per SM x coarse order, most interactions first
- * or grazing rays first x one launch or two, the first stopping at 128 or 512
- * iterations) and keeps the fastest.  The result is stored in the context for the
+ * layout with all resident blocks per SM: one launch in coarse order, most
+ * interactions first or grazing rays first; and two launches, the first in coarse
+ * order or most interactions first and stopping at 64, 128 or 512 iterations, the
+ * second in either of its orders; it keeps the fastest.  The result is stored in the context for the
  * calls that follow and written to `out` (may be NULL).  Every layout gives the same
  * results; tune on the workload itself where its refinement ends on long paths (a
  * small sample is one tail whatever the layout).  Times are CUDA events on `stream`;

@@ -545,6 +545,7 @@ static void to_public(const nb::Tuning& t, nimbus_tuning* o) {
   o->refine_ms = t.refine_ms;
   o->level_queue = t.level_queue;
   o->refine_split = t.refine_split;
+  o->refine_split_key = t.refine_split_key;
 }
 
 int nimbus_get_tuning(nimbus_ctx* ctx, nimbus_tuning* out) {
@@ -557,7 +558,8 @@ int nimbus_set_tuning(nimbus_ctx* ctx, const nimbus_tuning* t) {
   if (!ctx) return NIMBUS_ERR_ARG;
   if (!t || !(t->level_block == 128 || t->level_block == 256) || t->refine_blocks < 0 || t->refine_blocks > 8 ||
       !(t->refine_order >= 0 && t->refine_order <= 2) || !(t->graph == 0 || t->graph == 1) ||
-      !(t->level_queue == 0 || t->level_queue == 1) || t->refine_split < 0 || t->refine_split > 65535) {
+      !(t->level_queue == 0 || t->level_queue == 1) || t->refine_split < 0 || t->refine_split > 65535 ||
+      !(t->refine_split_key == 0 || t->refine_split_key == 1)) {
     ctx->err = "set_tuning: value out of range";
     return NIMBUS_ERR_ARG;
   }
@@ -569,6 +571,7 @@ int nimbus_set_tuning(nimbus_ctx* ctx, const nimbus_tuning* t) {
   ctx->tune.refine_ms = t->refine_ms;
   ctx->tune.level_queue = t->level_queue;
   ctx->tune.refine_split = t->refine_split;
+  ctx->tune.refine_split_key = t->refine_split_key;
   return NIMBUS_OK;
 }
 
@@ -617,28 +620,36 @@ int nimbus_autotune(nimbus_ctx* ctx, nimbus_handle scene, const double* tx, int3
     return rc;
   }
   double best_rf = -1.0;
-  const int rblocks[2] = {4, 0}, orders[3] = {0, 1, 2}, splits[3] = {0, 128, 512};
-  for (int sl : splits)
-  for (int rb : rblocks)
-    for (int od : orders) {
-      if (rc != NIMBUS_OK) break;   // an error ends the search (reported below)
-      nb::Tuning t = best;
-      t.refine_blocks = rb;
-      t.refine_order = od;
-      t.refine_split = sl;
-      auto* P = new nb::PathsObj();
-      P->mem = &ctx->mem;
-      rc = nb::refine_paths(ctx->mem, S, C, rp, P, st, t);
-      const double ms = P->counts.ms_refine;
-      drop_obj(ctx, P, st);
-      if (rc != NIMBUS_OK) continue;
-      if (best_rf < 0.0 || ms < best_rf) {
-        best_rf = ms;
-        best.refine_blocks = rb;
-        best.refine_order = od;
-        best.refine_split = sl;
-      }
+  // refinement layouts (all resident blocks per SM: fewer has not won since the flat
+  // point list): one launch in each order, then two launches
+  struct RefLayout {
+    int order, split, key;
+  };
+  std::vector<RefLayout> layouts = {{0, 0, 0}, {1, 0, 0}, {2, 0, 0}};
+  for (int sl : {64, 128, 512})
+    for (int od : {0, 1})
+      for (int key : {0, 1}) layouts.push_back({od, sl, key});
+  for (const RefLayout& L : layouts) {
+    if (rc != NIMBUS_OK) break;   // an error ends the search (reported below)
+    nb::Tuning t = best;
+    t.refine_blocks = 0;
+    t.refine_order = L.order;
+    t.refine_split = L.split;
+    t.refine_split_key = L.key;
+    auto* P = new nb::PathsObj();
+    P->mem = &ctx->mem;
+    rc = nb::refine_paths(ctx->mem, S, C, rp, P, st, t);
+    const double ms = P->counts.ms_refine;
+    drop_obj(ctx, P, st);
+    if (rc != NIMBUS_OK) continue;
+    if (best_rf < 0.0 || ms < best_rf) {
+      best_rf = ms;
+      best.refine_blocks = 0;
+      best.refine_order = L.order;
+      best.refine_split = L.split;
+      best.refine_split_key = L.key;
     }
+  }
   drop_obj(ctx, C, st);
   if (rc != NIMBUS_OK) return rc;
   best.refine_ms = best_rf;

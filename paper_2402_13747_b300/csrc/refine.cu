@@ -353,9 +353,11 @@ struct WarpPath {
 
 // Two-phase refinement (a launch layout; results are the same bit for bit).  Phase 1
 // runs every path for at most `cap` iterations; a path still running then saves its
-// iterate and leaves.  Phase 2 resumes those paths, the costliest per iteration
-// first, so the long ones start at the beginning of a launch instead of wherever the
-// hand-out order put them.  A resumed path continues the same iteration sequence from
+// iterate and leaves.  Phase 2 resumes those paths, longest first by one of two
+// rankings: the cost per iteration so far, or the predicted remaining time (that cost
+// times the iterations still needed at the gradient's rate of decrease over the second
+// half of phase 1), so the long ones start at the beginning of a launch instead of
+// wherever the hand-out order put them.  A resumed path continues the same iteration sequence from
 // the same FP64 state; its label caches are refilled, and a cache's content is a
 // function of its key only.
 struct PathState {
@@ -369,9 +371,10 @@ struct PathState {
 struct RefineSplit {
   int phase;              // 0: one pass; 1: stop at cap; 2: resume the saved paths
   int cap;
+  int key;                // resume order: 0 cost per iteration, 1 predicted remaining time
   PathState* st;          // [n] by coarse index
   uint32_t* cont;         // phase 1: coarse indices of the saved paths; phase 2: in resume order
-  uint64_t* cont_key;     // phase 1: 0xffff minus the cost per iteration (ascending sort = costliest first)
+  uint64_t* cont_key;     // phase 1: 2^40 - 1 minus the predicted remaining time (ascending sort = longest first)
   unsigned* cont_n;
 };
 
@@ -449,6 +452,7 @@ __global__ void __launch_bounds__(128, REFINE_BLOCKS_PER_SM) k_refine(DScene s, 
     }
     const long long t_path = clock64();
     bool saved = false;
+    float g_half = 0.f;   // phase 1: the gradient norm half-way to the cap
     float gn = 0.f;
     for (; it <= rp.rho; ++it) {
       if (sp.phase == 1 && it == sp.cap) {
@@ -464,9 +468,18 @@ __global__ void __launch_bounds__(128, REFINE_BLOCKS_PER_SM) k_refine(DScene s, 
         if (lane == 0) {
           ps.it = it;
           const unsigned slot = atomicAdd(sp.cont_n, 1u);
-          const long long per_it = (clock64() - t_path) / max(1, sp.cap) / 64;
+          // predicted remaining time: cost per iteration so far times the iterations
+          // still needed at the gradient's rate of decrease over the second half of
+          // phase 1 (rho - it when it did not decrease)
+          const double per_it = (double)(clock64() - t_path) / (double)max(1, sp.cap);
+          double rem = sp.key == 0 ? 1.0 : (double)(rp.rho - it);
+          if (sp.key == 1 && g_half > 0.f && gn > 0.f && gn < g_half) {
+            const double rate = log((double)gn / (double)g_half) / (double)max(1, it - sp.cap / 2);
+            rem = fmin(rem, fmax(1.0, log(rp.grad_stop / (double)gn) / rate));
+          }
+          const double cost = fmin(per_it * rem / 64.0, (double)((1ull << 40) - 1));
           sp.cont[slot] = (uint32_t)i;
-          sp.cont_key[slot] = 0xffffull - (uint64_t)min(per_it, 0xffffll);
+          sp.cont_key[slot] = (1ull << 40) - 1 - (uint64_t)cost;
         }
         saved = true;
         break;
@@ -514,6 +527,7 @@ __global__ void __launch_bounds__(128, REFINE_BLOCKS_PER_SM) k_refine(DScene s, 
         converged = true;
         break;
       }
+      if (sp.phase == 1 && it == sp.cap / 2) g_half = gn;
       if (it == rp.rho) break;
       bool off = false;
       if (node) W.In[lane] = W.I[lane];
@@ -796,7 +810,7 @@ __global__ void k_fresnel(const ExactRec* ex, const uint64_t* keys, const uint32
 __global__ void k_cont_fill(uint64_t* keys, uint32_t* vals, const unsigned* cnt, int64_t n) {
   const int64_t m = *cnt;
   for (int64_t i = m + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    keys[i] = 0x10000ull;
+    keys[i] = 1ull << 40;
     vals[i] = 0u;
   }
 }
@@ -861,8 +875,8 @@ int refine_paths(Mem& mem, SceneObj* S, CoarseObj* C, const nimbus_refine_params
     NB_TRY(sc.get(&cnt, 1));
     NB_TRY(sc.get(&ck_alt, n));
     NB_TRY(sc.get(&cv_alt, n));
-    sp1 = RefineSplit{1, tn.refine_split, st_buf, cont, ckey, cnt};
-    sp2 = RefineSplit{2, tn.refine_split, st_buf, cont, ckey, cnt};
+    sp1 = RefineSplit{1, tn.refine_split, tn.refine_split_key, st_buf, cont, ckey, cnt};
+    sp2 = RefineSplit{2, tn.refine_split, tn.refine_split_key, st_buf, cont, ckey, cnt};
   }
   const int n_cache = std::max(1, std::min(C->max_refl, NB_MAXI));
   const size_t dyn = sizeof(LabelCache) * 4 * n_cache;
@@ -889,7 +903,7 @@ int refine_paths(Mem& mem, SceneObj* S, CoarseObj* C, const nimbus_refine_params
   NB_TRY(sc.get(&pos, n));
   NB_TRY(sc.get(&nw, 1));
   const size_t arena_bytes = (tn.refine_order ? radix_arena_bytes(n, 8) : 0) + scan_arena_bytes(n, true) +
-                             (split ? radix_arena_bytes(n, 17) : 0);
+                             (split ? radix_arena_bytes(n, 41) : 0);
   char* arena;
   NB_TRY(sc.get(&arena, std::max<size_t>(1, arena_bytes)));
   const unsigned G2 = std::min<unsigned>(grid_for(n, 256), pgrid(256));
@@ -918,7 +932,7 @@ int refine_paths(Mem& mem, SceneObj* S, CoarseObj* C, const nimbus_refine_params
       NB_LAUNCHED(err);
       k_cont_fill<<<grid_for(n, 256), 256, 0, q>>>(sp1.cont_key, sp1.cont, sp1.cont_n, n);
       NB_LAUNCHED(err);
-      NB_TRY(radix_sort(ws, sp1.cont_key, sp1.cont, ck_alt, cv_alt, n, 17));
+      NB_TRY(radix_sort(ws, sp1.cont_key, sp1.cont, ck_alt, cv_alt, n, 41));
       NB_CUDA(err, cudaMemsetAsync(rbytes + 1, 0, sizeof(unsigned long long), q));
       k_refine<<<G, 128, dyn, q>>>(S->d, rp, cv, C->txd, C->rxd, P->all, rbytes, rbytes + 1, ovals, n_cache, sp2);
       NB_LAUNCHED(err);

@@ -415,22 +415,26 @@ def test_autotune_keeps_results(ctx):
     assert t["level_block"] in (128, 256)
     assert t["refine_blocks"] in (0, 4) and t["refine_order"] in (0, 1, 2) and t["refine_ms"] > 0
     assert t["level_queue"] in (0, 1)
-    assert t["refine_split"] in (0, 128, 512)
+    assert t["refine_split"] in (0, 64, 128, 512) and t["refine_split_key"] in (0, 1)
     for layout in (dict(level_block=128, refine_blocks=3, refine_order=0, level_queue=1, refine_split=0),
                    dict(level_block=256, refine_blocks=0, refine_order=2, level_queue=0, refine_split=0),
                    dict(level_block=256, refine_blocks=0, refine_order=1, level_queue=0, refine_split=5),
-                   dict(level_block=256, refine_blocks=2, refine_order=2, level_queue=0, refine_split=64), t):
-        ctx.set_tuning(**{k: layout[k] for k in ("level_block", "refine_blocks", "refine_order", "level_queue",
-                                                  "refine_split")})
+                   dict(level_block=256, refine_blocks=2, refine_order=2, level_queue=0, refine_split=64),
+                   dict(level_block=256, refine_blocks=0, refine_order=0, level_queue=0, refine_split=7,
+                        refine_split_key=1), t):
+        ctx.set_tuning(**{k: layout.get(k, 0) for k in ("level_block", "refine_blocks", "refine_order", "level_queue",
+                                                        "refine_split", "refine_split_key")})
         G = ctx.run(sc, p)
         assert len(G["n"]) == len(base["n"])
         for k in ("tx", "rx", "n", "type", "label", "pts", "length"):
             np.testing.assert_array_equal(G[k], base[k])
-    ctx.set_tuning(level_block=256, refine_blocks=0, refine_order=1, level_queue=0, refine_split=0)
+    ctx.set_tuning(level_block=256, refine_blocks=0, refine_order=1, level_queue=0, refine_split=0, refine_split_key=0)
     with pytest.raises(Exception):
         ctx.set_tuning(level_block=96)
     with pytest.raises(Exception):
         ctx.set_tuning(refine_split=-1)
+    with pytest.raises(Exception):
+        ctx.set_tuning(refine_split_key=2)
 
 
 def _coarse_rows(cq):

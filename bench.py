@@ -84,7 +84,13 @@ def dist_env():
 # (dram__bytes_read.sum + dram__bytes_write.sum, one-pass ncu capture), valid only for
 # the device code it was taken on: the hash covers that code -- refine.cu up to its
 # host launcher, and the two headers whole -- and a changed kernel reports null.
-REFINE_TRAFFIC = {"bytes": 97088256 + 145262848, "sources_sha256": "ae68539a93fb449df882e5d777c29402e0d9b7e9e9372f4bbadd67b105f34f18"}
+# DRAM bytes (read + write) of the refinement's launches in one timed step of the
+# default workload, from one-pass ncu captures, per refinement layout
+# (refine_order, refine_split, refine_split_key); reported only while the device
+# code's hash matches the capture
+REFINE_TRAFFIC = {"sources_sha256": "19b28f209c64a3a761daccf82bef14a15f07e05a2e28ca22ba1b533e3edf6047",
+                  "layouts": {"order=1,split=0,key=0": 97264640 + 145813248,
+                              "order=1,split=64,key=1": 181499904 + 215844096 + 335070464 + 90637568}}
 KERNEL_SOURCES = (("paper_2402_13747_b300/csrc/refine.cu", b"\nint refine_paths("),
                   ("paper_2402_13747_b300/csrc/warp_geom.cuh", None),
                   ("paper_2402_13747_b300/csrc/nimbus_internal.cuh", None))
@@ -342,7 +348,12 @@ def region_update_timing(ctx, reps: int = 3):
     return out
 
 
-def roofline_of(c0, pk):
+def refine_layout_key(tuning: dict) -> str:
+    return "order={refine_order},split={refine_split},key={refine_split_key}".format(
+        **{k: int(tuning.get(k, 0)) for k in ("refine_order", "refine_split", "refine_split_key")})
+
+
+def roofline_of(c0, pk, tuning=None):
     """Dominant stage and its roofline: algorithmic bytes / CUDA-event time against the
     measured HBM copy peak.  Eq. 1 reads each point's position and normal (6 FP32 =
     24 B); the same fraction at 16 B per point is printed beside it."""
@@ -354,8 +365,8 @@ def roofline_of(c0, pk):
     peak = pk["hbm_gbs"] if pk else 6400.0
     achieved = dbytes / (dms * 1e-3) / 1e9 if dms > 0 else 0.0
     traffic = None
-    if dom == "refine" and REFINE_TRAFFIC["bytes"] and REFINE_TRAFFIC["sources_sha256"] == kernel_sources_sha256():
-        traffic = REFINE_TRAFFIC["bytes"]
+    if dom == "refine" and REFINE_TRAFFIC["sources_sha256"] == kernel_sources_sha256():
+        traffic = REFINE_TRAFFIC["layouts"].get(refine_layout_key(tuning or {}))
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic, "kernel": dom, "kernel_ms": dms, "algorithmic_bytes": dbytes,
             "bytes_per_point": 24, "peak_source": "measured" if pk else "fallback",
@@ -385,6 +396,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-secondary", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--layout", default="", help="launch layout to set instead of tuning, e.g. "
+                    "'level_queue=1,refine_split=64,refine_split_key=1,refine_order=0'")
     ap.add_argument("--pairs", default="", help="TxR: only the first T TX and R RX (small profiling cases)")
     ap.add_argument("--rx-every", type=int, default=1, help="K: every K-th RX only (profiling cases spread over the RXs)")
     args = ap.parse_args()
@@ -443,7 +456,9 @@ def main():
     # layouts by noise (every 32nd RX of the indoor scan chose one launch, 1.60 s on the
     # full workload, where two phases take 1.34 s)
     tuning = ctx.get_tuning()
-    if not args.no_tune:
+    if args.layout:
+        tuning = ctx.set_tuning(**{k: int(v) for k, v in (kv.split("=") for kv in args.layout.split(","))})
+    elif not args.no_tune:
         s0 = ctx.voxelize(d_xyz, d_nrm, d_lab, d_mat, d_edges, d_elab, params=p)
         tuning = ctx.autotune(s0, my.tx, my.rx, p)
         ctx.release(s0)
@@ -522,7 +537,7 @@ def main():
     out = None
     if rank == 0:
         pk = peaks()
-        roof = roofline_of(c0, pk)
+        roof = roofline_of(c0, pk, tuning)
 
         # plain form: one trace + refine per TX/RX pair on the resident scene, timed on
         # the first pairs of the workload (rates; the batched form runs all pairs)

@@ -392,7 +392,9 @@ NIMBUS_API int nimbus_segment(nimbus_ctx* ctx, const nimbus_cloud* cloud, const 
  * they compute.  Every setting gives bit-identical results; only the time changes.
  */
 typedef struct {
-  int32_t level_block;      /* threads per block of the propagation levels: 128 or 256 */
+  int32_t level_block;      /* threads per block of the propagation levels: 128, 256 or 512 (with one launch
+                               per depth, a warp whose cones are done walks visibility rays of the cones
+                               still running in its block) */
   int32_t refine_blocks;    /* 4-warp refinement blocks per SM: 1..8 (at most as many as fit), 0 = as many as fit */
   int32_t refine_order;     /* 1: refine the paths with the most interactions first; 2: first the paths whose
                                re-projection rays graze their surfaces at the start (smallest |n . d|), then by
@@ -414,7 +416,7 @@ typedef struct {
                                rate of decrease over the second half of the first launch) */
 } nimbus_tuning;
 
-/* The context's launch configuration (defaults 256, 0, 1, 1, level_queue 0, refine_split 0,
+/* The context's launch configuration (defaults 512, 0, 1, 1, level_queue 0, refine_split 0,
  * refine_split_key 0). */
 NIMBUS_API int nimbus_get_tuning(nimbus_ctx* ctx, nimbus_tuning* out);
 
@@ -422,7 +424,7 @@ NIMBUS_API int nimbus_get_tuning(nimbus_ctx* ctx, nimbus_tuning* out);
 NIMBUS_API int nimbus_set_tuning(nimbus_ctx* ctx, const nimbus_tuning* t);
 
 /* Autotuner.  Traces the given TX/RX set on `scene` once per level layout (blocks
- * of 128 or 256 threads x one launch per depth or one for all depths) and keeps the
+ * of 128, 256 or 512 threads x one launch per depth or one for all depths) and keeps the
  * fastest propagation time.  Then it refines that coarse set once per refinement
  * layout with all resident blocks per SM: one launch in coarse order, most
  * interactions first or grazing rays first; and two launches, the first in coarse

@@ -556,7 +556,8 @@ int nimbus_get_tuning(nimbus_ctx* ctx, nimbus_tuning* out) {
 
 int nimbus_set_tuning(nimbus_ctx* ctx, const nimbus_tuning* t) {
   if (!ctx) return NIMBUS_ERR_ARG;
-  if (!t || !(t->level_block == 128 || t->level_block == 256) || t->refine_blocks < 0 || t->refine_blocks > 8 ||
+  if (!t || !(t->level_block == 128 || t->level_block == 256 || t->level_block == 512) || t->refine_blocks < 0 ||
+      t->refine_blocks > 8 ||
       !(t->refine_order >= 0 && t->refine_order <= 2) || !(t->graph == 0 || t->graph == 1) ||
       !(t->level_queue == 0 || t->level_queue == 1) || t->refine_split < 0 || t->refine_split > 65535 ||
       !(t->refine_split_key == 0 || t->refine_split_key == 1)) {
@@ -590,7 +591,7 @@ int nimbus_autotune(nimbus_ctx* ctx, nimbus_handle scene, const double* tx, int3
   nb::Tuning best = ctx->tune;
   // level layouts: propagation time of the sample's levels
   double best_lv = -1.0;
-  const int blocks[2] = {256, 128};
+  const int blocks[3] = {256, 128, 512};
   for (int lq = 0; lq < 2; ++lq)
   for (int bl : blocks) {
     nb::Tuning t = best;

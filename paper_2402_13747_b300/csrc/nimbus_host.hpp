@@ -334,7 +334,7 @@ struct PathsObj : Obj {
 
 // Launch layout of the propagation levels and the refinement (result-neutral).
 struct Tuning {
-  int level_block = 256;
+  int level_block = 512;
   int refine_blocks = 0;   // 0: as many as fit
   int refine_order = 1;
   int graph = 1;           // issue each host-free stretch of a call as one CUDA graph

@@ -51,6 +51,7 @@ struct DTrace {
   const int32_t* tx_max_int; // [n_tx] depth to which each TX's tree is expanded, or null
   unsigned long long* stats;
   uint32_t* overflow;        // [0] largest node slot requested, [1] coarse slot requested
+  uint32_t* err;             // propagation: nonzero once a bounded wait gave up
 };
 
 // Nodes of one level, structure of arrays (reflection and diffraction apart).
@@ -401,6 +402,146 @@ struct LevelCone {
   bool can_child, test_edges;
 };
 
+// The candidates of one evaluation of a cone (IEs and RXs in its accepted voxels)
+// wait in the warp's slot of its block's board, in the order the cone met them, so
+// that the warps of the block that have no cone left can walk some of their
+// visibility rays: the rays of one evaluation are independent, and a cone that meets
+// hundreds of occluded candidates otherwise keeps one warp busy for tens of
+// milliseconds after the rest of its launch has finished.  A ray is walked by one
+// whole warp whichever warp takes it, so every decision is the same.
+//   word: generation << 24 | entries << 12 | entries taken; a warp takes entry k
+//   with a compare-and-swap of the word (a stale generation fails).
+// At the last level a point IE only decides whether the cone stops, and the walk in
+// order skips the point IEs after the first visible one.  Here an entry is skipped
+// once a visible point IE with a smaller index is known (first_vis); the owner then
+// counts the rays and bytes of exactly the entries the walk in order tests, and no
+// entry before the first visible one can have been skipped.
+#ifndef HELP_CAP
+#define HELP_CAP 64
+#endif
+constexpr uint32_t CAND_RX = 2;
+struct HelpSlot {
+  unsigned word;
+  unsigned done;        // entries walked or skipped
+  unsigned first_vis;   // smallest index (within the evaluation) of a visible point IE
+  unsigned qbase;       // index of entry 0 within the evaluation
+  float4 h0;            // cone apex, origin label bits
+  uint4 h1;             // origin mode, tx | nr << 16 | nd << 20 | depth << 24, self_ref, can_child
+  float4 a[HELP_CAP];   // target, IE or RX index bits
+  uint2 b[HELP_CAP];    // kind (IE_POINT, IE_EDGE, CAND_RX), label or miss bits
+  unsigned r[HELP_CAP]; // bit 31: walked; the walk's bytes
+};
+
+// Walk entry t of slot H (any warp of the block, all lanes).
+__device__ __forceinline__ void help_walk(const DScene& s, const DTrace& tr, NodeLevel& next, CoarseBuf& cb,
+                                          HelpSlot& H, unsigned t, int lane) {
+  const float4 a = H.a[t];
+  const uint2 b = H.b[t];
+  const float4 h0 = H.h0;
+  const uint4 h1 = H.h1;
+  const unsigned q = H.qbase + t;
+  const bool can_child = h1.w != 0;
+  unsigned r = 0;
+  if (!(b.x == IE_POINT && !can_child && *(volatile unsigned*)&H.first_vis < q)) {
+    unsigned long long by = 0;
+    const float3 apex = xyz(h0), tgt = xyz(a);
+    const Endpoint origin{(int)h1.x, __float_as_uint(h0.w)};
+    const Endpoint eb = b.x == CAND_RX ? Endpoint{IGN_NONE, NB_NONE_LABEL}
+                                       : Endpoint{b.x == IE_EDGE ? IGN_ANY : IGN_LABEL, b.y};
+    const bool v = visible_warp(s, apex, tgt, origin, eb, lane, by);
+    r = (1u << 31) | min(__reduce_add_sync(FULL, (unsigned)by), 0x7fffffffu);
+    if (v && lane == 0) {
+      const uint32_t m = h1.y, tx = m & 0xffffu, nr = (m >> 16) & 0xfu, nd = (m >> 20) & 0xfu, dep = (m >> 24) & 0xfu;
+      if (b.x == CAND_RX) {
+        emit_coarse(tr, cb, tx, __float_as_uint(a.w), h1.z, dep, __uint_as_float(b.y));
+      } else {
+        if (can_child) emit_child(tr, next, __float_as_uint(a.w), tgt, apex, b.x, tx, nr, nd, dep, h1.z);
+        if (b.x == IE_POINT) atomicMin(&H.first_vis, q);
+      }
+    }
+  }
+  if (lane == 0) {
+    H.r[t] = r;
+    __threadfence_block();
+    atomicAdd(&H.done, 1u);
+  }
+  __syncwarp();
+}
+
+// Take the next entry of slot H: lane 0 claims it, every lane gets its index, or
+// 0xffffffff when every entry is taken.
+__device__ __forceinline__ unsigned help_take(HelpSlot& H, int lane) {
+  unsigned tk = 0xffffffffu;
+  if (lane == 0) {
+    unsigned w = *(volatile unsigned*)&H.word;
+    while (((w >> 12) & 0xfffu) > (w & 0xfffu)) {
+      const unsigned o = atomicCAS(&H.word, w, w + 1);
+      if (o == w) {
+        tk = w & 0xfffu;
+        break;
+      }
+      w = o;
+    }
+  }
+  tk = __shfl_sync(FULL, tk, 0);
+  __syncwarp();
+  return tk;
+}
+
+// The owner's side: publish the hn entries collected, walk them together with any
+// idle warps of the block, wait until all are done, close the slot, and count the
+// rays and bytes the walk in order would have.  The slot keeps, across the batches
+// of one evaluation, the first visible point IE so far (first_vis) and the entries
+// already walked (qbase); the owner resets both when an evaluation starts.
+__device__ __forceinline__ void help_flush(const DScene& s, const DTrace& tr, NodeLevel& next, CoarseBuf& cb,
+                                           HelpSlot& H, int& hn, int lane, unsigned long long& bytes, uint32_t& vis) {
+  if (hn == 0) return;
+  // the generation lives in the slot's word; only its owner changes it
+  const unsigned gen = *(volatile unsigned*)&H.word >> 24;
+  if (lane == 0) {
+    H.done = 0;
+    __threadfence_block();
+    atomicExch(&H.word, (gen << 24) | ((unsigned)hn << 12));
+  }
+  __syncwarp();
+  for (;;) {
+    const unsigned tk = help_take(H, lane);
+    if (tk == 0xffffffffu) break;
+    help_walk(s, tr, next, cb, H, tk, lane);
+  }
+  if (lane == 0) {
+    // entries taken by other warps: each is one visibility ray, at most milliseconds
+    const long long t0 = clock64();
+    while (*(volatile unsigned*)&H.done < (unsigned)hn) {
+      if (clock64() - t0 > 4000000000ll) {
+        atomicExch(tr.err, 3u);
+        break;
+      }
+      __nanosleep(32);
+    }
+    __threadfence_block();
+    atomicExch(&H.word, ((gen + 1) & 0xffu) << 24);
+  }
+  __syncwarp();
+  const unsigned Fn = *(volatile unsigned*)&H.first_vis, qn = H.qbase;
+  const bool can_child = H.h1.w != 0;
+  for (int t0 = 0; t0 < hn; t0 += 32) {
+    const int t = t0 + lane;
+    bool counted = false;
+    if (t < hn) {
+      const unsigned r = H.r[t];
+      counted = (r >> 31) && (can_child || H.b[t].x != IE_POINT || qn + (unsigned)t <= Fn);
+      if (counted) bytes += r & 0x7fffffffu;
+    }
+    const unsigned cm = __ballot_sync(FULL, counted);
+    if (lane == 0) vis += __popc(cm);
+  }
+  __syncwarp();
+  if (lane == 0) H.qbase = qn + (unsigned)hn;
+  hn = 0;
+  __syncwarp();
+}
+
 // Voxel cone tracing of one propagation cone by a whole warp (Section 2.2.4).  The
 // walk along the axis is the same on every lane.  At an evaluation lane l < 27
 // tests neighbour voxel l (already-evaluated voxels skipped, voxel sphere vs cone);
@@ -412,8 +553,16 @@ struct LevelCone {
 // level) the remaining point IEs of that evaluation are not tested: they can only
 // confirm the stop.
 __device__ void march_cone_warp(const DScene& s, const DTrace& tr, const ConeD& c, const LevelCone& lc,
-                                NodeLevel& next, CoarseBuf& cb, int lane, unsigned long long& bytes,
+                                NodeLevel& next, CoarseBuf& cb, HelpSlot& H, int lane, unsigned long long& bytes,
                                 uint32_t& evals, uint32_t& vis) {
+  if (lane == 0) {
+    // no entry of this slot is out (the last batch was waited for): the header is free
+    H.h0 = make_float4(c.apex.x, c.apex.y, c.apex.z, __uint_as_float(c.origin.label));
+    H.h1 = make_uint4((unsigned)c.origin.mode, lc.tx | (lc.nr << 16) | (lc.nd << 20) | (lc.depth << 24), lc.self_ref,
+                      lc.can_child ? 1u : 0u);
+  }
+  __syncwarp();
+  const unsigned lt = (1u << lane) - 1u;
   Walk w;
   walk_init(s, c.apex, c.axis, w);
   int last[3] = {0, 0, 0}, anchor[3] = {0, 0, 0};
@@ -448,68 +597,79 @@ __device__ void march_cone_warp(const DScene& s, const DTrace& tr, const ConeD& 
                  cone_sphere(c.apex, c.axis, c.sin_a, c.cos_a, voxel_center(s, u0, u1, u2), s.r_vox);
           }
         }
-        bool stop = false;
-        unsigned vm = __ballot_sync(FULL, ok && cell.y > 0);
-        while (vm) {
-          const int src = __ffs(vm) - 1;
-          vm &= vm - 1;
-          const uint32_t base = __shfl_sync(FULL, cell.x, src), cnt = __shfl_sync(FULL, cell.y, src);
-          for (uint32_t k0 = 0; k0 < cnt; k0 += 32) {
+        // Collect the evaluation's candidates in the order the walk in order meets them
+        // (IE voxels by lane, their IEs in chunks of 32, then the RX voxels' runs)
+        // until the slot is full, walk that batch, and go on from where collecting
+        // stopped (the chunk that did not fit is screened again; its bytes count once).
+        int hn = 0;                  // entries collected and not yet walked
+        if (lane == 0) {
+          H.first_vis = 0xffffffffu;
+          H.qbase = 0;
+        }
+        unsigned vm = __ballot_sync(FULL, ok && cell.y > 0);   // IE voxels left
+        unsigned rm = __ballot_sync(FULL, ok && has_rx);       // RX voxels left (never stop the cone)
+        uint32_t k0 = 0;             // next IE chunk of voxel ffs(vm)
+        int qb = -1;                 // next RX chunk of voxel ffs(rm); -1 before its first
+        for (;;) {
+          bool full = false;
+          while (vm) {
+            const int src = __ffs(vm) - 1;
+            const uint32_t base = __shfl_sync(FULL, cell.x, src), cnt = __shfl_sync(FULL, cell.y, src);
+            if (k0 >= cnt) {
+              vm &= vm - 1;
+              k0 = 0;
+              continue;
+            }
             const uint32_t k = k0 + lane, id = base + k;
             bool cand = false;
             uint32_t kind = IE_POINT, lbl = 0;
             float3 rp = f3(0.f, 0.f, 0.f);
+            unsigned by = 0;
             if (k < cnt) {
               const IERec* r = &s.ies[id];
               const float4 nm = __ldg(&r->nrm_meta), sc = __ldg(&r->sc_pc);
-              bytes += 32;
+              by += 32;
               kind = __float_as_uint(nm.w) & 1u;
               if ((kind == IE_POINT || lc.test_edges) && cone_sphere(c.apex, c.axis, c.sin_a, c.cos_a, xyz(sc), s.r_sub)) {
                 const float4 q = __ldg(&r->rp_lab);
-                bytes += 16;
+                by += 16;
                 rp = xyz(q);
                 lbl = __float_as_uint(q.w);
                 cand = planes_ok(c, rp, tr.sep_eps);
               }
             }
-            unsigned cm = __ballot_sync(FULL, cand);
-            while (cm) {
-              const int j = __ffs(cm) - 1;
-              cm &= cm - 1;
-              const uint32_t cid = __shfl_sync(FULL, id, j), ckind = __shfl_sync(FULL, kind, j);
-              const uint32_t clab = __shfl_sync(FULL, lbl, j);
-              const float3 crp = f3(__shfl_sync(FULL, rp.x, j), __shfl_sync(FULL, rp.y, j), __shfl_sync(FULL, rp.z, j));
-              if (ckind == IE_POINT && stop && !lc.can_child) continue;
-              if (lane == 0) ++vis;
-              const Endpoint eb{ckind == IE_EDGE ? IGN_ANY : IGN_LABEL, clab};
-              if (!visible_warp(s, c.apex, crp, c.origin, eb, lane, bytes)) continue;
-              if (lc.can_child && lane == 0)
-                emit_child(tr, next, cid, crp, c.apex, ckind, lc.tx, lc.nr, lc.nd, lc.depth, lc.self_ref);
-              if (ckind == IE_POINT) stop = true;
+            const unsigned cm = __ballot_sync(FULL, cand);
+            if (hn + __popc(cm) > HELP_CAP) {
+              full = true;
+              break;
             }
+            if (cand) {
+              const int k2 = hn + __popc(cm & lt);
+              H.a[k2] = make_float4(rp.x, rp.y, rp.z, __uint_as_float(id));
+              H.b[k2] = make_uint2(kind, lbl);
+            }
+            hn += __popc(cm);
+            bytes += by;
+            k0 += 32;
           }
-        }
-        // RXs in the accepted voxels (never stop the cone)
-        unsigned rm = __ballot_sync(FULL, ok && has_rx);
-        while (rm) {
-          const int src = __ffs(rm) - 1;
-          rm &= rm - 1;
-          const long long cus = __shfl_sync(FULL, cu, src);
-          const int q0 = rx_lower_bound(tr, (uint64_t)cus << 32);
-          for (int qb = q0;; qb += 32) {
+          while (!full && !vm && rm) {
+            const int src = __ffs(rm) - 1;
+            const long long cus = __shfl_sync(FULL, cu, src);
+            if (qb < 0) qb = rx_lower_bound(tr, (uint64_t)cus << 32);
             const int q = qb + lane;
             bool in = false, cand = false;
             int rj = 0;
             float3 pos = f3(0.f, 0.f, 0.f);
             float miss = 0.f;
+            unsigned by = 0;
             if (q < tr.n_rx_sorted) {
               const uint64_t e = tr.rx_sorted[q];
-              bytes += 8;
+              by += 8;
               in = (long long)(e >> 32) == cus;
               if (in) {
                 rj = (int)(e & 0xffffffffu);
                 pos = xyz(__ldg(&tr.rx[rj]));
-                bytes += 16;
+                by += 16;
                 cand = cone_sphere(c.apex, c.axis, c.sin_a, c.cos_a, pos, s.r_sub) && planes_ok(c, pos, tr.sep_eps) &&
                        !(tr.rx_owner && tr.rx_owner[rj] >= 0 && (uint32_t)tr.rx_owner[rj] != lc.tx) &&
                        !(tr.rx_max_int && tr.rx_max_int[rj] >= 0 && (int)lc.depth > tr.rx_max_int[rj]);
@@ -520,20 +680,30 @@ __device__ void march_cone_warp(const DScene& s, const DTrace& tr, const ConeD& 
               }
             }
             const unsigned inm = __ballot_sync(FULL, in);
-            unsigned cm = __ballot_sync(FULL, cand);
-            while (cm) {
-              const int j = __ffs(cm) - 1;
-              cm &= cm - 1;
-              const int crj = __shfl_sync(FULL, rj, j);
-              const float cmiss = __shfl_sync(FULL, miss, j);
-              const float3 cpos = f3(__shfl_sync(FULL, pos.x, j), __shfl_sync(FULL, pos.y, j), __shfl_sync(FULL, pos.z, j));
-              if (lane == 0) ++vis;
-              if (visible_warp(s, c.apex, cpos, c.origin, Endpoint{IGN_NONE, NB_NONE_LABEL}, lane, bytes) && lane == 0)
-                emit_coarse(tr, cb, lc.tx, (uint32_t)crj, lc.self_ref, lc.depth, cmiss);
+            const unsigned cm = __ballot_sync(FULL, cand);
+            if (hn + __popc(cm) > HELP_CAP) {
+              full = true;
+              break;
             }
-            if (inm != FULL) break;   // the voxel's RX run ended in this chunk
+            if (cand) {
+              const int k2 = hn + __popc(cm & lt);
+              H.a[k2] = make_float4(pos.x, pos.y, pos.z, __uint_as_float((uint32_t)rj));
+              H.b[k2] = make_uint2(CAND_RX, __float_as_uint(miss));
+            }
+            hn += __popc(cm);
+            bytes += by;
+            if (inm != FULL) {   // the voxel's RX run ended in this chunk
+              rm &= rm - 1;
+              qb = -1;
+            } else {
+              qb += 32;
+            }
           }
+          help_flush(s, tr, next, cb, H, hn, lane, bytes, vis);
+          if (!full) break;
         }
+        // a point IE of this evaluation was visible
+        const bool stop = *(volatile unsigned*)&H.first_vis != 0xffffffffu;
         have_last = true;
         last[0] = w.v[0]; last[1] = w.v[1]; last[2] = w.v[2];
         if (stop) break;
@@ -546,7 +716,7 @@ __device__ void march_cone_warp(const DScene& s, const DTrace& tr, const ConeD& 
 // One propagation cone of level `cur`: the reflected cone of node idx (refl) or cone
 // j of the Keller fan of diffraction node idx.
 __device__ __forceinline__ void level_cone(const DScene& s, const DTrace& tr, const NodeLevel& cur, NodeLevel& next,
-                                           CoarseBuf& cb, bool refl, uint32_t idx, int j, int lane,
+                                           CoarseBuf& cb, HelpSlot& H, bool refl, uint32_t idx, int j, int lane,
                                            unsigned long long& bytes, uint32_t& cones, uint32_t& evals,
                                            uint32_t& vis) {
   const float4 a = refl ? cur.ra[idx] : cur.da[idx];
@@ -605,20 +775,32 @@ __device__ __forceinline__ void level_cone(const DScene& s, const DTrace& tr, co
   lc.can_child = (int)lc.depth < tr.max_int && (!tr.tx_max_int || (int)lc.depth < tr.tx_max_int[lc.tx]);
   lc.test_edges = lc.can_child && (int)lc.nd < tr.max_diff;
   if (lane == 0) ++cones;
-  march_cone_warp(s, tr, c, lc, next, cb, lane, bytes, evals, vis);
+  march_cone_warp(s, tr, c, lc, next, cb, H, lane, bytes, evals, vis);
 }
 
 // One propagation level: the reflected cones and Keller-fan cones of every node,
-// one warp per cone, cones handed out by a counter (their costs differ widely).
+// one warp per cone, cones handed out by a counter (their costs differ widely).  A
+// warp with no cone left walks visibility rays of its block's running cones (the
+// board above) until every warp of the block has finished.
+// Blocks of 128, 256 or 512 threads, all at 128 registers a thread (16 warps per SM);
+// the board (one slot per warp) is the launch's dynamic shared memory.
 #ifndef LEVEL_MAX_THREADS
-#define LEVEL_MAX_THREADS 256
+#define LEVEL_MAX_THREADS 512
 #endif
 #ifndef LEVEL_MIN_BLOCKS
-#define LEVEL_MIN_BLOCKS 2
+#define LEVEL_MIN_BLOCKS 1
 #endif
 __global__ void __launch_bounds__(LEVEL_MAX_THREADS, LEVEL_MIN_BLOCKS) k_level(DScene s, DTrace tr, NodeLevel cur, NodeLevel next, CoarseBuf cb,
                                                unsigned long long* next_task) {
-  const int lane = threadIdx.x & 31;
+  extern __shared__ HelpSlot board[];
+  __shared__ unsigned s_active;   // warps of the block still taking cones
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (lane == 0) {
+    board[wib].word = 0;
+    board[wib].done = 0;
+  }
+  if (threadIdx.x == 0) s_active = (unsigned)nw;
+  __syncthreads();
   const uint32_t n_r = min(cur.cnt[0], cur.cap_r), n_d = min(cur.cnt[1], cur.cap_d);
   const int64_t total = (int64_t)n_r + (int64_t)n_d * tr.M;
   unsigned long long bytes = 0;
@@ -631,9 +813,40 @@ __global__ void __launch_bounds__(LEVEL_MAX_THREADS, LEVEL_MIN_BLOCKS) k_level(D
     const bool refl = task < n_r;
     const uint32_t idx = refl ? (uint32_t)task : (uint32_t)((task - n_r) / tr.M);
     const int j = refl ? 0 : (int)((task - n_r) % tr.M);
-    level_cone(s, tr, cur, next, cb, refl, idx, j, lane, bytes, cones, evals, vis);
+    level_cone(s, tr, cur, next, cb, board[wib], refl, idx, j, lane, bytes, cones, evals, vis);
   }
   add_stats(tr, cones, vis, bytes, evals);
+  if (lane == 0) atomicSub(&s_active, 1u);
+  // help: take entries of the other warps' slots until no warp of the block runs a
+  // cone (a running cone's owner waits for the entries it published, so once
+  // s_active reads zero no entry is left).  Bounded: ten seconds at most.
+  const long long t0 = clock64();
+  unsigned nap = 64;
+  for (;;) {
+    int v = -1;
+    unsigned tk = 0xffffffffu;
+    for (int k = 1; k < nw && v < 0; ++k) {
+      const int u = wib + k < nw ? wib + k : wib + k - nw;
+      tk = help_take(board[u], lane);
+      if (tk != 0xffffffffu) v = u;
+    }
+    if (v >= 0) {
+      help_walk(s, tr, next, cb, board[v], tk, lane);
+      nap = 64;
+      continue;
+    }
+    bool fin = false;
+    if (lane == 0) {
+      fin = *(volatile unsigned*)&s_active == 0u;
+      if (!fin && clock64() - t0 > 20000000000ll) {
+        atomicExch(tr.err, 4u);
+        fin = true;
+      }
+      if (!fin) __nanosleep(nap);
+    }
+    if (__shfl_sync(FULL, fin, 0)) break;
+    nap = min(nap * 2, 1024u);
+  }
 }
 
 // All propagation levels in one launch.  A cone of depth d + 1 becomes a task as
@@ -683,7 +896,15 @@ __device__ __forceinline__ bool levels_done(const LevelSet& L, int e) {
 
 __global__ void __launch_bounds__(LEVEL_MAX_THREADS, LEVEL_MIN_BLOCKS) k_levels(DScene s, DTrace tr, LevelSet L,
                                                                                  CoarseBuf cb) {
-  const int lane = threadIdx.x & 31;
+  // each warp's candidate slot (walked by the warp alone here: its waiting warps
+  // look for cones of any level instead)
+  extern __shared__ HelpSlot board[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  if (lane == 0) {
+    board[wib].word = 0;
+    board[wib].done = 0;
+  }
+  __syncwarp();
   unsigned long long bytes = 0;
   uint32_t cones = 0, vis = 0, evals = 0;
   const int M = tr.M;
@@ -775,7 +996,7 @@ __global__ void __launch_bounds__(LEVEL_MAX_THREADS, LEVEL_MIN_BLOCKS) k_levels(
     t = __shfl_sync(FULL, t, 0);
     const uint32_t idx = kind == 0 ? (uint32_t)t : (uint32_t)(t / (unsigned)M);
     const int j = kind == 0 ? 0 : (int)(t % (unsigned)M);
-    level_cone(s, tr, L.lv[d], L.lv[d + 1], cb, kind == 0, idx, j, lane, bytes, cones, evals, vis);
+    level_cone(s, tr, L.lv[d], L.lv[d + 1], cb, board[wib], kind == 0, idx, j, lane, bytes, cones, evals, vis);
     __syncwarp();
     if (lane == 0) {
       __threadfence();
@@ -1155,9 +1376,9 @@ int trace_coarse(Mem& mem, SceneObj* S, const double* txh, int n_tx, const doubl
   uint32_t* q_err = nullptr;
   size_t rdy_bytes = 0;
   uint8_t* rdy = nullptr;
+  NB_TRY(sc.get(&q_err, 1));   // both layouts: a bounded wait of the propagation gave up
   if (queue) {
     NB_TRY(sc.get(&q_ctr, 2 * (MAX_LEVELS + 1) + 1 + 20 + MAX_LEVELS + 1));
-    NB_TRY(sc.get(&q_err, 1));
     for (int d = 2; d <= max_int; ++d) rdy_bytes += (size_t)lv[d].cap_r + lv[d].cap_d;
     NB_TRY(sc.get(&rdy, std::max<size_t>(1, rdy_bytes)));
     size_t off = 0;
@@ -1186,10 +1407,13 @@ int trace_coarse(Mem& mem, SceneObj* S, const double* txh, int n_tx, const doubl
   char* arena;
   NB_TRY(sc.get(&arena, std::max<size_t>(1, arena_bytes)));
   const unsigned PG = persistent_grid(256);
-  const unsigned LG = persistent_grid(tn.level_block);
-  // the single launch's warps wait for one another's work: no more blocks than are resident
-  int q_blocks = 0;
-  if (queue) NB_CUDA(err, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q_blocks, k_levels, tn.level_block, 0));
+  // the levels' grids are what is resident (the single launch's warps wait for one
+  // another's work, and a block of the per-depth launch helps only its own warps)
+  const size_t board_bytes = (size_t)(tn.level_block / 32) * sizeof(HelpSlot);
+  int l_blocks = 0, q_blocks = 0;
+  NB_CUDA(err, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&l_blocks, k_level, tn.level_block, board_bytes));
+  if (queue) NB_CUDA(err, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q_blocks, k_levels, tn.level_block, board_bytes));
+  const unsigned LG = (unsigned)(num_sms() * std::max(1, l_blocks));
   const unsigned QG = (unsigned)(num_sms() * std::max(1, q_blocks));
   StageTimer tm(st);
   const int e0 = stretch_event(tm, mem, GRAPH_TRACE, 0), e1 = stretch_event(tm, mem, GRAPH_TRACE, 1),
@@ -1199,6 +1423,7 @@ int trace_coarse(Mem& mem, SceneObj* S, const double* txh, int n_tx, const doubl
   tr_vis.stats = stats + STAGE_VIS * N_STATS;
   tr_pri.stats = stats + STAGE_PRIMARY * N_STATS;
   tr_lev.stats = stats + STAGE_LEVELS * N_STATS;
+  tr_lev.err = q_err;
 
   // From the RX table to the last depth nothing returns to the host: the march field,
   // the transmission phase and every propagation level over all TX/RX pairs form one
@@ -1267,16 +1492,16 @@ int trace_coarse(Mem& mem, SceneObj* S, const double* txh, int n_tx, const doubl
       NB_LAUNCHED(err);
     }
     // propagation phase: one launch per depth, or one launch for all depths
+    NB_CUDA(err, cudaMemsetAsync(q_err, 0, sizeof(uint32_t), q));
     if (queue) {
       NB_CUDA(err, cudaMemsetAsync(q_ctr, 0, (2 * (MAX_LEVELS + 1) + 1 + 20 + MAX_LEVELS + 1) * sizeof(unsigned long long), q));
-      NB_CUDA(err, cudaMemsetAsync(q_err, 0, sizeof(uint32_t), q));
       if (rdy_bytes) NB_CUDA(err, cudaMemsetAsync(rdy, 0, rdy_bytes, q));
       k_levels_init<<<1, 1, 0, q>>>(lv[1], tr.M);
       NB_LAUNCHED(err);
     }
     tm.record(e3, q);
     if (queue) {
-      k_levels<<<QG, tn.level_block, 0, q>>>(s, tr_lev, LS, cb);
+      k_levels<<<QG, tn.level_block, board_bytes, q>>>(s, tr_lev, LS, cb);
       NB_LAUNCHED(err);
     } else {
       for (int d = 1; d <= max_int; ++d) {
@@ -1286,7 +1511,7 @@ int trace_coarse(Mem& mem, SceneObj* S, const double* txh, int n_tx, const doubl
           next.cap_d = 0;
           next.cnt = cnts + 2 * MAX_LEVELS - 2;  // unused sink
         }
-        k_level<<<LG, tn.level_block, 0, q>>>(s, tr_lev, lv[d], next, cb, task_ctr + d);
+        k_level<<<LG, tn.level_block, board_bytes, q>>>(s, tr_lev, lv[d], next, cb, task_ctr + d);
         NB_LAUNCHED(err);
       }
     }
@@ -1300,8 +1525,13 @@ int trace_coarse(Mem& mem, SceneObj* S, const double* txh, int n_tx, const doubl
   NB_CUDA(err, cudaMemcpyAsync(hov, overflow, sizeof hov, cudaMemcpyDeviceToHost, st));
   NB_CUDA(err, cudaMemcpyAsync(hs, stats, sizeof hs, cudaMemcpyDeviceToHost, st));
   uint32_t hqerr = 0;
-  if (queue) NB_CUDA(err, cudaMemcpyAsync(&hqerr, q_err, sizeof hqerr, cudaMemcpyDeviceToHost, st));
+  if (max_int >= 1) NB_CUDA(err, cudaMemcpyAsync(&hqerr, q_err, sizeof hqerr, cudaMemcpyDeviceToHost, st));
   NB_CUDA(err, cudaStreamSynchronize(st));
+  if (hqerr == 3u || hqerr == 4u) {
+    *err = hqerr == 3u ? "trace: a cone's wait for the visibility rays other warps took gave up"
+                       : "trace: a warp's wait for the cones of its block gave up";
+    return NIMBUS_ERR_TIMEOUT;
+  }
   if (hqerr) {
     unsigned long long hd[20];
     cudaMemcpy(hd, LS.dbg, sizeof hd, cudaMemcpyDeviceToHost);

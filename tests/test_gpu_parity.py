@@ -412,12 +412,13 @@ def test_autotune_keeps_results(ctx):
     s = ctx.voxelize_scene(sc, p)
     t = ctx.autotune(s, sc.tx, sc.rx[:2], p)
     ctx.release(s)
-    assert t["level_block"] in (128, 256)
+    assert t["level_block"] in (128, 256, 512)
     assert t["refine_blocks"] in (0, 4) and t["refine_order"] in (0, 1, 2) and t["refine_ms"] > 0
     assert t["level_queue"] in (0, 1)
     assert t["refine_split"] in (0, 64, 128, 512) and t["refine_split_key"] in (0, 1)
     for layout in (dict(level_block=128, refine_blocks=3, refine_order=0, level_queue=1, refine_split=0),
                    dict(level_block=256, refine_blocks=0, refine_order=2, level_queue=0, refine_split=0),
+                   dict(level_block=512, refine_blocks=0, refine_order=1, level_queue=1, refine_split=0),
                    dict(level_block=256, refine_blocks=0, refine_order=1, level_queue=0, refine_split=5),
                    dict(level_block=256, refine_blocks=2, refine_order=2, level_queue=0, refine_split=64),
                    dict(level_block=256, refine_blocks=0, refine_order=0, level_queue=0, refine_split=7,
@@ -428,7 +429,7 @@ def test_autotune_keeps_results(ctx):
         assert len(G["n"]) == len(base["n"])
         for k in ("tx", "rx", "n", "type", "label", "pts", "length"):
             np.testing.assert_array_equal(G[k], base[k])
-    ctx.set_tuning(level_block=256, refine_blocks=0, refine_order=1, level_queue=0, refine_split=0, refine_split_key=0)
+    ctx.set_tuning(level_block=512, refine_blocks=0, refine_order=1, level_queue=0, refine_split=0, refine_split_key=0)
     with pytest.raises(Exception):
         ctx.set_tuning(level_block=96)
     with pytest.raises(Exception):
@@ -499,8 +500,11 @@ def test_graph_launch_keeps_results(ctx):
 def test_single_launch_propagation_keeps_results(ctx, case):
     """All depths in one launch (a cone task queue across levels, level_queue=1)
     against one launch per depth: the same coarse rows, exact paths and counters, at
-    128- and 256-thread blocks, with request batching (per-RX owner and depth), and
-    at depth 1 where the queue holds only the first level."""
+    128-, 256- and 512-thread blocks, with request batching (per-RX owner and depth),
+    and at depth 1 where the queue holds only the first level.  The per-depth
+    launches' warps walk one another's visibility rays once their own cones are done;
+    the counters (rays walked, bytes) must still be those of each cone walking its
+    own rays in order."""
     full = scenes.room_noisy()
     kw = {}
     if case == "wedge_d2":
@@ -516,7 +520,7 @@ def test_single_launch_propagation_keeps_results(ctx, case):
     res = {}
     try:
         for lq in (0, 1):
-            for block in (128, 256):
+            for block in (128, 256, 512):
                 ctx.set_tuning(level_queue=lq, level_block=block)
                 co = ctx.trace(s, sc.tx, sc.rx, p, **kw)
                 cq, cc = ctx.query_coarse(co), ctx.coarse_counts(co)
@@ -525,7 +529,7 @@ def test_single_launch_propagation_keeps_results(ctx, case):
                 ctx.release(P)
                 ctx.release(co)
     finally:
-        ctx.set_tuning(level_queue=0, level_block=256)
+        ctx.set_tuning(level_queue=0, level_block=512)
         ctx.release(s)
     cq0, o0, cc0 = res[0, 256]
     assert cc0["n_coarse"] > 0

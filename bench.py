@@ -90,7 +90,10 @@ def dist_env():
 # code's hash matches the capture
 REFINE_TRAFFIC = {"sources_sha256": "19b28f209c64a3a761daccf82bef14a15f07e05a2e28ca22ba1b533e3edf6047",
                   "layouts": {"order=1,split=0,key=0": 97264640 + 145813248,
-                              "order=1,split=64,key=1": 181499904 + 215844096 + 335070464 + 90637568}}
+                              "order=1,split=64,key=1": 181499904 + 215844096 + 335070464 + 90637568,
+                              "order=0,split=64,key=1": 170051840 + 216637696 + 335920384 + 89661184,
+                              "order=0,split=128,key=1": 137812480 + 179663104 + 201041664 + 47555584,
+                              "order=1,split=128,key=1": 146720512 + 182213376 + 201800448 + 47206912}}
 KERNEL_SOURCES = (("paper_2402_13747_b300/csrc/refine.cu", b"\nint refine_paths("),
                   ("paper_2402_13747_b300/csrc/warp_geom.cuh", None),
                   ("paper_2402_13747_b300/csrc/nimbus_internal.cuh", None))

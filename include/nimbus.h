@@ -392,9 +392,7 @@ NIMBUS_API int nimbus_segment(nimbus_ctx* ctx, const nimbus_cloud* cloud, const 
  * they compute.  Every setting gives bit-identical results; only the time changes.
  */
 typedef struct {
-  int32_t level_block;      /* threads per block of the propagation levels: 128, 256 or 512 (with one launch
-                               per depth, a warp whose cones are done walks visibility rays of the cones
-                               still running in its block) */
+  int32_t level_block;      /* threads per block of the propagation levels: 128, 256 or 512 */
   int32_t refine_blocks;    /* 4-warp refinement blocks per SM: 1..8 (at most as many as fit), 0 = as many as fit */
   int32_t refine_order;     /* 1: refine the paths with the most interactions first; 2: first the paths whose
                                re-projection rays graze their surfaces at the start (smallest |n . d|), then by
@@ -414,28 +412,31 @@ typedef struct {
   int32_t refine_split_key; /* the second launch's order: 0 the cost per iteration so far; 1 the predicted
                                remaining time (that cost x the iterations still needed at the gradient's
                                rate of decrease over the second half of the first launch) */
+  int32_t level_help;       /* one launch per depth only: 1, a warp whose cones are done walks visibility rays
+                               of the cones still running in its block (the candidates of an evaluation wait in
+                               a shared-memory list); 0, every warp walks only its own cones' rays */
 } nimbus_tuning;
 
 /* The context's launch configuration (defaults 512, 0, 1, 1, level_queue 0, refine_split 0,
- * refine_split_key 0). */
+ * refine_split_key 0, level_help 1). */
 NIMBUS_API int nimbus_get_tuning(nimbus_ctx* ctx, nimbus_tuning* out);
 
 /* Replace it.  A value out of range returns NIMBUS_ERR_ARG and changes nothing. */
 NIMBUS_API int nimbus_set_tuning(nimbus_ctx* ctx, const nimbus_tuning* t);
 
-/* Autotuner.  Traces the given TX/RX set on `scene` once per level layout (blocks
- * of 128, 256 or 512 threads x one launch per depth or one for all depths) and keeps the
- * fastest propagation time.  Then it refines that coarse set once per refinement
- * layout with all resident blocks per SM: one launch in coarse order, most
- * interactions first or grazing rays first; and two launches, the first in coarse
- * order or most interactions first and stopping at 64, 128 or 512 iterations, the
- * second in either of its orders; it keeps the fastest.  The result is stored in the context for the
- * calls that follow and written to `out` (may be NULL).  Every layout gives the same
- * results; tune on the workload itself where its refinement ends on long paths (a
- * small sample is one tail whatever the layout).  Times are CUDA events on `stream`;
- * the call synchronises.  Errors of the trace or refinement (including
- * NIMBUS_ERR_OVERFLOW: the set needs larger bounds) are returned unchanged and leave
- * the configuration as it was. */
+/* Autotuner.  Traces the given TX/RX set on `scene` once per level layout (blocks of
+ * 128, 256 or 512 threads x one launch per depth, with or without idle warps walking
+ * other warps' visibility rays, or one launch for all depths) and keeps the fastest
+ * propagation time.  Then it refines that coarse set once per refinement layout with
+ * all resident blocks per SM: one launch in coarse order, most interactions first or
+ * grazing rays first; and two launches, the first in coarse order or most interactions
+ * first and stopping at 64, 128 or 512 iterations, the second in either of its orders;
+ * it keeps the fastest.  The result is stored in the context for the calls that follow
+ * and written to `out` (may be NULL).  Every layout gives the same results; tune on the
+ * workload itself where its refinement ends on long paths (a small sample is one tail
+ * whatever the layout).  Times are CUDA events on `stream`; the call synchronises.
+ * Errors of the trace or refinement (including NIMBUS_ERR_OVERFLOW: the set needs
+ * larger bounds) are returned unchanged and leave the configuration as it was. */
 NIMBUS_API int nimbus_autotune(nimbus_ctx* ctx, nimbus_handle scene, const double* tx, int32_t n_tx,
                                const double* rx, int32_t n_rx, const nimbus_trace_params* trace_params,
                                const nimbus_refine_params* refine_params, nimbus_tuning* out, void* stream);

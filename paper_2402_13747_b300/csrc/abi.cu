@@ -546,6 +546,7 @@ static void to_public(const nb::Tuning& t, nimbus_tuning* o) {
   o->level_queue = t.level_queue;
   o->refine_split = t.refine_split;
   o->refine_split_key = t.refine_split_key;
+  o->level_help = t.level_help;
 }
 
 int nimbus_get_tuning(nimbus_ctx* ctx, nimbus_tuning* out) {
@@ -560,7 +561,7 @@ int nimbus_set_tuning(nimbus_ctx* ctx, const nimbus_tuning* t) {
       t->refine_blocks > 8 ||
       !(t->refine_order >= 0 && t->refine_order <= 2) || !(t->graph == 0 || t->graph == 1) ||
       !(t->level_queue == 0 || t->level_queue == 1) || t->refine_split < 0 || t->refine_split > 65535 ||
-      !(t->refine_split_key == 0 || t->refine_split_key == 1)) {
+      !(t->refine_split_key == 0 || t->refine_split_key == 1) || !(t->level_help == 0 || t->level_help == 1)) {
     ctx->err = "set_tuning: value out of range";
     return NIMBUS_ERR_ARG;
   }
@@ -573,6 +574,7 @@ int nimbus_set_tuning(nimbus_ctx* ctx, const nimbus_tuning* t) {
   ctx->tune.level_queue = t->level_queue;
   ctx->tune.refine_split = t->refine_split;
   ctx->tune.refine_split_key = t->refine_split_key;
+  ctx->tune.level_help = t->level_help;
   return NIMBUS_OK;
 }
 
@@ -593,10 +595,12 @@ int nimbus_autotune(nimbus_ctx* ctx, nimbus_handle scene, const double* tx, int3
   double best_lv = -1.0;
   const int blocks[3] = {256, 128, 512};
   for (int lq = 0; lq < 2; ++lq)
-  for (int bl : blocks) {
+  for (int bl : blocks)
+  for (int hp = lq == 0 ? 1 : 0; hp >= 0; --hp) {   // the help board exists in the per-depth launch only
     nb::Tuning t = best;
     t.level_block = bl;
     t.level_queue = lq;
+    t.level_help = hp;
     auto* C = new nb::CoarseObj();
     C->mem = &ctx->mem;
     C->scene = scene;
@@ -608,6 +612,7 @@ int nimbus_autotune(nimbus_ctx* ctx, nimbus_handle scene, const double* tx, int3
       best_lv = ms;
       best.level_block = bl;
       best.level_queue = lq;
+      best.level_help = hp;
     }
   }
   best.level_ms = best_lv;

@@ -341,6 +341,7 @@ struct Tuning {
   int level_queue = 0;     // 1: all propagation depths in one launch (a task queue across levels)
   int refine_split = 0;    // > 0: two-phase refinement, phase 1 capped at this many iterations
   int refine_split_key = 0;  // phase 2 order: 0 cost per iteration, 1 predicted remaining time
+  int level_help = 1;      // per-depth levels: idle warps of a block walk its running cones' visibility rays
   double level_ms = 0, refine_ms = 0;
 };
 

@@ -552,16 +552,20 @@ __device__ __forceinline__ void help_flush(const DScene& s, const DTrace& tr, No
 // evaluation in which a point IE was visible.  Without children to emit (last
 // level) the remaining point IEs of that evaluation are not tested: they can only
 // confirm the stop.
+template <bool HELP>
 __device__ void march_cone_warp(const DScene& s, const DTrace& tr, const ConeD& c, const LevelCone& lc,
-                                NodeLevel& next, CoarseBuf& cb, HelpSlot& H, int lane, unsigned long long& bytes,
+                                NodeLevel& next, CoarseBuf& cb, HelpSlot* Hp, int lane, unsigned long long& bytes,
                                 uint32_t& evals, uint32_t& vis) {
-  if (lane == 0) {
-    // no entry of this slot is out (the last batch was waited for): the header is free
-    H.h0 = make_float4(c.apex.x, c.apex.y, c.apex.z, __uint_as_float(c.origin.label));
-    H.h1 = make_uint4((unsigned)c.origin.mode, lc.tx | (lc.nr << 16) | (lc.nd << 20) | (lc.depth << 24), lc.self_ref,
-                      lc.can_child ? 1u : 0u);
+  if constexpr (HELP) {
+    HelpSlot& H = *Hp;
+    if (lane == 0) {
+      // no entry of this slot is out (the last batch was waited for): the header is free
+      H.h0 = make_float4(c.apex.x, c.apex.y, c.apex.z, __uint_as_float(c.origin.label));
+      H.h1 = make_uint4((unsigned)c.origin.mode, lc.tx | (lc.nr << 16) | (lc.nd << 20) | (lc.depth << 24),
+                        lc.self_ref, lc.can_child ? 1u : 0u);
+    }
+    __syncwarp();
   }
-  __syncwarp();
   const unsigned lt = (1u << lane) - 1u;
   Walk w;
   walk_init(s, c.apex, c.axis, w);
@@ -597,113 +601,205 @@ __device__ void march_cone_warp(const DScene& s, const DTrace& tr, const ConeD& 
                  cone_sphere(c.apex, c.axis, c.sin_a, c.cos_a, voxel_center(s, u0, u1, u2), s.r_vox);
           }
         }
-        // Collect the evaluation's candidates in the order the walk in order meets them
-        // (IE voxels by lane, their IEs in chunks of 32, then the RX voxels' runs)
-        // until the slot is full, walk that batch, and go on from where collecting
-        // stopped (the chunk that did not fit is screened again; its bytes count once).
-        int hn = 0;                  // entries collected and not yet walked
-        if (lane == 0) {
-          H.first_vis = 0xffffffffu;
-          H.qbase = 0;
-        }
-        unsigned vm = __ballot_sync(FULL, ok && cell.y > 0);   // IE voxels left
-        unsigned rm = __ballot_sync(FULL, ok && has_rx);       // RX voxels left (never stop the cone)
-        uint32_t k0 = 0;             // next IE chunk of voxel ffs(vm)
-        int qb = -1;                 // next RX chunk of voxel ffs(rm); -1 before its first
-        for (;;) {
-          bool full = false;
-          while (vm) {
-            const int src = __ffs(vm) - 1;
-            const uint32_t base = __shfl_sync(FULL, cell.x, src), cnt = __shfl_sync(FULL, cell.y, src);
-            if (k0 >= cnt) {
-              vm &= vm - 1;
-              k0 = 0;
-              continue;
-            }
-            const uint32_t k = k0 + lane, id = base + k;
-            bool cand = false;
-            uint32_t kind = IE_POINT, lbl = 0;
-            float3 rp = f3(0.f, 0.f, 0.f);
-            unsigned by = 0;
-            if (k < cnt) {
-              const IERec* r = &s.ies[id];
-              const float4 nm = __ldg(&r->nrm_meta), sc = __ldg(&r->sc_pc);
-              by += 32;
-              kind = __float_as_uint(nm.w) & 1u;
-              if ((kind == IE_POINT || lc.test_edges) && cone_sphere(c.apex, c.axis, c.sin_a, c.cos_a, xyz(sc), s.r_sub)) {
-                const float4 q = __ldg(&r->rp_lab);
-                by += 16;
-                rp = xyz(q);
-                lbl = __float_as_uint(q.w);
-                cand = planes_ok(c, rp, tr.sep_eps);
-              }
-            }
-            const unsigned cm = __ballot_sync(FULL, cand);
-            if (hn + __popc(cm) > HELP_CAP) {
-              full = true;
-              break;
-            }
-            if (cand) {
-              const int k2 = hn + __popc(cm & lt);
-              H.a[k2] = make_float4(rp.x, rp.y, rp.z, __uint_as_float(id));
-              H.b[k2] = make_uint2(kind, lbl);
-            }
-            hn += __popc(cm);
-            bytes += by;
-            k0 += 32;
+        bool stop;
+        if constexpr (HELP) {
+          HelpSlot& H = *Hp;
+          // Collect the evaluation's candidates in the order the walk in order meets them
+          // (IE voxels by lane, their IEs in chunks of 32, then the RX voxels' runs)
+          // until the slot is full, walk that batch, and go on from where collecting
+          // stopped (the chunk that did not fit is screened again; its bytes count once).
+          int hn = 0;                  // entries collected and not yet walked
+          if (lane == 0) {
+            H.first_vis = 0xffffffffu;
+            H.qbase = 0;
           }
-          while (!full && !vm && rm) {
-            const int src = __ffs(rm) - 1;
-            const long long cus = __shfl_sync(FULL, cu, src);
-            if (qb < 0) qb = rx_lower_bound(tr, (uint64_t)cus << 32);
-            const int q = qb + lane;
-            bool in = false, cand = false;
-            int rj = 0;
-            float3 pos = f3(0.f, 0.f, 0.f);
-            float miss = 0.f;
-            unsigned by = 0;
-            if (q < tr.n_rx_sorted) {
-              const uint64_t e = tr.rx_sorted[q];
-              by += 8;
-              in = (long long)(e >> 32) == cus;
-              if (in) {
-                rj = (int)(e & 0xffffffffu);
-                pos = xyz(__ldg(&tr.rx[rj]));
-                by += 16;
-                cand = cone_sphere(c.apex, c.axis, c.sin_a, c.cos_a, pos, s.r_sub) && planes_ok(c, pos, tr.sep_eps) &&
-                       !(tr.rx_owner && tr.rx_owner[rj] >= 0 && (uint32_t)tr.rx_owner[rj] != lc.tx) &&
-                       !(tr.rx_max_int && tr.rx_max_int[rj] >= 0 && (int)lc.depth > tr.rx_max_int[rj]);
-                if (cand) {
-                  const float3 v = pos - c.apex;
-                  miss = len(v - dot(v, c.axis) * c.axis);
+          unsigned vm = __ballot_sync(FULL, ok && cell.y > 0);   // IE voxels left
+          unsigned rm = __ballot_sync(FULL, ok && has_rx);       // RX voxels left (never stop the cone)
+          uint32_t k0 = 0;             // next IE chunk of voxel ffs(vm)
+          int qb = -1;                 // next RX chunk of voxel ffs(rm); -1 before its first
+          for (;;) {
+            bool full = false;
+            while (vm) {
+              const int src = __ffs(vm) - 1;
+              const uint32_t base = __shfl_sync(FULL, cell.x, src), cnt = __shfl_sync(FULL, cell.y, src);
+              if (k0 >= cnt) {
+                vm &= vm - 1;
+                k0 = 0;
+                continue;
+              }
+              const uint32_t k = k0 + lane, id = base + k;
+              bool cand = false;
+              uint32_t kind = IE_POINT, lbl = 0;
+              float3 rp = f3(0.f, 0.f, 0.f);
+              unsigned by = 0;
+              if (k < cnt) {
+                const IERec* r = &s.ies[id];
+                const float4 nm = __ldg(&r->nrm_meta), sc = __ldg(&r->sc_pc);
+                by += 32;
+                kind = __float_as_uint(nm.w) & 1u;
+                if ((kind == IE_POINT || lc.test_edges) && cone_sphere(c.apex, c.axis, c.sin_a, c.cos_a, xyz(sc), s.r_sub)) {
+                  const float4 q = __ldg(&r->rp_lab);
+                  by += 16;
+                  rp = xyz(q);
+                  lbl = __float_as_uint(q.w);
+                  cand = planes_ok(c, rp, tr.sep_eps);
                 }
               }
+              const unsigned cm = __ballot_sync(FULL, cand);
+              if (hn + __popc(cm) > HELP_CAP) {
+                full = true;
+                break;
+              }
+              if (cand) {
+                const int k2 = hn + __popc(cm & lt);
+                H.a[k2] = make_float4(rp.x, rp.y, rp.z, __uint_as_float(id));
+                H.b[k2] = make_uint2(kind, lbl);
+              }
+              hn += __popc(cm);
+              bytes += by;
+              k0 += 32;
             }
-            const unsigned inm = __ballot_sync(FULL, in);
-            const unsigned cm = __ballot_sync(FULL, cand);
-            if (hn + __popc(cm) > HELP_CAP) {
-              full = true;
-              break;
+            while (!full && !vm && rm) {
+              const int src = __ffs(rm) - 1;
+              const long long cus = __shfl_sync(FULL, cu, src);
+              if (qb < 0) qb = rx_lower_bound(tr, (uint64_t)cus << 32);
+              const int q = qb + lane;
+              bool in = false, cand = false;
+              int rj = 0;
+              float3 pos = f3(0.f, 0.f, 0.f);
+              float miss = 0.f;
+              unsigned by = 0;
+              if (q < tr.n_rx_sorted) {
+                const uint64_t e = tr.rx_sorted[q];
+                by += 8;
+                in = (long long)(e >> 32) == cus;
+                if (in) {
+                  rj = (int)(e & 0xffffffffu);
+                  pos = xyz(__ldg(&tr.rx[rj]));
+                  by += 16;
+                  cand = cone_sphere(c.apex, c.axis, c.sin_a, c.cos_a, pos, s.r_sub) && planes_ok(c, pos, tr.sep_eps) &&
+                         !(tr.rx_owner && tr.rx_owner[rj] >= 0 && (uint32_t)tr.rx_owner[rj] != lc.tx) &&
+                         !(tr.rx_max_int && tr.rx_max_int[rj] >= 0 && (int)lc.depth > tr.rx_max_int[rj]);
+                  if (cand) {
+                    const float3 v = pos - c.apex;
+                    miss = len(v - dot(v, c.axis) * c.axis);
+                  }
+                }
+              }
+              const unsigned inm = __ballot_sync(FULL, in);
+              const unsigned cm = __ballot_sync(FULL, cand);
+              if (hn + __popc(cm) > HELP_CAP) {
+                full = true;
+                break;
+              }
+              if (cand) {
+                const int k2 = hn + __popc(cm & lt);
+                H.a[k2] = make_float4(pos.x, pos.y, pos.z, __uint_as_float((uint32_t)rj));
+                H.b[k2] = make_uint2(CAND_RX, __float_as_uint(miss));
+              }
+              hn += __popc(cm);
+              bytes += by;
+              if (inm != FULL) {   // the voxel's RX run ended in this chunk
+                rm &= rm - 1;
+                qb = -1;
+              } else {
+                qb += 32;
+              }
             }
-            if (cand) {
-              const int k2 = hn + __popc(cm & lt);
-              H.a[k2] = make_float4(pos.x, pos.y, pos.z, __uint_as_float((uint32_t)rj));
-              H.b[k2] = make_uint2(CAND_RX, __float_as_uint(miss));
-            }
-            hn += __popc(cm);
-            bytes += by;
-            if (inm != FULL) {   // the voxel's RX run ended in this chunk
-              rm &= rm - 1;
-              qb = -1;
-            } else {
-              qb += 32;
+            help_flush(s, tr, next, cb, H, hn, lane, bytes, vis);
+            if (!full) break;
+          }
+          // a point IE of this evaluation was visible
+          stop = *(volatile unsigned*)&H.first_vis != 0xffffffffu;
+        } else {
+          // each candidate walked at once by this warp
+          stop = false;
+          unsigned vm = __ballot_sync(FULL, ok && cell.y > 0);
+          while (vm) {
+            const int src = __ffs(vm) - 1;
+            vm &= vm - 1;
+            const uint32_t base = __shfl_sync(FULL, cell.x, src), cnt = __shfl_sync(FULL, cell.y, src);
+            for (uint32_t k0 = 0; k0 < cnt; k0 += 32) {
+              const uint32_t k = k0 + lane, id = base + k;
+              bool cand = false;
+              uint32_t kind = IE_POINT, lbl = 0;
+              float3 rp = f3(0.f, 0.f, 0.f);
+              if (k < cnt) {
+                const IERec* r = &s.ies[id];
+                const float4 nm = __ldg(&r->nrm_meta), sc = __ldg(&r->sc_pc);
+                bytes += 32;
+                kind = __float_as_uint(nm.w) & 1u;
+                if ((kind == IE_POINT || lc.test_edges) && cone_sphere(c.apex, c.axis, c.sin_a, c.cos_a, xyz(sc), s.r_sub)) {
+                  const float4 q = __ldg(&r->rp_lab);
+                  bytes += 16;
+                  rp = xyz(q);
+                  lbl = __float_as_uint(q.w);
+                  cand = planes_ok(c, rp, tr.sep_eps);
+                }
+              }
+              unsigned cm = __ballot_sync(FULL, cand);
+              while (cm) {
+                const int j = __ffs(cm) - 1;
+                cm &= cm - 1;
+                const uint32_t cid = __shfl_sync(FULL, id, j), ckind = __shfl_sync(FULL, kind, j);
+                const uint32_t clab = __shfl_sync(FULL, lbl, j);
+                const float3 crp = f3(__shfl_sync(FULL, rp.x, j), __shfl_sync(FULL, rp.y, j), __shfl_sync(FULL, rp.z, j));
+                if (ckind == IE_POINT && stop && !lc.can_child) continue;
+                if (lane == 0) ++vis;
+                const Endpoint eb{ckind == IE_EDGE ? IGN_ANY : IGN_LABEL, clab};
+                if (!visible_warp(s, c.apex, crp, c.origin, eb, lane, bytes)) continue;
+                if (lc.can_child && lane == 0)
+                  emit_child(tr, next, cid, crp, c.apex, ckind, lc.tx, lc.nr, lc.nd, lc.depth, lc.self_ref);
+                if (ckind == IE_POINT) stop = true;
+              }
             }
           }
-          help_flush(s, tr, next, cb, H, hn, lane, bytes, vis);
-          if (!full) break;
+          // RXs in the accepted voxels (never stop the cone)
+          unsigned rm = __ballot_sync(FULL, ok && has_rx);
+          while (rm) {
+            const int src = __ffs(rm) - 1;
+            rm &= rm - 1;
+            const long long cus = __shfl_sync(FULL, cu, src);
+            const int q0 = rx_lower_bound(tr, (uint64_t)cus << 32);
+            for (int qb = q0;; qb += 32) {
+              const int q = qb + lane;
+              bool in = false, cand = false;
+              int rj = 0;
+              float3 pos = f3(0.f, 0.f, 0.f);
+              float miss = 0.f;
+              if (q < tr.n_rx_sorted) {
+                const uint64_t e = tr.rx_sorted[q];
+                bytes += 8;
+                in = (long long)(e >> 32) == cus;
+                if (in) {
+                  rj = (int)(e & 0xffffffffu);
+                  pos = xyz(__ldg(&tr.rx[rj]));
+                  bytes += 16;
+                  cand = cone_sphere(c.apex, c.axis, c.sin_a, c.cos_a, pos, s.r_sub) && planes_ok(c, pos, tr.sep_eps) &&
+                         !(tr.rx_owner && tr.rx_owner[rj] >= 0 && (uint32_t)tr.rx_owner[rj] != lc.tx) &&
+                         !(tr.rx_max_int && tr.rx_max_int[rj] >= 0 && (int)lc.depth > tr.rx_max_int[rj]);
+                  if (cand) {
+                    const float3 v = pos - c.apex;
+                    miss = len(v - dot(v, c.axis) * c.axis);
+                  }
+                }
+              }
+              const unsigned inm = __ballot_sync(FULL, in);
+              unsigned cm = __ballot_sync(FULL, cand);
+              while (cm) {
+                const int j = __ffs(cm) - 1;
+                cm &= cm - 1;
+                const int crj = __shfl_sync(FULL, rj, j);
+                const float cmiss = __shfl_sync(FULL, miss, j);
+                const float3 cpos = f3(__shfl_sync(FULL, pos.x, j), __shfl_sync(FULL, pos.y, j), __shfl_sync(FULL, pos.z, j));
+                if (lane == 0) ++vis;
+                if (visible_warp(s, c.apex, cpos, c.origin, Endpoint{IGN_NONE, NB_NONE_LABEL}, lane, bytes) && lane == 0)
+                  emit_coarse(tr, cb, lc.tx, (uint32_t)crj, lc.self_ref, lc.depth, cmiss);
+              }
+              if (inm != FULL) break;   // the voxel's RX run ended in this chunk
+            }
+          }
         }
-        // a point IE of this evaluation was visible
-        const bool stop = *(volatile unsigned*)&H.first_vis != 0xffffffffu;
         have_last = true;
         last[0] = w.v[0]; last[1] = w.v[1]; last[2] = w.v[2];
         if (stop) break;
@@ -715,8 +811,9 @@ __device__ void march_cone_warp(const DScene& s, const DTrace& tr, const ConeD& 
 
 // One propagation cone of level `cur`: the reflected cone of node idx (refl) or cone
 // j of the Keller fan of diffraction node idx.
+template <bool HELP>
 __device__ __forceinline__ void level_cone(const DScene& s, const DTrace& tr, const NodeLevel& cur, NodeLevel& next,
-                                           CoarseBuf& cb, HelpSlot& H, bool refl, uint32_t idx, int j, int lane,
+                                           CoarseBuf& cb, HelpSlot* H, bool refl, uint32_t idx, int j, int lane,
                                            unsigned long long& bytes, uint32_t& cones, uint32_t& evals,
                                            uint32_t& vis) {
   const float4 a = refl ? cur.ra[idx] : cur.da[idx];
@@ -775,32 +872,37 @@ __device__ __forceinline__ void level_cone(const DScene& s, const DTrace& tr, co
   lc.can_child = (int)lc.depth < tr.max_int && (!tr.tx_max_int || (int)lc.depth < tr.tx_max_int[lc.tx]);
   lc.test_edges = lc.can_child && (int)lc.nd < tr.max_diff;
   if (lane == 0) ++cones;
-  march_cone_warp(s, tr, c, lc, next, cb, H, lane, bytes, evals, vis);
+  march_cone_warp<HELP>(s, tr, c, lc, next, cb, H, lane, bytes, evals, vis);
 }
 
 // One propagation level: the reflected cones and Keller-fan cones of every node,
-// one warp per cone, cones handed out by a counter (their costs differ widely).  A
-// warp with no cone left walks visibility rays of its block's running cones (the
-// board above) until every warp of the block has finished.
-// Blocks of 128, 256 or 512 threads, all at 128 registers a thread (16 warps per SM);
-// the board (one slot per warp) is the launch's dynamic shared memory.
+// one warp per cone, cones handed out by a counter (their costs differ widely).
+// With HELP, a warp with no cone left walks visibility rays of its block's running
+// cones (the board above) until every warp of the block has finished; the board (one
+// slot per warp) is the launch's dynamic shared memory.  Without it each warp walks
+// its own cones' rays as it meets them (the board's lists cost a little register
+// room and time where no cone runs long).  Blocks of 128, 256 or 512 threads, all at
+// 128 registers a thread (16 warps per SM).
 #ifndef LEVEL_MAX_THREADS
 #define LEVEL_MAX_THREADS 512
 #endif
 #ifndef LEVEL_MIN_BLOCKS
 #define LEVEL_MIN_BLOCKS 1
 #endif
+template <bool HELP>
 __global__ void __launch_bounds__(LEVEL_MAX_THREADS, LEVEL_MIN_BLOCKS) k_level(DScene s, DTrace tr, NodeLevel cur, NodeLevel next, CoarseBuf cb,
                                                unsigned long long* next_task) {
   extern __shared__ HelpSlot board[];
   __shared__ unsigned s_active;   // warps of the block still taking cones
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  if (lane == 0) {
-    board[wib].word = 0;
-    board[wib].done = 0;
+  if constexpr (HELP) {
+    if (lane == 0) {
+      board[wib].word = 0;
+      board[wib].done = 0;
+    }
+    if (threadIdx.x == 0) s_active = (unsigned)nw;
+    __syncthreads();
   }
-  if (threadIdx.x == 0) s_active = (unsigned)nw;
-  __syncthreads();
   const uint32_t n_r = min(cur.cnt[0], cur.cap_r), n_d = min(cur.cnt[1], cur.cap_d);
   const int64_t total = (int64_t)n_r + (int64_t)n_d * tr.M;
   unsigned long long bytes = 0;
@@ -813,9 +915,11 @@ __global__ void __launch_bounds__(LEVEL_MAX_THREADS, LEVEL_MIN_BLOCKS) k_level(D
     const bool refl = task < n_r;
     const uint32_t idx = refl ? (uint32_t)task : (uint32_t)((task - n_r) / tr.M);
     const int j = refl ? 0 : (int)((task - n_r) % tr.M);
-    level_cone(s, tr, cur, next, cb, board[wib], refl, idx, j, lane, bytes, cones, evals, vis);
+    level_cone<HELP>(s, tr, cur, next, cb, HELP ? board + wib : nullptr, refl, idx, j, lane, bytes, cones, evals,
+                     vis);
   }
   add_stats(tr, cones, vis, bytes, evals);
+  if constexpr (!HELP) return;
   if (lane == 0) atomicSub(&s_active, 1u);
   // help: take entries of the other warps' slots until no warp of the block runs a
   // cone (a running cone's owner waits for the entries it published, so once
@@ -896,15 +1000,9 @@ __device__ __forceinline__ bool levels_done(const LevelSet& L, int e) {
 
 __global__ void __launch_bounds__(LEVEL_MAX_THREADS, LEVEL_MIN_BLOCKS) k_levels(DScene s, DTrace tr, LevelSet L,
                                                                                  CoarseBuf cb) {
-  // each warp's candidate slot (walked by the warp alone here: its waiting warps
-  // look for cones of any level instead)
-  extern __shared__ HelpSlot board[];
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  if (lane == 0) {
-    board[wib].word = 0;
-    board[wib].done = 0;
-  }
-  __syncwarp();
+  // each warp walks its own cones' rays (its waiting warps look for cones of any
+  // level instead of walking other warps' rays)
+  const int lane = threadIdx.x & 31;
   unsigned long long bytes = 0;
   uint32_t cones = 0, vis = 0, evals = 0;
   const int M = tr.M;
@@ -996,7 +1094,7 @@ __global__ void __launch_bounds__(LEVEL_MAX_THREADS, LEVEL_MIN_BLOCKS) k_levels(
     t = __shfl_sync(FULL, t, 0);
     const uint32_t idx = kind == 0 ? (uint32_t)t : (uint32_t)(t / (unsigned)M);
     const int j = kind == 0 ? 0 : (int)(t % (unsigned)M);
-    level_cone(s, tr, L.lv[d], L.lv[d + 1], cb, board[wib], kind == 0, idx, j, lane, bytes, cones, evals, vis);
+    level_cone<false>(s, tr, L.lv[d], L.lv[d + 1], cb, nullptr, kind == 0, idx, j, lane, bytes, cones, evals, vis);
     __syncwarp();
     if (lane == 0) {
       __threadfence();
@@ -1409,10 +1507,12 @@ int trace_coarse(Mem& mem, SceneObj* S, const double* txh, int n_tx, const doubl
   const unsigned PG = persistent_grid(256);
   // the levels' grids are what is resident (the single launch's warps wait for one
   // another's work, and a block of the per-depth launch helps only its own warps)
-  const size_t board_bytes = (size_t)(tn.level_block / 32) * sizeof(HelpSlot);
+  const bool help = tn.level_help != 0;
+  const size_t board_bytes = help ? (size_t)(tn.level_block / 32) * sizeof(HelpSlot) : 0;
+  auto* k_lev = help ? k_level<true> : k_level<false>;
   int l_blocks = 0, q_blocks = 0;
-  NB_CUDA(err, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&l_blocks, k_level, tn.level_block, board_bytes));
-  if (queue) NB_CUDA(err, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q_blocks, k_levels, tn.level_block, board_bytes));
+  NB_CUDA(err, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&l_blocks, k_lev, tn.level_block, board_bytes));
+  if (queue) NB_CUDA(err, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q_blocks, k_levels, tn.level_block, 0));
   const unsigned LG = (unsigned)(num_sms() * std::max(1, l_blocks));
   const unsigned QG = (unsigned)(num_sms() * std::max(1, q_blocks));
   StageTimer tm(st);
@@ -1501,7 +1601,7 @@ int trace_coarse(Mem& mem, SceneObj* S, const double* txh, int n_tx, const doubl
     }
     tm.record(e3, q);
     if (queue) {
-      k_levels<<<QG, tn.level_block, board_bytes, q>>>(s, tr_lev, LS, cb);
+      k_levels<<<QG, tn.level_block, 0, q>>>(s, tr_lev, LS, cb);
       NB_LAUNCHED(err);
     } else {
       for (int d = 1; d <= max_int; ++d) {
@@ -1511,7 +1611,7 @@ int trace_coarse(Mem& mem, SceneObj* S, const double* txh, int n_tx, const doubl
           next.cap_d = 0;
           next.cnt = cnts + 2 * MAX_LEVELS - 2;  // unused sink
         }
-        k_level<<<LG, tn.level_block, board_bytes, q>>>(s, tr_lev, lv[d], next, cb, task_ctr + d);
+        k_lev<<<LG, tn.level_block, board_bytes, q>>>(s, tr_lev, lv[d], next, cb, task_ctr + d);
         NB_LAUNCHED(err);
       }
     }

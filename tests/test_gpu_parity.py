@@ -416,22 +416,28 @@ def test_autotune_keeps_results(ctx):
     assert t["refine_blocks"] in (0, 4) and t["refine_order"] in (0, 1, 2) and t["refine_ms"] > 0
     assert t["level_queue"] in (0, 1)
     assert t["refine_split"] in (0, 64, 128, 512) and t["refine_split_key"] in (0, 1)
+    assert t["level_help"] in (0, 1) and not (t["level_help"] and t["level_queue"])
     for layout in (dict(level_block=128, refine_blocks=3, refine_order=0, level_queue=1, refine_split=0),
                    dict(level_block=256, refine_blocks=0, refine_order=2, level_queue=0, refine_split=0),
                    dict(level_block=512, refine_blocks=0, refine_order=1, level_queue=1, refine_split=0),
+                   dict(level_block=512, refine_blocks=0, refine_order=1, level_queue=0, refine_split=0,
+                        level_help=1),
                    dict(level_block=256, refine_blocks=0, refine_order=1, level_queue=0, refine_split=5),
                    dict(level_block=256, refine_blocks=2, refine_order=2, level_queue=0, refine_split=64),
                    dict(level_block=256, refine_blocks=0, refine_order=0, level_queue=0, refine_split=7,
                         refine_split_key=1), t):
         ctx.set_tuning(**{k: layout.get(k, 0) for k in ("level_block", "refine_blocks", "refine_order", "level_queue",
-                                                        "refine_split", "refine_split_key")})
+                                                        "refine_split", "refine_split_key", "level_help")})
         G = ctx.run(sc, p)
         assert len(G["n"]) == len(base["n"])
         for k in ("tx", "rx", "n", "type", "label", "pts", "length"):
             np.testing.assert_array_equal(G[k], base[k])
-    ctx.set_tuning(level_block=512, refine_blocks=0, refine_order=1, level_queue=0, refine_split=0, refine_split_key=0)
+    ctx.set_tuning(level_block=512, refine_blocks=0, refine_order=1, level_queue=0, refine_split=0, refine_split_key=0,
+                   level_help=1)
     with pytest.raises(Exception):
         ctx.set_tuning(level_block=96)
+    with pytest.raises(Exception):
+        ctx.set_tuning(level_help=2)
     with pytest.raises(Exception):
         ctx.set_tuning(refine_split=-1)
     with pytest.raises(Exception):
@@ -501,10 +507,10 @@ def test_single_launch_propagation_keeps_results(ctx, case):
     """All depths in one launch (a cone task queue across levels, level_queue=1)
     against one launch per depth: the same coarse rows, exact paths and counters, at
     128-, 256- and 512-thread blocks, with request batching (per-RX owner and depth),
-    and at depth 1 where the queue holds only the first level.  The per-depth
-    launches' warps walk one another's visibility rays once their own cones are done;
-    the counters (rays walked, bytes) must still be those of each cone walking its
-    own rays in order."""
+    and at depth 1 where the queue holds only the first level.  With level_help the
+    per-depth launches' warps walk one another's visibility rays once their own cones
+    are done; the counters (rays walked, bytes) must still be those of each cone
+    walking its own rays in order."""
     full = scenes.room_noisy()
     kw = {}
     if case == "wedge_d2":
@@ -519,25 +525,25 @@ def test_single_launch_propagation_keeps_results(ctx, case):
     s = ctx.voxelize_scene(sc, p)
     res = {}
     try:
-        for lq in (0, 1):
+        for lq, help_ in ((0, 0), (0, 1), (1, 0)):
             for block in (128, 256, 512):
-                ctx.set_tuning(level_queue=lq, level_block=block)
+                ctx.set_tuning(level_queue=lq, level_block=block, level_help=help_)
                 co = ctx.trace(s, sc.tx, sc.rx, p, **kw)
                 cq, cc = ctx.query_coarse(co), ctx.coarse_counts(co)
                 P = ctx.refine(s, co, p)
-                res[lq, block] = (cq, ctx.query(P, 0), cc)
+                res[lq, help_, block] = (cq, ctx.query(P, 0), cc)
                 ctx.release(P)
                 ctx.release(co)
     finally:
-        ctx.set_tuning(level_queue=0, level_block=512)
+        ctx.set_tuning(level_queue=0, level_block=512, level_help=1)
         ctx.release(s)
-    cq0, o0, cc0 = res[0, 256]
+    cq0, o0, cc0 = res[0, 0, 256]
     assert cc0["n_coarse"] > 0
     for key, (cq, o, cc) in res.items():
         assert _coarse_rows(cq) == _coarse_rows(cq0), key
         for k in ("tx", "rx", "n", "type", "label", "pts", "length"):
             np.testing.assert_array_equal(o[k], o0[k], err_msg=f"{key} {k}")
-        for k in ("n_cones", "n_vis", "n_nodes", "n_coarse", "n_coarse_raw"):
+        for k in ("n_cones", "n_vis", "n_nodes", "n_coarse", "n_coarse_raw", "bytes_levels"):
             assert cc[k] == cc0[k], (key, k)
     with pytest.raises(Exception):
         ctx.set_tuning(level_queue=2)

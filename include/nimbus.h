@@ -424,6 +424,16 @@ NIMBUS_API int nimbus_get_tuning(nimbus_ctx* ctx, nimbus_tuning* out);
 /* Replace it.  A value out of range returns NIMBUS_ERR_ARG and changes nothing. */
 NIMBUS_API int nimbus_set_tuning(nimbus_ctx* ctx, const nimbus_tuning* t);
 
+/* Testing the bounded waits.  Every device wait of the propagation levels (a warp of
+ * the single launch waiting for a task or a record, a cone waiting for the visibility
+ * rays other warps took, a warp waiting for the cones of its block) gives up after a
+ * limit in SM clock cycles: seconds by default.  This sets that limit for the
+ * context's later trace calls (`cycles` > 0), or restores the defaults (0).  With a
+ * limit of a few cycles the waits give up at once: the call then returns
+ * NIMBUS_ERR_TIMEOUT and frees what it allocated, and the context stays usable.
+ * Negative values return NIMBUS_ERR_ARG. */
+NIMBUS_API int nimbus_set_wait_limit(nimbus_ctx* ctx, int64_t cycles);
+
 /* Autotuner.  Traces the given TX/RX set on `scene` once per level layout (blocks of
  * 128, 256 or 512 threads x one launch per depth, with or without idle warps walking
  * other warps' visibility rays, or one launch for all depths) and keeps the fastest

@@ -27,7 +27,7 @@ EXPORTS = ("nimbus_create", "nimbus_destroy", "nimbus_last_error", "nimbus_voxel
            "nimbus_trace_coarse", "nimbus_refine", "nimbus_query", "nimbus_query_coarse", "nimbus_scene_info",
            "nimbus_scene_tables", "nimbus_release", "nimbus_memory_used", "nimbus_kernel_launches",
            "nimbus_device_allocations", "nimbus_voxelize_static", "nimbus_get_tuning", "nimbus_set_tuning", "nimbus_autotune",
-           "nimbus_scene_save", "nimbus_scene_load", "nimbus_segment")
+           "nimbus_scene_save", "nimbus_scene_load", "nimbus_segment", "nimbus_set_wait_limit")
 
 _vp = C.c_void_p
 
@@ -187,6 +187,7 @@ def load():
     L.nimbus_scene_load.argtypes = [ctxp, C.c_char_p, P(C.c_uint64), _vp]
     L.nimbus_segment.argtypes = [ctxp, P(Cloud), P(SegmentParamsC), _vp, _vp, _vp, C.c_int64, P(SegmentCounts), _vp]
     L.nimbus_get_tuning.argtypes = [ctxp, P(Tuning)]
+    L.nimbus_set_wait_limit.argtypes = [ctxp, C.c_int64]
     L.nimbus_set_tuning.argtypes = [ctxp, P(Tuning)]
     L.nimbus_autotune.argtypes = [ctxp, C.c_uint64, _vp, C.c_int32, _vp, C.c_int32, P(TraceParams), P(RefineParams),
                                   P(Tuning), _vp]
@@ -432,6 +433,11 @@ class Context:
             setattr(t, k, v)
         self._check(self.L.nimbus_set_tuning(self.h, C.byref(t)), "set_tuning")
         return t.as_dict()
+
+    def set_wait_limit(self, cycles: int):
+        """Limit, in SM cycles, of the propagation levels' bounded waits (0: defaults);
+        for tests of the timeout path (nimbus_set_wait_limit)."""
+        self._check(self.L.nimbus_set_wait_limit(self.h, int(cycles)), "set_wait_limit")
 
     def autotune(self, scene: int, tx, rx, params: Params = None, stream=None) -> dict:
         """Time the launch layouts on a TX/RX sample and keep the fastest (nimbus_autotune)."""

@@ -578,6 +578,16 @@ int nimbus_set_tuning(nimbus_ctx* ctx, const nimbus_tuning* t) {
   return NIMBUS_OK;
 }
 
+int nimbus_set_wait_limit(nimbus_ctx* ctx, int64_t cycles) {
+  if (!ctx) return NIMBUS_ERR_ARG;
+  if (cycles < 0) {
+    ctx->err = "set_wait_limit: negative limit";
+    return NIMBUS_ERR_ARG;
+  }
+  ctx->tune.wait_limit = (long long)cycles;
+  return NIMBUS_OK;
+}
+
 int nimbus_autotune(nimbus_ctx* ctx, nimbus_handle scene, const double* tx, int32_t n_tx, const double* rx,
                     int32_t n_rx, const nimbus_trace_params* tp, const nimbus_refine_params* rp, nimbus_tuning* out,
                     void* stream) {

@@ -52,7 +52,13 @@ struct DTrace {
   unsigned long long* stats;
   uint32_t* overflow;        // [0] largest node slot requested, [1] coarse slot requested
   uint32_t* err;             // propagation: nonzero once a bounded wait gave up
+  long long wait_limit;      // cycles after which a wait gives up; 0: each wait's default
 };
+
+// The limit of a bounded wait: its default, or the context's test limit.
+__device__ __forceinline__ long long wait_cap(const DTrace& tr, long long dflt) {
+  return tr.wait_limit > 0 ? tr.wait_limit : dflt;
+}
 
 // Nodes of one level, structure of arrays (reflection and diffraction apart).
 //   a: apex (reception point) xyz, IE index bits
@@ -513,7 +519,7 @@ __device__ __forceinline__ void help_flush(const DScene& s, const DTrace& tr, No
     // entries taken by other warps: each is one visibility ray, at most milliseconds
     const long long t0 = clock64();
     while (*(volatile unsigned*)&H.done < (unsigned)hn) {
-      if (clock64() - t0 > 4000000000ll) {
+      if (clock64() - t0 > wait_cap(tr, 4000000000ll)) {
         atomicExch(tr.err, 3u);
         break;
       }
@@ -942,7 +948,7 @@ __global__ void __launch_bounds__(LEVEL_MAX_THREADS, LEVEL_MIN_BLOCKS) k_level(D
     bool fin = false;
     if (lane == 0) {
       fin = *(volatile unsigned*)&s_active == 0u;
-      if (!fin && clock64() - t0 > 20000000000ll) {
+      if (!fin && clock64() - t0 > wait_cap(tr, 20000000000ll)) {
         atomicExch(tr.err, 4u);
         fin = true;
       }
@@ -1040,7 +1046,7 @@ __global__ void __launch_bounds__(LEVEL_MAX_THREADS, LEVEL_MIN_BLOCKS) k_levels(
               }
               break;
             }
-            if (clock64() - t0 > 20000000000ll) break;
+            if (clock64() - t0 > wait_cap(tr, 20000000000ll)) break;
             __nanosleep(nap);
             nap = min(nap * 2, 16384u);
           }
@@ -1051,7 +1057,7 @@ __global__ void __launch_bounds__(LEVEL_MAX_THREADS, LEVEL_MIN_BLOCKS) k_levels(
                ldv64(&L.take[2 * lo + 1]) >= level_total(L, lo, 1, M) && levels_done(L, lo))
           ++lo;
         if (lo > L.max_int) break;   // no level can grow and every task is ticketed: done
-        if (clock64() - t0 > 20000000000ll) {
+        if (clock64() - t0 > wait_cap(tr, 20000000000ll)) {
           if (atomicExch(L.err, 1u) == 0u) {
             L.dbg[0] = 1;
             for (int q = 1; q <= L.max_int && q < 8; ++q) {
@@ -1073,7 +1079,7 @@ __global__ void __launch_bounds__(LEVEL_MAX_THREADS, LEVEL_MIN_BLOCKS) k_levels(
         if (rdy) {
           const long long t1 = clock64();
           while (*(const volatile uint8_t*)(rdy + node) == 0) {
-            if (clock64() - t1 > 3000000000ll) {
+            if (clock64() - t1 > wait_cap(tr, 3000000000ll)) {
               if (atomicExch(L.err, 2u) == 0u) {
                 L.dbg[0] = 2;
                 L.dbg[1] = (unsigned long long)d | ((unsigned long long)kind << 8);
@@ -1524,6 +1530,7 @@ int trace_coarse(Mem& mem, SceneObj* S, const double* txh, int n_tx, const doubl
   tr_pri.stats = stats + STAGE_PRIMARY * N_STATS;
   tr_lev.stats = stats + STAGE_LEVELS * N_STATS;
   tr_lev.err = q_err;
+  tr_lev.wait_limit = tn.wait_limit;
 
   // From the RX table to the last depth nothing returns to the host: the march field,
   // the transmission phase and every propagation level over all TX/RX pairs form one

@@ -147,6 +147,8 @@ typedef struct {
   int64_t bytes_levels;
   int64_t bytes_refine;     /* algorithmic bytes read by the refinement kernel */
   int64_t launches;         /* kernels launched by trace_coarse + refine for this handle */
+  int64_t n_cones_no_rx;    /* of n_cones: last-level cones that no RX can lie in, so that their march (which
+                               could only reach RXs) was not run */
 } nimbus_path_counts;
 
 /* Caller-owned host arrays for nimbus_query, each sized for n_paths entries

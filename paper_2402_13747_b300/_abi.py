@@ -65,7 +65,8 @@ class Counts(C.Structure):
                 [("overflow", C.c_int32), ("n_levels", C.c_int32)] +
                 [(n, C.c_double) for n in ("ms_vis", "ms_primary", "ms_levels", "ms_kappa", "ms_refine",
                                            "ms_dedup")] +
-                [(n, C.c_int64) for n in ("bytes_primary", "bytes_levels", "bytes_refine", "launches")])
+                [(n, C.c_int64) for n in ("bytes_primary", "bytes_levels", "bytes_refine", "launches",
+                                          "n_cones_no_rx")])
 
     def as_dict(self):
         return {f[0]: (float if f[1] is C.c_double else int)(getattr(self, f[0])) for f in self._fields_}

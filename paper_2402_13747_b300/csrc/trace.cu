@@ -27,7 +27,7 @@ constexpr uint32_t NO_NODE = 0xFFFFFFFFu;
 
 enum { CONE_PRIMARY = 0, CONE_REFLECT = 1, CONE_DIFFRACT = 2 };
 // per-stage counters: [stage * N_STATS + ST_*] for stages vis tables, primary, levels
-enum { ST_CONES = 0, ST_VIS = 1, ST_BYTES = 2, ST_EVALS = 3, N_STATS = 4 };
+enum { ST_CONES = 0, ST_VIS = 1, ST_BYTES = 2, ST_EVALS = 3, ST_NO_RX = 4, N_STATS = 5 };
 enum { STAGE_VIS = 0, STAGE_PRIMARY = 1, STAGE_LEVELS = 2, N_STAGES = 3 };
 
 struct DTrace {
@@ -220,21 +220,23 @@ struct PrimaryAcc {
 };
 
 __device__ __forceinline__ void add_stats(const DTrace& tr, uint32_t cones, uint32_t vis, unsigned long long bytes,
-                                          uint32_t evals) {
+                                          uint32_t evals, uint32_t no_rx = 0) {
   // warp-aggregated counters
-  unsigned long long c = cones, v = vis, b = bytes, e = evals;
+  unsigned long long c = cones, v = vis, b = bytes, e = evals, z = no_rx;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     c += __shfl_xor_sync(0xffffffffu, c, o);
     v += __shfl_xor_sync(0xffffffffu, v, o);
     b += __shfl_xor_sync(0xffffffffu, b, o);
     e += __shfl_xor_sync(0xffffffffu, e, o);
+    z += __shfl_xor_sync(0xffffffffu, z, o);
   }
   if ((threadIdx.x & 31) == 0) {
     atomicAdd(&tr.stats[ST_CONES], c);
     atomicAdd(&tr.stats[ST_VIS], v);
     atomicAdd(&tr.stats[ST_BYTES], b);
     atomicAdd(&tr.stats[ST_EVALS], e);
+    if (z) atomicAdd(&tr.stats[ST_NO_RX], z);
   }
 }
 
@@ -815,13 +817,43 @@ __device__ void march_cone_warp(const DScene& s, const DTrace& tr, const ConeD& 
   }
 }
 
+// Whether any RX could pass the RX screening of this cone's march (march_cone_warp):
+// the same cone-sphere, separation-plane, owner and depth tests, each loosened by
+// 1e-5 (|v| + 1) m (|v|: the RX's distance from the apex), ten times the FP32 error of
+// the screening's dot products at these distances, so that no RX the screening could
+// accept is rejected here.  A cone that can emit no child (the last level) and that no
+// RX can pass produces nothing whatever its march finds: its march is skipped.
+#ifndef NO_RX_MAX
+#define NO_RX_MAX 4096
+#endif
+__device__ __forceinline__ bool rx_in_reach(const DScene& s, const DTrace& tr, const ConeD& c, const LevelCone& lc,
+                                            int lane) {
+  const float r = s.r_sub, r2 = r * r;
+  bool any = false;
+  for (int j = lane; j < tr.n_rx && !any; j += 32) {
+    if (tr.rx_owner && tr.rx_owner[j] >= 0 && (uint32_t)tr.rx_owner[j] != lc.tx) continue;
+    if (tr.rx_max_int && tr.rx_max_int[j] >= 0 && (int)lc.depth > tr.rx_max_int[j]) continue;
+    const float3 v = xyz(__ldg(&tr.rx[j])) - c.apex;
+    const float d2 = dot(v, v), tol = 1e-5f * (sqrtf(d2) + 1.f);
+    bool in = d2 <= r2 * 1.001f + 1e-6f ||
+              dot(v, c.axis) + r * c.sin_a + tol >= c.cos_a * sqrtf(fmaxf(d2 - r2, 0.f));
+    if (in) {
+      if (c.kind == CONE_REFLECT) in = dot(v, c.pn) > tr.sep_eps - tol;
+      else if (c.kind == CONE_DIFFRACT)
+        in = dot(v, c.tlo) >= -tol && dot(v, c.thi) < tol && dot(v, c.rmid) > -tol;
+    }
+    any = in;
+  }
+  return __any_sync(FULL, any);
+}
+
 // One propagation cone of level `cur`: the reflected cone of node idx (refl) or cone
 // j of the Keller fan of diffraction node idx.
 template <bool HELP>
 __device__ __forceinline__ void level_cone(const DScene& s, const DTrace& tr, const NodeLevel& cur, NodeLevel& next,
                                            CoarseBuf& cb, HelpSlot* H, bool refl, uint32_t idx, int j, int lane,
                                            unsigned long long& bytes, uint32_t& cones, uint32_t& evals,
-                                           uint32_t& vis) {
+                                           uint32_t& vis, uint32_t& no_rx) {
   const float4 a = refl ? cur.ra[idx] : cur.da[idx];
   const float4 b = refl ? cur.rb[idx] : cur.db[idx];
   const uint32_t meta = refl ? cur.rm[idx] : cur.dm[idx];
@@ -878,6 +910,10 @@ __device__ __forceinline__ void level_cone(const DScene& s, const DTrace& tr, co
   lc.can_child = (int)lc.depth < tr.max_int && (!tr.tx_max_int || (int)lc.depth < tr.tx_max_int[lc.tx]);
   lc.test_edges = lc.can_child && (int)lc.nd < tr.max_diff;
   if (lane == 0) ++cones;
+  if (!lc.can_child && tr.n_rx <= NO_RX_MAX && !rx_in_reach(s, tr, c, lc, lane)) {
+    if (lane == 0) ++no_rx;
+    return;
+  }
   march_cone_warp<HELP>(s, tr, c, lc, next, cb, H, lane, bytes, evals, vis);
 }
 
@@ -912,7 +948,7 @@ __global__ void __launch_bounds__(LEVEL_MAX_THREADS, LEVEL_MIN_BLOCKS) k_level(D
   const uint32_t n_r = min(cur.cnt[0], cur.cap_r), n_d = min(cur.cnt[1], cur.cap_d);
   const int64_t total = (int64_t)n_r + (int64_t)n_d * tr.M;
   unsigned long long bytes = 0;
-  uint32_t cones = 0, vis = 0, evals = 0;
+  uint32_t cones = 0, vis = 0, evals = 0, no_rx = 0;
   for (;;) {
     unsigned long long grab = 0;
     if (lane == 0) grab = atomicAdd(next_task, 1ull);
@@ -922,9 +958,9 @@ __global__ void __launch_bounds__(LEVEL_MAX_THREADS, LEVEL_MIN_BLOCKS) k_level(D
     const uint32_t idx = refl ? (uint32_t)task : (uint32_t)((task - n_r) / tr.M);
     const int j = refl ? 0 : (int)((task - n_r) % tr.M);
     level_cone<HELP>(s, tr, cur, next, cb, HELP ? board + wib : nullptr, refl, idx, j, lane, bytes, cones, evals,
-                     vis);
+                     vis, no_rx);
   }
-  add_stats(tr, cones, vis, bytes, evals);
+  add_stats(tr, cones, vis, bytes, evals, no_rx);
   if constexpr (!HELP) return;
   if (lane == 0) atomicSub(&s_active, 1u);
   // help: take entries of the other warps' slots until no warp of the block runs a
@@ -1010,7 +1046,7 @@ __global__ void __launch_bounds__(LEVEL_MAX_THREADS, LEVEL_MIN_BLOCKS) k_levels(
   // level instead of walking other warps' rays)
   const int lane = threadIdx.x & 31;
   unsigned long long bytes = 0;
-  uint32_t cones = 0, vis = 0, evals = 0;
+  uint32_t cones = 0, vis = 0, evals = 0, no_rx = 0;
   const int M = tr.M;
   int lo = 1;   // lane 0: levels below lo are final and every task of theirs is ticketed
   for (;;) {
@@ -1100,14 +1136,15 @@ __global__ void __launch_bounds__(LEVEL_MAX_THREADS, LEVEL_MIN_BLOCKS) k_levels(
     t = __shfl_sync(FULL, t, 0);
     const uint32_t idx = kind == 0 ? (uint32_t)t : (uint32_t)(t / (unsigned)M);
     const int j = kind == 0 ? 0 : (int)(t % (unsigned)M);
-    level_cone<false>(s, tr, L.lv[d], L.lv[d + 1], cb, nullptr, kind == 0, idx, j, lane, bytes, cones, evals, vis);
+    level_cone<false>(s, tr, L.lv[d], L.lv[d + 1], cb, nullptr, kind == 0, idx, j, lane, bytes, cones, evals, vis,
+                      no_rx);
     __syncwarp();
     if (lane == 0) {
       __threadfence();
       atomicAdd(L.lv[d].outstanding, ~0ull);   // this task is finished
     }
   }
-  add_stats(tr, cones, vis, bytes, evals);
+  add_stats(tr, cones, vis, bytes, evals, no_rx);
 }
 
 // Tasks of the first level (written before the launch) for the single launch.
@@ -1662,6 +1699,7 @@ int trace_coarse(Mem& mem, SceneObj* S, const double* txh, int n_tx, const doubl
   }
   cnt.bytes_primary = (int64_t)hs[STAGE_PRIMARY * N_STATS + ST_BYTES];
   cnt.bytes_levels = (int64_t)hs[STAGE_LEVELS * N_STATS + ST_BYTES];
+  cnt.n_cones_no_rx = (int64_t)hs[STAGE_LEVELS * N_STATS + ST_NO_RX];
   cnt.n_levels = max_int;
   cnt.ms_vis = tm.ms(e0, e1);
   cnt.ms_primary = tm.ms(e1, e2);

@@ -36,6 +36,7 @@ struct DTrace {
   float dphi, sep_eps;
   int max_refl, max_diff, max_int;
   int n_launch, n_tx, n_rx;
+  uint32_t n_ie, n_edges;    // the scene's IE and edge counts (self-checks)
   double golden;
   const float4* tx;          // xyz
   const float4* rx;          // xyz
@@ -51,9 +52,20 @@ struct DTrace {
   const int32_t* tx_max_int; // [n_tx] depth to which each TX's tree is expanded, or null
   unsigned long long* stats;
   uint32_t* overflow;        // [0] largest node slot requested, [1] coarse slot requested
-  uint32_t* err;             // propagation: nonzero once a bounded wait gave up
+  uint32_t* err;             // [4] propagation: 1-4 a bounded wait gave up, >= 5 a self-check failed; details
   long long wait_limit;      // cycles after which a wait gives up; 0: each wait's default
 };
+
+// Self-checks of the propagation's indices (never expected to fail): the first failure
+// writes its code and three details to err[0..3] (err[0] from zero by compare-and-swap)
+// and the access it guards is skipped; the call then returns NIMBUS_ERR_STATE.
+__device__ __forceinline__ void check_fail(const DTrace& tr, unsigned code, unsigned a, unsigned b, unsigned c) {
+  if (tr.err && atomicCAS(tr.err, 0u, code) == 0u) {
+    tr.err[1] = a;
+    tr.err[2] = b;
+    tr.err[3] = c;
+  }
+}
 
 // The limit of a bounded wait: its default, or the context's test limit.
 __device__ __forceinline__ long long wait_cap(const DTrace& tr, long long dflt) {
@@ -346,6 +358,10 @@ __global__ void k_first_counts(const uint32_t* tot_r, const uint32_t* tot_d, Nod
 
 __device__ __forceinline__ void emit_coarse(const DTrace& tr, CoarseBuf& cb, uint32_t t, uint32_t j, uint32_t node,
                                             uint32_t depth, float miss) {
+  if (t >= (uint32_t)tr.n_tx || j >= (uint32_t)tr.n_rx) {
+    check_fail(tr, 11u, t, j, node);
+    return;
+  }
   uint32_t slot = atomicAdd(cb.cnt, 1u);
   if (slot >= cb.cap) {
     atomicMax(&tr.overflow[1], slot + 1);
@@ -377,6 +393,10 @@ __global__ void k_los(DTrace tr, const uint32_t* los, CoarseBuf cb) {
 // of a reflected cone (point IE) or of a Keller fan (edge IE).
 __device__ void emit_child(const DTrace& tr, NodeLevel& next, uint32_t id, float3 rp, float3 apex, uint32_t kind,
                            uint32_t tx, uint32_t nr, uint32_t nd, uint32_t depth, uint32_t self_ref) {
+  if (id >= tr.n_ie || kind > IE_EDGE || tx >= (uint32_t)tr.n_tx) {
+    check_fail(tr, 10u, id, kind, tx);
+    return;
+  }
   const uint32_t cnr = nr + (kind == IE_POINT), cnd = nd + (kind == IE_EDGE);
   if ((int)cnr > tr.max_refl || (int)cnd > tr.max_diff) return;
   const bool refl = kind == IE_POINT;
@@ -450,7 +470,17 @@ __device__ __forceinline__ void help_walk(const DScene& s, const DTrace& tr, Nod
   const unsigned q = H.qbase + t;
   const bool can_child = h1.w != 0;
   unsigned r = 0;
-  if (!(b.x == IE_POINT && !can_child && *(volatile unsigned*)&H.first_vis < q)) {
+  const uint32_t id = __float_as_uint(a.w);
+  bool bad = b.x > CAND_RX || (b.x == CAND_RX ? id >= (uint32_t)tr.n_rx : id >= tr.n_ie);
+  if (!bad && b.x != CAND_RX) bad = (__float_as_uint(__ldg(&s.ies[id].nrm_meta).w) & 1u) != b.x;
+  // the skip must be the same on every lane (the walk below is a whole-warp walk), but
+  // other warps lower first_vis concurrently: lane 0 reads it once for the warp
+  unsigned fv = 0xffffffffu;
+  if (lane == 0) fv = *(volatile unsigned*)&H.first_vis;
+  fv = __shfl_sync(FULL, fv, 0);
+  if (bad) {   // an entry that was not what its owner stored (never expected)
+    if (lane == 0) check_fail(tr, 8u, id, b.x, t);
+  } else if (!(b.x == IE_POINT && !can_child && fv < q)) {
     unsigned long long by = 0;
     const float3 apex = xyz(h0), tgt = xyz(a);
     const Endpoint origin{(int)h1.x, __float_as_uint(h0.w)};
@@ -486,6 +516,7 @@ __device__ __forceinline__ unsigned help_take(HelpSlot& H, int lane) {
       const unsigned o = atomicCAS(&H.word, w, w + 1);
       if (o == w) {
         tk = w & 0xfffu;
+        __threadfence_block();   // acquire: the entries were published before the word
         break;
       }
       w = o;
@@ -504,8 +535,12 @@ __device__ __forceinline__ unsigned help_take(HelpSlot& H, int lane) {
 __device__ __forceinline__ void help_flush(const DScene& s, const DTrace& tr, NodeLevel& next, CoarseBuf& cb,
                                            HelpSlot& H, int& hn, int lane, unsigned long long& bytes, uint32_t& vis) {
   if (hn == 0) return;
-  // the generation lives in the slot's word; only its owner changes it
-  const unsigned gen = *(volatile unsigned*)&H.word >> 24;
+  // the entries were stored by the lanes that found them: order every lane's stores
+  // before lane 0's fence and the publishing exchange, so that a warp that takes an
+  // entry reads what was stored, not what the slot held before
+  __syncwarp();
+  // the generation lives in the slot's word; only its owner changes it (lane 0 uses it)
+  const unsigned gen = lane == 0 ? *(volatile unsigned*)&H.word >> 24 : 0u;
   if (lane == 0) {
     H.done = 0;
     __threadfence_block();
@@ -531,7 +566,7 @@ __device__ __forceinline__ void help_flush(const DScene& s, const DTrace& tr, No
     atomicExch(&H.word, ((gen + 1) & 0xffu) << 24);
   }
   __syncwarp();
-  const unsigned Fn = *(volatile unsigned*)&H.first_vis, qn = H.qbase;
+  const unsigned Fn = __shfl_sync(FULL, lane == 0 ? *(volatile unsigned*)&H.first_vis : 0u, 0), qn = H.qbase;
   const bool can_child = H.h1.w != 0;
   for (int t0 = 0; t0 < hn; t0 += 32) {
     const int t = t0 + lane;
@@ -562,8 +597,8 @@ __device__ __forceinline__ void help_flush(const DScene& s, const DTrace& tr, No
 // confirm the stop.
 template <bool HELP>
 __device__ void march_cone_warp(const DScene& s, const DTrace& tr, const ConeD& c, const LevelCone& lc,
-                                NodeLevel& next, CoarseBuf& cb, HelpSlot* Hp, int lane, unsigned long long& bytes,
-                                uint32_t& evals, uint32_t& vis) {
+                                NodeLevel& next, CoarseBuf& cb, HelpSlot* Hp, float t_end, int lane,
+                                unsigned long long& bytes, uint32_t& evals, uint32_t& vis) {
   if constexpr (HELP) {
     HelpSlot& H = *Hp;
     if (lane == 0) {
@@ -581,7 +616,6 @@ __device__ void march_cone_warp(const DScene& s, const DTrace& tr, const ConeD& 
   bool have_last = false;
   int rad = -1;
   const int max_steps = s.nx + s.ny + s.nz + 3;
-  const float inf = __int_as_float(0x7f800000);
   const int ldx = lane % 3 - 1, ldy = (lane / 3) % 3 - 1, ldz = lane / 9 - 1;   // lanes 0..26
   for (int step = 0; step < max_steps; ++step) {
     const bool in_box = rad >= 0 && abs(w.v[0] - anchor[0]) <= rad && abs(w.v[1] - anchor[1]) <= rad &&
@@ -718,7 +752,7 @@ __device__ void march_cone_warp(const DScene& s, const DTrace& tr, const ConeD& 
             if (!full) break;
           }
           // a point IE of this evaluation was visible
-          stop = *(volatile unsigned*)&H.first_vis != 0xffffffffu;
+          stop = __shfl_sync(FULL, lane == 0 ? *(volatile unsigned*)&H.first_vis : 0u, 0) != 0xffffffffu;
         } else {
           // each candidate walked at once by this warp
           stop = false;
@@ -813,24 +847,28 @@ __device__ void march_cone_warp(const DScene& s, const DTrace& tr, const ConeD& 
         if (stop) break;
       }
     }
-    if (!walk_next(s, w, inf)) break;
+    if (!walk_next(s, w, t_end)) break;
   }
 }
 
-// Whether any RX could pass the RX screening of this cone's march (march_cone_warp):
+// The RXs that could pass the RX screening of this cone's march (march_cone_warp):
 // the same cone-sphere, separation-plane, owner and depth tests, each loosened by
 // 1e-5 (|v| + 1) m (|v|: the RX's distance from the apex), ten times the FP32 error of
 // the screening's dot products at these distances, so that no RX the screening could
-// accept is rejected here.  A cone that can emit no child (the last level) and that no
-// RX can pass produces nothing whatever its march finds: its march is skipped.
+// accept is rejected here.  Returns the largest axial distance dot(v, axis) among
+// them, or -1 when there is none (every lane gets the same value).  A cone that can
+// emit no child (the last level) produces nothing but coarse paths to such RXs: with
+// none its march is skipped, else the march stops once its walk is past the farthest
+// (an RX is screened from walk voxels within one voxel of its own, whose axis points
+// lie at most 2 sqrt(3) voxel edges further along the axis).
 #ifndef NO_RX_MAX
 #define NO_RX_MAX 4096
 #endif
-__device__ __forceinline__ bool rx_in_reach(const DScene& s, const DTrace& tr, const ConeD& c, const LevelCone& lc,
-                                            int lane) {
+__device__ __forceinline__ float rx_reach(const DScene& s, const DTrace& tr, const ConeD& c, const LevelCone& lc,
+                                          int lane) {
   const float r = s.r_sub, r2 = r * r;
-  bool any = false;
-  for (int j = lane; j < tr.n_rx && !any; j += 32) {
+  float far = -1.f;
+  for (int j = lane; j < tr.n_rx; j += 32) {
     if (tr.rx_owner && tr.rx_owner[j] >= 0 && (uint32_t)tr.rx_owner[j] != lc.tx) continue;
     if (tr.rx_max_int && tr.rx_max_int[j] >= 0 && (int)lc.depth > tr.rx_max_int[j]) continue;
     const float3 v = xyz(__ldg(&tr.rx[j])) - c.apex;
@@ -842,9 +880,11 @@ __device__ __forceinline__ bool rx_in_reach(const DScene& s, const DTrace& tr, c
       else if (c.kind == CONE_DIFFRACT)
         in = dot(v, c.tlo) >= -tol && dot(v, c.thi) < tol && dot(v, c.rmid) > -tol;
     }
-    any = in;
+    if (in) far = fmaxf(far, fmaxf(dot(v, c.axis) + tol, 0.f));
   }
-  return __any_sync(FULL, any);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) far = fmaxf(far, __shfl_xor_sync(FULL, far, o));
+  return far;
 }
 
 // One propagation cone of level `cur`: the reflected cone of node idx (refl) or cone
@@ -858,8 +898,17 @@ __device__ __forceinline__ void level_cone(const DScene& s, const DTrace& tr, co
   const float4 b = refl ? cur.rb[idx] : cur.db[idx];
   const uint32_t meta = refl ? cur.rm[idx] : cur.dm[idx];
   const uint32_t ie = __float_as_uint(a.w);
+  if (ie >= (uint32_t)s.n_ie) {   // a node record the level did not write (never expected)
+    if (lane == 0) check_fail(tr, 5u, ie, idx, refl ? 0u : 1u);
+    return;
+  }
   const IERec* r = &s.ies[ie];
   const float4 nm = __ldg(&r->nrm_meta);
+  if ((__float_as_uint(nm.w) & 1u) != (refl ? (uint32_t)IE_POINT : (uint32_t)IE_EDGE) ||
+      (!refl && __float_as_uint(__ldg(&r->bbc_pb).w) >= tr.n_edges)) {   // node kind and IE kind disagree
+    if (lane == 0) check_fail(tr, 6u, ie, idx, (refl ? 0u : 1u) | ((__float_as_uint(nm.w) & 1u) << 1));
+    return;
+  }
   const uint32_t label = __float_as_uint(__ldg(&r->rp_lab).w);
   if (lane == 0) bytes += 32 + 36;
   const float3 e = xyz(b);
@@ -910,11 +959,16 @@ __device__ __forceinline__ void level_cone(const DScene& s, const DTrace& tr, co
   lc.can_child = (int)lc.depth < tr.max_int && (!tr.tx_max_int || (int)lc.depth < tr.tx_max_int[lc.tx]);
   lc.test_edges = lc.can_child && (int)lc.nd < tr.max_diff;
   if (lane == 0) ++cones;
-  if (!lc.can_child && tr.n_rx <= NO_RX_MAX && !rx_in_reach(s, tr, c, lc, lane)) {
-    if (lane == 0) ++no_rx;
-    return;
+  float t_end = __int_as_float(0x7f800000);
+  if (!lc.can_child && tr.n_rx <= NO_RX_MAX) {
+    const float far = rx_reach(s, tr, c, lc, lane);
+    if (far < 0.f) {
+      if (lane == 0) ++no_rx;
+      return;
+    }
+    t_end = far + 4.f * s.h + 0.01f;
   }
-  march_cone_warp<HELP>(s, tr, c, lc, next, cb, H, lane, bytes, evals, vis);
+  march_cone_warp<HELP>(s, tr, c, lc, next, cb, H, t_end, lane, bytes, evals, vis);
 }
 
 // One propagation level: the reflected cones and Keller-fan cones of every node,
@@ -1401,6 +1455,8 @@ int trace_coarse(Mem& mem, SceneObj* S, const double* txh, int n_tx, const doubl
                                 : (int)std::llround(4.0 * PI_D / (p->launch_spacing * p->launch_spacing));
   tr.n_tx = n_tx;
   tr.n_rx = n_rx;
+  tr.n_ie = (uint32_t)n_ie;
+  tr.n_edges = (uint32_t)s.n_edges;
   tr.golden = PI_D * (3.0 - std::sqrt(5.0));
   tr.ie_words = (int)((n_ie + 31) / 32);
   float4 *tx4, *rx4;
@@ -1517,7 +1573,8 @@ int trace_coarse(Mem& mem, SceneObj* S, const double* txh, int n_tx, const doubl
   uint32_t* q_err = nullptr;
   size_t rdy_bytes = 0;
   uint8_t* rdy = nullptr;
-  NB_TRY(sc.get(&q_err, 1));   // both layouts: a bounded wait of the propagation gave up
+  NB_TRY(sc.get(&q_err, 4));   // both layouts: a bounded wait gave up, or a self-check failed
+  tr.err = q_err;
   if (queue) {
     NB_TRY(sc.get(&q_ctr, 2 * (MAX_LEVELS + 1) + 1 + 20 + MAX_LEVELS + 1));
     for (int d = 2; d <= max_int; ++d) rdy_bytes += (size_t)lv[d].cap_r + lv[d].cap_d;
@@ -1636,7 +1693,7 @@ int trace_coarse(Mem& mem, SceneObj* S, const double* txh, int n_tx, const doubl
       NB_LAUNCHED(err);
     }
     // propagation phase: one launch per depth, or one launch for all depths
-    NB_CUDA(err, cudaMemsetAsync(q_err, 0, sizeof(uint32_t), q));
+    NB_CUDA(err, cudaMemsetAsync(q_err, 0, 4 * sizeof(uint32_t), q));
     if (queue) {
       NB_CUDA(err, cudaMemsetAsync(q_ctr, 0, (2 * (MAX_LEVELS + 1) + 1 + 20 + MAX_LEVELS + 1) * sizeof(unsigned long long), q));
       if (rdy_bytes) NB_CUDA(err, cudaMemsetAsync(rdy, 0, rdy_bytes, q));
@@ -1668,13 +1725,21 @@ int trace_coarse(Mem& mem, SceneObj* S, const double* txh, int n_tx, const doubl
   NB_CUDA(err, cudaMemcpyAsync(hc, cnts, sizeof hc, cudaMemcpyDeviceToHost, st));
   NB_CUDA(err, cudaMemcpyAsync(hov, overflow, sizeof hov, cudaMemcpyDeviceToHost, st));
   NB_CUDA(err, cudaMemcpyAsync(hs, stats, sizeof hs, cudaMemcpyDeviceToHost, st));
-  uint32_t hqerr = 0;
-  if (max_int >= 1) NB_CUDA(err, cudaMemcpyAsync(&hqerr, q_err, sizeof hqerr, cudaMemcpyDeviceToHost, st));
+  uint32_t hq[4] = {0, 0, 0, 0};
+  NB_CUDA(err, cudaMemcpyAsync(hq, q_err, sizeof hq, cudaMemcpyDeviceToHost, st));
+  const uint32_t hqerr = hq[0];
   NB_CUDA(err, cudaStreamSynchronize(st));
   if (hqerr == 3u || hqerr == 4u) {
     *err = hqerr == 3u ? "trace: a cone's wait for the visibility rays other warps took gave up"
                        : "trace: a warp's wait for the cones of its block gave up";
     return NIMBUS_ERR_TIMEOUT;
+  }
+  if (hqerr >= 5u) {
+    char buf[160];
+    std::snprintf(buf, sizeof buf, "trace: propagation self-check %u failed (%u %u %u); the access was skipped",
+                  hqerr, hq[1], hq[2], hq[3]);
+    *err = buf;
+    return NIMBUS_ERR_STATE;
   }
   if (hqerr) {
     unsigned long long hd[20];

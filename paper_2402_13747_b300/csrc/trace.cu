@@ -439,6 +439,11 @@ struct LevelCone {
 // whole warp whichever warp takes it, so every decision is the same.
 //   word: generation << 24 | entries << 12 | entries taken; a warp takes entry k
 //   with a compare-and-swap of the word (a stale generation fails).
+// Ordering: the owner's lanes store the entries, a __syncwarp orders them before
+// lane 0's fence and the exchange that publishes the word, and a taker fences after
+// its compare-and-swap before reading an entry.  Every board word that steers a warp
+// (the word, first_vis, done) is read by lane 0 and broadcast, so that no warp splits
+// around the whole-warp walk.
 // At the last level a point IE only decides whether the cone stops, and the walk in
 // order skips the point IEs after the first visible one.  Here an entry is skipped
 // once a visible point IE with a smaller index is known (first_vis); the owner then

@@ -645,8 +645,10 @@ def main():
                "e2e": e2e, "secondary": secondary,
                "gathered_paths": None if gathered is None else int(len(gathered["n"])),
                "gpu_launches": launches, "clocks": clocks,
+               # n_cones counts every launched cone; n_cones_no_rx of them (last depth, no RX
+               # within reach) were resolved by the RX test without a march
                "counts_last_step": {k: c0[k] for k in ("n_paths", "n_coarse", "n_coarse_raw", "n_nodes", "n_vis",
-                                                       "n_cones", "launches")}}
+                                                       "n_cones", "n_cones_no_rx", "launches")}}
         print(json.dumps(out), flush=True)
     ctx.close()
     if world > 1:

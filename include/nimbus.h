@@ -240,7 +240,14 @@ NIMBUS_API int nimbus_update_region(nimbus_ctx* ctx, nimbus_handle scene, const 
  * cone-sphere tests, separation planes and visibility rays decide which
  * entities a cone reaches, RXs reached give coarse paths, and at most kappa
  * coarse paths are kept per (TX, RX, label sequence).  tx [n_tx*3], rx [n_rx*3]
- * (host or device).  coarse_out receives the coarse set handle. */
+ * (host or device).  coarse_out receives the coarse set handle.  A cone of the last
+ * depth that no RX can lie in produces nothing, so it is counted but not marched
+ * (nimbus_path_counts.n_cones_no_rx).  Errors: NIMBUS_ERR_ARG for bad parameters or
+ * a TX/RX outside the grid; NIMBUS_ERR_OVERFLOW with the needed bounds in the counts
+ * (the handle is still returned); NIMBUS_ERR_TIMEOUT when a bounded device wait of the
+ * propagation gave up; NIMBUS_ERR_STATE when a self-check of the propagation's
+ * indices failed (never expected; the message names the check and its values);
+ * NIMBUS_ERR_OOM past the budget. */
 NIMBUS_API int nimbus_trace_coarse(nimbus_ctx* ctx, nimbus_handle scene, const double* tx, int32_t n_tx,
                         const double* rx, int32_t n_rx, const nimbus_trace_params* params,
                         nimbus_handle* coarse_out, void* stream);

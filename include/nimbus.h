@@ -38,7 +38,7 @@ extern "C" {
 #define NIMBUS_ERR_CUDA 3     /* a CUDA runtime error; see nimbus_last_error() */
 #define NIMBUS_ERR_OVERFLOW 4 /* a bounded device buffer overflowed; sizes in nimbus_path_counts */
 #define NIMBUS_ERR_TIMEOUT 5  /* a bounded device wait gave up */
-#define NIMBUS_ERR_STATE 6    /* unknown handle or a handle of the wrong kind */
+#define NIMBUS_ERR_STATE 6    /* unknown handle, a handle of the wrong kind, or a failed internal self-check */
 #define NIMBUS_ERR_IO 7       /* a file could not be written or read, or is not an intact scene checkpoint */
 
 #define NIMBUS_MAX_INTERACTIONS 8 /* interactions per path, upper bound of max_int */
@@ -147,8 +147,9 @@ typedef struct {
   int64_t bytes_levels;
   int64_t bytes_refine;     /* algorithmic bytes read by the refinement kernel */
   int64_t launches;         /* kernels launched by trace_coarse + refine for this handle */
-  int64_t n_cones_no_rx;    /* of n_cones: last-level cones that no RX can lie in, so that their march (which
-                               could only reach RXs) was not run */
+  int64_t n_cones_no_rx;    /* of n_cones: last-level cones whose march was not run because it could emit
+                               nothing: no RX can lie in them, or (level_rx_first) none of those that can sees
+                               the apex */
 } nimbus_path_counts;
 
 /* Caller-owned host arrays for nimbus_query, each sized for n_paths entries
@@ -241,7 +242,8 @@ NIMBUS_API int nimbus_update_region(nimbus_ctx* ctx, nimbus_handle scene, const 
  * entities a cone reaches, RXs reached give coarse paths, and at most kappa
  * coarse paths are kept per (TX, RX, label sequence).  tx [n_tx*3], rx [n_rx*3]
  * (host or device).  coarse_out receives the coarse set handle.  A cone of the last
- * depth that no RX can lie in produces nothing, so it is counted but not marched
+ * depth that no RX can lie in, or (level_rx_first) none of whose reachable RXs sees
+ * its apex, produces nothing, so it is counted but not marched
  * (nimbus_path_counts.n_cones_no_rx).  Errors: NIMBUS_ERR_ARG for bad parameters or
  * a TX/RX outside the grid; NIMBUS_ERR_OVERFLOW with the needed bounds in the counts
  * (the handle is still returned); NIMBUS_ERR_TIMEOUT when a bounded device wait of the
@@ -424,10 +426,12 @@ typedef struct {
   int32_t level_help;       /* one launch per depth only: 1, a warp whose cones are done walks visibility rays
                                of the cones still running in its block (the candidates of an evaluation wait in
                                a shared-memory list); 0, every warp walks only its own cones' rays */
+  int32_t level_rx_first;   /* 1: at the last depth, a cone none of whose reachable RXs sees its apex is not
+                               marched (it could emit nothing); pays where few reachable RXs are visible */
 } nimbus_tuning;
 
 /* The context's launch configuration (defaults 512, 0, 1, 1, level_queue 0, refine_split 0,
- * refine_split_key 0, level_help 1). */
+ * refine_split_key 0, level_help 1, level_rx_first 1). */
 NIMBUS_API int nimbus_get_tuning(nimbus_ctx* ctx, nimbus_tuning* out);
 
 /* Replace it.  A value out of range returns NIMBUS_ERR_ARG and changes nothing. */
@@ -446,7 +450,7 @@ NIMBUS_API int nimbus_set_wait_limit(nimbus_ctx* ctx, int64_t cycles);
 /* Autotuner.  Traces the given TX/RX set on `scene` once per level layout (blocks of
  * 128, 256 or 512 threads x one launch per depth, with or without idle warps walking
  * other warps' visibility rays, or one launch for all depths) and keeps the fastest
- * propagation time.  Then it refines that coarse set once per refinement layout with
+ * propagation time; then it tries the last depth's RX visibility test the other way.  Then it refines that coarse set once per refinement layout with
  * all resident blocks per SM: one launch in coarse order, most interactions first or
  * grazing rays first; and two launches, the first in coarse order or most interactions
  * first and stopping at 64, 128 or 512 iterations, the second in either of its orders;

@@ -96,7 +96,7 @@ class Tuning(C.Structure):
     _fields_ = [("level_block", C.c_int32), ("refine_blocks", C.c_int32), ("refine_order", C.c_int32),
                 ("graph", C.c_int32), ("level_ms", C.c_double), ("refine_ms", C.c_double),
                 ("level_queue", C.c_int32), ("refine_split", C.c_int32), ("refine_split_key", C.c_int32),
-                ("level_help", C.c_int32)]
+                ("level_help", C.c_int32), ("level_rx_first", C.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -547,6 +547,7 @@ static void to_public(const nb::Tuning& t, nimbus_tuning* o) {
   o->refine_split = t.refine_split;
   o->refine_split_key = t.refine_split_key;
   o->level_help = t.level_help;
+  o->level_rx_first = t.level_rx_first;
 }
 
 int nimbus_get_tuning(nimbus_ctx* ctx, nimbus_tuning* out) {
@@ -561,7 +562,8 @@ int nimbus_set_tuning(nimbus_ctx* ctx, const nimbus_tuning* t) {
       t->refine_blocks > 8 ||
       !(t->refine_order >= 0 && t->refine_order <= 2) || !(t->graph == 0 || t->graph == 1) ||
       !(t->level_queue == 0 || t->level_queue == 1) || t->refine_split < 0 || t->refine_split > 65535 ||
-      !(t->refine_split_key == 0 || t->refine_split_key == 1) || !(t->level_help == 0 || t->level_help == 1)) {
+      !(t->refine_split_key == 0 || t->refine_split_key == 1) || !(t->level_help == 0 || t->level_help == 1) ||
+      !(t->level_rx_first == 0 || t->level_rx_first == 1)) {
     ctx->err = "set_tuning: value out of range";
     return NIMBUS_ERR_ARG;
   }
@@ -575,6 +577,7 @@ int nimbus_set_tuning(nimbus_ctx* ctx, const nimbus_tuning* t) {
   ctx->tune.refine_split = t->refine_split;
   ctx->tune.refine_split_key = t->refine_split_key;
   ctx->tune.level_help = t->level_help;
+  ctx->tune.level_rx_first = t->level_rx_first;
   return NIMBUS_OK;
 }
 
@@ -623,6 +626,22 @@ int nimbus_autotune(nimbus_ctx* ctx, nimbus_handle scene, const double* tx, int3
       best.level_block = bl;
       best.level_queue = lq;
       best.level_help = hp;
+    }
+  }
+  {
+    // the last level's RX test: tried once, flipped, on the best layout
+    nb::Tuning t = best;
+    t.level_rx_first = 1 - best.level_rx_first;
+    auto* C = new nb::CoarseObj();
+    C->mem = &ctx->mem;
+    C->scene = scene;
+    int rc = nb::trace_coarse(ctx->mem, S, tx, n_tx, rx, n_rx, tp, C, st, t);
+    const double ms = C->counts.ms_levels;
+    drop_obj(ctx, C, st);
+    if (rc != NIMBUS_OK) return rc;
+    if (ms < best_lv) {
+      best_lv = ms;
+      best.level_rx_first = t.level_rx_first;
     }
   }
   best.level_ms = best_lv;

@@ -342,6 +342,7 @@ struct Tuning {
   int refine_split = 0;    // > 0: two-phase refinement, phase 1 capped at this many iterations
   int refine_split_key = 0;  // phase 2 order: 0 cost per iteration, 1 predicted remaining time
   int level_help = 1;      // per-depth levels: idle warps of a block walk its running cones' visibility rays
+  int level_rx_first = 1;   // last level: skip cones none of whose reachable RXs sees the apex
   long long wait_limit = 0;  // cycles after which a level wait gives up (0: the defaults); for tests
   double level_ms = 0, refine_ms = 0;
 };

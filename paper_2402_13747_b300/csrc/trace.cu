@@ -54,6 +54,7 @@ struct DTrace {
   uint32_t* overflow;        // [0] largest node slot requested, [1] coarse slot requested
   uint32_t* err;             // [4] propagation: 1-4 a bounded wait gave up, >= 5 a self-check failed; details
   long long wait_limit;      // cycles after which a wait gives up; 0: each wait's default
+  int rx_first;              // last level: test the reachable RXs' visibility before marching
 };
 
 // Self-checks of the propagation's indices (never expected to fail): the first failure
@@ -869,23 +870,30 @@ __device__ void march_cone_warp(const DScene& s, const DTrace& tr, const ConeD& 
 #ifndef NO_RX_MAX
 #define NO_RX_MAX 4096
 #endif
+__device__ __forceinline__ bool rx_could_pass(const DScene& s, const DTrace& tr, const ConeD& c, const LevelCone& lc,
+                                              int j, float* axial = nullptr) {
+  if (tr.rx_owner && tr.rx_owner[j] >= 0 && (uint32_t)tr.rx_owner[j] != lc.tx) return false;
+  if (tr.rx_max_int && tr.rx_max_int[j] >= 0 && (int)lc.depth > tr.rx_max_int[j]) return false;
+  const float r = s.r_sub, r2 = r * r;
+  const float3 v = xyz(__ldg(&tr.rx[j])) - c.apex;
+  const float d2 = dot(v, v), tol = 1e-5f * (sqrtf(d2) + 1.f);
+  bool in = d2 <= r2 * 1.001f + 1e-6f ||
+            dot(v, c.axis) + r * c.sin_a + tol >= c.cos_a * sqrtf(fmaxf(d2 - r2, 0.f));
+  if (in) {
+    if (c.kind == CONE_REFLECT) in = dot(v, c.pn) > tr.sep_eps - tol;
+    else if (c.kind == CONE_DIFFRACT)
+      in = dot(v, c.tlo) >= -tol && dot(v, c.thi) < tol && dot(v, c.rmid) > -tol;
+  }
+  if (in && axial) *axial = fmaxf(dot(v, c.axis) + tol, 0.f);
+  return in;
+}
+
 __device__ __forceinline__ float rx_reach(const DScene& s, const DTrace& tr, const ConeD& c, const LevelCone& lc,
                                           int lane) {
-  const float r = s.r_sub, r2 = r * r;
   float far = -1.f;
   for (int j = lane; j < tr.n_rx; j += 32) {
-    if (tr.rx_owner && tr.rx_owner[j] >= 0 && (uint32_t)tr.rx_owner[j] != lc.tx) continue;
-    if (tr.rx_max_int && tr.rx_max_int[j] >= 0 && (int)lc.depth > tr.rx_max_int[j]) continue;
-    const float3 v = xyz(__ldg(&tr.rx[j])) - c.apex;
-    const float d2 = dot(v, v), tol = 1e-5f * (sqrtf(d2) + 1.f);
-    bool in = d2 <= r2 * 1.001f + 1e-6f ||
-              dot(v, c.axis) + r * c.sin_a + tol >= c.cos_a * sqrtf(fmaxf(d2 - r2, 0.f));
-    if (in) {
-      if (c.kind == CONE_REFLECT) in = dot(v, c.pn) > tr.sep_eps - tol;
-      else if (c.kind == CONE_DIFFRACT)
-        in = dot(v, c.tlo) >= -tol && dot(v, c.thi) < tol && dot(v, c.rmid) > -tol;
-    }
-    if (in) far = fmaxf(far, fmaxf(dot(v, c.axis) + tol, 0.f));
+    float t;
+    if (rx_could_pass(s, tr, c, lc, j, &t)) far = fmaxf(far, t);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) far = fmaxf(far, __shfl_xor_sync(FULL, far, o));
@@ -972,6 +980,29 @@ __device__ __forceinline__ void level_cone(const DScene& s, const DTrace& tr, co
       return;
     }
     t_end = far + 4.f * s.h + 0.01f;
+    // With rx_first: an RX is emitted only if it also sees the apex (the screening's
+    // visibility ray: apex to RX, the cone's origin ignored, nothing at the RX).  When
+    // none of the RXs that could pass the screening does, the cone emits nothing
+    // whatever its march finds, so the march (and its point IEs' rays, which only
+    // decide where it stops) is skipped.  The rays are the screening's own call with
+    // the same arguments.  It pays where few reachable RXs are visible (an indoor
+    // scan), not where many are (a street of a thousand RXs): a layout choice.
+    bool seen = !tr.rx_first;
+    for (int j0 = 0; j0 < tr.n_rx && !seen; j0 += 32) {
+      const int j = j0 + lane;
+      unsigned m = __ballot_sync(FULL, j < tr.n_rx && rx_could_pass(s, tr, c, lc, j));
+      while (m && !seen) {
+        const int src = __ffs(m) - 1;
+        m &= m - 1;
+        if (lane == 0) ++vis;
+        seen = visible_warp(s, c.apex, xyz(__ldg(&tr.rx[j0 + src])), c.origin, Endpoint{IGN_NONE, NB_NONE_LABEL},
+                            lane, bytes);
+      }
+    }
+    if (!seen) {
+      if (lane == 0) ++no_rx;
+      return;
+    }
   }
   march_cone_warp<HELP>(s, tr, c, lc, next, cb, H, t_end, lane, bytes, evals, vis);
 }
@@ -1630,6 +1661,7 @@ int trace_coarse(Mem& mem, SceneObj* S, const double* txh, int n_tx, const doubl
   tr_lev.stats = stats + STAGE_LEVELS * N_STATS;
   tr_lev.err = q_err;
   tr_lev.wait_limit = tn.wait_limit;
+  tr_lev.rx_first = tn.level_rx_first;
 
   // From the RX table to the last depth nothing returns to the host: the march field,
   // the transmission phase and every propagation level over all TX/RX pairs form one

@@ -417,27 +417,31 @@ def test_autotune_keeps_results(ctx):
     assert t["level_queue"] in (0, 1)
     assert t["refine_split"] in (0, 64, 128, 512) and t["refine_split_key"] in (0, 1)
     assert t["level_help"] in (0, 1) and not (t["level_help"] and t["level_queue"])
+    assert t["level_rx_first"] in (0, 1)
     for layout in (dict(level_block=128, refine_blocks=3, refine_order=0, level_queue=1, refine_split=0),
                    dict(level_block=256, refine_blocks=0, refine_order=2, level_queue=0, refine_split=0),
                    dict(level_block=512, refine_blocks=0, refine_order=1, level_queue=1, refine_split=0),
                    dict(level_block=512, refine_blocks=0, refine_order=1, level_queue=0, refine_split=0,
-                        level_help=1),
+                        level_help=1, level_rx_first=1),
                    dict(level_block=256, refine_blocks=0, refine_order=1, level_queue=0, refine_split=5),
                    dict(level_block=256, refine_blocks=2, refine_order=2, level_queue=0, refine_split=64),
                    dict(level_block=256, refine_blocks=0, refine_order=0, level_queue=0, refine_split=7,
                         refine_split_key=1), t):
         ctx.set_tuning(**{k: layout.get(k, 0) for k in ("level_block", "refine_blocks", "refine_order", "level_queue",
-                                                        "refine_split", "refine_split_key", "level_help")})
+                                                        "refine_split", "refine_split_key", "level_help",
+                                                        "level_rx_first")})
         G = ctx.run(sc, p)
         assert len(G["n"]) == len(base["n"])
         for k in ("tx", "rx", "n", "type", "label", "pts", "length"):
             np.testing.assert_array_equal(G[k], base[k])
     ctx.set_tuning(level_block=512, refine_blocks=0, refine_order=1, level_queue=0, refine_split=0, refine_split_key=0,
-                   level_help=1)
+                   level_help=1, level_rx_first=1)
     with pytest.raises(Exception):
         ctx.set_tuning(level_block=96)
     with pytest.raises(Exception):
         ctx.set_tuning(level_help=2)
+    with pytest.raises(Exception):
+        ctx.set_tuning(level_rx_first=2)
     with pytest.raises(Exception):
         ctx.set_tuning(refine_split=-1)
     with pytest.raises(Exception):
